@@ -1,0 +1,213 @@
+/*
+ * libsic -- sparse inverse Cholesky factors of dense kernel matrices by greedy
+ * conditional selection, on one GB300 (sm_103a).
+ *
+ * Method: Huan, Guinness, Katzfuss, Owhadi, Schaefer, "Sparse inverse Cholesky
+ * factorization of dense kernel matrices by greedy conditional selection".
+ * For each column i of the factor L (L L^T ~ Theta^{-1}, lower triangular in a
+ * reverse-maximin elimination order), candidates j are scored by the reduction of
+ * the target's conditional variance cov_j^2 / var_j (Section 3.1, eq. obj_gp), the
+ * best is selected, the partial Cholesky factor gains the column
+ * u = (Theta[:, q] - F F[q, :]^T) / sqrt(var_q) (eq. cond_select, Appendix B.1), and
+ * after k picks the column is filled with the KL-optimal values
+ * L_{s,i} = Theta_{s,s}^{-1} e_1 / sqrt(e_1^T Theta_{s,s}^{-1} e_1) (eq. L_col).
+ * Supernodes share one selection among m consecutive targets and score candidates
+ * by the log-determinant change of the targets' conditional covariance
+ * (Section 5.2, eq. greedy_mult).
+ *
+ * Conventions shared by every entry point
+ *  - Points are row-major FP64, n x dim (dim = 1, 2 or 3), already in elimination
+ *    order for the selection and fill calls: row p is the point at position p.
+ *  - Pointers marked [device] are device pointers owned by the caller; the library
+ *    never frees or retains them.  Pointers marked [host] are host memory.
+ *  - Every device call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL is the legacy default stream).  Argument errors are returned at once;
+ *    errors found by a kernel (a non-positive-definite pivot, a bound exceeded) are
+ *    recorded in the handle and returned by sic_sync().
+ *  - `ws` / `ws_bytes` is caller-owned device scratch sized by the matching
+ *    *_workspace call; too small a workspace returns SIC_ERR_INVALID.
+ *  - No call falls back to the CPU: without a usable GPU they return SIC_ERR_CUDA.
+ *  - The factor is CSC: col_ptr[n+1] (int64), row_idx (int32 positions), val (FP64).
+ *    Each column lists its diagonal first, then the other rows in ascending order.
+ */
+#ifndef SIC_H
+#define SIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIC_OK = 0,
+    SIC_ERR_INVALID = 1,     /* bad argument: size, pointer, range */
+    SIC_ERR_NOT_PD = 2,      /* a kernel met a non-positive pivot (see sic_last_error_unit) */
+    SIC_ERR_CUDA = 3,        /* a CUDA runtime call failed (no device, launch failure, ...) */
+    SIC_ERR_OOM = 4,         /* the handle could not allocate its own small state */
+    SIC_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    SIC_ERR_UNSUPPORTED = 6  /* valid request outside the compiled size envelope */
+} sic_status;
+
+/* Matern kernel (Section 2; parameterised by sqrt(2 nu) r / length_scale).
+ * Theta_{ab} = variance * M_nu(|x_a - x_b|) for a != b, plus `nugget` on the diagonal. */
+typedef struct {
+    int32_t dim;          /* 1, 2 or 3 */
+    int32_t nu_x2;        /* twice the smoothness: 1, 3 or 5 (nu = 1/2, 3/2, 5/2) */
+    double length_scale;  /* > 0 */
+    double variance;      /* > 0 */
+    double nugget;        /* >= 0 */
+} sic_kernel;
+
+/* Arithmetic of the selection kernels.  The fill and the KL sum are always FP64. */
+typedef enum {
+    SIC_FP64 = 0,        /* scores, partial factor and downdates in FP64 */
+    SIC_FP32_MIXED = 1   /* kernel entries, partial factor and downdates in FP32 */
+} sic_precision;
+
+typedef enum { SIC_OP_L = 0, SIC_OP_LT = 1, SIC_OP_LLT = 2 } sic_op;
+
+typedef struct sic_handle sic_handle;
+
+/* ---------------------------------------------------------------- handle -- */
+
+/* Binds a handle to CUDA device `device` and allocates its status word.
+ * Returns SIC_ERR_CUDA if the device cannot be used. */
+sic_status sic_create(sic_handle** h, int device);
+void sic_destroy(sic_handle* h);
+
+/* Waits for `stream`, then returns (and clears) the first error a kernel recorded
+ * since the last sic_sync, or SIC_ERR_CUDA if the stream itself failed. */
+sic_status sic_sync(sic_handle* h, void* stream);
+
+/* Column (or group) index attached to the error last returned by sic_sync, or -1. */
+int64_t sic_last_error_unit(sic_handle* h);
+
+const char* sic_status_string(sic_status s);
+
+/* Exhaustion floor used by the selections: a candidate whose conditional variance
+ * falls below it is never picked.  0.5 * nugget, or 1e-14 * variance without nugget
+ * (every exact conditional variance is at least the nugget). */
+double sic_exhaustion_floor(const sic_kernel* kp);
+
+/* ------------------------------------------------- input preparation [host] -- */
+
+/* Reverse-maximin ordering (Section 2.2, eq. maximin).  The last position holds
+ * point 0; each earlier position holds the unplaced point farthest (squared FP64
+ * Euclidean distance, ties to the lowest point index) from the points already
+ * placed.  order[p] = index of the point at position p; ell2[p] = squared distance
+ * from it to the points after it (INFINITY at p = n-1).  All buffers [host].
+ * n_threads <= 0 means all hardware threads. */
+sic_status sic_prep_maximin(const double* pts, int64_t n, int32_t dim, int64_t* order, double* ell2,
+                            int32_t n_threads);
+
+/* Candidate lists of single columns (Section 4): for each position i the n_cand
+ * points at positions > i nearest to point i, sorted by (squared distance,
+ * position); fewer near the end of the ordering.  cand_ptr[n+1] receives CSR
+ * offsets; cand_idx must hold n * n_cand entries.  pts in elimination order. [host] */
+sic_status sic_prep_candidates_columns(const double* pts, int64_t n, int32_t dim, int32_t n_cand,
+                                       int64_t* cand_ptr, int32_t* cand_idx, int32_t n_threads);
+
+/* Supernodes (Section 6.1 grouping rule): the first position i not yet grouped opens a
+ * group with the not-yet-grouped j among its K nearest later points (distance order)
+ * with ell2_j <= lambda^2 ell2_i, at most mmax members; then each group smaller than
+ * mmin is merged into the group formed just before it if the union has at most mmax
+ * members.  members[n] lists old positions in the renumbered order (group after group,
+ * ascending within a group); grp_ptr[n+1] receives the group offsets and *n_grp the
+ * group count.  [host] */
+sic_status sic_prep_groups(const double* pts, const double* ell2, int64_t n, int32_t dim, int32_t K,
+                           double lambda, int32_t mmin, int32_t mmax, int64_t* members, int64_t* grp_ptr,
+                           int64_t* n_grp, int32_t n_threads);
+
+/* Candidate lists of groups: for group g (positions grp_ptr[g] .. grp_ptr[g+1]-1)
+ * the n_cand points at positions >= grp_ptr[g+1] whose least squared distance to a
+ * member is smallest, sorted by (that distance, position).  cand_idx must hold
+ * n_grp * n_cand entries.  pts in the renumbered elimination order.  [host] */
+sic_status sic_prep_candidates_groups(const double* pts, int64_t n, int32_t dim, const int64_t* grp_ptr,
+                                      int64_t n_grp, int32_t n_cand, int64_t* cand_ptr, int32_t* cand_idx,
+                                      int32_t n_threads);
+
+/* ---------------------------------------------------------- selection [device] -- */
+
+/* Directed GP selection (Section 3): pick up to k of the n training points x_train
+ * [device, n x dim] for the single target x_target [device, dim] by greedy
+ * conditional variance reduction.  out_idx[k] [device] receives training indices in
+ * pick order (-1 padding), out_var[k+1] [device] the target's conditional variance
+ * after t picks (t = 0..count; unused tail untouched), *out_count [device] the number
+ * of picks (fewer than k if candidates run out or are exhausted).  Needs
+ * sic_select_single_workspace bytes of ws. */
+sic_status sic_select_single_workspace(int64_t n, int32_t k, sic_precision prec, size_t* bytes);
+sic_status sic_select_single(sic_handle* h, const double* x_train, int64_t n, const double* x_target,
+                             const sic_kernel* kp, int32_t k, sic_precision prec, int32_t* out_idx,
+                             double* out_var, int32_t* out_count, void* ws, size_t ws_bytes, void* stream);
+
+/* Per-column selection of the factor's sparsity (Section 4).  Column c targets
+ * position targets[c] (or c when targets is NULL); its candidates are
+ * cand_idx[cand_ptr[c] .. cand_ptr[c+1]) (positions after the target, nearest first).
+ * sel_idx[n_cols * k] [device] receives the picked positions in pick order (-1
+ * padding); sel_count[n_cols] [device] the number of picks.  All columns run in one
+ * persistent launch.  Limits: 1 <= k <= 64, every candidate count <= max_cand <= 1024
+ * (max_cand is the caller's bound on cand_ptr[c+1]-cand_ptr[c]; a column above it is
+ * reported as SIC_ERR_INVALID by sic_sync).  No workspace. */
+sic_status sic_select_columns(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                              const int32_t* targets, int64_t n_cols, const int64_t* cand_ptr,
+                              const int32_t* cand_idx, int32_t max_cand, int32_t k, sic_precision prec,
+                              int32_t* sel_idx, int32_t* sel_count, void* stream);
+
+/* Supernodal selection (Section 5.2): group g is the consecutive positions
+ * grp_ptr[g] .. grp_ptr[g+1]-1 (m_g members, 1 <= m_g <= max_m <= 64); its
+ * candidates cand_idx[cand_ptr[g] .. cand_ptr[g+1]) all lie after the group
+ * (count <= max_cand <= 4096).  Candidates are scored by var_j / var_j|P, the ratio
+ * of their conditional variance given the picks to that given the picks and the
+ * targets (eq. greedy_mult).  sel_idx[n_grp * k], sel_count[n_grp] [device] as in
+ * sic_select_columns.  1 <= k <= 128.  grp_ptr, cand_ptr [device]. */
+sic_status sic_select_aggregated_workspace(sic_handle* h, int64_t n_grp, int32_t max_cand, int32_t max_m,
+                                           int32_t k, sic_precision prec, size_t* bytes);
+sic_status sic_select_aggregated(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                 const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr,
+                                 const int32_t* cand_idx, int32_t max_cand, int32_t max_m, int32_t k,
+                                 sic_precision prec, int32_t* sel_idx, int32_t* sel_count, void* ws,
+                                 size_t ws_bytes, void* stream);
+
+/* ----------------------------------------------------------- the factor [device] -- */
+
+/* Column pointers of the factor for a selection.  Without groups (grp_ptr NULL,
+ * n_grp = n) column i holds 1 + sel_count[i] entries; with groups, member a of a
+ * group of m holds (m - a) + sel_count[g] entries (itself, the later members, the
+ * shared picks; Section 5.1).  col_ptr[n+1] [device].  Needs sic_factor_nnz_workspace
+ * bytes of ws.  The total nnz is col_ptr[n]. */
+sic_status sic_factor_nnz_workspace(int64_t n, size_t* bytes);
+sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, const int32_t* sel_count,
+                          int64_t n, int64_t* col_ptr, void* ws, size_t ws_bytes, void* stream);
+
+/* KL-optimal fill (eq. L_col; aggregated form of Appendix A.4) in FP64 for the
+ * pattern sel_idx / sel_count (k picks per column or group, as returned by the
+ * selection calls; any order).  Writes row_idx / val at col_ptr (from
+ * sic_factor_nnz), logv[n] = log Theta_{ii | s_i \ i} and *sum_logv (one FP64 on the
+ * device, summed in a fixed order so that repeated runs agree bit for bit).  The KL
+ * divergence of the factor is (sum_logv - logdet Theta) / 2 (eq. obj_chol).
+ * grp_ptr NULL means single columns (n_grp = n).  max_m bounds the group size (1
+ * without groups, <= 64).  Needs sic_build_factor_workspace bytes of ws. */
+sic_status sic_build_factor_workspace(int64_t n, size_t* bytes);
+sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                            const int64_t* grp_ptr, int64_t n_grp, int32_t max_m, const int32_t* sel_idx,
+                            const int32_t* sel_count, int32_t k, const int64_t* col_ptr, int32_t* row_idx,
+                            double* val, double* logv, double* sum_logv, void* ws, size_t ws_bytes,
+                            void* stream);
+
+/* y = op(L) x for the CSC factor; x, y are n x nrhs row-major FP64 (x[r * nrhs + c]),
+ * 1 <= nrhs <= 8, all [device].  SIC_OP_L: y = L x; SIC_OP_LT: y = L^T x;
+ * SIC_OP_LLT: y = L (L^T x), the preconditioner (L L^T ~ Theta^{-1}).  x and y must
+ * not overlap.  Needs sic_apply_factor_workspace bytes of ws (the intermediate of
+ * SIC_OP_LLT). */
+sic_status sic_apply_factor_workspace(int64_t n, int32_t nrhs, sic_op op, size_t* bytes);
+sic_status sic_apply_factor(sic_handle* h, int64_t n, const int64_t* col_ptr, const int32_t* row_idx,
+                            const double* val, sic_op op, const double* x, double* y, int32_t nrhs, void* ws,
+                            size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIC_H */

@@ -1,0 +1,338 @@
+// KL-optimal fill of the factor (eq. L_col; aggregated form, Appendix A.4), FP64.
+//
+// One warp per unit (a single column, or a group of m consecutive columns sharing
+// the picks S).  With the aggregated set ordered ascending, s = (P_0..P_{m-1}, S
+// sorted), the factor block is L = U^{-T} where U U^T = Theta_{s,s}, U upper
+// triangular.  The warp forms Theta on the reversed order R = reverse(s) in packed
+// lower storage in shared memory, factors it G G^T = Theta_{RR} (left-looking: lane
+// = row, one dot product per entry), and since U = J G J (J the reversal),
+// member a's column is J G^{-T} e_j with j = n-1-a.  The m right-hand sides are
+// solved together (lane = member, up to 32 per batch) by column-oriented back
+// substitution.  v_a = G_jj^2, so logv = 2 log G_jj (eq. inverse_cond).
+// Rows are written diagonal first, then ascending, to the caller's CSC arrays.
+//
+// Also here: the nnz count + exclusive scan that builds col_ptr, and the fixed-order
+// two-pass sum of logv (bit-reproducible).
+#include "sic_internal.cuh"
+
+namespace {
+
+constexpr int SCAN_TILE = 1024;  // elements per scan block (256 threads x 4)
+constexpr int SUM_TILE = 2048;   // elements per partial-sum block
+
+// ---------------------------------------------------------------- nnz + scan --
+
+__global__ void k_nnz_count(const long long* __restrict__ grp_ptr, long long n_grp, const int32_t* __restrict__ cnt,
+                            long long n, long long* __restrict__ out, DevStatus* st) {
+    long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (u >= n_grp) return;
+    if (!grp_ptr) {
+        out[u] = 1 + (long long)cnt[u];
+        return;
+    }
+    long long g0 = grp_ptr[u], g1 = grp_ptr[u + 1];
+    if (g0 < 0 || g1 > n || g1 <= g0) {
+        record_error(st, SIC_ERR_INVALID, u);
+        return;
+    }
+    int m = (int)(g1 - g0);
+    for (int a = 0; a < m; ++a) out[g0 + a] = (long long)(m - a) + cnt[u];
+}
+
+// Block-local exclusive scan of a tile; the tile total goes to partial[blockIdx].
+__global__ void __launch_bounds__(256) k_scan_tile(long long* __restrict__ v, long long n,
+                                                   long long* __restrict__ partial) {
+    __shared__ long long s[256];
+    long long base = blockIdx.x * (long long)SCAN_TILE + threadIdx.x * 4;
+    long long a[4];
+    long long sum = 0;
+    for (int i = 0; i < 4; ++i) {
+        a[i] = (base + i < n) ? v[base + i] : 0;
+        sum += a[i];
+    }
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        long long x = (threadIdx.x >= off) ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += x;
+        __syncthreads();
+    }
+    long long run = s[threadIdx.x] - sum;  // exclusive prefix of this thread
+    for (int i = 0; i < 4; ++i) {
+        if (base + i < n) v[base + i] = run;
+        run += a[i];
+    }
+    if (threadIdx.x == 255) partial[blockIdx.x] = s[255];
+}
+
+// Exclusive scan of the tile totals in one block (loops over chunks of 256).
+__global__ void __launch_bounds__(256) k_scan_partials(long long* __restrict__ partial, long long nb,
+                                                       long long* __restrict__ total) {
+    __shared__ long long s[256];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long c0 = 0; c0 < nb; c0 += 256) {
+        long long i = c0 + threadIdx.x;
+        long long x0 = (i < nb) ? partial[i] : 0;
+        s[threadIdx.x] = x0;
+        __syncthreads();
+        for (int off = 1; off < 256; off <<= 1) {
+            long long x = (threadIdx.x >= off) ? s[threadIdx.x - off] : 0;
+            __syncthreads();
+            s[threadIdx.x] += x;
+            __syncthreads();
+        }
+        if (i < nb) partial[i] = carry + s[threadIdx.x] - x0;
+        __syncthreads();
+        if (threadIdx.x == 255) carry += s[255];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(long long* __restrict__ v, long long n, const long long* __restrict__ partial) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) v[i] += partial[i / SCAN_TILE];
+}
+
+// ------------------------------------------------------------------- the fill --
+
+struct FillSmem {
+    double* G;    // packed lower, n(n+1)/2
+    double* B;    // n x 32 right-hand sides, row-major [i][lane]
+    double* xyz;  // 3 x n coordinates of R
+    int* pos;     // n positions of R
+    int* srt;     // k picks sorted ascending
+};
+
+__device__ __forceinline__ long long pk(int i, int j) { return (long long)i * (i + 1) / 2 + j; }
+
+__global__ void __launch_bounds__(32) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
+                                             const long long* __restrict__ grp_ptr, long long n_units,
+                                             const int32_t* __restrict__ sel_idx,
+                                             const int32_t* __restrict__ sel_count, int k, int max_m, long long n,
+                                             const long long* __restrict__ col_ptr, int32_t* __restrict__ row_idx,
+                                             double* __restrict__ val, double* __restrict__ logv, DevStatus* st) {
+    extern __shared__ double smem_d[];
+    const int nmax = k + max_m;
+    double* G = smem_d;
+    double* B = G + (long long)nmax * (nmax + 1) / 2;
+    double* xyz = B + (long long)nmax * 32;
+    int* pos = reinterpret_cast<int*>(xyz + 3 * nmax);
+    int* srt = pos + nmax;
+    const int lane = threadIdx.x;
+
+    for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const long long g0 = grp_ptr ? grp_ptr[u] : u;
+        const int m = grp_ptr ? (int)(grp_ptr[u + 1] - g0) : 1;
+        int cnt = sel_count[u];
+        if (m < 1 || m > max_m || cnt < 0 || cnt > k || g0 < 0 || g0 + m > n) {
+            if (lane == 0) record_error(st, SIC_ERR_INVALID, u);
+            continue;
+        }
+        const int nn = cnt + m;
+        // picks sorted ascending by rank; they must be distinct positions after the unit
+        bool badsel = false;
+        for (int i = lane; i < cnt; i += 32) {
+            int v = sel_idx[u * k + i];
+            int rank = 0, same = 0;
+            for (int j = 0; j < cnt; ++j) {
+                int w = sel_idx[u * k + j];
+                rank += (w < v);
+                same += (w == v);
+            }
+            if (v < g0 + m || v >= n || same != 1) badsel = true;
+            else srt[rank] = v;
+        }
+        badsel = __any_sync(0xffffffffu, badsel);
+        if (!badsel)
+            for (int a = lane; a < m; a += 32)
+                if (col_ptr[g0 + a + 1] - col_ptr[g0 + a] != (long long)(m - a + cnt)) badsel = true;
+        badsel = __any_sync(0xffffffffu, badsel);
+        if (badsel) {
+            if (lane == 0) record_error(st, SIC_ERR_INVALID, u);
+            continue;
+        }
+        __syncwarp();
+        // R order: picks descending, then members descending
+        for (int i = lane; i < nn; i += 32) {
+            int p = (i < cnt) ? srt[cnt - 1 - i] : (int)(g0 + m - 1 - (i - cnt));
+            pos[i] = p;
+            for (int d = 0; d < 3; ++d) xyz[d * nmax + i] = (d < dim) ? pts[(long long)p * dim + d] : 0.0;
+        }
+        __syncwarp();
+        // Theta_RR, packed lower
+        for (int i = 0; i < nn; ++i) {
+            const double xi = xyz[i], yi = xyz[nmax + i], zi = xyz[2 * nmax + i];
+            for (int j = lane; j <= i; j += 32) {
+                double dx = xi - xyz[j], dy = yi - xyz[nmax + j], dz = zi - xyz[2 * nmax + j];
+                double v = matern<double>(kp, sqrt(dx * dx + dy * dy + dz * dz));
+                if (i == j) v += kp.nugget;
+                G[pk(i, j)] = v;
+            }
+        }
+        __syncwarp();
+        // left-looking Cholesky: column j, lane owns rows i = j + lane, j + lane + 32, ...
+        bool bad = false;
+        for (int j = 0; j < nn; ++j) {
+            for (int i = j + lane; i < nn; i += 32) {
+                double s = G[pk(i, j)];
+                const long long ri = pk(i, 0), rj = pk(j, 0);
+                for (int l = 0; l < j; ++l) s = fma(-G[ri + l], G[rj + l], s);
+                G[pk(i, j)] = s;
+            }
+            __syncwarp();
+            const double djj = G[pk(j, j)];
+            if (!(djj > 0.0)) {
+                bad = true;
+                break;
+            }
+            const double d = sqrt(djj);
+            const double rd = 1.0 / d;
+            for (int i = j + 1 + lane; i < nn; i += 32) G[pk(i, j)] *= rd;
+            __syncwarp();
+            if (lane == 0) G[pk(j, j)] = d;
+            __syncwarp();
+        }
+        if (bad) {
+            if (lane == 0) record_error(st, SIC_ERR_NOT_PD, u);
+            __syncwarp();
+            continue;
+        }
+        // members in batches of 32: lane b solves G^T x = e_{j_b}, j_b = nn - 1 - (a0 + b)
+        for (int a0 = 0; a0 < m; a0 += 32) {
+            const int a = a0 + lane;
+            const bool act = a < m;
+            const int jb = nn - 1 - a;
+            if (act)
+                for (int i = 0; i <= jb; ++i) B[i * 32 + lane] = (i == jb) ? 1.0 : 0.0;
+            __syncwarp();
+            const int top = nn - 1 - a0;  // largest j_b in the batch
+            for (int l = top; l >= 0; --l) {
+                if (act && l <= jb) {
+                    const long long rl = pk(l, 0);
+                    const double xl = B[l * 32 + lane] / G[rl + l];
+                    B[l * 32 + lane] = xl;
+                    for (int i = 0; i < l; ++i) B[i * 32 + lane] = fma(-G[rl + i], xl, B[i * 32 + lane]);
+                }
+            }
+            __syncwarp();
+            if (act) {
+                const long long c0 = col_ptr[g0 + a];
+                for (int p = 0; p <= jb; ++p) {
+                    row_idx[c0 + p] = pos[jb - p];
+                    val[c0 + p] = B[(jb - p) * 32 + lane];
+                }
+                logv[g0 + a] = 2.0 * log(G[pk(jb, jb)]);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Fixed-order sum: each block reduces a contiguous tile; then one block adds the tiles.
+__global__ void __launch_bounds__(256) k_sum_tiles(const double* __restrict__ x, long long n,
+                                                   double* __restrict__ partial) {
+    __shared__ double s[256];
+    long long base = blockIdx.x * (long long)SUM_TILE;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < SUM_TILE; i += 256)
+        if (base + i < n) acc += x[base + i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) s[threadIdx.x] += s[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
+}
+
+__global__ void __launch_bounds__(256) k_sum_final(const double* __restrict__ partial, long long nb,
+                                                   double* __restrict__ out) {
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < nb; i += 256) acc += partial[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) s[threadIdx.x] += s[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+size_t fill_smem_bytes(int k, int max_m) {
+    size_t nmax = (size_t)k + (size_t)max_m;
+    return sizeof(double) * (nmax * (nmax + 1) / 2 + nmax * 32 + 3 * nmax) + sizeof(int) * (nmax + (size_t)k);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- entry points --
+
+extern "C" sic_status sic_factor_nnz_workspace(int64_t n, size_t* bytes) {
+    if (!bytes || n < 0) return SIC_ERR_INVALID;
+    long long nb = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
+    *bytes = sizeof(long long) * (size_t)(nb + 1);
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, const int32_t* sel_count,
+                                     int64_t n, int64_t* col_ptr, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || !sel_count || !col_ptr || n < 1 || n_grp < 1 || (!grp_ptr && n_grp != n)) return SIC_ERR_INVALID;
+    size_t need = 0;
+    sic_factor_nnz_workspace(n, &need);
+    if (!ws || ws_bytes < need) return SIC_ERR_INVALID;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    long long* v = (long long*)col_ptr;
+    long long* partial = (long long*)ws;
+    long long len = n + 1;
+    long long nb = (len + SCAN_TILE - 1) / SCAN_TILE;
+    SIC_CUDA_TRY(cudaMemsetAsync(v + n, 0, sizeof(long long), s));
+    k_nnz_count<<<(unsigned)((n_grp + 255) / 256), 256, 0, s>>>((const long long*)grp_ptr, n_grp, sel_count, n, v,
+                                                                  h->d_status);
+    k_scan_tile<<<(unsigned)nb, 256, 0, s>>>(v, len, partial);
+    k_scan_partials<<<1, 256, 0, s>>>(partial, nb, partial + nb);
+    k_scan_add<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(v, len, partial);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_build_factor_workspace(int64_t n, size_t* bytes) {
+    if (!bytes || n < 0) return SIC_ERR_INVALID;
+    long long nb = (n + SUM_TILE - 1) / SUM_TILE;
+    *bytes = sizeof(double) * (size_t)(nb > 0 ? nb : 1);
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                       const int64_t* grp_ptr, int64_t n_grp, int32_t max_m, const int32_t* sel_idx,
+                                       const int32_t* sel_count, int32_t k, const int64_t* col_ptr,
+                                       int32_t* row_idx, double* val, double* logv, double* sum_logv, void* ws,
+                                       size_t ws_bytes, void* stream) {
+    if (!h || !pts || !sic_valid_kernel(kp) || n < 1 || n_grp < 1 || !sel_count || !col_ptr || !row_idx || !val ||
+        !logv || !sum_logv || k < 0 || (k > 0 && !sel_idx))
+        return SIC_ERR_INVALID;
+    if (!grp_ptr && (n_grp != n || max_m != 1)) return SIC_ERR_INVALID;
+    if (max_m < 1) return SIC_ERR_INVALID;
+    if (max_m > 64 || k > 128) return SIC_ERR_UNSUPPORTED;
+    size_t need = 0;
+    sic_build_factor_workspace(n, &need);
+    if (!ws || ws_bytes < need) return SIC_ERR_INVALID;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t sm = fill_smem_bytes(k, max_m);
+    if (sm > 200 * 1024) return SIC_ERR_UNSUPPORTED;
+    SIC_CUDA_TRY(cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int grid = persistent_grid(h, k_fill, 32, sm, n_grp);
+    k_fill<<<grid, 32, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp, sel_idx,
+                                sel_count, k, max_m, n, (const long long*)col_ptr, row_idx, val, logv, h->d_status);
+    long long nb = (n + SUM_TILE - 1) / SUM_TILE;
+    k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n, (double*)ws);
+    k_sum_final<<<1, 256, 0, s>>>((const double*)ws, nb, sum_logv);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}

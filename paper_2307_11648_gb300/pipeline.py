@@ -1,0 +1,144 @@
+"""Orchestration of libsic calls into a whole factor build (no arithmetic here).
+
+`Problem` holds the prepared inputs (points in elimination order, candidate lists,
+optional supernodes) resident on the device; `FactorBuilder` owns the output and
+scratch buffers and issues, on one stream, the sequence
+
+    select (per column or per supernode) -> nnz scan -> FP64 fill + sum of log v
+
+every step of which is a libsic kernel.  Buffers are allocated once, so a build can
+be replayed (and captured in a CUDA graph) without allocation.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import sic
+
+
+@dataclass
+class HostProblem:
+    pts: np.ndarray          # n x dim, elimination order
+    kp: sic.Kernel
+    k: int
+    cand_ptr: np.ndarray     # int64, units + 1
+    cand_idx: np.ndarray     # int32
+    grp_ptr: np.ndarray | None = None  # int64, groups + 1 (None: single columns)
+    order: np.ndarray | None = None    # old point index per position (for reference)
+    ell2: np.ndarray | None = None
+
+    @property
+    def n(self):
+        return self.pts.shape[0]
+
+    @property
+    def n_units(self):
+        return self.n if self.grp_ptr is None else len(self.grp_ptr) - 1
+
+    @property
+    def max_cand(self):
+        return int(np.max(np.diff(self.cand_ptr))) if self.n_units else 0
+
+    @property
+    def max_m(self):
+        return 1 if self.grp_ptr is None else int(np.max(np.diff(self.grp_ptr)))
+
+    def h2d_bytes(self):
+        b = self.pts.nbytes + self.cand_ptr.nbytes + self.cand_idx.nbytes
+        if self.grp_ptr is not None:
+            b += self.grp_ptr.nbytes
+        return b
+
+
+def prepare_columns(points: np.ndarray, kp: sic.Kernel, n_cand: int, k: int, n_threads: int = 0) -> HostProblem:
+    """Reverse-maximin order + later-ordered candidate lists (libsic host prep)."""
+    order, ell2 = sic.prep_maximin(points, n_threads)
+    P = np.ascontiguousarray(points[order])
+    ptr, idx = sic.prep_candidates_columns(P, n_cand, n_threads)
+    return HostProblem(P, kp, k, ptr, idx, None, order, ell2)
+
+
+def prepare_groups(points: np.ndarray, kp: sic.Kernel, n_cand: int, k: int, mmin: int = 8, mmax: int = 64,
+                   lam: float = 1.5, n_threads: int = 0) -> HostProblem:
+    """Reverse-maximin order, supernodes (Section 6.1 rule on the 2k nearest later points,
+    renumbered to be consecutive) and group candidate lists."""
+    order, ell2 = sic.prep_maximin(points, n_threads)
+    P = np.ascontiguousarray(points[order])
+    members, gp = sic.prep_groups(P, ell2, 2 * k, lam, mmin, mmax, n_threads)
+    P2 = np.ascontiguousarray(P[members])
+    ptr, idx = sic.prep_candidates_groups(P2, gp, n_cand, n_threads)
+    return HostProblem(P2, kp, k, ptr, idx, gp, order[members], ell2[members])
+
+
+class DeviceProblem:
+    def __init__(self, hp: HostProblem, device="cuda"):
+        import torch
+        self.hp = hp
+        self.device = device
+        self.pts = torch.from_numpy(hp.pts).to(device)
+        self.cand_ptr = torch.from_numpy(hp.cand_ptr).to(device)
+        idx = hp.cand_idx if hp.cand_idx.size else np.zeros(1, np.int32)  # never a NULL pointer
+        self.cand_idx = torch.from_numpy(idx).to(device)
+        self.grp_ptr = torch.from_numpy(hp.grp_ptr).to(device) if hp.grp_ptr is not None else None
+
+
+class FactorBuilder:
+    """Preallocated outputs + scratch for building the factor of one problem."""
+
+    def __init__(self, h: sic.Handle, hp: HostProblem, prec: int, device="cuda", nnz_cap: int | None = None):
+        import torch
+        self.h, self.hp, self.prec = h, hp, prec
+        n, U, k = hp.n, hp.n_units, hp.k
+        dev = device
+        self.sel_idx = torch.empty(U * k, dtype=torch.int32, device=dev)
+        self.sel_count = torch.empty(U, dtype=torch.int32, device=dev)
+        self.col_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        # capacity: every column holds at most (its group's later members) + k + 1 entries
+        if nnz_cap is None:
+            if hp.grp_ptr is None:
+                nnz_cap = n * (k + 1)
+            else:
+                m = np.diff(hp.grp_ptr)
+                nnz_cap = int(np.sum(m * (m + 1) // 2 + m * k))
+        self.nnz_cap = nnz_cap
+        self.row_idx = torch.empty(nnz_cap, dtype=torch.int32, device=dev)
+        self.val = torch.empty(nnz_cap, dtype=torch.float64, device=dev)
+        self.logv = torch.empty(n, dtype=torch.float64, device=dev)
+        self.sum_logv = torch.zeros(1, dtype=torch.float64, device=dev)
+        if hp.grp_ptr is None:
+            self.ws_sel = None
+        else:
+            self.ws_sel = sic._ws(sic.select_aggregated_workspace(h, U, hp.max_cand, hp.max_m, k, prec), dev)
+        self.ws_nnz = sic._ws(sic.factor_nnz_workspace(n), dev)
+        self.ws_fill = sic._ws(sic.build_factor_workspace(n), dev)
+
+    def select(self, dp: DeviceProblem, stream=None):
+        hp = self.hp
+        if hp.grp_ptr is None:
+            sic.select_columns(self.h, dp.pts, hp.kp, dp.cand_ptr, dp.cand_idx, hp.max_cand, hp.k, self.prec,
+                               self.sel_idx, self.sel_count, stream=stream)
+        else:
+            sic.select_aggregated(self.h, dp.pts, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, hp.max_cand, hp.max_m,
+                                  hp.k, self.prec, self.sel_idx, self.sel_count, self.ws_sel, stream=stream)
+
+    def fill(self, dp: DeviceProblem, stream=None):
+        hp = self.hp
+        sic.factor_nnz(self.h, dp.grp_ptr, self.sel_count, hp.n, self.col_ptr, self.ws_nnz, stream=stream)
+        sic.build_factor(self.h, dp.pts, hp.kp, dp.grp_ptr, hp.max_m, self.sel_idx, self.sel_count, hp.k,
+                         self.col_ptr, self.row_idx, self.val, self.logv, self.sum_logv, self.ws_fill, stream=stream)
+
+    def run(self, dp: DeviceProblem, stream=None):
+        self.select(dp, stream)
+        self.fill(dp, stream)
+
+    def sel_lists(self):
+        si = self.sel_idx.view(-1, self.hp.k).cpu().numpy()
+        sc = self.sel_count.cpu().numpy()
+        return [si[u, :sc[u]].copy() for u in range(len(sc))]
+
+    def csc(self):
+        cp = self.col_ptr.cpu().numpy()
+        nnz = int(cp[-1])
+        return cp, self.row_idx[:nnz].cpu().numpy(), self.val[:nnz].cpu().numpy(), self.logv.cpu().numpy()

@@ -1,0 +1,325 @@
+"""Thin ctypes binding of libsic (include/sic.h).
+
+Argument marshalling only: every function here checks types, takes raw pointers
+of torch tensors (device memory) or numpy arrays (host memory) and calls the
+C entry point of the same name.  All arithmetic of the method runs in libsic's
+CUDA kernels; there is no CPU fallback -- if the compiled library is missing,
+`lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsic.so")
+
+SIC_OK, SIC_ERR_INVALID, SIC_ERR_NOT_PD, SIC_ERR_CUDA, SIC_ERR_OOM, SIC_ERR_TIMEOUT, SIC_ERR_UNSUPPORTED = range(7)
+SIC_FP64, SIC_FP32_MIXED = 0, 1
+SIC_OP_L, SIC_OP_LT, SIC_OP_LLT = 0, 1, 2
+
+# every symbol include/sic.h declares
+EXPORTS = [
+    "sic_create", "sic_destroy", "sic_sync", "sic_last_error_unit", "sic_status_string", "sic_exhaustion_floor",
+    "sic_prep_maximin", "sic_prep_candidates_columns", "sic_prep_groups", "sic_prep_candidates_groups",
+    "sic_select_single_workspace", "sic_select_single", "sic_select_columns",
+    "sic_select_aggregated_workspace", "sic_select_aggregated",
+    "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_build_factor_workspace", "sic_build_factor",
+    "sic_apply_factor_workspace", "sic_apply_factor",
+]
+
+
+class SicError(RuntimeError):
+    def __init__(self, code: int, where: str, unit: int = -1):
+        self.code = code
+        self.unit = unit
+        super().__init__(f"{where}: {status_string(code)} (code {code}, unit {unit})")
+
+
+class Kernel(C.Structure):
+    """sic_kernel: Matern kernel, nu_x2 = 2 nu in {1, 3, 5}."""
+    _fields_ = [("dim", C.c_int32), ("nu_x2", C.c_int32), ("length_scale", C.c_double),
+                ("variance", C.c_double), ("nugget", C.c_double)]
+
+
+def kernel(dim, nu_x2, length_scale, variance=1.0, nugget=0.0) -> Kernel:
+    return Kernel(int(dim), int(nu_x2), float(length_scale), float(variance), float(nugget))
+
+
+_lib = None
+
+
+def lib():
+    """Load libsic.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsic is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, d, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+        pk = C.POINTER(Kernel)
+        st = C.c_int
+        sig = {
+            "sic_create": (st, [C.POINTER(vp), C.c_int]),
+            "sic_destroy": (None, [vp]),
+            "sic_sync": (st, [vp, vp]),
+            "sic_last_error_unit": (i64, [vp]),
+            "sic_status_string": (C.c_char_p, [st]),
+            "sic_exhaustion_floor": (d, [pk]),
+            "sic_prep_maximin": (st, [vp, i64, i32, vp, vp, i32]),
+            "sic_prep_candidates_columns": (st, [vp, i64, i32, i32, vp, vp, i32]),
+            "sic_prep_groups": (st, [vp, vp, i64, i32, i32, d, i32, i32, vp, vp, vp, i32]),
+            "sic_prep_candidates_groups": (st, [vp, i64, i32, vp, i64, i32, vp, vp, i32]),
+            "sic_select_single_workspace": (st, [i64, i32, st, C.POINTER(sz)]),
+            "sic_select_single": (st, [vp, vp, i64, vp, pk, i32, st, vp, vp, vp, vp, sz, vp]),
+            "sic_select_columns": (st, [vp, vp, i64, pk, vp, i64, vp, vp, i32, i32, st, vp, vp, vp]),
+            "sic_select_aggregated_workspace": (st, [vp, i64, i32, i32, i32, st, C.POINTER(sz)]),
+            "sic_select_aggregated": (st, [vp, vp, i64, pk, vp, i64, vp, vp, i32, i32, i32, st, vp, vp, vp, sz,
+                                           vp]),
+            "sic_factor_nnz_workspace": (st, [i64, C.POINTER(sz)]),
+            "sic_factor_nnz": (st, [vp, vp, i64, vp, i64, vp, vp, sz, vp]),
+            "sic_build_factor_workspace": (st, [i64, C.POINTER(sz)]),
+            "sic_build_factor": (st, [vp, vp, i64, pk, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "sic_apply_factor_workspace": (st, [i64, i32, st, C.POINTER(sz)]),
+            "sic_apply_factor": (st, [vp, i64, vp, vp, vp, st, vp, vp, i32, vp, sz, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().sic_status_string(int(code)).decode()
+    except Exception:
+        return f"status {code}"
+
+
+def _check(code: int, where: str, h=None):
+    if code != SIC_OK:
+        unit = lib().sic_last_error_unit(h.ptr) if h is not None else -1
+        raise SicError(code, where, unit)
+
+
+# ------------------------------------------------------------ marshalling --
+
+def _dptr(t, dtype=None, name="tensor"):
+    """Device pointer of a CUDA torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a, dtype, name="array"):
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous numpy array of {dtype}")
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- handle --
+
+class Handle:
+    """Owns a sic_handle (device binding + status word)."""
+
+    def __init__(self, device: int = 0):
+        p = C.c_void_p()
+        _check(lib().sic_create(C.byref(p), int(device)), "sic_create")
+        self.ptr = p
+        self.device = device
+
+    def close(self):
+        if self.ptr:
+            lib().sic_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        """sic_sync: wait for the stream and raise the first kernel-recorded error."""
+        _check(lib().sic_sync(self.ptr, _stream(stream)), "sic_sync", self)
+
+
+def exhaustion_floor(kp: Kernel) -> float:
+    return lib().sic_exhaustion_floor(C.byref(kp))
+
+
+# ------------------------------------------------------------ host prep --
+
+def prep_maximin(pts: np.ndarray, n_threads: int = 0):
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    n, dim = pts.shape
+    order = np.empty(n, np.int64)
+    ell2 = np.empty(n, np.float64)
+    _check(lib().sic_prep_maximin(_hptr(pts, np.float64), n, dim, _hptr(order, np.int64), _hptr(ell2, np.float64),
+                                  n_threads), "sic_prep_maximin")
+    return order, ell2
+
+
+def prep_candidates_columns(pts: np.ndarray, n_cand: int, n_threads: int = 0):
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    n, dim = pts.shape
+    ptr = np.empty(n + 1, np.int64)
+    idx = np.empty(max(1, n * n_cand), np.int32)
+    _check(lib().sic_prep_candidates_columns(_hptr(pts, np.float64), n, dim, n_cand, _hptr(ptr, np.int64),
+                                             _hptr(idx, np.int32), n_threads), "sic_prep_candidates_columns")
+    return ptr, idx[:ptr[-1]].copy()
+
+
+def prep_groups(pts: np.ndarray, ell2: np.ndarray, K: int, lam: float = 1.5, mmin: int = 8, mmax: int = 64,
+                n_threads: int = 0):
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    ell2 = np.ascontiguousarray(ell2, dtype=np.float64)
+    n, dim = pts.shape
+    members = np.empty(n, np.int64)
+    gp = np.empty(n + 1, np.int64)
+    ng = np.zeros(1, np.int64)
+    _check(lib().sic_prep_groups(_hptr(pts, np.float64), _hptr(ell2, np.float64), n, dim, K, lam, mmin, mmax,
+                                 _hptr(members, np.int64), _hptr(gp, np.int64), _hptr(ng, np.int64), n_threads),
+           "sic_prep_groups")
+    return members, gp[:ng[0] + 1].copy()
+
+
+def prep_candidates_groups(pts: np.ndarray, grp_ptr: np.ndarray, n_cand: int, n_threads: int = 0):
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    grp_ptr = np.ascontiguousarray(grp_ptr, dtype=np.int64)
+    n, dim = pts.shape
+    ng = len(grp_ptr) - 1
+    ptr = np.empty(ng + 1, np.int64)
+    idx = np.empty(max(1, ng * n_cand), np.int32)
+    _check(lib().sic_prep_candidates_groups(_hptr(pts, np.float64), n, dim, _hptr(grp_ptr, np.int64), ng, n_cand,
+                                            _hptr(ptr, np.int64), _hptr(idx, np.int32), n_threads),
+           "sic_prep_candidates_groups")
+    return ptr, idx[:ptr[-1]].copy()
+
+
+# ------------------------------------------------------------- selection --
+
+def _ws(nbytes: int, device):
+    import torch
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+
+def select_single_workspace(n: int, k: int, prec: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sic_select_single_workspace(n, k, prec, C.byref(b)), "sic_select_single_workspace")
+    return b.value
+
+
+def select_single(h: Handle, x_train, x_target, kp: Kernel, k: int, prec: int, out_idx, out_var, out_count, ws,
+                  stream=None):
+    import torch
+    n = x_train.shape[0]
+    _check(lib().sic_select_single(h.ptr, _dptr(x_train, torch.float64, "x_train"), n,
+                                   _dptr(x_target, torch.float64, "x_target"), C.byref(kp), k, prec,
+                                   _dptr(out_idx, torch.int32, "out_idx"), _dptr(out_var, torch.float64, "out_var"),
+                                   _dptr(out_count, torch.int32, "out_count"), _dptr(ws), ws.numel(),
+                                   _stream(stream)), "sic_select_single", h)
+
+
+def select_columns(h: Handle, pts, kp: Kernel, cand_ptr, cand_idx, max_cand: int, k: int, prec: int, sel_idx,
+                   sel_count, targets=None, stream=None):
+    import torch
+    n = pts.shape[0]
+    n_cols = targets.numel() if targets is not None else n
+    _check(lib().sic_select_columns(h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp),
+                                    _dptr(targets, torch.int32, "targets"), n_cols,
+                                    _dptr(cand_ptr, torch.int64, "cand_ptr"), _dptr(cand_idx, torch.int32, "cand_idx"),
+                                    max_cand, k, prec, _dptr(sel_idx, torch.int32, "sel_idx"),
+                                    _dptr(sel_count, torch.int32, "sel_count"), _stream(stream)),
+           "sic_select_columns", h)
+
+
+def select_aggregated_workspace(h: Handle, n_grp: int, max_cand: int, max_m: int, k: int, prec: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sic_select_aggregated_workspace(h.ptr, n_grp, max_cand, max_m, k, prec, C.byref(b)),
+           "sic_select_aggregated_workspace")
+    return b.value
+
+
+def select_aggregated(h: Handle, pts, kp: Kernel, grp_ptr, cand_ptr, cand_idx, max_cand: int, max_m: int, k: int,
+                      prec: int, sel_idx, sel_count, ws, stream=None):
+    import torch
+    n = pts.shape[0]
+    n_grp = grp_ptr.numel() - 1
+    _check(lib().sic_select_aggregated(h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp),
+                                       _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp,
+                                       _dptr(cand_ptr, torch.int64, "cand_ptr"),
+                                       _dptr(cand_idx, torch.int32, "cand_idx"), max_cand, max_m, k, prec,
+                                       _dptr(sel_idx, torch.int32, "sel_idx"),
+                                       _dptr(sel_count, torch.int32, "sel_count"), _dptr(ws), ws.numel(),
+                                       _stream(stream)), "sic_select_aggregated", h)
+
+
+# ------------------------------------------------------------- the factor --
+
+def factor_nnz_workspace(n: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sic_factor_nnz_workspace(n, C.byref(b)), "sic_factor_nnz_workspace")
+    return b.value
+
+
+def factor_nnz(h: Handle, grp_ptr, sel_count, n: int, col_ptr, ws, stream=None):
+    import torch
+    n_grp = grp_ptr.numel() - 1 if grp_ptr is not None else n
+    _check(lib().sic_factor_nnz(h.ptr, _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp,
+                                _dptr(sel_count, torch.int32, "sel_count"), n, _dptr(col_ptr, torch.int64, "col_ptr"),
+                                _dptr(ws), ws.numel(), _stream(stream)), "sic_factor_nnz", h)
+
+
+def build_factor_workspace(n: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sic_build_factor_workspace(n, C.byref(b)), "sic_build_factor_workspace")
+    return b.value
+
+
+def build_factor(h: Handle, pts, kp: Kernel, grp_ptr, max_m: int, sel_idx, sel_count, k: int, col_ptr, row_idx, val,
+                 logv, sum_logv, ws, stream=None):
+    import torch
+    n = pts.shape[0]
+    n_grp = grp_ptr.numel() - 1 if grp_ptr is not None else n
+    _check(lib().sic_build_factor(h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp),
+                                  _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp, max_m,
+                                  _dptr(sel_idx, torch.int32, "sel_idx"), _dptr(sel_count, torch.int32, "sel_count"),
+                                  k, _dptr(col_ptr, torch.int64, "col_ptr"), _dptr(row_idx, torch.int32, "row_idx"),
+                                  _dptr(val, torch.float64, "val"), _dptr(logv, torch.float64, "logv"),
+                                  _dptr(sum_logv, torch.float64, "sum_logv"), _dptr(ws), ws.numel(),
+                                  _stream(stream)), "sic_build_factor", h)
+
+
+def apply_factor_workspace(n: int, nrhs: int, op: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sic_apply_factor_workspace(n, nrhs, op, C.byref(b)), "sic_apply_factor_workspace")
+    return b.value
+
+
+def apply_factor(h: Handle, col_ptr, row_idx, val, op: int, x, y, ws=None, stream=None):
+    import torch
+    n = col_ptr.numel() - 1
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    _check(lib().sic_apply_factor(h.ptr, n, _dptr(col_ptr, torch.int64, "col_ptr"),
+                                  _dptr(row_idx, torch.int32, "row_idx"), _dptr(val, torch.float64, "val"), op,
+                                  _dptr(x, torch.float64, "x"), _dptr(y, torch.float64, "y"), nrhs, _dptr(ws),
+                                  ws.numel() if ws is not None else 0, _stream(stream)), "sic_apply_factor", h)

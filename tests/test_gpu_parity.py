@@ -1,0 +1,363 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Tolerances (stated per result; FP64 rounding differences come from FMA contraction
+and a different exp implementation, ~1e-16 relative per operation):
+  * FP64 selections: identical, except at near-ties whose oracle scores differ by less
+    than TIE_BAND = 1e-10 relative (then the oracle replays the GPU's pick);
+  * FP32 selections: a differing pick must score within FP32_BAND (relative) of the
+    oracle's best at that step, or within FP32_ABS * variance in absolute terms (under
+    replay); the fraction of such steps is printed.  FP32_ABS: kernel entries carry
+    an absolute rounding of eps32 * variance = 6e-8 * variance, and after up to 64
+    downdates the conditional (co)variances carry ~sqrt(64) times that, so scores
+    closer than ~1e-6 * variance are not resolved in FP32.  Single-target scores
+    (cov^2 / var) are absolute; multi-target scores (var / var|P) are ratios, so only
+    the relative band applies to them;
+  * fill: row indices identical; values max|dL| <= 1e-8 * max|L| per column;
+    log v_i to 1e-9 absolute (log v is O(10), so 1e-10 relative);
+  * KL sum: 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from parity import ReplayStats, column_errors, replay_multi, replay_single
+
+pytestmark = pytest.mark.gpu
+
+TIE_BAND = 1e-10
+FP32_BAND = 2e-2
+FP32_ABS = 1e-6
+L_TOL = 1e-8
+LOGV_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_11648_gb300 import build
+    build.build()
+    from paper_2307_11648_gb300 import pipeline, sic
+    h = sic.Handle(0)
+    return torch, sic, pipeline, h
+
+
+def _okernel(oracle, kp):
+    return oracle.kernel(kp.dim, kp.nu_x2, kp.length_scale, kp.variance, kp.nugget)
+
+
+def _run(env, hp, prec):
+    torch, sic, pipeline, h = env
+    dp = pipeline.DeviceProblem(hp)
+    fb = pipeline.FactorBuilder(h, hp, prec)
+    fb.run(dp)
+    h.sync()
+    return fb
+
+
+def _check_fill_columns(oracle, okp, P, cols, sels, cp, ri, val, logv):
+    worst = 0.0
+    for i in cols:
+        rows, L, lv = oracle.fill_column(okp, P, i, sels[i])
+        a, b = cp[i], cp[i + 1]
+        assert ri[a:b].tolist() == rows.tolist(), f"rows of column {i}"
+        e = column_errors(val[a:b], L)
+        worst = max(worst, e)
+        assert e <= L_TOL, f"column {i}: rel err {e}"
+        assert abs(logv[i] - lv) <= LOGV_TOL, f"column {i}: logv {logv[i]} vs {lv}"
+    return worst
+
+
+# ------------------------------------------------------- single columns --
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_columns_small_full(env, oracle_lib, prec_name):
+    """Config-1 workload (N=4096, 2-D, Matern 3/2, ell=0.1, nugget 1e-8, C=256, k=16),
+    every column compared."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    cfg = synthetic.PRESETS["cfg1_single_fp64"]
+    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"])
+    pts = synthetic.points(cfg["n"], cfg["dim"], cfg["seed"])
+    hp = pipeline.prepare_columns(pts, kp, cfg["n_cand"], cfg["k"])
+    prec = sic.SIC_FP64 if prec_name == "fp64" else sic.SIC_FP32_MIXED
+    fb = _run(env, hp, prec)
+    sels = fb.sel_lists()
+    okp = _okernel(oracle, kp)
+    P = hp.pts
+    stats = ReplayStats()
+    band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    ab = 0.0 if prec_name == "fp64" else FP32_ABS * kp.variance
+    for i in range(hp.n):
+        cand = hp.cand_idx[hp.cand_ptr[i]:hp.cand_ptr[i + 1]]
+        replay_single(oracle, okp, P, i, cand, hp.k, sels[i], band, stats, abs_band=ab)
+    print(prec_name, stats)
+    cp, ri, val, logv = fb.csc()
+    worst = _check_fill_columns(oracle, okp, P, range(hp.n), sels, cp, ri, val, logv)
+    _, _, _, ologv = oracle.factor_columns(okp, P, sels)
+    s = float(fb.sum_logv.cpu()[0])
+    assert s == pytest.approx(float(np.sum(ologv)), rel=1e-9)
+    ld = oracle.logdet_theta(okp, P)
+    kl = oracle.kl_from_logv(s, ld)
+    print(f"{prec_name}: worst fill err {worst:.2e}, KL = {kl:.6g}")
+    assert kl >= 0
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_columns_batched_full_size_sampled(env, oracle_lib, prec_name):
+    """Config-2 workload at full size (N=65536, 3-D, Matern 5/2, ell=0.05, nugget 1e-6,
+    C=512, k=32) in the launch configuration the benchmark uses; sampled columns
+    (random ones plus the ragged tail) are checked, with the oracle computing their
+    candidate lists itself; the ordering is checked by the maximin property."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    cfg = synthetic.PRESETS["cfg2_single_batched"]
+    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"])
+    pts = synthetic.points(cfg["n"], cfg["dim"], cfg["seed"])
+    hp = pipeline.prepare_columns(pts, kp, cfg["n_cand"], cfg["k"])
+    prec = sic.SIC_FP64 if prec_name == "fp64" else sic.SIC_FP32_MIXED
+    fb = _run(env, hp, prec)
+    sels = fb.sel_lists()
+    okp = _okernel(oracle, kp)
+    P = hp.pts
+    n = hp.n
+    rng = np.random.default_rng(7)
+    cols = sorted(set(rng.choice(n - 600, 40, replace=False).tolist()) |
+                  {n - 513, n - 512, n - 300, n - 33, n - 32, n - 2, n - 1})
+    _check_ordering_sampled(oracle, pts, hp, rng)
+    stats = ReplayStats()
+    band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    ab = 0.0 if prec_name == "fp64" else FP32_ABS * kp.variance
+    for i in cols:
+        cand = oracle.knn_later(P, [i], i + 1, cfg["n_cand"])
+        assert cand.tolist() == hp.cand_idx[hp.cand_ptr[i]:hp.cand_ptr[i + 1]].tolist()
+        replay_single(oracle, okp, P, i, cand, hp.k, sels[i], band, stats, abs_band=ab)
+    print(prec_name, stats)
+    cp, ri, val, logv = fb.csc()
+    _check_fill_columns(oracle, okp, P, cols, sels, cp, ri, val, logv)
+    assert np.all(np.isfinite(logv))
+
+
+def _check_ordering_sampled(oracle, pts, hp, rng, n_pos=24, n_earlier=64):
+    """Reverse-maximin at any size: ell2[p] is the squared distance to the later set and no
+    sampled earlier point is farther from that set."""
+    P = hp.pts if hp.grp_ptr is None else pts[hp.order]
+    n = P.shape[0]
+    assert sorted(hp.order.tolist()) == list(range(n)) if n <= 70000 else True
+    assert hp.order[-1] == 0 or hp.grp_ptr is not None
+    if hp.grp_ptr is not None:
+        return
+    for p in rng.choice(n - 1, n_pos, replace=False):
+        later = P[p + 1:]
+        d = np.min(np.sum((later - P[p]) ** 2, axis=1))
+        assert d == hp.ell2[p]
+        for j in rng.choice(p + 1, min(n_earlier, p + 1), replace=False):
+            assert np.min(np.sum((later - P[j]) ** 2, axis=1)) <= hp.ell2[p]
+
+
+# ----------------------------------------------------------- supernodes --
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_aggregated_small_full(env, oracle_lib, prec_name):
+    """Supernodes on a small problem (N=4096, 2-D, Matern 3/2, ell=0.05, nugget 1e-6,
+    C=192, k=24, m in [4, 32]); every group compared."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    kp = sic.kernel(2, 3, 0.05, 1.0, 1e-6)
+    pts = synthetic.points(4096, 2, 11)
+    hp = pipeline.prepare_groups(pts, kp, 192, 24, mmin=4, mmax=32)
+    prec = sic.SIC_FP64 if prec_name == "fp64" else sic.SIC_FP32_MIXED
+    fb = _run(env, hp, prec)
+    sels = fb.sel_lists()
+    okp = _okernel(oracle, kp)
+    P = hp.pts
+    stats = ReplayStats()
+    band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    gp = hp.grp_ptr
+    for g in range(len(gp) - 1):
+        g0, g1 = int(gp[g]), int(gp[g + 1])
+        cand = hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]]
+        replay_multi(oracle, okp, P, g0, g1 - g0, cand, hp.k, sels[g], band, stats)
+    print(prec_name, stats)
+    cp, ri, val, logv = fb.csc()
+    worst = 0.0
+    for g in range(len(gp) - 1):
+        g0, g1 = int(gp[g]), int(gp[g + 1])
+        for a in range(g1 - g0):
+            rows, L, lv = oracle.fill_member(okp, P, g0, g1 - g0, a, sels[g])
+            c = g0 + a
+            assert ri[cp[c]:cp[c + 1]].tolist() == rows.tolist()
+            e = column_errors(val[cp[c]:cp[c + 1]], L)
+            worst = max(worst, e)
+            assert e <= L_TOL, f"member {a} of group {g}: {e}"
+            assert abs(logv[c] - lv) <= LOGV_TOL
+    ld = oracle.logdet_theta(okp, P)
+    print(f"{prec_name}: worst fill err {worst:.2e}; KL {oracle.kl_from_logv(float(fb.sum_logv.cpu()[0]), ld):.6g}")
+
+
+@pytest.mark.parametrize("prec_name", ["fp32", "fp64"])
+def test_aggregated_full_size_sampled(env, oracle_lib, prec_name):
+    """Config-3 workload at full size (N=2^20, 2-D, Matern 3/2, ell=0.02, nugget 1e-6,
+    C=1024, k=64, supernodes m in [8, 64]) in the benchmark's launch configuration;
+    sampled groups are checked against the oracle, which computes their candidate
+    lists itself."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    cfg = synthetic.PRESETS["cfg3_aggregated"]
+    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"])
+    hp = _cfg3_problem(env)
+    prec = sic.SIC_FP64 if prec_name == "fp64" else sic.SIC_FP32_MIXED
+    fb = _run(env, hp, prec)
+    sels = fb.sel_lists()
+    okp = _okernel(oracle, kp)
+    P = hp.pts
+    gp = hp.grp_ptr
+    G = len(gp) - 1
+    rng = np.random.default_rng(3)
+    groups = sorted(set(rng.choice(G - 50, 10, replace=False).tolist()) | {G - 40, G - 3, G - 1})
+    stats = ReplayStats()
+    band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    cp, ri, val, logv = fb.csc()
+    for g in groups:
+        g0, g1 = int(gp[g]), int(gp[g + 1])
+        cand = oracle.knn_later(P, np.arange(g0, g1), g1, cfg["n_cand"])
+        assert cand.tolist() == hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]].tolist()
+        replay_multi(oracle, okp, P, g0, g1 - g0, cand, hp.k, sels[g], band, stats)
+        for a in range(g1 - g0):
+            rows, L, lv = oracle.fill_member(okp, P, g0, g1 - g0, a, sels[g])
+            c = g0 + a
+            assert ri[cp[c]:cp[c + 1]].tolist() == rows.tolist()
+            assert column_errors(val[cp[c]:cp[c + 1]], L) <= L_TOL
+            assert abs(logv[c] - lv) <= LOGV_TOL
+    print(prec_name, stats, "sum logv", float(fb.sum_logv.cpu()[0]))
+    assert np.all(np.isfinite(logv))
+
+
+_CFG3 = {}
+
+
+def _cfg3_problem(env):
+    torch, sic, pipeline, h = env
+    if "hp" not in _CFG3:
+        cfg = synthetic.PRESETS["cfg3_aggregated"]
+        kp = sic.kernel(cfg["dim"], cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"])
+        pts = synthetic.points(cfg["n"], cfg["dim"], cfg["seed"])
+        _CFG3["hp"] = pipeline.prepare_groups(pts, kp, cfg["n_cand"], cfg["k"], cfg["m_min"], cfg["m_max"])
+    return _CFG3["hp"]
+
+
+# -------------------------------------------------------- other entries --
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_select_single_directed(env, oracle_lib, prec_name):
+    """Directed GP selection over 5000 training points for one target (Section 3)."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    kp = sic.kernel(2, 5, 0.2, 1.0, 1e-6)
+    xtr = synthetic.points(5000, 2, 21)
+    xt = np.array([0.43, 0.61])
+    prec = sic.SIC_FP64 if prec_name == "fp64" else sic.SIC_FP32_MIXED
+    k = 24
+    ws = sic._ws(sic.select_single_workspace(5000, k, prec), "cuda")
+    oi = torch.empty(k, dtype=torch.int32, device="cuda")
+    ov = torch.empty(k + 1, dtype=torch.float64, device="cuda")
+    oc = torch.empty(1, dtype=torch.int32, device="cuda")
+    sic.select_single(h, torch.from_numpy(xtr).cuda(), torch.from_numpy(xt).cuda(), kp, k, prec, oi, ov, oc, ws)
+    h.sync()
+    cnt = int(oc.cpu()[0])
+    sel = oi.cpu().numpy()[:cnt]
+    okp = _okernel(oracle, kp)
+    P = np.vstack([xt[None, :], xtr])  # row 0 = target, rows 1.. = training points
+    cand = np.arange(1, 5001, dtype=np.int32)
+    stats = ReplayStats()
+    replay_single(oracle, okp, P, 0, cand, k, sel + 1, TIE_BAND if prec_name == "fp64" else FP32_BAND, stats,
+                  abs_band=0.0 if prec_name == "fp64" else FP32_ABS * kp.variance)
+    if prec_name == "fp64":
+        r = oracle.select_single(okp, P, 0, cand, k, forced=(sel).tolist())
+        assert np.allclose(ov.cpu().numpy()[:cnt + 1], r["vtar"], rtol=1e-8)
+    print(prec_name, stats)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 8])
+def test_apply_factor(env, oracle_lib, nrhs):
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    kp = sic.kernel(2, 3, 0.1, 1.0, 1e-6)
+    pts = synthetic.points(3000, 2, 5)
+    hp = pipeline.prepare_columns(pts, kp, 64, 12)
+    fb = _run(env, hp, sic.SIC_FP64)
+    cp, ri, val, _ = fb.csc()
+    x = synthetic.normal(9, hp.n * nrhs).reshape(hp.n, nrhs)
+    xd = torch.from_numpy(x).cuda()
+    for op in [sic.SIC_OP_L, sic.SIC_OP_LT, sic.SIC_OP_LLT]:
+        y = torch.empty_like(xd)
+        ws = sic._ws(sic.apply_factor_workspace(hp.n, nrhs, op), "cuda")
+        nnz = int(cp[-1])
+        sic.apply_factor(h, fb.col_ptr, fb.row_idx[:nnz].contiguous(), fb.val[:nnz].contiguous(), op, xd, y, ws)
+        h.sync()
+        ref = oracle.apply_factor(hp.n, cp, ri, val, op, x)
+        assert np.allclose(y.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_edge_cases_and_determinism(env, oracle_lib):
+    """Tiny problems (n = 1, 2, 3: empty and single candidate lists), k larger than the
+    candidate count, and bit-identical repeated FP64 runs."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    kp = sic.kernel(2, 3, 0.3, 1.0, 1e-6)
+    okp = _okernel(oracle, kp)
+    for n in [1, 2, 3, 40]:
+        pts = synthetic.points(n, 2, 4)
+        hp = pipeline.prepare_columns(pts, kp, 8, 16)
+        fb = _run(env, hp, sic.SIC_FP64)
+        sels = fb.sel_lists()
+        for i in range(n):
+            cand = hp.cand_idx[hp.cand_ptr[i]:hp.cand_ptr[i + 1]]
+            r = oracle.select_single(okp, hp.pts, i, cand, 16)
+            assert sels[i].tolist() == r["sel"].tolist()
+        cp, ri, val, logv = fb.csc()
+        _, _, oval, ologv = oracle.factor_columns(okp, hp.pts, sels)
+        assert np.allclose(val, oval, rtol=1e-9, atol=1e-9 * np.abs(oval).max())
+    pts = synthetic.points(2048, 2, 6)
+    hp = pipeline.prepare_columns(pts, kp, 100, 20)
+    a = _run(env, hp, sic.SIC_FP64)
+    b = _run(env, hp, sic.SIC_FP64)
+    nnz = int(a.col_ptr[-1].item())
+    assert torch.equal(a.sel_idx, b.sel_idx) and torch.equal(a.col_ptr, b.col_ptr)
+    assert torch.equal(a.val[:nnz], b.val[:nnz]) and torch.equal(a.row_idx[:nnz], b.row_idx[:nnz])
+    assert float(a.sum_logv.cpu()[0]) == float(b.sum_logv.cpu()[0])
+
+
+def test_errors_reported_by_sync(env):
+    """Kernel-detected errors come back through sic_sync: a candidate list longer than the
+    stated bound (invalid) and a singular pattern (duplicate points, no nugget)."""
+    torch, sic, pipeline, h = env
+    kp = sic.kernel(2, 3, 0.3, 1.0, 1e-6)
+    pts = synthetic.points(300, 2, 8)
+    hp = pipeline.prepare_columns(pts, kp, 32, 8)
+    dp = pipeline.DeviceProblem(hp)
+    fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP64)
+    sic.select_columns(h, dp.pts, kp, dp.cand_ptr, dp.cand_idx, 16, 8, sic.SIC_FP64, fb.sel_idx, fb.sel_count)
+    with pytest.raises(sic.SicError) as e:
+        h.sync()
+    assert e.value.code == sic.SIC_ERR_INVALID and 0 <= e.value.unit < 300
+    h.sync()  # cleared
+    # duplicate points without a nugget: with k = 1 the pattern {i, duplicate} is
+    # exactly singular (Theta_{ss} = [[1, 1], [1, 1]])
+    kp0 = sic.kernel(2, 3, 0.3, 1.0, 0.0)
+    p2 = synthetic.points(64, 2, 9)
+    hp2 = pipeline.prepare_columns(p2, kp0, 16, 1)
+    P = hp2.pts.copy()
+    P[5] = P[hp2.cand_idx[hp2.cand_ptr[5]]]  # column 5's nearest candidate coincides with it
+    hp2.pts = P
+    dp2 = pipeline.DeviceProblem(hp2)
+    fb2 = pipeline.FactorBuilder(h, hp2, sic.SIC_FP64)
+    fb2.select(dp2)
+    h.sync()
+    sels = fb2.sel_lists()
+    assert sels[5][0] == hp2.cand_idx[hp2.cand_ptr[5]]
+    fb2.fill(dp2)
+    with pytest.raises(sic.SicError) as e:
+        h.sync()
+    assert e.value.code == sic.SIC_ERR_NOT_PD and e.value.unit == 5
