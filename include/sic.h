@@ -189,6 +189,24 @@ sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, 
  * divergence of the factor is (sum_logv - logdet Theta) / 2 (eq. obj_chol).
  * grp_ptr NULL means single columns (n_grp = n).  max_m bounds the group size (1
  * without groups, <= 64).  Needs sic_build_factor_workspace bytes of ws. */
+/* Allocation-free variant of sic_factor_nnz (the paper has no counterpart; it is a
+ * convenience of this library).  For callers that cannot allocate device memory --
+ * for example code running inside a host framework that has reserved the device's
+ * memory for its own allocator, or a latency-critical loop where cudaMalloc's implicit
+ * device synchronisation is not acceptable -- and so cannot provide the workspace of
+ * sic_factor_nnz.  Same arguments and result as sic_factor_nnz without the workspace.
+ * Its scratch is a fixed static device array inside libsic (512 KiB, held by every GPU
+ * that loads the library until the process exits), so n + 1 may not exceed
+ * 67,108,864 (= 2^26); larger n returns SIC_ERR_UNSUPPORTED.  The call allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and caches it; make
+ * that first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents (nothing in it needs to start at zero): calls that
+ * may overlap on the GPU -- on different streams without an ordering between them, or
+ * from several threads -- race on it and must be serialised by the caller. */
+sic_status sic_factor_nnz_noalloc(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, const int32_t* sel_count,
+                                  int64_t n, int64_t* col_ptr, void* stream);
+
 sic_status sic_build_factor_workspace(int64_t n, size_t* bytes);
 sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
                             const int64_t* grp_ptr, int64_t n_grp, int32_t max_m, const int32_t* sel_idx,

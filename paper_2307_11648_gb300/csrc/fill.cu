@@ -13,6 +13,8 @@
 //
 // Also here: the nnz count + exclusive scan that builds col_ptr, and the fixed-order
 // two-pass sum of logv (bit-reproducible).
+#include <mutex>
+
 #include "sic_internal.cuh"
 
 namespace {
@@ -333,6 +335,61 @@ extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t
     long long nb = (n + SUM_TILE - 1) / SUM_TILE;
     k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n, (double*)ws);
     k_sum_final<<<1, 256, 0, s>>>((const double*)ws, nb, sum_logv);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
+
+// ------------------------------------------------ allocation-free nnz scan --
+//
+// sic_factor_nnz_noalloc runs the same count + scan kernels as sic_factor_nnz, with
+// the per-tile totals kept in this file-scope device array instead of a caller
+// workspace.  Every GPU that loads libsic holds one copy until the process exits.
+namespace {
+
+constexpr long long NOALLOC_MAX_TILES = 65536;  // n + 1 <= 65536 * SCAN_TILE = 67,108,864 entries
+static __device__ __align__(256) long long g_nnz_scratch[NOALLOC_MAX_TILES + 1];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+long long* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_nnz_scratch on `device` (the current device).  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once per
+// device and cached.
+cudaError_t noalloc_scratch(int device, long long** out) {
+    if (device < 0 || device >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_nnz_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = (long long*)ptr;
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" sic_status sic_factor_nnz_noalloc(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp,
+                                             const int32_t* sel_count, int64_t n, int64_t* col_ptr, void* stream) {
+    if (!h || !sel_count || !col_ptr || n < 1 || n_grp < 1 || (!grp_ptr && n_grp != n)) return SIC_ERR_INVALID;
+    const long long len = n + 1;
+    const long long nb = (len + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb > NOALLOC_MAX_TILES) return SIC_ERR_UNSUPPORTED;  // beyond the static scratch
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    long long* partial = nullptr;
+    SIC_CUDA_TRY(noalloc_scratch(h->device, &partial));
+    cudaStream_t s = (cudaStream_t)stream;
+    long long* v = (long long*)col_ptr;
+    // the tile totals are written before they are read, so the scratch needs no clearing;
+    // only the output's last entry must start at zero (as in sic_factor_nnz)
+    SIC_CUDA_TRY(cudaMemsetAsync(v + n, 0, sizeof(long long), s));
+    k_nnz_count<<<(unsigned)((n_grp + 255) / 256), 256, 0, s>>>((const long long*)grp_ptr, n_grp, sel_count, n, v,
+                                                                  h->d_status);
+    k_scan_tile<<<(unsigned)nb, 256, 0, s>>>(v, len, partial);
+    k_scan_partials<<<1, 256, 0, s>>>(partial, nb, partial + nb);
+    k_scan_add<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(v, len, partial);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }

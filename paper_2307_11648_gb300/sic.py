@@ -26,7 +26,8 @@ EXPORTS = [
     "sic_prep_maximin", "sic_prep_candidates_columns", "sic_prep_groups", "sic_prep_candidates_groups",
     "sic_select_single_workspace", "sic_select_single", "sic_select_columns",
     "sic_select_aggregated_workspace", "sic_select_aggregated",
-    "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_build_factor_workspace", "sic_build_factor",
+    "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
+    "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
 ]
 
@@ -80,6 +81,7 @@ def lib():
                                            vp]),
             "sic_factor_nnz_workspace": (st, [i64, C.POINTER(sz)]),
             "sic_factor_nnz": (st, [vp, vp, i64, vp, i64, vp, vp, sz, vp]),
+            "sic_factor_nnz_noalloc": (st, [vp, vp, i64, vp, i64, vp, vp]),
             "sic_build_factor_workspace": (st, [i64, C.POINTER(sz)]),
             "sic_build_factor": (st, [vp, vp, i64, pk, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
             "sic_apply_factor_workspace": (st, [i64, i32, st, C.POINTER(sz)]),
@@ -287,6 +289,16 @@ def factor_nnz(h: Handle, grp_ptr, sel_count, n: int, col_ptr, ws, stream=None):
     _check(lib().sic_factor_nnz(h.ptr, _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp,
                                 _dptr(sel_count, torch.int32, "sel_count"), n, _dptr(col_ptr, torch.int64, "col_ptr"),
                                 _dptr(ws), ws.numel(), _stream(stream)), "sic_factor_nnz", h)
+
+
+def factor_nnz_noalloc(h: Handle, grp_ptr, sel_count, n: int, col_ptr, stream=None):
+    """sic_factor_nnz without a workspace (static scratch inside libsic; see include/sic.h)."""
+    import torch
+    n_grp = grp_ptr.numel() - 1 if grp_ptr is not None else n
+    _check(lib().sic_factor_nnz_noalloc(h.ptr, _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp,
+                                        _dptr(sel_count, torch.int32, "sel_count"), n,
+                                        _dptr(col_ptr, torch.int64, "col_ptr"), _stream(stream)),
+           "sic_factor_nnz_noalloc", h)
 
 
 def build_factor_workspace(n: int) -> int:
