@@ -1,15 +1,19 @@
 // Supernodal greedy selection (Section 5.2, multiple targets sharing one selection).
 //
-// One CTA (512 threads) owns one group at a time over a persistent grid.  The two
-// partial Cholesky factors of the paper's Cholesky approach (Appendix C.2) live in a
-// per-CTA slab of the caller's workspace, column-major with leading dimension
-// ld = max_cand + max_m so that thread r touches row r of every column (coalesced):
-//   F1 [k][ld]        columns of the picks, conditioned on earlier picks only;
-//   F2 [max_m+k][ld]  first the m target columns (left-looking Cholesky of the
-//                     targets), then the picks conditioned on targets and picks;
-//   X  [3][ld]        staged coordinates (FP32 mode: relative to the first member);
-//   V1, V2 [ld]       var_j = Theta_{jj|I} and var_j|P = Theta_{jj|I,P}.
-// Rows 0..C-1 are the candidates, rows C..C+m-1 the targets.
+// One CTA owns one group at a time over a persistent grid.  The two partial Cholesky
+// factors of the paper's Cholesky approach (Appendix C.2) live in shared memory when
+// they fit (e.g. 256 candidates in FP32) and otherwise in a per-CTA slab of the
+// caller's workspace.  Layout (elements of T), column-major so that thread r touches
+// row r of every column:
+//   F1  [k][Cm]       columns of the picks, conditioned on earlier picks only;
+//   F2c [mm+k][Cm]    candidate rows of F2: first the m target columns (left-looking
+//                     Cholesky of the targets), then the picks conditioned on targets
+//                     and earlier picks;
+//   F2t [mm][mm]      target rows of the m target columns (only they are non-zero);
+//   X   [3][Cm+mm]    staged coordinates, candidates then targets (FP32 mode: relative
+//                     to the first member, formed in FP64);
+//   V1, V2 [Cm]       var_j = Theta_{jj|I} and var_j|P = Theta_{jj|I,P}.
+// Cm = max_cand rounded up to 32, mm = max_m.
 // Per step the score is V1_j / V2_j (eq. greedy_mult: picking j changes
 // logdet Theta_{PP|I} by log V2_j - log V1_j); the argmax (ties: lowest candidate
 // index) is found by warp shuffles and one shared-memory pass; the pivot rows of F1
@@ -20,32 +24,54 @@
 
 namespace {
 
-constexpr int NT = 512;
-constexpr int NW = NT / 32;
-
 template <typename T>
 __device__ __forceinline__ bool better(T s, int i, T bs, int bi) {
     return s > bs || (s == bs && i < bi);
 }
 
-template <typename T>
+struct AggLayout {
+    long long Cm, mm, k;
+    __host__ __device__ long long f1() const { return 0; }
+    __host__ __device__ long long f2c() const { return k * Cm; }
+    __host__ __device__ long long f2t() const { return f2c() + (mm + k) * Cm; }
+    __host__ __device__ long long x() const { return f2t() + mm * mm; }
+    __host__ __device__ long long v1() const { return x() + 3 * (Cm + mm); }
+    __host__ __device__ long long v2() const { return v1() + Cm; }
+    __host__ __device__ long long size() const { return v2() + Cm; }
+};
+
+inline AggLayout agg_layout(int max_cand, int max_m, int k) {
+    AggLayout L;
+    L.Cm = ((long long)max_cand + 31) / 32 * 32;
+    if (L.Cm < 32) L.Cm = 32;
+    L.mm = max_m;
+    L.k = k;
+    return L;
+}
+
+template <typename T, int NT, bool SMEM>
 __global__ void __launch_bounds__(NT) k_select_agg(
     const double* __restrict__ pts, long long n, int dim, KP<T> kp, T floor_, const long long* __restrict__ grp_ptr,
     long long n_grp, const long long* __restrict__ cand_ptr, const int32_t* __restrict__ cand_idx, int max_cand,
     int max_m, int k, int32_t* __restrict__ sel_idx, int32_t* __restrict__ sel_count, T* __restrict__ ws,
-    long long ld, long long slab, DevStatus* st) {
-    extern __shared__ unsigned char smem_raw[];
-    T* p1 = reinterpret_cast<T*>(smem_raw);  // k
-    T* p2 = p1 + k;                          // max_m + k
+    AggLayout L, DevStatus* st) {
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    T* base = SMEM ? sm : ws + (long long)blockIdx.x * L.size();
+    T* p1 = SMEM ? sm + L.size() : sm;  // k
+    T* p2 = p1 + k;                      // max_m + k
     __shared__ T wsc[NW];
     __shared__ int wix[NW];
     __shared__ int s_fail;
 
-    T* F1 = ws + (long long)blockIdx.x * slab;
-    T* F2 = F1 + (long long)k * ld;
-    T* X = F2 + (long long)(max_m + k) * ld;
-    T* V1 = X + 3 * ld;
-    T* V2 = V1 + ld;
+    const long long Cm = L.Cm, mm = L.mm, ldx = L.Cm + L.mm;
+    T* F1 = base + L.f1();
+    T* F2c = base + L.f2c();
+    T* F2t = base + L.f2t();
+    T* X = base + L.x();
+    T* V1 = base + L.v1();
+    T* V2 = base + L.v2();
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T NEG = -INFINITY;
@@ -64,22 +90,23 @@ __global__ void __launch_bounds__(NT) k_select_agg(
             for (int q = tid; q < k; q += NT) sel_idx[g * k + q] = -1;
             continue;
         }
-        const int R = C + m;
         double org[3] = {0.0, 0.0, 0.0};
         if constexpr (sizeof(T) == 4)
             for (int d = 0; d < dim; ++d) org[d] = pts[g0 * dim + d];
-        for (int r = tid; r < R; r += NT) {
-            long long p = (r < C) ? (long long)cand_idx[b0 + r] : g0 + (r - C);
+        for (int i = tid; i < C + m; i += NT) {
+            const bool cnd = i < C;
+            long long p = cnd ? (long long)cand_idx[b0 + i] : g0 + (i - C);
+            const long long xi = cnd ? i : Cm + (i - C);
             bool ok = true;
-            if (r < C && (p < g0 + m || p >= n)) {  // candidates must lie after the group
+            if (cnd && (p < g0 + m || p >= n)) {  // candidates must lie after the group
                 record_error(st, SIC_ERR_INVALID, g);
                 p = g0;
                 ok = false;
             }
-            for (int d = 0; d < 3; ++d) X[d * ld + r] = (d < dim) ? (T)(pts[p * dim + d] - org[d]) : (T)0;
-            if (r < C) {
-                V1[r] = ok ? diag : NEG;
-                V2[r] = ok ? diag : NEG;
+            for (int d = 0; d < 3; ++d) X[d * ldx + xi] = (d < dim) ? (T)(pts[p * dim + d] - org[d]) : (T)0;
+            if (cnd) {
+                V1[i] = ok ? diag : NEG;
+                V2[i] = ok ? diag : NEG;
             }
         }
         if (tid == 0) s_fail = 0;
@@ -87,8 +114,7 @@ __global__ void __launch_bounds__(NT) k_select_agg(
 
         // ---- the target columns of F2 (left-looking Cholesky of the targets) ----
         for (int a = 0; a < m; ++a) {
-            const int pr = C + a;
-            if (tid < a) p2[tid] = F2[(long long)tid * ld + pr];
+            if (tid < a) p2[tid] = F2t[(long long)tid * mm + a];
             __syncthreads();
             T dv = diag;
             for (int b = 0; b < a; ++b) dv = fma(-p2[b], p2[b], dv);
@@ -99,30 +125,40 @@ __global__ void __launch_bounds__(NT) k_select_agg(
                 }
                 break;
             }
-            const T rs = (T)1 / sic_sqrt(dv);
-            const T ax = X[pr], ay = X[ld + pr], az = X[2 * ld + pr];
-            for (int r = tid; r < R; r += NT) {
-                T u;
-                if (r >= C && r < pr) {
-                    u = (T)0;
-                } else if (r == pr) {
-                    u = sic_sqrt(dv);
-                } else {
-                    T dx = X[r] - ax, dy = X[ld + r] - ay, dz = X[2 * ld + r] - az;
+            const T dsq = sic_sqrt(dv);
+            const T rs = (T)1 / dsq;
+            const long long xa = Cm + a;
+            const T ax = X[xa], ay = X[ldx + xa], az = X[2 * ldx + xa];
+            for (int i = tid; i < C + m; i += NT) {
+                if (i < C) {
+                    T dx = X[i] - ax, dy = X[ldx + i] - ay, dz = X[2 * ldx + i] - az;
                     T num = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
-                    for (int b = 0; b < a; ++b) num = fma(-F2[(long long)b * ld + r], p2[b], num);
-                    u = num * rs;
-                    if (r < C) V2[r] = fma(-u, u, V2[r]);
+                    for (int b = 0; b < a; ++b) num = fma(-F2c[(long long)b * Cm + i], p2[b], num);
+                    const T u = num * rs;
+                    F2c[(long long)a * Cm + i] = u;
+                    V2[i] = fma(-u, u, V2[i]);
+                } else {
+                    const int ta = i - C;
+                    T u;
+                    if (ta < a) {
+                        u = (T)0;
+                    } else if (ta == a) {
+                        u = dsq;
+                    } else {
+                        const long long xt = Cm + ta;
+                        T dx = X[xt] - ax, dy = X[ldx + xt] - ay, dz = X[2 * ldx + xt] - az;
+                        T num = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
+                        for (int b = 0; b < a; ++b) num = fma(-F2t[(long long)b * mm + ta], p2[b], num);
+                        u = num * rs;
+                    }
+                    F2t[(long long)a * mm + ta] = u;
                 }
-                F2[(long long)a * ld + r] = u;
             }
             __syncthreads();
         }
         __syncthreads();
         int t = 0;
-        if (s_fail) {
-            t = 0;
-        } else {
+        if (!s_fail) {
             for (; t < k; ++t) {
                 T bs = NEG;
                 int bi = 0x7fffffff;
@@ -151,23 +187,23 @@ __global__ void __launch_bounds__(NT) k_select_agg(
                     if (better(wsc[w], wix[w], gs, q)) { gs = wsc[w]; q = wix[w]; }
                 if (q == 0x7fffffff) break;
                 const T v1q = V1[q], v2q = V2[q];
-                const T qx = X[q], qy = X[ld + q], qz = X[2 * ld + q];
-                for (int tau = tid; tau < t; tau += NT) p1[tau] = F1[(long long)tau * ld + q];
-                for (int tau = tid; tau < m + t; tau += NT) p2[tau] = F2[(long long)tau * ld + q];
+                const T qx = X[q], qy = X[ldx + q], qz = X[2 * ldx + q];
+                for (int tau = tid; tau < t; tau += NT) p1[tau] = F1[(long long)tau * Cm + q];
+                for (int tau = tid; tau < m + t; tau += NT) p2[tau] = F2c[(long long)tau * Cm + q];
                 __syncthreads();
                 const T r1 = (T)1 / sic_sqrt(v1q);
                 const T r2 = (T)1 / sic_sqrt(v2q);
                 for (int r = tid; r < C; r += NT) {
                     if (V2[r] == NEG) continue;
-                    T dx = X[r] - qx, dy = X[ld + r] - qy, dz = X[2 * ld + r] - qz;
+                    T dx = X[r] - qx, dy = X[ldx + r] - qy, dz = X[2 * ldx + r] - qz;
                     T th = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
                     if (r == q) th += kp.nugget;
                     T n1 = th, n2 = th;
-                    for (int tau = 0; tau < t; ++tau) n1 = fma(-F1[(long long)tau * ld + r], p1[tau], n1);
-                    for (int tau = 0; tau < m + t; ++tau) n2 = fma(-F2[(long long)tau * ld + r], p2[tau], n2);
+                    for (int tau = 0; tau < t; ++tau) n1 = fma(-F1[(long long)tau * Cm + r], p1[tau], n1);
+                    for (int tau = 0; tau < m + t; ++tau) n2 = fma(-F2c[(long long)tau * Cm + r], p2[tau], n2);
                     const T u1 = n1 * r1, u2 = n2 * r2;
-                    F1[(long long)t * ld + r] = u1;
-                    F2[(long long)(m + t) * ld + r] = u2;
+                    F1[(long long)t * Cm + r] = u1;
+                    F2c[(long long)(m + t) * Cm + r] = u2;
                     if (r == q) {
                         V1[r] = NEG;
                         V2[r] = NEG;
@@ -185,21 +221,52 @@ __global__ void __launch_bounds__(NT) k_select_agg(
     }
 }
 
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
 template <typename T>
-long long slab_elems(int max_cand, int max_m, int k, long long* ld_out) {
-    long long ld = max_cand + max_m;
-    ld = (ld + 31) / 32 * 32;
-    if (ld_out) *ld_out = ld;
-    return ld * (long long)(k + max_m + k + 3 + 2);
+size_t agg_smem_bytes(const AggLayout& L, bool in_smem) {
+    size_t piv = sizeof(T) * (size_t)(L.k + L.mm + L.k);
+    return in_smem ? sizeof(T) * (size_t)L.size() + piv : piv;
+}
+
+// Plan of one launch: where the state lives, threads per CTA, grid, workspace.
+struct AggPlan {
+    AggLayout L;
+    bool smem;
+    int nt;
+    int grid;
+    size_t smem_bytes;
+    size_t ws_bytes;
+};
+
+template <typename T, int NT, bool SMEM>
+int agg_grid_for(sic_handle* h, size_t smem, long long n_grp) {
+    auto kern = k_select_agg<T, NT, SMEM>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int g = persistent_grid(h, kern, NT, smem, n_grp);
+    if (!SMEM) {
+        long long cap = 2LL * h->num_sms;  // bound the workspace (and keep the slabs L2-friendly)
+        if (g > cap) g = (int)cap;
+    }
+    return g;
 }
 
 template <typename T>
-int agg_grid(sic_handle* h, int k, int max_m, long long n_grp) {
-    size_t sm = sizeof(T) * (size_t)(k + max_m + k);
-    int g = persistent_grid(h, k_select_agg<T>, NT, sm, n_grp);
-    long long cap = 2LL * h->num_sms;
-    if (g > cap) g = (int)cap;
-    return g;
+AggPlan agg_plan(sic_handle* h, long long n_grp, int max_cand, int max_m, int k) {
+    AggPlan P;
+    P.L = agg_layout(max_cand, max_m, k);
+    P.smem = agg_smem_bytes<T>(P.L, true) <= SMEM_LIMIT;
+    P.nt = (max_cand <= 256) ? 256 : 512;
+    P.smem_bytes = agg_smem_bytes<T>(P.L, P.smem);
+    long long work = n_grp > 0 ? n_grp : 1;
+    if (P.nt == 256)
+        P.grid = P.smem ? agg_grid_for<T, 256, true>(h, P.smem_bytes, work)
+                        : agg_grid_for<T, 256, false>(h, P.smem_bytes, work);
+    else
+        P.grid = P.smem ? agg_grid_for<T, 512, true>(h, P.smem_bytes, work)
+                        : agg_grid_for<T, 512, false>(h, P.smem_bytes, work);
+    P.ws_bytes = P.smem ? 0 : sizeof(T) * (size_t)P.L.size() * (size_t)P.grid;
+    return P;
 }
 
 }  // namespace
@@ -210,31 +277,36 @@ extern "C" sic_status sic_select_aggregated_workspace(sic_handle* h, int64_t n_g
     if (!h || !bytes || n_grp < 0 || max_cand < 0 || max_m < 1 || k < 1) return SIC_ERR_INVALID;
     if (max_m > 64 || max_cand > 4096 || k > 128) return SIC_ERR_UNSUPPORTED;
     if (cudaSetDevice(h->device) != cudaSuccess) return SIC_ERR_CUDA;
-    if (prec == SIC_FP64) {
-        *bytes = sizeof(double) * (size_t)slab_elems<double>(max_cand, max_m, k, nullptr) *
-                 (size_t)agg_grid<double>(h, k, max_m, n_grp > 0 ? n_grp : 1);
-    } else if (prec == SIC_FP32_MIXED) {
-        *bytes = sizeof(float) * (size_t)slab_elems<float>(max_cand, max_m, k, nullptr) *
-                 (size_t)agg_grid<float>(h, k, max_m, n_grp > 0 ? n_grp : 1);
-    } else {
+    if (prec == SIC_FP64)
+        *bytes = agg_plan<double>(h, n_grp, max_cand, max_m, k).ws_bytes;
+    else if (prec == SIC_FP32_MIXED)
+        *bytes = agg_plan<float>(h, n_grp, max_cand, max_m, k).ws_bytes;
+    else
         return SIC_ERR_INVALID;
-    }
     return SIC_OK;
 }
 
 namespace {
 template <typename T>
-sic_status launch_agg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp, const int64_t* grp_ptr, int64_t n_grp,
-                      const int64_t* cand_ptr, const int32_t* cand_idx, int max_cand, int max_m, int k,
+sic_status launch_agg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp, const int64_t* grp_ptr,
+                      int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx, int max_cand, int max_m, int k,
                       int32_t* sel_idx, int32_t* sel_count, void* ws, size_t ws_bytes, cudaStream_t s) {
-    long long ld = 0;
-    long long slab = slab_elems<T>(max_cand, max_m, k, &ld);
-    int grid = agg_grid<T>(h, k, max_m, n_grp);
-    if (ws_bytes < sizeof(T) * (size_t)slab * (size_t)grid || !ws) return SIC_ERR_INVALID;
-    size_t sm = sizeof(T) * (size_t)(k + max_m + k);
-    k_select_agg<T><<<grid, NT, sm, s>>>(pts, n, kp->dim, make_kp<T>(*kp), (T)sic_floor_of(kp),
-                                         (const long long*)grp_ptr, n_grp, (const long long*)cand_ptr, cand_idx,
-                                         max_cand, max_m, k, sel_idx, sel_count, (T*)ws, ld, slab, h->d_status);
+    AggPlan P = agg_plan<T>(h, n_grp, max_cand, max_m, k);
+    if (P.ws_bytes > 0 && (!ws || ws_bytes < P.ws_bytes)) return SIC_ERR_INVALID;
+    KP<T> kpt = make_kp<T>(*kp);
+    T fl = (T)sic_floor_of(kp);
+    const long long* gp = (const long long*)grp_ptr;
+    const long long* cp = (const long long*)cand_ptr;
+#define SIC_AGG_LAUNCH(NTV, SM)                                                                                   \
+    k_select_agg<T, NTV, SM><<<P.grid, NTV, P.smem_bytes, s>>>(pts, n, kp->dim, kpt, fl, gp, n_grp, cp, cand_idx, \
+                                                               max_cand, max_m, k, sel_idx, sel_count, (T*)ws,    \
+                                                               P.L, h->d_status)
+    if (P.nt == 256) {
+        if (P.smem) SIC_AGG_LAUNCH(256, true); else SIC_AGG_LAUNCH(256, false);
+    } else {
+        if (P.smem) SIC_AGG_LAUNCH(512, true); else SIC_AGG_LAUNCH(512, false);
+    }
+#undef SIC_AGG_LAUNCH
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }
