@@ -224,6 +224,67 @@ sic_status sic_apply_factor(sic_handle* h, int64_t n, const int64_t* col_ptr, co
                             const double* val, sic_op op, const double* x, double* y, int32_t nrhs, void* ws,
                             size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------ learned proposal [device] -- */
+/*
+ * Not part of the paper: a small MLP ranks each supernode's candidates so that the
+ * exact greedy selection above runs only on the `top` best of them; the plain greedy
+ * stays the reference (and the source of the training labels).
+ *
+ * Features: 8 FP32 per candidate, row-major feat[(cand_ptr[g] + r) * 8 + f], for the
+ * group P = grp_ptr[g] .. grp_ptr[g+1]-1 (m <= 64 members) with ell = sqrt(ell2[g0])
+ * (1 if not finite or zero), a* the nearest member (lowest index on ties), K the
+ * kernel without nugget:  f0, f1 = (x_j - x_a*)[0], [1] / ell;  f2 = |x_j - x_a*| / ell;
+ * f3 = |x_j - centroid(P)| / ell;  f4 = r / C;  f5 = K(|x_j - x_a*|) / variance;
+ * f6 = m / 64;  f7 = mean over members of K(|x_j - x_a|) / variance.
+ *
+ * Network: s = w3 . gelu(W2^T gelu(W1^T f + b1) + b2) + b3 with exact (erf) GELU,
+ * 8 -> 128 -> 128 -> 1.  Parameters are one flat FP32 array of sic_mlp_param_count()
+ * = 17793 values: W1 [8][128] (row = input), b1 [128], W2 [128][128] (row = input),
+ * b2 [128], w3 [128], b3 [1].
+ */
+int32_t sic_mlp_param_count(void);
+
+/* feat must hold cand_ptr[n_grp] * 8 floats.  ell2[n] [device]: squared length scale
+ * of each position (as returned by sic_prep_maximin, in the same order as pts). */
+sic_status sic_proposal_features(sic_handle* h, const double* pts, int64_t n, const double* ell2,
+                                 const sic_kernel* kp, const int64_t* grp_ptr, int64_t n_grp,
+                                 const int64_t* cand_ptr, const int32_t* cand_idx, float* feat, void* stream);
+
+/* score[rows] = the network applied to feat[rows x 8] with BF16 weights and inputs and
+ * FP32 accumulation on the tensor cores (the hidden activations are rounded to BF16 as
+ * the second layer's input).  ws: sic_proposal_score_workspace bytes. */
+sic_status sic_proposal_score_workspace(size_t* bytes);
+sic_status sic_proposal_score(sic_handle* h, const float* params, const float* feat, int64_t rows, float* score,
+                              void* ws, size_t ws_bytes, void* stream);
+
+/* Keeps, per group, the min(top, C) candidates of highest score (ties: earlier in the
+ * list), in their original list order.  out_ptr[n_grp+1] receives the CSR offsets,
+ * out_idx must hold n_grp * top entries.  C <= 4096. */
+sic_status sic_proposal_topk(sic_handle* h, const int64_t* cand_ptr, const int32_t* cand_idx, const float* score,
+                             int64_t n_grp, int32_t top, int64_t* out_ptr, int32_t* out_idx, void* stream);
+
+/* label[cand_ptr[g] + r] = 1 if candidate r of group g is among the picks sel_idx[g*k ..
+ * g*k + sel_count[g]) of a selection (the training labels), else 0.  k <= 256. */
+sic_status sic_proposal_labels(sic_handle* h, const int64_t* cand_ptr, const int32_t* cand_idx, int64_t n_grp,
+                               const int32_t* sel_idx, const int32_t* sel_count, int32_t k, float* label,
+                               void* stream);
+
+/* Training (FP32): loss = mean over the batch of
+ * pos_weight * y * softplus(-s) + (1 - y) * softplus(s), and its gradient with respect
+ * to the flat parameters (grads, same layout).  With bf16 != 0 the forward pass uses
+ * BF16-rounded weights, inputs and first-layer activations, as inference does (the
+ * gradient passes straight through the rounding).  score[batch] (optional, may be NULL)
+ * receives the logits, *loss the mean loss [device].  ws: sic_mlp_train_workspace. */
+sic_status sic_mlp_train_workspace(int64_t batch, size_t* bytes);
+sic_status sic_mlp_grads(sic_handle* h, const float* params, const float* feat, const float* label, int64_t batch,
+                         float pos_weight, int32_t bf16, float* grads, float* loss, float* score, void* ws,
+                         size_t ws_bytes, void* stream);
+
+/* One AdamW step (decoupled weight decay, bias-corrected moments; step counts from 1)
+ * on n parameters: m, v are the moment buffers [device]. */
+sic_status sic_adamw_step(sic_handle* h, float* params, float* m, float* v, const float* grads, int32_t n,
+                          int32_t step, float lr, float beta1, float beta2, float eps, float wd, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

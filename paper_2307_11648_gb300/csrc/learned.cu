@@ -1,0 +1,672 @@
+// Learned candidate proposal for supernodal selection (not part of the paper: a
+// small MLP ranks each group's candidates so that the exact greedy selection of
+// Section 5.2 runs only on the best `top` of them).
+//
+//   k_features      8 features per (group, candidate), FP32
+//   k_pack_frags    BF16 weight fragments in mma.sync B-operand order
+//   k_mlp_infer     8 -> 128 -> 128 -> 1 with exact GELU; BF16 tensor-core MMAs
+//                   (mma.sync m16n8k16, FP32 accumulate), the first layer's
+//                   accumulators re-used as the second layer's A fragments in registers
+//   k_topk_*        per group: keep the `top` best-scored candidates, in list order
+//   training        FP32 forward/backward (strided tiled GEMM, split over K with a
+//                   fixed-order reduction), weighted BCE with logits, AdamW
+//
+// Feature definitions (ell = sqrt(ell2[g0]), or 1 if not finite / zero; a* the nearest
+// member, lowest index on ties; K the kernel without nugget):
+//   f0, f1 = (x_j - x_a*)[0], [1] / ell;  f2 = |x_j - x_a*| / ell;
+//   f3 = |x_j - centroid| / ell;  f4 = rank / C;  f5 = K(|x_j - x_a*|) / sigma^2;
+//   f6 = m / 64;  f7 = mean_a K(|x_j - x_a|) / sigma^2.
+#include <cuda_bf16.h>
+
+#include "sic_internal.cuh"
+
+namespace {
+
+constexpr int NF = 8;
+constexpr int HID = 128;
+constexpr int OFF_W1 = 0, OFF_B1 = NF * HID, OFF_W2 = OFF_B1 + HID, OFF_B2 = OFF_W2 + HID * HID,
+              OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID, NPARAM = OFF_B3 + 1;
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float dgelu_f(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// ------------------------------------------------------------------ features --
+
+__global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts, long long n, int dim,
+                                                  const double* __restrict__ ell2, KP<double> kp,
+                                                  const long long* __restrict__ grp_ptr, long long n_grp,
+                                                  const long long* __restrict__ cand_ptr,
+                                                  const int32_t* __restrict__ cand_idx, float* __restrict__ feat,
+                                                  DevStatus* st) {
+    __shared__ double mx[64 * 3];
+    __shared__ double cen[3];
+    for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
+        const long long g0 = grp_ptr[g];
+        const int m = (int)(grp_ptr[g + 1] - g0);
+        const long long b0 = cand_ptr[g];
+        const int C = (int)(cand_ptr[g + 1] - b0);
+        if (m < 1 || m > 64 || g0 < 0 || g0 + m > n || C < 0) {
+            if (threadIdx.x == 0) record_error(st, SIC_ERR_INVALID, g);
+            continue;
+        }
+        for (int i = threadIdx.x; i < m * 3; i += blockDim.x) {
+            int a = i / 3, d = i % 3;
+            mx[i] = (d < dim) ? pts[(g0 + a) * dim + d] : 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double s = 0.0;
+            for (int a = 0; a < m; ++a) s += mx[a * 3 + threadIdx.x];
+            cen[threadIdx.x] = s / m;
+        }
+        __syncthreads();
+        const double e2 = ell2[g0];
+        const double ell = (isfinite(e2) && e2 > 0.0) ? sqrt(e2) : 1.0;
+        const double ri = 1.0 / ell;
+        for (int r = threadIdx.x; r < C; r += blockDim.x) {
+            const long long p = cand_idx[b0 + r];
+            float* f = feat + (b0 + r) * NF;
+            if (p < 0 || p >= n) {
+                record_error(st, SIC_ERR_INVALID, g);
+                for (int q = 0; q < NF; ++q) f[q] = 0.f;
+                continue;
+            }
+            double x[3];
+            for (int d = 0; d < 3; ++d) x[d] = (d < dim) ? pts[p * dim + d] : 0.0;
+            double best = INFINITY, ksum = 0.0;
+            int ab = 0;
+            for (int a = 0; a < m; ++a) {
+                double dx = x[0] - mx[a * 3], dy = x[1] - mx[a * 3 + 1], dz = x[2] - mx[a * 3 + 2];
+                double d2 = dx * dx + dy * dy + dz * dz;
+                ksum += matern<double>(kp, sqrt(d2));
+                if (d2 < best) { best = d2; ab = a; }
+            }
+            const double dmin = sqrt(best);
+            double cx = x[0] - cen[0], cy = x[1] - cen[1], cz = x[2] - cen[2];
+            f[0] = (float)((x[0] - mx[ab * 3]) * ri);
+            f[1] = (float)((x[1] - mx[ab * 3 + 1]) * ri);
+            f[2] = (float)(dmin * ri);
+            f[3] = (float)(sqrt(cx * cx + cy * cy + cz * cz) * ri);
+            f[4] = (float)((double)r / (double)C);
+            f[5] = (float)(matern<double>(kp, dmin) / kp.s2);
+            f[6] = (float)((double)m / 64.0);
+            f[7] = (float)(ksum / ((double)m * kp.s2));
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ tensor-core inference --
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t a0, const uint32_t a1, const uint32_t a2,
+                                         const uint32_t a3, const uint32_t b0, const uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// B fragments of a K x 128 row-major FP32 matrix W (K a multiple of 16 after zero
+// padding of rows >= kval): frag[(kk * 16 + nt) * 32 + lane] = {b0, b1} with
+// b0 = (W[16kk + 2t][8nt + g], W[16kk + 2t + 1][8nt + g]),
+// b1 = (W[16kk + 8 + 2t][8nt + g], W[16kk + 9 + 2t][8nt + g]), g = lane / 4, t = lane % 4.
+__global__ void k_pack_frags(const float* __restrict__ W, int kval, int ktiles, uint2* __restrict__ frag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ktiles * 16 * 32) return;
+    int lane = i & 31, nt = (i >> 5) & 15, kk = i >> 9;
+    int g = lane >> 2, t = lane & 3, col = 8 * nt + g;
+    auto w = [&](int k) { return (k < kval) ? W[k * HID + col] : 0.0f; };
+    int k0 = 16 * kk + 2 * t;
+    frag[i] = make_uint2(pack_bf16(w(k0), w(k0 + 1)), pack_bf16(w(k0 + 8), w(k0 + 9)));
+}
+
+__global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ X, long long rows,
+                                                   const uint2* __restrict__ W1f, const uint2* __restrict__ W2f,
+                                                   const float* __restrict__ params, float* __restrict__ out) {
+    __shared__ uint2 sW2[8 * 16 * 32];
+    __shared__ uint2 sW1[16 * 32];
+    __shared__ float sb1[HID], sb2[HID], sw3[HID];
+    for (int i = threadIdx.x; i < 8 * 16 * 32; i += blockDim.x) sW2[i] = W2f[i];
+    for (int i = threadIdx.x; i < 16 * 32; i += blockDim.x) sW1[i] = W1f[i];
+    for (int i = threadIdx.x; i < HID; i += blockDim.x) {
+        sb1[i] = params[OFF_B1 + i];
+        sb2[i] = params[OFF_B2 + i];
+        sw3[i] = params[OFF_W3 + i];
+    }
+    const float b3 = params[OFF_B3];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const long long ntiles = (rows + 15) / 16;
+    for (long long tile = (long long)blockIdx.x * 4 + warp; tile < ntiles; tile += (long long)gridDim.x * 4) {
+        const long long r0 = tile * 16 + g, r1 = r0 + 8;
+        float x00 = 0.f, x01 = 0.f, x10 = 0.f, x11 = 0.f;
+        if (r0 < rows) {
+            x00 = X[r0 * NF + 2 * t];
+            x01 = X[r0 * NF + 2 * t + 1];
+        }
+        if (r1 < rows) {
+            x10 = X[r1 * NF + 2 * t];
+            x11 = X[r1 * NF + 2 * t + 1];
+        }
+        const uint32_t a0 = pack_bf16(x00, x01), a1 = pack_bf16(x10, x11);
+        // layer 1 -> GELU -> bf16 A fragments of layer 2
+        uint32_t A2[8][4];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            float h[2][4];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int nt = 2 * kk + half;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                const uint2 b = sW1[nt * 32 + lane];
+                mma16816(acc, a0, a1, 0u, 0u, b.x, b.y);
+                const int c0 = nt * 8 + 2 * t;
+                h[half][0] = gelu_f(acc[0] + sb1[c0]);
+                h[half][1] = gelu_f(acc[1] + sb1[c0 + 1]);
+                h[half][2] = gelu_f(acc[2] + sb1[c0]);
+                h[half][3] = gelu_f(acc[3] + sb1[c0 + 1]);
+            }
+            A2[kk][0] = pack_bf16(h[0][0], h[0][1]);
+            A2[kk][1] = pack_bf16(h[0][2], h[0][3]);
+            A2[kk][2] = pack_bf16(h[1][0], h[1][1]);
+            A2[kk][3] = pack_bf16(h[1][2], h[1][3]);
+        }
+        // layer 2 + GELU + head, one n-tile at a time
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
+        for (int nt = 0; nt < 16; ++nt) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const uint2 b = sW2[(kk * 16 + nt) * 32 + lane];
+                mma16816(acc, A2[kk][0], A2[kk][1], A2[kk][2], A2[kk][3], b.x, b.y);
+            }
+            const int c0 = nt * 8 + 2 * t;
+            s0 += gelu_f(acc[0] + sb2[c0]) * sw3[c0] + gelu_f(acc[1] + sb2[c0 + 1]) * sw3[c0 + 1];
+            s1 += gelu_f(acc[2] + sb2[c0]) * sw3[c0] + gelu_f(acc[3] + sb2[c0 + 1]) * sw3[c0 + 1];
+        }
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+        if (t == 0) {
+            if (r0 < rows) out[r0] = s0 + b3;
+            if (r1 < rows) out[r1] = s1 + b3;
+        }
+    }
+}
+
+// -------------------------------------------------------------------- top-k --
+
+__global__ void k_topk_counts(const long long* __restrict__ cand_ptr, long long n_grp, int top,
+                              long long* __restrict__ out_ptr) {
+    long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= n_grp) return;
+    long long c = cand_ptr[g + 1] - cand_ptr[g];
+    out_ptr[g] = c < top ? c : top;
+}
+
+// single-CTA exclusive scan of out_ptr[0..n) in place; out_ptr[n] receives the total
+__global__ void __launch_bounds__(1024) k_scan_one_block(long long* __restrict__ v, long long n) {
+    __shared__ long long s[1024];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long c0 = 0; c0 < n; c0 += 1024) {
+        long long i = c0 + threadIdx.x;
+        long long x0 = (i < n) ? v[i] : 0;
+        s[threadIdx.x] = x0;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            long long x = (threadIdx.x >= off) ? s[threadIdx.x - off] : 0;
+            __syncthreads();
+            s[threadIdx.x] += x;
+            __syncthreads();
+        }
+        if (i < n) v[i] = carry + s[threadIdx.x] - x0;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += s[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) v[n] = carry;
+}
+
+// Order key: larger score first, then lower list index.  Scores are finite floats
+// (NaN is treated as -inf).
+__device__ __forceinline__ unsigned long long topk_key(float s, int r) {
+    if (!(s == s)) s = -INFINITY;
+    unsigned int u = __float_as_uint(s);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);  // monotone in s
+    return ((unsigned long long)u << 32) | (unsigned int)(0x7fffffff - r);
+}
+
+__global__ void __launch_bounds__(512) k_topk_compact(const long long* __restrict__ cand_ptr,
+                                                      const int32_t* __restrict__ cand_idx,
+                                                      const float* __restrict__ score, long long n_grp, int top,
+                                                      const long long* __restrict__ out_ptr,
+                                                      int32_t* __restrict__ out_idx, DevStatus* st) {
+    __shared__ unsigned long long key[4096];
+    __shared__ unsigned long long thr;
+    __shared__ int warp_cnt[16];
+    for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
+        const long long b0 = cand_ptr[g];
+        const int C = (int)(cand_ptr[g + 1] - b0);
+        const long long o0 = out_ptr[g];
+        if (C <= top) {
+            for (int r = threadIdx.x; r < C; r += blockDim.x) out_idx[o0 + r] = cand_idx[b0 + r];
+            continue;
+        }
+        if (C > 4096) {
+            if (threadIdx.x == 0) record_error(st, SIC_ERR_UNSUPPORTED, g);
+            continue;
+        }
+        int P = 1;
+        while (P < C) P <<= 1;
+        for (int r = threadIdx.x; r < P; r += blockDim.x) key[r] = (r < C) ? topk_key(score[b0 + r], r) : 0ull;
+        __syncthreads();
+        // bitonic sort, descending
+        for (int size = 2; size <= P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                    int lo = 2 * i - (i & (stride - 1));
+                    int hi = lo + stride;
+                    bool desc = ((lo & size) == 0);
+                    unsigned long long a = key[lo], b = key[hi];
+                    if ((a < b) == desc) {
+                        key[lo] = b;
+                        key[hi] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) thr = key[top - 1];
+        __syncthreads();
+        const unsigned long long th = thr;
+        // compaction in list order: chunks of 512 with a block prefix count
+        int base = 0;
+        for (int c0 = 0; c0 < C; c0 += blockDim.x) {
+            const int r = c0 + threadIdx.x;
+            const bool keep = r < C && topk_key(score[b0 + r], r) >= th;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (lane == 0) warp_cnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                if (w < warp) before += warp_cnt[w];
+                total += warp_cnt[w];
+            }
+            if (keep) out_idx[o0 + base + before + __popc(bal & ((1u << lane) - 1u))] = cand_idx[b0 + r];
+            base += total;
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+}
+
+// label[b0 + r] = 1 if candidate r of group g is among the group's picks
+__global__ void __launch_bounds__(256) k_labels(const long long* __restrict__ cand_ptr,
+                                                const int32_t* __restrict__ cand_idx,
+                                                const int32_t* __restrict__ sel_idx,
+                                                const int32_t* __restrict__ sel_count, int k, long long n_grp,
+                                                float* __restrict__ label) {
+    __shared__ int sel[256];
+    for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
+        const int cnt = min(sel_count[g], min(k, 256));
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) sel[i] = sel_idx[g * k + i];
+        __syncthreads();
+        const long long b0 = cand_ptr[g];
+        const int C = (int)(cand_ptr[g + 1] - b0);
+        for (int r = threadIdx.x; r < C; r += blockDim.x) {
+            const int p = cand_idx[b0 + r];
+            float y = 0.f;
+            for (int i = 0; i < cnt; ++i) y = (sel[i] == p) ? 1.f : y;
+            label[b0 + r] = y;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- training --
+
+// C[z] = A * B over the K-range of split z (C has M x N, row-major; z-th partial at
+// C + z * M * N).  A(m, k) = A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn].
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kchunk, const float* __restrict__ A,
+                                              long long sam, long long sak, const float* __restrict__ B,
+                                              long long sbk, long long sbn, float* __restrict__ C) {
+    __shared__ float As[16][64 + 1];
+    __shared__ float Bs[16][64 + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    float acc[4][4] = {};
+    for (int k0 = kb; k0 < ke; k0 += 16) {
+        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+            int kk = i / 64, mm = i % 64;
+            int k = k0 + kk;
+            As[kk][mm] = (k < ke && m0 + mm < M) ? A[(long long)(m0 + mm) * sam + (long long)k * sak] : 0.f;
+            Bs[kk][mm] = (k < ke && n0 + mm < N) ? B[(long long)k * sbk + (long long)(n0 + mm) * sbn] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][ty * 4 + i];
+                b[i] = Bs[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float* Cz = C + (long long)blockIdx.z * M * N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+            if (m < M && n < N) Cz[(long long)m * N + n] = acc[i][j];
+        }
+}
+
+// out[i] = sum_z part[z * len + i] (fixed order)
+__global__ void k_sum_splits(const float* __restrict__ part, int nz, long long len, float* __restrict__ out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    float s = 0.f;
+    for (int z = 0; z < nz; ++z) s += part[(long long)z * len + i];
+    out[i] = s;
+}
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// W_used = round_bf16(master) (or a copy when bf16 is off)
+__global__ void k_round_params(const float* __restrict__ p, float* __restrict__ q, int n, int bf16) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) q[i] = bf16 ? bf16_round(p[i]) : p[i];
+}
+
+__global__ void k_round_rows(const float* __restrict__ x, float* __restrict__ y, long long n, int bf16) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = bf16 ? bf16_round(x[i]) : x[i];
+}
+
+// Z += bias (row-broadcast); H = gelu(Z) (H optionally rounded to bf16)
+__global__ void k_bias_gelu(float* __restrict__ Z, float* __restrict__ H, const float* __restrict__ bias,
+                            long long rows, int bf16) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= rows * HID) return;
+    float z = Z[i] + bias[i % HID];
+    Z[i] = z;
+    float h = gelu_f(z);
+    H[i] = bf16 ? bf16_round(h) : h;
+}
+
+// s = H2 w3 + b3; per-row loss and dS = (pw y (sigma - 1) + (1 - y) sigma) / B
+__global__ void __launch_bounds__(128) k_head(const float* __restrict__ H2, const float* __restrict__ w3,
+                                              const float* __restrict__ b3, const float* __restrict__ y,
+                                              long long rows, float pw, float* __restrict__ s_out,
+                                              float* __restrict__ dS, float* __restrict__ lrow) {
+    long long r = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float acc = 0.f;
+    for (int j = lane; j < HID; j += 32) acc = fmaf(H2[r * HID + j], w3[j], acc);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+        float s = acc + b3[0];
+        float yy = y[r];
+        float sig = 1.f / (1.f + expf(-s));
+        // softplus(x) = max(x, 0) + log1p(exp(-|x|))
+        float spn = fmaxf(-s, 0.f) + log1pf(expf(-fabsf(s)));
+        float spp = fmaxf(s, 0.f) + log1pf(expf(-fabsf(s)));
+        lrow[r] = pw * yy * spn + (1.f - yy) * spp;
+        dS[r] = (pw * yy * (sig - 1.f) + (1.f - yy) * sig) / (float)rows;
+        if (s_out) s_out[r] = s;
+    }
+}
+
+// dZ2 = (dS w3^T) .* gelu'(Z2)
+__global__ void k_dz2(const float* __restrict__ dS, const float* __restrict__ w3, const float* __restrict__ Z2,
+                      float* __restrict__ dZ, long long rows) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= rows * HID) return;
+    dZ[i] = dS[i / HID] * w3[i % HID] * dgelu_f(Z2[i]);
+}
+
+__global__ void k_mul_dgelu(float* __restrict__ dH, const float* __restrict__ Z, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dH[i] *= dgelu_f(Z[i]);
+}
+
+// column sums of a rows x cols matrix in fixed order: one thread per column
+__global__ void k_colsum(const float* __restrict__ M, long long rows, int cols, float* __restrict__ out) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (long long r = 0; r < rows; ++r) s += M[r * cols + c];
+    out[c] = s;
+}
+
+__global__ void __launch_bounds__(256) k_sum_loss(const float* __restrict__ l, long long n, float* __restrict__ out) {
+    __shared__ float s[256];
+    float a = 0.f;
+    for (long long i = threadIdx.x; i < n; i += 256) a += l[i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) s[threadIdx.x] += s[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0] / (float)n;
+}
+
+__global__ void k_adamw(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                        const float* __restrict__ g, int n, float lr, float b1, float b2, float eps, float wd,
+                        float c1, float c2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.f - b1) * gi;
+    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    float mh = mi / c1, vh = vi / c2;
+    p[i] = p[i] - lr * (mh / (sqrtf(vh) + eps) + wd * p[i]);
+}
+
+// scratch layout of one training step on B rows (floats)
+struct TrainWs {
+    long long B;
+    int nz;  // K-splits of the weight-gradient GEMMs
+    long long q() const { return 0; }                        // rounded params, NPARAM
+    long long xr() const { return NPARAM + 15; }             // rounded features B x 8
+    long long z1() const { return xr() + B * NF; }           // B x 128
+    long long h1() const { return z1() + B * HID; }
+    long long z2() const { return h1() + B * HID; }
+    long long h2() const { return z2() + B * HID; }
+    long long ds() const { return h2() + B * HID; }          // B
+    long long lrow() const { return ds() + B; }              // B
+    long long part() const { return lrow() + B; }            // nz x 128 x 128
+    long long size() const { return part() + (long long)nz * HID * HID; }
+};
+
+TrainWs train_ws(long long B) {
+    TrainWs w;
+    w.B = B;
+    w.nz = (int)((B + 4095) / 4096);
+    if (w.nz > 64) w.nz = 64;
+    return w;
+}
+
+void gemm(cudaStream_t s, int M, int N, int K, const float* A, long long sam, long long sak, const float* B,
+          long long sbk, long long sbn, float* C, int nz, float* part) {
+    int kchunk = (K + nz - 1) / nz;
+    kchunk = (kchunk + 15) / 16 * 16;
+    dim3 grid((N + 63) / 64, (M + 63) / 64, nz);
+    if (nz == 1) {
+        k_gemm<<<grid, 256, 0, s>>>(M, N, K, kchunk, A, sam, sak, B, sbk, sbn, C);
+    } else {
+        k_gemm<<<grid, 256, 0, s>>>(M, N, K, kchunk, A, sam, sak, B, sbk, sbn, part);
+        long long len = (long long)M * N;
+        k_sum_splits<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(part, nz, len, C);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- entry points --
+
+extern "C" sic_status sic_proposal_features(sic_handle* h, const double* pts, int64_t n, const double* ell2,
+                                            const sic_kernel* kp, const int64_t* grp_ptr, int64_t n_grp,
+                                            const int64_t* cand_ptr, const int32_t* cand_idx, float* feat,
+                                            void* stream) {
+    if (!h || !pts || n < 1 || !ell2 || !sic_valid_kernel(kp) || !grp_ptr || n_grp < 1 || !cand_ptr || !cand_idx ||
+        !feat)
+        return SIC_ERR_INVALID;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int grid = persistent_grid(h, k_features, 256, 0, n_grp);
+    k_features<<<grid, 256, 0, s>>>(pts, n, kp->dim, ell2, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp,
+                                    (const long long*)cand_ptr, cand_idx, feat, h->d_status);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_proposal_score_workspace(size_t* bytes) {
+    if (!bytes) return SIC_ERR_INVALID;
+    *bytes = sizeof(uint2) * (size_t)(16 * 32 + 8 * 16 * 32);
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_proposal_score(sic_handle* h, const float* params, const float* feat, int64_t rows,
+                                         float* score, void* ws, size_t ws_bytes, void* stream) {
+    size_t need = 0;
+    sic_proposal_score_workspace(&need);
+    if (!h || !params || !feat || rows < 0 || !score || !ws || ws_bytes < need) return SIC_ERR_INVALID;
+    if (rows == 0) return SIC_OK;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    uint2* W1f = (uint2*)ws;
+    uint2* W2f = W1f + 16 * 32;
+    k_pack_frags<<<2, 256, 0, s>>>(params + OFF_W1, NF, 1, W1f);
+    k_pack_frags<<<16, 256, 0, s>>>(params + OFF_W2, HID, 8, W2f);
+    int grid = persistent_grid(h, k_mlp_infer, 128, 0, (rows + 63) / 64);
+    k_mlp_infer<<<grid, 128, 0, s>>>(feat, rows, W1f, W2f, params, score);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_proposal_topk(sic_handle* h, const int64_t* cand_ptr, const int32_t* cand_idx,
+                                        const float* score, int64_t n_grp, int32_t top, int64_t* out_ptr,
+                                        int32_t* out_idx, void* stream) {
+    if (!h || !cand_ptr || !cand_idx || !score || n_grp < 1 || top < 1 || !out_ptr || !out_idx)
+        return SIC_ERR_INVALID;
+    if (top > 4096) return SIC_ERR_UNSUPPORTED;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    k_topk_counts<<<(unsigned)((n_grp + 255) / 256), 256, 0, s>>>((const long long*)cand_ptr, n_grp, top,
+                                                                    (long long*)out_ptr);
+    k_scan_one_block<<<1, 1024, 0, s>>>((long long*)out_ptr, n_grp);
+    int grid = persistent_grid(h, k_topk_compact, 512, 0, n_grp);
+    k_topk_compact<<<grid, 512, 0, s>>>((const long long*)cand_ptr, cand_idx, score, n_grp, top,
+                                        (const long long*)out_ptr, out_idx, h->d_status);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_proposal_labels(sic_handle* h, const int64_t* cand_ptr, const int32_t* cand_idx,
+                                          int64_t n_grp, const int32_t* sel_idx, const int32_t* sel_count, int32_t k,
+                                          float* label, void* stream) {
+    if (!h || !cand_ptr || !cand_idx || n_grp < 1 || !sel_idx || !sel_count || k < 1 || !label)
+        return SIC_ERR_INVALID;
+    if (k > 256) return SIC_ERR_UNSUPPORTED;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    int grid = persistent_grid(h, k_labels, 256, 0, n_grp);
+    k_labels<<<grid, 256, 0, (cudaStream_t)stream>>>((const long long*)cand_ptr, cand_idx, sel_idx, sel_count, k,
+                                                      n_grp, label);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_mlp_train_workspace(int64_t batch, size_t* bytes) {
+    if (!bytes || batch < 1) return SIC_ERR_INVALID;
+    *bytes = sizeof(float) * (size_t)train_ws(batch).size();
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_mlp_grads(sic_handle* h, const float* params, const float* feat, const float* label,
+                                    int64_t batch, float pos_weight, int32_t bf16, float* grads, float* loss,
+                                    float* score, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || !params || !feat || !label || batch < 1 || !grads || !loss || !ws) return SIC_ERR_INVALID;
+    TrainWs L = train_ws(batch);
+    if (ws_bytes < sizeof(float) * (size_t)L.size()) return SIC_ERR_INVALID;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    float* W = (float*)ws;
+    float* q = W + L.q();
+    float* xr = W + L.xr();
+    float* Z1 = W + L.z1();
+    float* H1 = W + L.h1();
+    float* Z2 = W + L.z2();
+    float* H2 = W + L.h2();
+    float* dS = W + L.ds();
+    float* lrow = W + L.lrow();
+    float* part = W + L.part();
+    const long long B = batch;
+    const unsigned ew = (unsigned)((B * HID + 255) / 256);
+    k_round_params<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, q, NPARAM, bf16);
+    k_round_rows<<<(unsigned)((B * NF + 255) / 256), 256, 0, s>>>(feat, xr, B * NF, bf16);
+    // forward
+    gemm(s, (int)B, HID, NF, xr, NF, 1, q + OFF_W1, HID, 1, Z1, 1, part);
+    k_bias_gelu<<<ew, 256, 0, s>>>(Z1, H1, q + OFF_B1, B, bf16);
+    gemm(s, (int)B, HID, HID, H1, HID, 1, q + OFF_W2, HID, 1, Z2, 1, part);
+    k_bias_gelu<<<ew, 256, 0, s>>>(Z2, H2, q + OFF_B2, B, 0);
+    k_head<<<(unsigned)((B + 3) / 4), 128, 0, s>>>(H2, q + OFF_W3, q + OFF_B3, label, B, pos_weight, score, dS,
+                                                   lrow);
+    k_sum_loss<<<1, 256, 0, s>>>(lrow, B, loss);
+    // backward: w3, b3
+    gemm(s, HID, 1, (int)B, H2, 1, HID, dS, 1, 1, grads + OFF_W3, L.nz, part);
+    k_colsum<<<1, 32, 0, s>>>(dS, B, 1, grads + OFF_B3);
+    // dZ2 into H2's storage (H2 is no longer needed)
+    k_dz2<<<ew, 256, 0, s>>>(dS, q + OFF_W3, Z2, H2, B);
+    float* dZ2 = H2;
+    gemm(s, HID, HID, (int)B, H1, 1, HID, dZ2, HID, 1, grads + OFF_W2, L.nz, part);
+    k_colsum<<<1, 128, 0, s>>>(dZ2, B, HID, grads + OFF_B2);
+    // dH1 = dZ2 W2^T  -> into Z2's storage, then dZ1 = dH1 .* gelu'(Z1)
+    gemm(s, (int)B, HID, HID, dZ2, HID, 1, q + OFF_W2, 1, HID, Z2, 1, part);
+    float* dZ1 = Z2;
+    k_mul_dgelu<<<ew, 256, 0, s>>>(dZ1, Z1, B * HID);
+    gemm(s, NF, HID, (int)B, xr, 1, NF, dZ1, HID, 1, grads + OFF_W1, L.nz, part);
+    k_colsum<<<1, 128, 0, s>>>(dZ1, B, HID, grads + OFF_B1);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
+
+extern "C" sic_status sic_adamw_step(sic_handle* h, float* params, float* m, float* v, const float* grads,
+                                     int32_t n, int32_t step, float lr, float beta1, float beta2, float eps,
+                                     float wd, void* stream) {
+    if (!h || !params || !m || !v || !grads || n < 1 || step < 1) return SIC_ERR_INVALID;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    k_adamw<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params, m, v, grads, n, lr, beta1, beta2, eps, wd,
+                                                               c1, c2);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
+
+extern "C" int32_t sic_mlp_param_count(void) { return NPARAM; }

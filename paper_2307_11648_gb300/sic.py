@@ -29,6 +29,8 @@ EXPORTS = [
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
+    "sic_mlp_param_count", "sic_proposal_features", "sic_proposal_score_workspace", "sic_proposal_score",
+    "sic_proposal_topk", "sic_proposal_labels", "sic_mlp_train_workspace", "sic_mlp_grads", "sic_adamw_step",
 ]
 
 
@@ -86,6 +88,16 @@ def lib():
             "sic_build_factor": (st, [vp, vp, i64, pk, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
             "sic_apply_factor_workspace": (st, [i64, i32, st, C.POINTER(sz)]),
             "sic_apply_factor": (st, [vp, i64, vp, vp, vp, st, vp, vp, i32, vp, sz, vp]),
+            "sic_mlp_param_count": (i32, []),
+            "sic_proposal_features": (st, [vp, vp, i64, vp, pk, vp, i64, vp, vp, vp, vp]),
+            "sic_proposal_score_workspace": (st, [C.POINTER(sz)]),
+            "sic_proposal_score": (st, [vp, vp, vp, i64, vp, vp, sz, vp]),
+            "sic_proposal_topk": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),
+            "sic_proposal_labels": (st, [vp, vp, vp, i64, vp, vp, i32, vp, vp]),
+            "sic_mlp_train_workspace": (st, [i64, C.POINTER(sz)]),
+            "sic_mlp_grads": (st, [vp, vp, vp, vp, i64, C.c_float, i32, vp, vp, vp, vp, sz, vp]),
+            "sic_adamw_step": (st, [vp, vp, vp, vp, vp, i32, i32, C.c_float, C.c_float, C.c_float, C.c_float,
+                                    C.c_float, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -335,3 +347,74 @@ def apply_factor(h: Handle, col_ptr, row_idx, val, op: int, x, y, ws=None, strea
                                   _dptr(row_idx, torch.int32, "row_idx"), _dptr(val, torch.float64, "val"), op,
                                   _dptr(x, torch.float64, "x"), _dptr(y, torch.float64, "y"), nrhs, _dptr(ws),
                                   ws.numel() if ws is not None else 0, _stream(stream)), "sic_apply_factor", h)
+
+
+# ------------------------------------------------------- learned proposal --
+
+def mlp_param_count() -> int:
+    return int(lib().sic_mlp_param_count())
+
+
+def proposal_features(h: Handle, pts, ell2, kp: Kernel, grp_ptr, cand_ptr, cand_idx, feat, stream=None):
+    import torch
+    _check(lib().sic_proposal_features(h.ptr, _dptr(pts, torch.float64, "pts"), pts.shape[0],
+                                       _dptr(ell2, torch.float64, "ell2"), C.byref(kp),
+                                       _dptr(grp_ptr, torch.int64, "grp_ptr"), grp_ptr.numel() - 1,
+                                       _dptr(cand_ptr, torch.int64, "cand_ptr"),
+                                       _dptr(cand_idx, torch.int32, "cand_idx"), _dptr(feat, torch.float32, "feat"),
+                                       _stream(stream)), "sic_proposal_features", h)
+
+
+def proposal_score_workspace() -> int:
+    b = C.c_size_t()
+    _check(lib().sic_proposal_score_workspace(C.byref(b)), "sic_proposal_score_workspace")
+    return b.value
+
+
+def proposal_score(h: Handle, params, feat, score, ws, stream=None):
+    import torch
+    rows = feat.shape[0]
+    _check(lib().sic_proposal_score(h.ptr, _dptr(params, torch.float32, "params"), _dptr(feat, torch.float32, "feat"),
+                                    rows, _dptr(score, torch.float32, "score"), _dptr(ws), ws.numel(),
+                                    _stream(stream)), "sic_proposal_score", h)
+
+
+def proposal_topk(h: Handle, cand_ptr, cand_idx, score, top: int, out_ptr, out_idx, stream=None):
+    import torch
+    _check(lib().sic_proposal_topk(h.ptr, _dptr(cand_ptr, torch.int64, "cand_ptr"),
+                                   _dptr(cand_idx, torch.int32, "cand_idx"), _dptr(score, torch.float32, "score"),
+                                   cand_ptr.numel() - 1, top, _dptr(out_ptr, torch.int64, "out_ptr"),
+                                   _dptr(out_idx, torch.int32, "out_idx"), _stream(stream)), "sic_proposal_topk", h)
+
+
+def proposal_labels(h: Handle, cand_ptr, cand_idx, sel_idx, sel_count, k: int, label, stream=None):
+    import torch
+    _check(lib().sic_proposal_labels(h.ptr, _dptr(cand_ptr, torch.int64, "cand_ptr"),
+                                     _dptr(cand_idx, torch.int32, "cand_idx"), cand_ptr.numel() - 1,
+                                     _dptr(sel_idx, torch.int32, "sel_idx"), _dptr(sel_count, torch.int32, "sel_count"),
+                                     k, _dptr(label, torch.float32, "label"), _stream(stream)),
+           "sic_proposal_labels", h)
+
+
+def mlp_train_workspace(batch: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sic_mlp_train_workspace(batch, C.byref(b)), "sic_mlp_train_workspace")
+    return b.value
+
+
+def mlp_grads(h: Handle, params, feat, label, pos_weight: float, bf16: bool, grads, loss, ws, score=None,
+              stream=None):
+    import torch
+    _check(lib().sic_mlp_grads(h.ptr, _dptr(params, torch.float32, "params"), _dptr(feat, torch.float32, "feat"),
+                               _dptr(label, torch.float32, "label"), feat.shape[0], float(pos_weight), int(bf16),
+                               _dptr(grads, torch.float32, "grads"), _dptr(loss, torch.float32, "loss"),
+                               _dptr(score, torch.float32, "score"), _dptr(ws), ws.numel(), _stream(stream)),
+           "sic_mlp_grads", h)
+
+
+def adamw_step(h: Handle, params, m, v, grads, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0,
+               stream=None):
+    import torch
+    _check(lib().sic_adamw_step(h.ptr, _dptr(params, torch.float32), _dptr(m, torch.float32), _dptr(v, torch.float32),
+                                _dptr(grads, torch.float32), params.numel(), int(step), float(lr), float(beta1),
+                                float(beta2), float(eps), float(wd), _stream(stream)), "sic_adamw_step", h)
