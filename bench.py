@@ -2,15 +2,20 @@
 (N = 2^20 points uniform in the unit square, Matern 3/2, length scale 0.02, nugget 1e-6,
 supernodes of 8..64 targets, 1024 candidates and k = 64 picks per supernode).
 
-One step = the whole device path over the prepared inputs: supernodal greedy selection
-(FP32-mixed, the headline; FP64 timed alongside) -> nnz scan -> FP64 KL-optimal fill ->
-sum of log conditional variances.  Ordering / candidate / grouping prep is host set-up,
-timed and reported separately.
+Headline step (one pass of the whole device path over the prepared inputs):
+  learned proposal (features -> BF16 tensor-core MLP -> top 256 of 1024 per supernode)
+  -> FP32-mixed supernodal greedy selection on the survivors -> nnz scan
+  -> FP64 KL-optimal fill -> sum of log conditional variances.
+Timed alongside: the plain FP32-mixed and plain FP64 paths on all 1024 candidates, a
+2k-pick reference factor for the KL gap (S_A - S_plain64) / (S_plain64 - S_ref) with
+S = sum log v, and the plain distance truncation to 256 candidates.  Ordering /
+candidate / grouping prep and the proposal's training are host / set-up work, timed and
+reported separately.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sic|reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank builds its own problem
-(seed = rank; weak scaling, no data-path collective) and the max step time over ranks
+(seed + rank; weak scaling, no data-path collective) and the max step time over ranks
 is used.  `--impl reference` times the CPU oracle (FP64, all host cores) on a bounded
 sample of the same workload.
 """
@@ -18,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -34,16 +40,10 @@ import synthetic  # noqa: E402
 
 METRIC = "factor columns/s at N=2^20,k=64 (learned+FP32 vs plain FP64); KL gap"
 WORKLOAD = "cfg3_aggregated"
-FFMA_PER_SM_CLK = 128          # FP32 FMA lanes per SM per clock (Blackwell SM)
 SMS = 152
 SM_MAX_MHZ = 2070.0
-
-
-def peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
+FFMA_PER_SM_CLK = 128   # FP32 FMA lanes per SM per clock
+DFMA_PER_SM_CLK = 2     # FP64 FMA per SM per clock on GB300 (1.26 TFLOP/s nominal at 2070 MHz)
 
 
 # ------------------------------------------------------------- clocks ---
@@ -101,26 +101,32 @@ class ClockSampler:
 
 # ------------------------------------------------------ flop accounting ---
 
-def select_flops(hp) -> float:
-    """Algorithmic FP32 FLOPs of the supernodal selection for the whole problem
-    (2 per fused multiply-add): target columns R*m^2/2 FMA (R = C + m rows), then per
-    step t the two left-looking dot products C*(t) + C*(m + t), the two downdates 2C and
-    the score C (one division counted as one FMA); kernel evaluations not counted."""
-    m = np.diff(hp.grp_ptr).astype(np.float64)
-    C = np.diff(hp.cand_ptr).astype(np.float64)
-    k = float(hp.k)
+def select_flops(grp_ptr, cand_ptr, k) -> float:
+    """Algorithmic FLOPs of the supernodal selection (2 per fused multiply-add): target
+    columns R*m(m-1)/2 FMA (R = C + m rows), then per step t the two left-looking dot
+    products C*t + C*(m + t), the two downdates and the score 3C; kernel evaluations
+    not counted."""
+    m = np.diff(grp_ptr).astype(np.float64)
+    C = np.diff(cand_ptr).astype(np.float64)
     R = C + m
-    init = R * m * (m - 1) / 2.0
-    steps = C * (k * (k - 1) + k * m + 3.0 * k)
-    return float(2.0 * np.sum(init + steps))
+    return float(2.0 * np.sum(R * m * (m - 1) / 2.0 + C * (k * (k - 1) + k * m + 3.0 * k)))
+
+
+def fill_flops(grp_ptr, sel_count) -> float:
+    """Algorithmic FP64 FLOPs of the fill (2 per FMA): Cholesky of the n x n reversed set
+    n^3/6 and the m member back substitutions sum_a (n - a)^2 / 2, n = picks + m; the
+    n(n+1)/2 kernel evaluations are not counted."""
+    m = np.diff(grp_ptr).astype(np.float64)
+    n = sel_count.astype(np.float64) + m
+    back = np.array([np.sum((nn - np.arange(mm)) ** 2) / 2.0 for nn, mm in zip(n, m)])
+    return float(2.0 * np.sum(n ** 3 / 6.0 + back))
 
 
 # ------------------------------------------------------------- oracle ----
 
 def oracle_sample(hp, seconds: float, threads: int):
-    """Time the CPU oracle (FP64 two-factor greedy + per-member dense fill) on a sample
-    of supernodes spread over the ordering until `seconds` have elapsed.  Returns
-    (columns/s, columns done, groups done)."""
+    """Time the CPU oracle (FP64 two-factor greedy + per-member dense fill) on random
+    supernodes until `seconds` have elapsed.  Returns (columns/s, columns, groups, s)."""
     from concurrent.futures import ThreadPoolExecutor
 
     import oracle
@@ -129,8 +135,7 @@ def oracle_sample(hp, seconds: float, threads: int):
     okp = oracle.kernel(kp.dim, kp.nu_x2, kp.length_scale, kp.variance, kp.nugget)
     gp, P = hp.grp_ptr, hp.pts
     G = len(gp) - 1
-    rng = np.random.default_rng(0)
-    order = rng.permutation(G)
+    order = np.random.default_rng(0).permutation(G)
 
     def one(g):
         g0, g1 = int(gp[g]), int(gp[g + 1])
@@ -156,10 +161,8 @@ def oracle_sample(hp, seconds: float, threads: int):
 # ---------------------------------------------------------------- main ---
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(
+        os.environ.get("LOCAL_RANK", "0"))
 
 
 def max_over_ranks(x: float, ws: int) -> float:
@@ -180,19 +183,24 @@ def barrier(ws):
         dist.barrier()
 
 
+def problem(cfg, seed, n=None):
+    from paper_2307_11648_gb300 import pipeline, sic
+    n = n or cfg["n"]
+    ell = cfg["length_scale"] * math.sqrt(cfg["n"] / n)  # same ell / spacing as the full size
+    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], ell, cfg["variance"], cfg["nugget"])
+    pts = synthetic.points(n, cfg["dim"], seed)
+    return pipeline.prepare_groups(pts, kp, cfg["n_cand"], cfg["k"], cfg["m_min"], cfg["m_max"])
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     cfg = synthetic.PRESETS[WORKLOAD]
-    from paper_2307_11648_gb300 import pipeline, sic
-    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"])
-    pts = synthetic.points(cfg["n"], cfg["dim"], cfg["seed"])
-    hp = pipeline.prepare_groups(pts, kp, cfg["n_cand"], cfg["k"], cfg["m_min"], cfg["m_max"])
+    hp = problem(cfg, cfg["seed"])
     threads = os.cpu_count() or 1
-    vals = []
-    cols_tot = 0
+    vals, cols_tot = [], 0
     for _ in range(args.warmup):
-        oracle_sample(hp, 2.0, threads)
+        oracle_sample(hp, 1.0, threads)
     for _ in range(args.steps):
         v, cols, groups, el = oracle_sample(hp, args.ref_seconds, threads)
         vals.append(v)
@@ -202,7 +210,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * hp.n / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "N=2^20 uniform [0,1]^2, Matern 3/2, ell=0.02, nugget 1e-6, supernodes 8..64, "
-                                   "C=1024, k=64", "groups": hp.n_units},
+                                   "C=1024, k=64 (plain greedy, FP64 CPU oracle)", "groups": hp.n_units},
             "cpu_baseline": {"value": v, "unit": "columns/s", "cores": threads, "kind": "oracle",
                              "sample": f"random supernodes, {args.ref_seconds:.0f} s per step of FP64 two-factor "
                                        f"greedy + dense fill ({cols_tot} columns over {args.steps} steps)"},
@@ -219,7 +227,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--n", type=int, default=0, help="override N (smaller runs for profiling)")
+    ap.add_argument("--train-n", type=int, default=1 << 18, help="points per training problem")
+    ap.add_argument("--epochs", type=int, default=3)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if ws > 1:
@@ -234,75 +243,105 @@ def main():
 
     import torch
 
-    from paper_2307_11648_gb300 import build, pipeline, sic
+    from paper_2307_11648_gb300 import build, learned, pipeline, sic
     build.build()
     torch.cuda.set_device(local)
-    cfg = dict(synthetic.PRESETS[WORKLOAD])
-    if args.n:
-        cfg["n"] = args.n
-    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"])
+    cfg = synthetic.PRESETS[WORKLOAD]
     t0 = time.perf_counter()
-    pts = synthetic.points(cfg["n"], cfg["dim"], cfg["seed"] + rank)
-    hp = pipeline.prepare_groups(pts, kp, cfg["n_cand"], cfg["k"], cfg["m_min"], cfg["m_max"])
+    hp = problem(cfg, cfg["seed"] + rank)
     prep_s = time.perf_counter() - t0
     h = sic.Handle(local)
     dp = pipeline.DeviceProblem(hp)
     stream = torch.cuda.current_stream()
     N = hp.n
 
-    def timed(fb, steps, warmup, sampler=None):
+    # ---- the proposal network: trained on plain-greedy labels of disjoint seeds
+    t0 = time.perf_counter()
+    train_probs = [problem(cfg, 1000 + 2 * rank + i, args.train_n) for i in (1, 2)]
+    feat, label, n_sel = learned.training_set(h, train_probs)
+    params, hist = learned.train(h, feat, label, epochs=args.epochs, batch=65536, lr=2e-3, seed=rank)
+    del feat, label, train_probs
+    torch.cuda.empty_cache()
+    train_s = time.perf_counter() - t0
+    proposal = learned.Proposal(h, params, top=4 * cfg["k"])
+
+    def timed(phases, steps, warmup, sampler=None):
+        """phases: list of callables issuing kernels on the stream; returns per-phase ms."""
         for _ in range(warmup):
-            fb.run(dp)
+            for f in phases:
+                f()
         h.sync()
         barrier(ws)
         torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-                torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)] for _ in range(steps)]
         if sampler:
             sampler.start()
-        start = torch.cuda.Event(enable_timing=True)
-        end = torch.cuda.Event(enable_timing=True)
-        start.record(stream)
-        for e0, e1, e2 in evs:
-            e0.record(stream)
-            fb.select(dp)
-            e1.record(stream)
-            fb.fill(dp)
-            e2.record(stream)
-        end.record(stream)
+        for ev in evs:
+            ev[0].record(stream)
+            for i, f in enumerate(phases):
+                f()
+                ev[i + 1].record(stream)
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
         h.sync()
-        total_ms = start.elapsed_time(end)
-        sel_ms = [a.elapsed_time(b) for a, b, _ in evs]
-        fill_ms = [b.elapsed_time(c) for _, b, c in evs]
-        return total_ms, sel_ms, fill_ms, clocks
+        per = [[ev[i].elapsed_time(ev[i + 1]) for ev in evs] for i in range(len(phases))]
+        total = evs[0][0].elapsed_time(evs[-1][-1])
+        return total / steps, [statistics.mean(p) for p in per], clocks
 
-    # ---- headline: FP32-mixed selection + FP64 fill
-    fb32 = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
+    # ---- headline: learned proposal + FP32-mixed selection + FP64 fill
+    lb = learned.LearnedFactorBuilder(h, hp, proposal, sic.SIC_FP32_MIXED)
+    rdp = lb._reduced_device(dp)
     sampler = ClockSampler(local)
-    total_ms, sel_ms, fill_ms, clocks = timed(fb32, args.steps, args.warmup, sampler)
-    t_step = max_over_ranks(total_ms / args.steps, ws)
+    t_ms, (prop_ms, sel_ms, fill_ms), clocks = timed(
+        [lambda: lb.propose(dp), lambda: lb.fb.select(rdp), lambda: lb.fb.fill(rdp)], args.steps, args.warmup,
+        sampler)
+    t_step = max_over_ranks(t_ms, ws)
     value = ws * N / (t_step * 1e-3)
-    sum_logv32 = float(fb32.sum_logv.cpu()[0])
+    S = {"learned_fp32": float(lb.sum_logv.cpu()[0])}
+    nnz = int(lb.col_ptr[-1].item())
+    sel_count_learned = lb.fb.sel_count.cpu().numpy()
 
-    # ---- plain FP64 path (same pipeline, FP64 selection)
+    # ---- plain FP32-mixed and plain FP64 on all candidates
+    fb32 = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
+    p32_ms, (p32_sel, p32_fill), _ = timed([lambda: fb32.select(dp), lambda: fb32.fill(dp)], args.steps, 1)
+    S["plain_fp32"] = float(fb32.sum_logv.cpu()[0])
+    del fb32
     fb64 = pipeline.FactorBuilder(h, hp, sic.SIC_FP64)
-    t64, sel64, fill64, _ = timed(fb64, args.fp64_steps, 1)
-    t64_step = max_over_ranks(t64 / args.fp64_steps, ws)
-    sum_logv64 = float(fb64.sum_logv.cpu()[0])
+    p64_ms, (p64_sel, p64_fill), _ = timed([lambda: fb64.select(dp), lambda: fb64.fill(dp)], args.fp64_steps, 1)
+    p64_ms = max_over_ranks(p64_ms, ws)
+    S["plain_fp64"] = float(fb64.sum_logv.cpu()[0])
     del fb64
+    # ---- KL reference (2k picks from the same candidates) and distance truncation
+    ref_hp = pipeline.HostProblem(hp.pts, hp.kp, 2 * cfg["k"], hp.cand_ptr, hp.cand_idx, hp.grp_ptr, hp.order,
+                                  hp.ell2)
+    fr = pipeline.FactorBuilder(h, ref_hp, sic.SIC_FP32_MIXED)
+    fr.run(dp)
+    h.sync()
+    S["reference_2k"] = float(fr.sum_logv.cpu()[0])
+    del fr
+    top = 4 * cfg["k"]
+    cnt = np.minimum(np.diff(hp.cand_ptr), top)
+    dptr = np.zeros(len(cnt) + 1, np.int64)
+    dptr[1:] = np.cumsum(cnt)
+    didx = np.concatenate([hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g] + cnt[g]] for g in range(len(cnt))])
+    dhp = pipeline.HostProblem(hp.pts, hp.kp, hp.k, dptr, didx, hp.grp_ptr, hp.order, hp.ell2)
+    ddp = pipeline.DeviceProblem(dhp)
+    fd = pipeline.FactorBuilder(h, dhp, sic.SIC_FP32_MIXED)
+    d_ms, _, _ = timed([lambda: fd.run(ddp)], 2, 1)
+    S["distance_fp32"] = float(fd.sum_logv.cpu()[0])
+    del fd, ddp
+    torch.cuda.empty_cache()
+    base = S["plain_fp64"] - S["reference_2k"]
+    kl_gap = {k: (S[k] - S["plain_fp64"]) / base for k in ["learned_fp32", "plain_fp32", "distance_fp32"]}
 
     # ---- end to end through the C-ABI with host buffers (pinned), copies in the region
     hpin = {k: torch.from_numpy(v).pin_memory() for k, v in
-            dict(pts=hp.pts, grp_ptr=hp.grp_ptr, cand_ptr=hp.cand_ptr, cand_idx=hp.cand_idx).items()}
-    nnz_cap = fb32.nnz_cap
+            dict(pts=hp.pts, grp_ptr=hp.grp_ptr, cand_ptr=hp.cand_ptr, cand_idx=hp.cand_idx, ell2=hp.ell2).items()}
     out_host = dict(col_ptr=torch.empty(N + 1, dtype=torch.int64).pin_memory(),
-                    row_idx=torch.empty(nnz_cap, dtype=torch.int32).pin_memory(),
-                    val=torch.empty(nnz_cap, dtype=torch.float64).pin_memory(),
+                    row_idx=torch.empty(nnz, dtype=torch.int32).pin_memory(),
+                    val=torch.empty(nnz, dtype=torch.float64).pin_memory(),
                     sum_logv=torch.empty(1, dtype=torch.float64).pin_memory())
     h2d = sum(t.numel() * t.element_size() for t in hpin.values())
-    nnz = int(fb32.col_ptr[-1].item())
     d2h = (N + 1) * 8 + nnz * 12 + 8
 
     def e2e_step():
@@ -310,39 +349,45 @@ def main():
         dp.grp_ptr.copy_(hpin["grp_ptr"], non_blocking=True)
         dp.cand_ptr.copy_(hpin["cand_ptr"], non_blocking=True)
         dp.cand_idx.copy_(hpin["cand_idx"], non_blocking=True)
-        fb32.run(dp)
-        out_host["col_ptr"].copy_(fb32.col_ptr, non_blocking=True)
-        out_host["row_idx"][:nnz].copy_(fb32.row_idx[:nnz], non_blocking=True)
-        out_host["val"][:nnz].copy_(fb32.val[:nnz], non_blocking=True)
-        out_host["sum_logv"].copy_(fb32.sum_logv, non_blocking=True)
+        lb.ell2.copy_(hpin["ell2"], non_blocking=True)
+        lb.run(dp)
+        out_host["col_ptr"].copy_(lb.fb.col_ptr, non_blocking=True)
+        out_host["row_idx"].copy_(lb.fb.row_idx[:nnz], non_blocking=True)
+        out_host["val"].copy_(lb.fb.val[:nnz], non_blocking=True)
+        out_host["sum_logv"].copy_(lb.fb.sum_logv, non_blocking=True)
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    barrier(ws)
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    s1.record(stream)
-    torch.cuda.synchronize()
-    h.sync()
-    e2e_ms = max_over_ranks(s0.elapsed_time(s1) / args.steps, ws)
+    e2e_ms, _, _ = timed([e2e_step], args.steps, 2)
+    e2e_ms = max_over_ranks(e2e_ms, ws)
 
-    # ---- roofline of the dominant kernel (FP32 selection; ALU bound)
-    flops = select_flops(hp)
-    sel_avg = statistics.mean(sel_ms)
-    achieved = flops / (sel_avg * 1e-3) / 1e12
-    peak_tf = SMS * FFMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    fill_avg = statistics.mean(fill_ms)
+    # ---- rooflines (ALU bound; peaks derived from unit counts and the maximum clock)
+    rp = lb.rhp
+    f32_peak = SMS * FFMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    f64_peak = SMS * DFMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    sel_tf = select_flops(rp.grp_ptr, rp.cand_ptr, hp.k) / (sel_ms * 1e-3) / 1e12
+    fill_tf = fill_flops(hp.grp_ptr, sel_count_learned) / (fill_ms * 1e-3) / 1e12
+    kernels = {
+        "k_select_agg<float> (256 candidates)": {"ms": sel_ms, "achieved_tflops": sel_tf, "peak_tflops": f32_peak,
+                                                 "frac": sel_tf / f32_peak, "unit_peak": "FP32 FFMA"},
+        "k_fill (FP64)": {"ms": fill_ms, "achieved_tflops": fill_tf, "peak_tflops": f64_peak,
+                          "frac": fill_tf / f64_peak, "unit_peak": "FP64 DFMA"},
+        "proposal (features + MLP + top-k)": {"ms": prop_ms},
+    }
+    if fill_ms >= sel_ms:
+        roof = {"bound": "alu", "kernel": "k_fill (FP64 fill)", "achieved": fill_tf, "peak": f64_peak,
+                "unit": "TFLOP/s", "frac": fill_tf / f64_peak, "traffic": None,
+                "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (derived; measured probe 1.20 TFLOP/s)"}
+    else:
+        roof = {"bound": "alu", "kernel": "k_select_agg<float>", "achieved": sel_tf, "peak": f32_peak,
+                "unit": "TFLOP/s", "frac": sel_tf / f32_peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz (derived; measured probe 75 TFLOP/s)"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         v, cols, groups, el = oracle_sample(hp, args.ref_seconds, threads)
         cpu = {"value": v, "unit": "columns/s", "cores": threads, "kind": "oracle",
-               "sample": f"{groups} random supernodes ({cols} columns), FP64 two-factor greedy + dense fill, "
-                         f"{el:.1f} s"}
+               "sample": f"{groups} random supernodes ({cols} columns), FP64 two-factor greedy + dense fill on all "
+                         f"1024 candidates, {el:.1f} s"}
 
     if rank == 0:
         line = {
@@ -351,23 +396,29 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"N={N} uniform [0,1]^2 (seed {cfg['seed']}+rank), Matern 3/2, ell=0.02, "
                                    f"nugget 1e-6, supernodes {cfg['m_min']}..{cfg['m_max']} (mean "
-                                   f"{N / hp.n_units:.1f}), C=1024, k=64; FP32-mixed selection, FP64 fill",
+                                   f"{N / hp.n_units:.1f}), C=1024, k=64",
+                       "path": f"learned proposal (top {top} of 1024) -> select_aggregated FP32 -> factor_nnz -> "
+                               "build_factor FP64 -> sum log v",
                        "groups": hp.n_units, "nnz": nnz, "l2": "inputs larger than L2 (candidate lists "
-                       f"{hp.cand_idx.nbytes / 2**20:.0f} MiB, factor {nnz * 12 / 2**20:.0f} MiB)",
-                       "parallelism": f"independent problems per rank ({ws})", "path": "select_aggregated(FP32) "
-                       "-> factor_nnz -> build_factor(FP64) -> sum log v"},
-            "fp64_plain": {"value": ws * N / (t64_step * 1e-3), "unit": "columns/s", "ms_per_step": t64_step,
-                           "select_ms": statistics.mean(sel64), "fill_ms": statistics.mean(fill64)},
-            "speedup_vs_fp64_plain": t64_step / t_step,
-            "sum_logv": {"fp32_mixed": sum_logv32, "fp64_plain": sum_logv64,
-                         "rel_diff": (sum_logv32 - sum_logv64) / abs(sum_logv64)},
-            "phases_ms": {"select": sel_avg, "fill_and_kl": fill_avg, "prep_host_s": prep_s},
-            "roofline": {"bound": "alu", "kernel": "k_select_agg<float>", "achieved": achieved,
-                         "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": None,
-                         "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz (derived, not measured)"},
+                       f"{hp.cand_idx.nbytes / 2**20:.0f} MiB, features {int(hp.cand_ptr[-1]) * 32 / 2**20:.0f} MiB, "
+                       f"factor {nnz * 12 / 2**20:.0f} MiB)",
+                       "parallelism": f"independent problems per rank ({ws})"},
+            "kl_gap": kl_gap,
+            "sum_logv": S,
+            "fp64_plain": {"value": ws * N / (p64_ms * 1e-3), "unit": "columns/s", "ms_per_step": p64_ms,
+                           "select_ms": p64_sel, "fill_ms": p64_fill},
+            "fp32_plain": {"value": ws * N / (p32_ms * 1e-3), "unit": "columns/s", "ms_per_step": p32_ms,
+                           "select_ms": p32_sel, "fill_ms": p32_fill},
+            "distance_top256_fp32": {"value": ws * N / (d_ms * 1e-3), "unit": "columns/s", "ms_per_step": d_ms},
+            "speedup_vs_fp64_plain": p64_ms / t_step,
+            "phases_ms": {"proposal": prop_ms, "select": sel_ms, "fill_and_kl": fill_ms},
+            "setup_s": {"prep_host": prep_s, "train_proposal": train_s, "train_selections": n_sel,
+                        "train_loss": [hist[0][1], hist[-1][1]]},
+            "kernels": kernels,
+            "roofline": roof,
             "e2e": {"value": ws * N / (e2e_ms * 1e-3), "unit": "columns/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": 8 * args.steps,
+            "gpu_launches": 15 * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
