@@ -101,136 +101,145 @@ __global__ void k_scan_add(long long* __restrict__ v, long long n, const long lo
 
 // ------------------------------------------------------------------- the fill --
 
-struct FillSmem {
-    double* G;    // packed lower, n(n+1)/2
-    double* B;    // n x 32 right-hand sides, row-major [i][lane]
-    double* xyz;  // 3 x n coordinates of R
-    int* pos;     // n positions of R
-    int* srt;     // k picks sorted ascending
-};
+constexpr int FILL_NT = 128;  // 4 warps per unit
 
 __device__ __forceinline__ long long pk(int i, int j) { return (long long)i * (i + 1) / 2 + j; }
 
-__global__ void __launch_bounds__(32) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
-                                             const long long* __restrict__ grp_ptr, long long n_units,
-                                             const int32_t* __restrict__ sel_idx,
-                                             const int32_t* __restrict__ sel_count, int k, int max_m, long long n,
-                                             const long long* __restrict__ col_ptr, int32_t* __restrict__ row_idx,
-                                             double* __restrict__ val, double* __restrict__ logv, DevStatus* st) {
+// row i of the packed lower triangle that holds flat entry e (i(i+1)/2 <= e < (i+1)(i+2)/2)
+__device__ __forceinline__ int pk_row(long long e) {
+    int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while ((long long)i * (i + 1) / 2 > e) --i;
+    while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
+    return i;
+}
+
+__global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
+                                                  const long long* __restrict__ grp_ptr, long long n_units,
+                                                  const int32_t* __restrict__ sel_idx,
+                                                  const int32_t* __restrict__ sel_count, int k, int max_m,
+                                                  long long n, const long long* __restrict__ col_ptr,
+                                                  int32_t* __restrict__ row_idx, double* __restrict__ val,
+                                                  double* __restrict__ logv, DevStatus* st) {
     extern __shared__ double smem_d[];
     const int nmax = k + max_m;
-    double* G = smem_d;
-    double* B = G + (long long)nmax * (nmax + 1) / 2;
-    double* xyz = B + (long long)nmax * 32;
-    int* pos = reinterpret_cast<int*>(xyz + 3 * nmax);
-    int* srt = pos + nmax;
-    const int lane = threadIdx.x;
+    double* G = smem_d;                                     // packed lower, nmax(nmax+1)/2
+    double* bvec = G + (long long)nmax * (nmax + 1) / 2;    // 4 x nmax, one right-hand side per warp
+    double* rG = bvec + 4 * nmax;                           // 1 / G_jj
+    double* xyz = rG + nmax;                                // 3 x nmax
+    int* pos = reinterpret_cast<int*>(xyz + 3 * nmax);      // nmax
+    int* srt = pos + nmax;                                  // k
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         const long long g0 = grp_ptr ? grp_ptr[u] : u;
         const int m = grp_ptr ? (int)(grp_ptr[u + 1] - g0) : 1;
-        int cnt = sel_count[u];
+        const int cnt = sel_count[u];
         if (m < 1 || m > max_m || cnt < 0 || cnt > k || g0 < 0 || g0 + m > n) {
-            if (lane == 0) record_error(st, SIC_ERR_INVALID, u);
+            if (tid == 0) record_error(st, SIC_ERR_INVALID, u);
             continue;
         }
         const int nn = cnt + m;
-        // picks sorted ascending by rank; they must be distinct positions after the unit
-        bool badsel = false;
-        for (int i = lane; i < cnt; i += 32) {
-            int v = sel_idx[u * k + i];
+        // picks sorted ascending by rank; they must be distinct positions after the unit,
+        // and col_ptr must match the pattern
+        bool bad = false;
+        for (int i = tid; i < cnt; i += FILL_NT) {
+            const int v = sel_idx[u * k + i];
             int rank = 0, same = 0;
             for (int j = 0; j < cnt; ++j) {
-                int w = sel_idx[u * k + j];
+                const int w = sel_idx[u * k + j];
                 rank += (w < v);
                 same += (w == v);
             }
-            if (v < g0 + m || v >= n || same != 1) badsel = true;
+            if (v < g0 + m || v >= n || same != 1) bad = true;
             else srt[rank] = v;
         }
-        badsel = __any_sync(0xffffffffu, badsel);
-        if (!badsel)
-            for (int a = lane; a < m; a += 32)
-                if (col_ptr[g0 + a + 1] - col_ptr[g0 + a] != (long long)(m - a + cnt)) badsel = true;
-        badsel = __any_sync(0xffffffffu, badsel);
-        if (badsel) {
-            if (lane == 0) record_error(st, SIC_ERR_INVALID, u);
+        for (int a = tid; a < m; a += FILL_NT)
+            if (col_ptr[g0 + a + 1] - col_ptr[g0 + a] != (long long)(m - a + cnt)) bad = true;
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) record_error(st, SIC_ERR_INVALID, u);
             continue;
         }
-        __syncwarp();
         // R order: picks descending, then members descending
-        for (int i = lane; i < nn; i += 32) {
-            int p = (i < cnt) ? srt[cnt - 1 - i] : (int)(g0 + m - 1 - (i - cnt));
+        for (int i = tid; i < nn; i += FILL_NT) {
+            const int p = (i < cnt) ? srt[cnt - 1 - i] : (int)(g0 + m - 1 - (i - cnt));
             pos[i] = p;
             for (int d = 0; d < 3; ++d) xyz[d * nmax + i] = (d < dim) ? pts[(long long)p * dim + d] : 0.0;
         }
-        __syncwarp();
-        // Theta_RR, packed lower
-        for (int i = 0; i < nn; ++i) {
-            const double xi = xyz[i], yi = xyz[nmax + i], zi = xyz[2 * nmax + i];
-            for (int j = lane; j <= i; j += 32) {
-                double dx = xi - xyz[j], dy = yi - xyz[nmax + j], dz = zi - xyz[2 * nmax + j];
-                double v = matern<double>(kp, sqrt(dx * dx + dy * dy + dz * dz));
-                if (i == j) v += kp.nugget;
-                G[pk(i, j)] = v;
-            }
+        if (tid == 0) s_bad = 0;
+        __syncthreads();
+        // Theta_RR, packed lower, one flat entry per thread
+        const long long tri = (long long)nn * (nn + 1) / 2;
+        for (long long e = tid; e < tri; e += FILL_NT) {
+            const int i = pk_row(e);
+            const int j = (int)(e - (long long)i * (i + 1) / 2);
+            const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j],
+                         dz = xyz[2 * nmax + i] - xyz[2 * nmax + j];
+            double v = matern<double>(kp, sqrt(dx * dx + dy * dy + dz * dz));
+            if (i == j) v += kp.nugget;
+            G[e] = v;
         }
-        __syncwarp();
-        // left-looking Cholesky: column j, lane owns rows i = j + lane, j + lane + 32, ...
-        bool bad = false;
+        __syncthreads();
+        // left-looking Cholesky: column j, thread owns row j + tid (nn <= 192 < 2 * FILL_NT)
         for (int j = 0; j < nn; ++j) {
-            for (int i = j + lane; i < nn; i += 32) {
-                double s = G[pk(i, j)];
-                const long long ri = pk(i, 0), rj = pk(j, 0);
-                for (int l = 0; l < j; ++l) s = fma(-G[ri + l], G[rj + l], s);
-                G[pk(i, j)] = s;
+            const long long rj = pk(j, 0);
+            for (int i = j + tid; i < nn; i += FILL_NT) {
+                const long long ri = pk(i, 0);
+                double s0 = G[ri + j], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                int l = 0;
+                for (; l + 4 <= j; l += 4) {
+                    s0 = fma(-G[ri + l], G[rj + l], s0);
+                    s1 = fma(-G[ri + l + 1], G[rj + l + 1], s1);
+                    s2 = fma(-G[ri + l + 2], G[rj + l + 2], s2);
+                    s3 = fma(-G[ri + l + 3], G[rj + l + 3], s3);
+                }
+                for (; l < j; ++l) s0 = fma(-G[ri + l], G[rj + l], s0);
+                G[ri + j] = (s0 + s1) + (s2 + s3);
             }
-            __syncwarp();
-            const double djj = G[pk(j, j)];
+            __syncthreads();
+            const double djj = G[rj + j];
             if (!(djj > 0.0)) {
-                bad = true;
+                if (tid == 0) s_bad = 1;
                 break;
             }
             const double d = sqrt(djj);
             const double rd = 1.0 / d;
-            for (int i = j + 1 + lane; i < nn; i += 32) G[pk(i, j)] *= rd;
-            __syncwarp();
-            if (lane == 0) G[pk(j, j)] = d;
-            __syncwarp();
+            for (int i = j + 1 + tid; i < nn; i += FILL_NT) G[pk(i, j)] *= rd;
+            if (tid == 0) {
+                G[rj + j] = d;
+                rG[j] = rd;
+            }
+            __syncthreads();
         }
-        if (bad) {
-            if (lane == 0) record_error(st, SIC_ERR_NOT_PD, u);
-            __syncwarp();
+        __syncthreads();
+        if (s_bad) {
+            if (tid == 0) record_error(st, SIC_ERR_NOT_PD, u);
+            __syncthreads();
             continue;
         }
-        // members in batches of 32: lane b solves G^T x = e_{j_b}, j_b = nn - 1 - (a0 + b)
-        for (int a0 = 0; a0 < m; a0 += 32) {
-            const int a = a0 + lane;
-            const bool act = a < m;
+        // member a: solve G^T x = e_jb (jb = nn-1-a), one right-hand side per warp
+        double* b = bvec + warp * nmax;
+        for (int a = warp; a < m; a += 4) {
             const int jb = nn - 1 - a;
-            if (act)
-                for (int i = 0; i <= jb; ++i) B[i * 32 + lane] = (i == jb) ? 1.0 : 0.0;
+            for (int i = lane; i <= jb; i += 32) b[i] = (i == jb) ? 1.0 : 0.0;
             __syncwarp();
-            const int top = nn - 1 - a0;  // largest j_b in the batch
-            for (int l = top; l >= 0; --l) {
-                if (act && l <= jb) {
-                    const long long rl = pk(l, 0);
-                    const double xl = B[l * 32 + lane] / G[rl + l];
-                    B[l * 32 + lane] = xl;
-                    for (int i = 0; i < l; ++i) B[i * 32 + lane] = fma(-G[rl + i], xl, B[i * 32 + lane]);
-                }
+            for (int l = jb; l >= 0; --l) {
+                const double xl = b[l] * rG[l];
+                const long long rl = pk(l, 0);
+                for (int i = lane; i < l; i += 32) b[i] = fma(-G[rl + i], xl, b[i]);
+                __syncwarp();
+                if (lane == 0) b[l] = xl;
+                __syncwarp();
             }
-            __syncwarp();
-            if (act) {
-                const long long c0 = col_ptr[g0 + a];
-                for (int p = 0; p <= jb; ++p) {
-                    row_idx[c0 + p] = pos[jb - p];
-                    val[c0 + p] = B[(jb - p) * 32 + lane];
-                }
-                logv[g0 + a] = 2.0 * log(G[pk(jb, jb)]);
+            const long long c0 = col_ptr[g0 + a];
+            for (int p = lane; p <= jb; p += 32) {
+                row_idx[c0 + p] = pos[jb - p];
+                val[c0 + p] = b[jb - p];
             }
+            if (lane == 0) logv[g0 + a] = 2.0 * log(G[pk(jb, jb)]);
             __syncwarp();
         }
+        __syncthreads();
     }
 }
 
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(256) k_sum_final(const double* __restrict__ pa
 
 size_t fill_smem_bytes(int k, int max_m) {
     size_t nmax = (size_t)k + (size_t)max_m;
-    return sizeof(double) * (nmax * (nmax + 1) / 2 + nmax * 32 + 3 * nmax) + sizeof(int) * (nmax + (size_t)k);
+    return sizeof(double) * (nmax * (nmax + 1) / 2 + 4 * nmax + nmax + 3 * nmax) + sizeof(int) * (nmax + (size_t)k);
 }
 
 }  // namespace
@@ -327,10 +336,10 @@ extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
     size_t sm = fill_smem_bytes(k, max_m);
-    if (sm > 200 * 1024) return SIC_ERR_UNSUPPORTED;
+    if (sm > 227 * 1024) return SIC_ERR_UNSUPPORTED;
     SIC_CUDA_TRY(cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int grid = persistent_grid(h, k_fill, 32, sm, n_grp);
-    k_fill<<<grid, 32, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp, sel_idx,
+    int grid = persistent_grid(h, k_fill, FILL_NT, sm, n_grp);
+    k_fill<<<grid, FILL_NT, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp, sel_idx,
                                 sel_count, k, max_m, n, (const long long*)col_ptr, row_idx, val, logv, h->d_status);
     long long nb = (n + SUM_TILE - 1) / SUM_TILE;
     k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n, (double*)ws);
