@@ -229,6 +229,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-n", type=int, default=1 << 18, help="points per training problem")
     ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--case-only", type=int, default=0, metavar="N",
+                    help="profiling case: one FP32-mixed supernodal factor build at N points, no timing")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if ws > 1:
@@ -247,6 +249,16 @@ def main():
     build.build()
     torch.cuda.set_device(local)
     cfg = synthetic.PRESETS[WORKLOAD]
+    if args.case_only:
+        # one FP32-mixed supernodal factor build at the requested size (for ncu captures)
+        hp = problem(cfg, cfg["seed"], args.case_only)
+        h = sic.Handle(local)
+        dp = pipeline.DeviceProblem(hp)
+        fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
+        fb.run(dp)
+        h.sync()
+        print(json.dumps({"case": args.case_only, "groups": hp.n_units, "sum_logv": float(fb.sum_logv.cpu()[0])}))
+        return
     t0 = time.perf_counter()
     hp = problem(cfg, cfg["seed"] + rank)
     prep_s = time.perf_counter() - t0
@@ -292,9 +304,11 @@ def main():
     lb = learned.LearnedFactorBuilder(h, hp, proposal, sic.SIC_FP32_MIXED)
     rdp = lb._reduced_device(dp)
     sampler = ClockSampler(local)
-    t_ms, (prop_ms, sel_ms, fill_ms), clocks = timed(
-        [lambda: lb.propose(dp), lambda: lb.fb.select(rdp), lambda: lb.fb.fill(rdp)], args.steps, args.warmup,
-        sampler)
+    pr = lb.proposal
+    t_ms, (feat_ms, mlp_ms, topk_ms, sel_ms, fill_ms), clocks = timed(
+        [lambda: pr.features(dp, lb.buf), lambda: pr.score(dp, lb.buf), lambda: pr.topk(dp, lb.buf),
+         lambda: lb.fb.select(rdp), lambda: lb.fb.fill(rdp)], args.steps, args.warmup, sampler)
+    prop_ms = feat_ms + mlp_ms + topk_ms
     t_step = max_over_ranks(t_ms, ws)
     value = ws * N / (t_step * 1e-3)
     S = {"learned_fp32": float(lb.sum_logv.cpu()[0])}
@@ -336,7 +350,7 @@ def main():
 
     # ---- end to end through the C-ABI with host buffers (pinned), copies in the region
     hpin = {k: torch.from_numpy(v).pin_memory() for k, v in
-            dict(pts=hp.pts, grp_ptr=hp.grp_ptr, cand_ptr=hp.cand_ptr, cand_idx=hp.cand_idx, ell2=hp.ell2).items()}
+            dict(pts=hp.pts, grp_ptr=hp.grp_ptr, cand_ptr=hp.cand_ptr, cand_idx=hp.cand_idx).items()}
     out_host = dict(col_ptr=torch.empty(N + 1, dtype=torch.int64).pin_memory(),
                     row_idx=torch.empty(nnz, dtype=torch.int32).pin_memory(),
                     val=torch.empty(nnz, dtype=torch.float64).pin_memory(),
@@ -349,7 +363,6 @@ def main():
         dp.grp_ptr.copy_(hpin["grp_ptr"], non_blocking=True)
         dp.cand_ptr.copy_(hpin["cand_ptr"], non_blocking=True)
         dp.cand_idx.copy_(hpin["cand_idx"], non_blocking=True)
-        lb.ell2.copy_(hpin["ell2"], non_blocking=True)
         lb.run(dp)
         out_host["col_ptr"].copy_(lb.fb.col_ptr, non_blocking=True)
         out_host["row_idx"].copy_(lb.fb.row_idx[:nnz], non_blocking=True)
@@ -364,13 +377,22 @@ def main():
     f32_peak = SMS * FFMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
     f64_peak = SMS * DFMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
     sel_tf = select_flops(rp.grp_ptr, rp.cand_ptr, hp.k) / (sel_ms * 1e-3) / 1e12
+    rows = float(hp.cand_ptr[-1])
+    mlp_tf = rows * 2.0 * (16 * 128 + 128 * 128 + 128) / (mlp_ms * 1e-3) / 1e12  # layer 1 padded to K = 16
+    try:
+        bf16_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        bf16_peak = 1900.0
     fill_tf = fill_flops(hp.grp_ptr, sel_count_learned) / (fill_ms * 1e-3) / 1e12
     kernels = {
         "k_select_agg<float> (256 candidates)": {"ms": sel_ms, "achieved_tflops": sel_tf, "peak_tflops": f32_peak,
                                                  "frac": sel_tf / f32_peak, "unit_peak": "FP32 FFMA"},
         "k_fill (FP64)": {"ms": fill_ms, "achieved_tflops": fill_tf, "peak_tflops": f64_peak,
                           "frac": fill_tf / f64_peak, "unit_peak": "FP64 DFMA"},
-        "proposal (features + MLP + top-k)": {"ms": prop_ms},
+        "k_features": {"ms": feat_ms},
+        "k_mlp_infer (BF16 mma.sync)": {"ms": mlp_ms, "achieved_tflops": mlp_tf, "peak_tflops": bf16_peak,
+                                        "frac": mlp_tf / bf16_peak, "unit_peak": "measured cuBLAS BF16 (burst)"},
+        "top-k": {"ms": topk_ms},
     }
     if fill_ms >= sel_ms:
         roof = {"bound": "alu", "kernel": "k_fill (FP64 fill)", "achieved": fill_tf, "peak": f64_peak,
@@ -411,7 +433,8 @@ def main():
                            "select_ms": p32_sel, "fill_ms": p32_fill},
             "distance_top256_fp32": {"value": ws * N / (d_ms * 1e-3), "unit": "columns/s", "ms_per_step": d_ms},
             "speedup_vs_fp64_plain": p64_ms / t_step,
-            "phases_ms": {"proposal": prop_ms, "select": sel_ms, "fill_and_kl": fill_ms},
+            "phases_ms": {"features": feat_ms, "mlp": mlp_ms, "topk": topk_ms, "select": sel_ms,
+                          "fill_and_kl": fill_ms},
             "setup_s": {"prep_host": prep_s, "train_proposal": train_s, "train_selections": n_sel,
                         "train_loss": [hist[0][1], hist[-1][1]]},
             "kernels": kernels,

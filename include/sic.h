@@ -224,6 +224,30 @@ sic_status sic_apply_factor(sic_handle* h, int64_t n, const int64_t* col_ptr, co
                             const double* val, sic_op op, const double* x, double* y, int32_t nrhs, void* ws,
                             size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------- preconditioning [device] -- */
+
+/* y = (Theta + shift I) x without forming Theta (O(n^2) kernel evaluations), x, y
+ * n x nrhs row-major FP64, 1 <= nrhs <= 8.  SIC_FP32_MIXED evaluates the kernel entries
+ * in FP32 (a fixed symmetric rounding of Theta) and sums the products with double-FP32
+ * compensated arithmetic (x split into two FP32 parts), tiles added in FP64; SIC_FP64
+ * is FP64 throughout (reference for small n).  x and y must not overlap. */
+sic_status sic_matern_matvec(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp, double shift,
+                             sic_precision prec, const double* x, double* y, int32_t nrhs, void* stream);
+
+/* Preconditioned conjugate gradients for (Theta + shift I) x = b, nrhs <= 8 right-hand
+ * sides solved together (the use of the factor as a preconditioner, Section 6.4):
+ * M^{-1} = L L^T from the CSC factor (col_ptr, row_idx, val), or no preconditioner when
+ * all three are NULL.  Starts from x = 0; a right-hand side stops when its recursively
+ * updated residual satisfies |r| / |b| < tol or after max_iter iterations.  iters[nrhs]
+ * and relres[nrhs] are HOST arrays receiving the iteration counts and final relative
+ * residuals.  The call synchronises the stream once per iteration (the loop runs on the
+ * host).  ws: sic_pcg_workspace bytes. */
+sic_status sic_pcg_workspace(int64_t n, int32_t nrhs, size_t* bytes);
+sic_status sic_pcg_solve(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp, double shift,
+                         sic_precision prec, const int64_t* col_ptr, const int32_t* row_idx, const double* val,
+                         const double* b, double* x, int32_t nrhs, double tol, int32_t max_iter, int32_t* iters,
+                         double* relres, void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------ learned proposal [device] -- */
 /*
  * Not part of the paper: a small MLP ranks each supernode's candidates so that the
@@ -231,11 +255,13 @@ sic_status sic_apply_factor(sic_handle* h, int64_t n, const int64_t* col_ptr, co
  * stays the reference (and the source of the training labels).
  *
  * Features: 8 FP32 per candidate, row-major feat[(cand_ptr[g] + r) * 8 + f], for the
- * group P = grp_ptr[g] .. grp_ptr[g+1]-1 (m <= 64 members) with ell = sqrt(ell2[g0])
- * (1 if not finite or zero), a* the nearest member (lowest index on ties), K the
- * kernel without nugget:  f0, f1 = (x_j - x_a*)[0], [1] / ell;  f2 = |x_j - x_a*| / ell;
- * f3 = |x_j - centroid(P)| / ell;  f4 = r / C;  f5 = K(|x_j - x_a*|) / variance;
- * f6 = m / 64;  f7 = mean over members of K(|x_j - x_a|) / variance.
+ * group P = grp_ptr[g] .. grp_ptr[g+1]-1 (m <= 64 members) with R the distance from
+ * the group's last (farthest) candidate to its nearest member (1 if zero), a* the
+ * nearest member (lowest index on ties), K the kernel without nugget:
+ * f0, f1 = (x_j - x_a*)[0], [1] / R;  f2 = |x_j - x_a*| / R;  f3 = |x_j - centroid(P)| / R;
+ * f4 = r / C;  f5 = K(|x_j - x_a*|) / variance;  f6 = m / 64;
+ * f7 = mean over members of K(|x_j - x_a|) / variance.  Computed in FP32 from
+ * coordinates taken relative to the group's first member in FP64.
  *
  * Network: s = w3 . gelu(W2^T gelu(W1^T f + b1) + b2) + b3 with exact (erf) GELU,
  * 8 -> 128 -> 128 -> 1.  Parameters are one flat FP32 array of sic_mlp_param_count()
@@ -244,11 +270,10 @@ sic_status sic_apply_factor(sic_handle* h, int64_t n, const int64_t* col_ptr, co
  */
 int32_t sic_mlp_param_count(void);
 
-/* feat must hold cand_ptr[n_grp] * 8 floats.  ell2[n] [device]: squared length scale
- * of each position (as returned by sic_prep_maximin, in the same order as pts). */
-sic_status sic_proposal_features(sic_handle* h, const double* pts, int64_t n, const double* ell2,
-                                 const sic_kernel* kp, const int64_t* grp_ptr, int64_t n_grp,
-                                 const int64_t* cand_ptr, const int32_t* cand_idx, float* feat, void* stream);
+/* feat must hold cand_ptr[n_grp] * 8 floats [device]. */
+sic_status sic_proposal_features(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                 const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr,
+                                 const int32_t* cand_idx, float* feat, void* stream);
 
 /* score[rows] = the network applied to feat[rows x 8] with BF16 weights and inputs and
  * FP32 accumulation on the tensor cores (the hidden activations are rounded to BF16 as

@@ -6,11 +6,12 @@ exact (erf) GELU, a weighted binary cross-entropy against plain-greedy labels an
 Plain numpy, unblocked; pinned by central finite differences in the tests.
 
 Features of candidate j (list rank r of C) for the group P = positions g0..g0+m-1,
-with ell = sqrt(ell2[g0]) (1 if not finite or zero), a* the nearest member (lowest
-index on ties), K the kernel without nugget and sigma^2 its variance:
-  f0, f1  (x_j - x_a*)[0], [1] / ell          (0 for a missing coordinate)
-  f2      |x_j - x_a*| / ell
-  f3      |x_j - mean_a x_a| / ell
+with R the distance from the last candidate of the list to its nearest member (1 if
+zero), a* the nearest member (lowest index on ties), K the kernel without nugget and
+sigma^2 its variance:
+  f0, f1  (x_j - x_a*)[0], [1] / R            (0 for a missing coordinate)
+  f2      |x_j - x_a*| / R
+  f3      |x_j - mean_a x_a| / R
   f4      r / C
   f5      K(|x_j - x_a*|) / sigma^2
   f6      m / 64
@@ -53,16 +54,15 @@ def matern_np(nu_x2, ell, s2, r):
     return s2 * (1 + t + t * t / 3) * np.exp(-t)
 
 
-def features(kp, pts, ell2, g0, m, cand):
+def features(kp, pts, g0, m, cand):
     """8 features of every candidate of one group (definitions in the module docstring)."""
     P = pts[g0:g0 + m]
     X = pts[np.asarray(cand, dtype=np.int64)]
     C = len(cand)
-    e2 = ell2[g0]
-    ell = math.sqrt(e2) if (np.isfinite(e2) and e2 > 0) else 1.0
     D = np.sqrt(((X[:, None, :] - P[None, :, :]) ** 2).sum(-1))  # C x m
     a = np.argmin(D, axis=1)
     dmin = D[np.arange(C), a]
+    ell = dmin[-1] if C and dmin[-1] > 0 else 1.0
     diff = X - P[a]
     f = np.zeros((C, N_FEAT))
     f[:, 0] = diff[:, 0] / ell

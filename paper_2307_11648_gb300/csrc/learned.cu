@@ -11,11 +11,13 @@
 //   training        FP32 forward/backward (strided tiled GEMM, split over K with a
 //                   fixed-order reduction), weighted BCE with logits, AdamW
 //
-// Feature definitions (ell = sqrt(ell2[g0]), or 1 if not finite / zero; a* the nearest
+// Feature definitions (R = distance from the last, i.e. farthest, candidate of the list to
+// its nearest member -- the group's candidate radius -- or 1 if zero; a* the nearest
 // member, lowest index on ties; K the kernel without nugget):
-//   f0, f1 = (x_j - x_a*)[0], [1] / ell;  f2 = |x_j - x_a*| / ell;
-//   f3 = |x_j - centroid| / ell;  f4 = rank / C;  f5 = K(|x_j - x_a*|) / sigma^2;
+//   f0, f1 = (x_j - x_a*)[0], [1] / R;  f2 = |x_j - x_a*| / R;
+//   f3 = |x_j - centroid| / R;  f4 = rank / C;  f5 = K(|x_j - x_a*|) / sigma^2;
 //   f6 = m / 64;  f7 = mean_a K(|x_j - x_a|) / sigma^2.
+// All features are O(1), whatever the group's scale.
 #include <cuda_bf16.h>
 
 #include "sic_internal.cuh"
@@ -34,14 +36,17 @@ __device__ __forceinline__ float dgelu_f(float z) {
 
 // ------------------------------------------------------------------ features --
 
-__global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts, long long n, int dim,
-                                                  const double* __restrict__ ell2, KP<double> kp,
+__global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts, long long n, int dim, KP<float> kp,
                                                   const long long* __restrict__ grp_ptr, long long n_grp,
                                                   const long long* __restrict__ cand_ptr,
                                                   const int32_t* __restrict__ cand_idx, float* __restrict__ feat,
                                                   DevStatus* st) {
-    __shared__ double mx[64 * 3];
-    __shared__ double cen[3];
+    // member coordinates relative to the first member (formed in FP64, kept in FP32),
+    // so that candidate-member differences keep their digits in FP32
+    __shared__ float mx[64 * 3];
+    __shared__ float cen[3];
+    __shared__ float s_ri;
+    __shared__ double org[3];
     for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
         const long long g0 = grp_ptr[g];
         const int m = (int)(grp_ptr[g + 1] - g0);
@@ -51,20 +56,39 @@ __global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts
             if (threadIdx.x == 0) record_error(st, SIC_ERR_INVALID, g);
             continue;
         }
+        if (threadIdx.x < 3) org[threadIdx.x] = ((int)threadIdx.x < dim) ? pts[g0 * dim + threadIdx.x] : 0.0;
+        __syncthreads();
         for (int i = threadIdx.x; i < m * 3; i += blockDim.x) {
             int a = i / 3, d = i % 3;
-            mx[i] = (d < dim) ? pts[(g0 + a) * dim + d] : 0.0;
+            mx[i] = (d < dim) ? (float)(pts[(g0 + a) * dim + d] - org[d]) : 0.f;
         }
         __syncthreads();
         if (threadIdx.x < 3) {
-            double s = 0.0;
+            float s = 0.f;
             for (int a = 0; a < m; ++a) s += mx[a * 3 + threadIdx.x];
-            cen[threadIdx.x] = s / m;
+            cen[threadIdx.x] = s / (float)m;
+        }
+        if (threadIdx.x == 32) {
+            // candidate radius: nearest-member distance of the last candidate
+            float R = 0.f;
+            if (C > 0) {
+                const long long pl = cand_idx[b0 + C - 1];
+                if (pl >= 0 && pl < n) {
+                    float xl[3];
+                    for (int d = 0; d < 3; ++d) xl[d] = (d < dim) ? (float)(pts[pl * dim + d] - org[d]) : 0.f;
+                    float best = INFINITY;
+                    for (int a = 0; a < m; ++a) {
+                        float dx = xl[0] - mx[a * 3], dy = xl[1] - mx[a * 3 + 1], dz = xl[2] - mx[a * 3 + 2];
+                        best = fminf(best, dx * dx + dy * dy + dz * dz);
+                    }
+                    R = sqrtf(best);
+                }
+            }
+            s_ri = (R > 0.f) ? 1.f / R : 1.f;
         }
         __syncthreads();
-        const double e2 = ell2[g0];
-        const double ell = (isfinite(e2) && e2 > 0.0) ? sqrt(e2) : 1.0;
-        const double ri = 1.0 / ell;
+        const float ri = s_ri;
+        const float inv_s2 = 1.f / kp.s2, inv_m = 1.f / (float)m;
         for (int r = threadIdx.x; r < C; r += blockDim.x) {
             const long long p = cand_idx[b0 + r];
             float* f = feat + (b0 + r) * NF;
@@ -73,26 +97,26 @@ __global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts
                 for (int q = 0; q < NF; ++q) f[q] = 0.f;
                 continue;
             }
-            double x[3];
-            for (int d = 0; d < 3; ++d) x[d] = (d < dim) ? pts[p * dim + d] : 0.0;
-            double best = INFINITY, ksum = 0.0;
+            float x[3];
+            for (int d = 0; d < 3; ++d) x[d] = (d < dim) ? (float)(pts[p * dim + d] - org[d]) : 0.f;
+            float best = INFINITY, ksum = 0.f;
             int ab = 0;
             for (int a = 0; a < m; ++a) {
-                double dx = x[0] - mx[a * 3], dy = x[1] - mx[a * 3 + 1], dz = x[2] - mx[a * 3 + 2];
-                double d2 = dx * dx + dy * dy + dz * dz;
-                ksum += matern<double>(kp, sqrt(d2));
+                float dx = x[0] - mx[a * 3], dy = x[1] - mx[a * 3 + 1], dz = x[2] - mx[a * 3 + 2];
+                float d2 = dx * dx + dy * dy + dz * dz;
+                ksum += matern<float>(kp, sqrtf(d2));
                 if (d2 < best) { best = d2; ab = a; }
             }
-            const double dmin = sqrt(best);
-            double cx = x[0] - cen[0], cy = x[1] - cen[1], cz = x[2] - cen[2];
-            f[0] = (float)((x[0] - mx[ab * 3]) * ri);
-            f[1] = (float)((x[1] - mx[ab * 3 + 1]) * ri);
-            f[2] = (float)(dmin * ri);
-            f[3] = (float)(sqrt(cx * cx + cy * cy + cz * cz) * ri);
-            f[4] = (float)((double)r / (double)C);
-            f[5] = (float)(matern<double>(kp, dmin) / kp.s2);
-            f[6] = (float)((double)m / 64.0);
-            f[7] = (float)(ksum / ((double)m * kp.s2));
+            const float dmin = sqrtf(best);
+            float cx = x[0] - cen[0], cy = x[1] - cen[1], cz = x[2] - cen[2];
+            f[0] = (x[0] - mx[ab * 3]) * ri;
+            f[1] = (x[1] - mx[ab * 3 + 1]) * ri;
+            f[2] = dmin * ri;
+            f[3] = sqrtf(cx * cx + cy * cy + cz * cz) * ri;
+            f[4] = (float)r / (float)C;
+            f[5] = matern<float>(kp, dmin) * inv_s2;
+            f[6] = (float)m * (1.f / 64.f);
+            f[7] = ksum * inv_m * inv_s2;
         }
         __syncthreads();
     }
@@ -531,17 +555,16 @@ void gemm(cudaStream_t s, int M, int N, int K, const float* A, long long sam, lo
 
 // ---------------------------------------------------------------- entry points --
 
-extern "C" sic_status sic_proposal_features(sic_handle* h, const double* pts, int64_t n, const double* ell2,
-                                            const sic_kernel* kp, const int64_t* grp_ptr, int64_t n_grp,
+extern "C" sic_status sic_proposal_features(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp, const int64_t* grp_ptr, int64_t n_grp,
                                             const int64_t* cand_ptr, const int32_t* cand_idx, float* feat,
                                             void* stream) {
-    if (!h || !pts || n < 1 || !ell2 || !sic_valid_kernel(kp) || !grp_ptr || n_grp < 1 || !cand_ptr || !cand_idx ||
+    if (!h || !pts || n < 1 || !sic_valid_kernel(kp) || !grp_ptr || n_grp < 1 || !cand_ptr || !cand_idx ||
         !feat)
         return SIC_ERR_INVALID;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
     int grid = persistent_grid(h, k_features, 256, 0, n_grp);
-    k_features<<<grid, 256, 0, s>>>(pts, n, kp->dim, ell2, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp,
+    k_features<<<grid, 256, 0, s>>>(pts, n, kp->dim, make_kp<float>(*kp), (const long long*)grp_ptr, n_grp,
                                     (const long long*)cand_ptr, cand_idx, feat, h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;

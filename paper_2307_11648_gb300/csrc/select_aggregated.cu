@@ -29,6 +29,23 @@ __device__ __forceinline__ bool better(T s, int i, T bs, int bi) {
     return s > bs || (s == bs && i < bi);
 }
 
+// acc - sum_{tau < len} col[tau * ld] * piv[tau], with four independent partial sums so
+// that the loads of consecutive terms are in flight together
+template <typename T>
+__device__ __forceinline__ T dot_down(T acc, const T* __restrict__ col, long long ld, const T* __restrict__ piv,
+                                      int len) {
+    T a1 = (T)0, a2 = (T)0, a3 = (T)0;
+    int tau = 0;
+    for (; tau + 4 <= len; tau += 4) {
+        acc = fma(-col[(long long)tau * ld], piv[tau], acc);
+        a1 = fma(-col[(long long)(tau + 1) * ld], piv[tau + 1], a1);
+        a2 = fma(-col[(long long)(tau + 2) * ld], piv[tau + 2], a2);
+        a3 = fma(-col[(long long)(tau + 3) * ld], piv[tau + 3], a3);
+    }
+    for (; tau < len; ++tau) acc = fma(-col[(long long)tau * ld], piv[tau], acc);
+    return (acc + a1) + (a2 + a3);
+}
+
 struct AggLayout {
     long long Cm, mm, k;
     __host__ __device__ long long f1() const { return 0; }
@@ -50,7 +67,7 @@ inline AggLayout agg_layout(int max_cand, int max_m, int k) {
 }
 
 template <typename T, int NT, bool SMEM>
-__global__ void __launch_bounds__(NT) k_select_agg(
+__global__ void __launch_bounds__(NT, 1) k_select_agg(
     const double* __restrict__ pts, long long n, int dim, KP<T> kp, T floor_, const long long* __restrict__ grp_ptr,
     long long n_grp, const long long* __restrict__ cand_ptr, const int32_t* __restrict__ cand_idx, int max_cand,
     int max_m, int k, int32_t* __restrict__ sel_idx, int32_t* __restrict__ sel_count, T* __restrict__ ws,
@@ -133,7 +150,7 @@ __global__ void __launch_bounds__(NT) k_select_agg(
                 if (i < C) {
                     T dx = X[i] - ax, dy = X[ldx + i] - ay, dz = X[2 * ldx + i] - az;
                     T num = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
-                    for (int b = 0; b < a; ++b) num = fma(-F2c[(long long)b * Cm + i], p2[b], num);
+                    num = dot_down(num, F2c + i, Cm, p2, a);
                     const T u = num * rs;
                     F2c[(long long)a * Cm + i] = u;
                     V2[i] = fma(-u, u, V2[i]);
@@ -148,7 +165,7 @@ __global__ void __launch_bounds__(NT) k_select_agg(
                         const long long xt = Cm + ta;
                         T dx = X[xt] - ax, dy = X[ldx + xt] - ay, dz = X[2 * ldx + xt] - az;
                         T num = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
-                        for (int b = 0; b < a; ++b) num = fma(-F2t[(long long)b * mm + ta], p2[b], num);
+                        num = dot_down(num, F2t + ta, mm, p2, a);
                         u = num * rs;
                     }
                     F2t[(long long)a * mm + ta] = u;
@@ -198,9 +215,8 @@ __global__ void __launch_bounds__(NT) k_select_agg(
                     T dx = X[r] - qx, dy = X[ldx + r] - qy, dz = X[2 * ldx + r] - qz;
                     T th = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
                     if (r == q) th += kp.nugget;
-                    T n1 = th, n2 = th;
-                    for (int tau = 0; tau < t; ++tau) n1 = fma(-F1[(long long)tau * Cm + r], p1[tau], n1);
-                    for (int tau = 0; tau < m + t; ++tau) n2 = fma(-F2c[(long long)tau * Cm + r], p2[tau], n2);
+                    const T n1 = dot_down(th, F1 + r, Cm, p1, t);
+                    const T n2 = dot_down(th, F2c + r, Cm, p2, m + t);
                     const T u1 = n1 * r1, u2 = n2 * r2;
                     F1[(long long)t * Cm + r] = u1;
                     F2c[(long long)(m + t) * Cm + r] = u2;

@@ -56,15 +56,24 @@ class Proposal:
                     out_ptr=torch.empty(G + 1, dtype=torch.int64, device=dev),
                     out_idx=torch.empty(max(G * self.top, 1), dtype=torch.int32, device=dev))
 
-    def run(self, dp: pipeline.DeviceProblem, ell2, buf, stream=None):
-        """features -> scores -> per-group top-k; fills buf['out_ptr'], buf['out_idx']."""
+    def features(self, dp, buf, stream=None):
         hp = dp.hp
         rows = int(hp.cand_ptr[-1])
-        feat = buf["feat"][:rows]
-        sic.proposal_features(self.h, dp.pts, ell2, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, feat, stream)
-        sic.proposal_score(self.h, self.params, feat, buf["score"][:rows], self.ws_score, stream)
-        sic.proposal_topk(self.h, dp.cand_ptr, dp.cand_idx, buf["score"], self.top, buf["out_ptr"],
-                          buf["out_idx"], stream)
+        sic.proposal_features(self.h, dp.pts, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, buf["feat"][:rows], stream)
+
+    def score(self, dp, buf, stream=None):
+        rows = int(dp.hp.cand_ptr[-1])
+        sic.proposal_score(self.h, self.params, buf["feat"][:rows], buf["score"][:rows], self.ws_score, stream)
+
+    def topk(self, dp, buf, stream=None):
+        sic.proposal_topk(self.h, dp.cand_ptr, dp.cand_idx, buf["score"], self.top, buf["out_ptr"], buf["out_idx"],
+                          stream)
+
+    def run(self, dp: pipeline.DeviceProblem, buf, stream=None):
+        """features -> scores -> per-group top-k; fills buf['out_ptr'], buf['out_idx']."""
+        self.features(dp, buf, stream)
+        self.score(dp, buf, stream)
+        self.topk(dp, buf, stream)
 
 
 def reduced_problem(hp: pipeline.HostProblem, top: int) -> pipeline.HostProblem:
@@ -86,7 +95,6 @@ class LearnedFactorBuilder:
         self.buf = proposal.buffers(hp)
         self.rhp = reduced_problem(hp, proposal.top)
         self.fb = pipeline.FactorBuilder(h, self.rhp, prec, device)
-        self.ell2 = torch.from_numpy(hp.ell2).to(device)
         self.rdp = None
 
     def _reduced_device(self, dp):
@@ -100,7 +108,7 @@ class LearnedFactorBuilder:
         return self.rdp
 
     def propose(self, dp, stream=None):
-        self.proposal.run(dp, self.ell2, self.buf, stream)
+        self.proposal.run(dp, self.buf, stream)
 
     def select(self, dp, stream=None):
         self.propose(dp, stream)
@@ -143,8 +151,7 @@ def training_set(h: sic.Handle, problems, prec=sic.SIC_FP32_MIXED, device="cuda"
         rows = int(hp.cand_ptr[-1])
         f = torch.empty((rows, N_FEAT), dtype=torch.float32, device=device)
         y = torch.empty(rows, dtype=torch.float32, device=device)
-        ell2 = torch.from_numpy(hp.ell2).to(device)
-        sic.proposal_features(h, dp.pts, ell2, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, f)
+        sic.proposal_features(h, dp.pts, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, f)
         sic.proposal_labels(h, dp.cand_ptr, dp.cand_idx, fb.sel_idx, fb.sel_count, hp.k, y)
         h.sync()
         n_sel += int(fb.sel_count.sum().item())

@@ -29,6 +29,7 @@ EXPORTS = [
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
+    "sic_matern_matvec", "sic_pcg_workspace", "sic_pcg_solve",
     "sic_mlp_param_count", "sic_proposal_features", "sic_proposal_score_workspace", "sic_proposal_score",
     "sic_proposal_topk", "sic_proposal_labels", "sic_mlp_train_workspace", "sic_mlp_grads", "sic_adamw_step",
 ]
@@ -88,8 +89,11 @@ def lib():
             "sic_build_factor": (st, [vp, vp, i64, pk, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
             "sic_apply_factor_workspace": (st, [i64, i32, st, C.POINTER(sz)]),
             "sic_apply_factor": (st, [vp, i64, vp, vp, vp, st, vp, vp, i32, vp, sz, vp]),
+            "sic_matern_matvec": (st, [vp, vp, i64, pk, d, st, vp, vp, i32, vp]),
+            "sic_pcg_workspace": (st, [i64, i32, C.POINTER(sz)]),
+            "sic_pcg_solve": (st, [vp, vp, i64, pk, d, st, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp, sz, vp]),
             "sic_mlp_param_count": (i32, []),
-            "sic_proposal_features": (st, [vp, vp, i64, vp, pk, vp, i64, vp, vp, vp, vp]),
+            "sic_proposal_features": (st, [vp, vp, i64, pk, vp, i64, vp, vp, vp, vp]),
             "sic_proposal_score_workspace": (st, [C.POINTER(sz)]),
             "sic_proposal_score": (st, [vp, vp, vp, i64, vp, vp, sz, vp]),
             "sic_proposal_topk": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),
@@ -355,10 +359,9 @@ def mlp_param_count() -> int:
     return int(lib().sic_mlp_param_count())
 
 
-def proposal_features(h: Handle, pts, ell2, kp: Kernel, grp_ptr, cand_ptr, cand_idx, feat, stream=None):
+def proposal_features(h: Handle, pts, kp: Kernel, grp_ptr, cand_ptr, cand_idx, feat, stream=None):
     import torch
-    _check(lib().sic_proposal_features(h.ptr, _dptr(pts, torch.float64, "pts"), pts.shape[0],
-                                       _dptr(ell2, torch.float64, "ell2"), C.byref(kp),
+    _check(lib().sic_proposal_features(h.ptr, _dptr(pts, torch.float64, "pts"), pts.shape[0], C.byref(kp),
                                        _dptr(grp_ptr, torch.int64, "grp_ptr"), grp_ptr.numel() - 1,
                                        _dptr(cand_ptr, torch.int64, "cand_ptr"),
                                        _dptr(cand_idx, torch.int32, "cand_idx"), _dptr(feat, torch.float32, "feat"),
@@ -418,3 +421,35 @@ def adamw_step(h: Handle, params, m, v, grads, step: int, lr: float, beta1=0.9, 
     _check(lib().sic_adamw_step(h.ptr, _dptr(params, torch.float32), _dptr(m, torch.float32), _dptr(v, torch.float32),
                                 _dptr(grads, torch.float32), params.numel(), int(step), float(lr), float(beta1),
                                 float(beta2), float(eps), float(wd), _stream(stream)), "sic_adamw_step", h)
+
+
+# -------------------------------------------------------- preconditioning --
+
+def matern_matvec(h: Handle, pts, kp: Kernel, shift: float, prec: int, x, y, stream=None):
+    import torch
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    _check(lib().sic_matern_matvec(h.ptr, _dptr(pts, torch.float64, "pts"), pts.shape[0], C.byref(kp), float(shift),
+                                   prec, _dptr(x, torch.float64, "x"), _dptr(y, torch.float64, "y"), nrhs,
+                                   _stream(stream)), "sic_matern_matvec", h)
+
+
+def pcg_workspace(n: int, nrhs: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sic_pcg_workspace(n, nrhs, C.byref(b)), "sic_pcg_workspace")
+    return b.value
+
+
+def pcg_solve(h: Handle, pts, kp: Kernel, shift: float, prec: int, factor, b, x, tol: float, max_iter: int, ws,
+              stream=None):
+    """factor = (col_ptr, row_idx, val) device tensors or None.  Returns (iters, relres) numpy arrays."""
+    import torch
+    nrhs = 1 if b.dim() == 1 else b.shape[1]
+    iters = np.zeros(nrhs, np.int32)
+    relres = np.zeros(nrhs, np.float64)
+    cp, ri, vv = factor if factor is not None else (None, None, None)
+    _check(lib().sic_pcg_solve(h.ptr, _dptr(pts, torch.float64, "pts"), pts.shape[0], C.byref(kp), float(shift), prec,
+                               _dptr(cp, torch.int64, "col_ptr"), _dptr(ri, torch.int32, "row_idx"),
+                               _dptr(vv, torch.float64, "val"), _dptr(b, torch.float64, "b"),
+                               _dptr(x, torch.float64, "x"), nrhs, float(tol), int(max_iter), _hptr(iters, np.int32),
+                               _hptr(relres, np.float64), _dptr(ws), ws.numel(), _stream(stream)), "sic_pcg_solve", h)
+    return iters, relres

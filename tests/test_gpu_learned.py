@@ -1,6 +1,6 @@
 """GPU tests of the learned proposal against the FP64 oracle (oracle/learned.py).
 
-Tolerances: features are FP32 roundings of FP64 values (rel 1e-6); FP32 gradients
+Tolerances: features are computed in FP32 (kernel values with the FP32 exponential), 2e-5; FP32 gradients
 without BF16 rounding agree with the FP64 oracle to rel 1e-3 of the largest gradient
 entry (FP32 accumulation over the batch); with BF16 rounding (as inference) the stated
 BF16 tolerance is a relative L2 error of 3e-2 on the whole gradient; tensor-core scores
@@ -45,8 +45,7 @@ def test_features_match_oracle(env, oracle_lib):
     dp = pipeline.DeviceProblem(hp)
     rows = int(hp.cand_ptr[-1])
     feat = torch.empty((rows, 8), dtype=torch.float32, device="cuda")
-    sic.proposal_features(h, dp.pts, torch.from_numpy(hp.ell2).cuda(), hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx,
-                          feat)
+    sic.proposal_features(h, dp.pts, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, feat)
     h.sync()
     F = feat.cpu().numpy()
     okp = oracle_lib.kernel(2, 3, 0.05, 1.0, 1e-6)
@@ -54,8 +53,15 @@ def test_features_match_oracle(env, oracle_lib):
     for g in range(len(gp) - 1):
         g0, g1 = int(gp[g]), int(gp[g + 1])
         a, b = hp.cand_ptr[g], hp.cand_ptr[g + 1]
-        ref = OL.features(okp, hp.pts, hp.ell2, g0, g1 - g0, hp.cand_idx[a:b])
-        assert np.allclose(F[a:b], ref, rtol=1e-6, atol=1e-6), g
+        cand = hp.cand_idx[a:b]
+        ref = OL.features(okp, hp.pts, g0, g1 - g0, cand)
+        # rows whose two nearest members are within FP32 resolution of each other may
+        # name a different nearest member: skip their offset features f0, f1
+        D = np.sort(np.sqrt(((hp.pts[cand][:, None, :] - hp.pts[g0:g1][None, :, :]) ** 2).sum(-1)), axis=1)
+        amb = (D[:, 1] - D[:, 0] <= 1e-5 * D[:, 1]) if g1 - g0 > 1 else np.zeros(len(cand), bool)
+        err = np.abs(F[a:b] - ref)
+        err[amb, :2] = 0
+        assert np.all(err <= 2e-5 * np.maximum(1.0, np.abs(ref))), g
 
 
 @pytest.mark.parametrize("bf16", [False, True])

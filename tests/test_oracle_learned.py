@@ -57,9 +57,8 @@ def test_features_on_a_hand_made_group():
     from oracle import kernel
     kp = kernel(2, 3, 0.5, 2.0, 0.0)
     pts = np.array([[0.0, 0.0], [0.2, 0.0], [0.3, 0.4], [1.0, 1.0], [0.0, 0.1]])
-    ell2 = np.array([0.04, 0.09, np.inf, np.inf, np.inf])
-    f = OL.features(kp, pts, ell2, 0, 2, [2, 3, 4])
-    ell = 0.2
+    f = OL.features(kp, pts, 0, 2, [2, 3, 4])
+    ell = 0.1  # the last candidate (0, 0.1) is at distance 0.1 from its nearest member
     # candidate 2 (0.3, 0.4): nearest member is point 1 (0.2, 0): offset (0.1, 0.4)
     assert f[0, 0] == pytest.approx(0.1 / ell) and f[0, 1] == pytest.approx(0.4 / ell)
     assert f[0, 2] == pytest.approx(math.hypot(0.1, 0.4) / ell)
@@ -70,3 +69,4 @@ def test_features_on_a_hand_made_group():
     t = math.sqrt(3) * 0.1 / 0.5
     assert f[2, 5] == pytest.approx((1 + t) * math.exp(-t))
     assert f[2, 7] <= f[2, 5] + 1e-15
+    assert f[2, 2] == pytest.approx(1.0)

@@ -358,3 +358,22 @@ def test_apply_factor_dense(oracle_lib, op):
     x = synthetic.normal(1, n * 3).reshape(n, 3)
     ref = [L @ x, L.T @ x, L @ (L.T @ x)][op]
     assert np.allclose(oracle.apply_factor(n, cp, ri, val, op, x), ref, rtol=1e-12, atol=1e-12)
+
+
+def test_pcg_oracle_textbook_properties():
+    """CG terminates in as many iterations as the matrix has distinct eigenvalues, and the
+    preconditioned solve agrees with a direct solve."""
+    from oracle.pcg import pcg
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    eig = np.repeat([1.0, 4.0, 9.0], 10)
+    A = Q @ np.diag(eig) @ Q.T
+    b = rng.standard_normal(30)
+    x, it, rel = pcg(A, b, tol=1e-12)
+    assert it == 3 and np.allclose(A @ x, b, atol=1e-10)
+    B = rng.standard_normal((40, 40))
+    A2 = B @ B.T + 40 * np.eye(40)
+    M = np.diag(1 / np.diag(A2))
+    x2, it2, _ = pcg(A2, b[:20].repeat(2), Minv=M, tol=1e-12)
+    assert np.allclose(x2, np.linalg.solve(A2, b[:20].repeat(2)), rtol=1e-9)
+    assert it2 <= 40
