@@ -192,6 +192,66 @@ def problem(cfg, seed, n=None):
     return pipeline.prepare_groups(pts, kp, cfg["n_cand"], cfg["k"], cfg["m_min"], cfg["m_max"])
 
 
+def truncated(hp, top):
+    """The same problem with every candidate list cut to its first `top` (nearest) entries."""
+    from paper_2307_11648_gb300 import pipeline
+    cnt = np.minimum(np.diff(hp.cand_ptr), top)
+    ptr = np.zeros(len(cnt) + 1, np.int64)
+    ptr[1:] = np.cumsum(cnt)
+    idx = np.concatenate([hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g] + cnt[g]] for g in range(len(cnt))])
+    return pipeline.HostProblem(hp.pts, hp.kp, hp.k, ptr, idx, hp.grp_ptr, hp.order, hp.ell2)
+
+
+def pcg_comparison(h, cfg, params, n, nrhs=8, shift=1e-4, tol=1e-8):
+    """Config-5 style comparison: CG on (Theta + shift I) x = b, b ~ N(0, 1), with the factors of
+    that matrix from the learned proposal, plain greedy and k nearest neighbours (first k
+    candidates) as preconditioners, and without; FP32-entry matvec with compensated sums."""
+    import torch
+
+    from paper_2307_11648_gb300 import learned, pipeline, sic
+    ell = cfg["length_scale"] * math.sqrt(cfg["n"] / n)
+    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], ell, cfg["variance"], cfg["nugget"] + shift)
+    hp = pipeline.prepare_groups(synthetic.points(n, cfg["dim"], cfg["seed"]), kp, cfg["n_cand"], cfg["k"],
+                                 cfg["m_min"], cfg["m_max"])
+    dp = pipeline.DeviceProblem(hp)
+    B = torch.from_numpy(synthetic.normal(7, n * nrhs).reshape(n, nrhs)).cuda()
+    ws = sic._ws(sic.pcg_workspace(n, nrhs), "cuda")
+    out = {"n": n, "nrhs": nrhs, "tol": tol, "system": f"Theta (nugget {cfg['nugget']}) + {shift} I; factors of the "
+           "same matrix; k=64, C=1024"}
+
+    def solve(factor, cap):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, rel = sic.pcg_solve(h, dp.pts, kp, 0.0, sic.SIC_FP32_MIXED, factor, B, torch.empty_like(B), tol, cap, ws)
+        return its.tolist(), float(np.max(rel)), 1e3 * (time.perf_counter() - t0)
+
+    def csc(fb):
+        nnz = int(fb.col_ptr[-1].item())
+        return (fb.col_ptr, fb.row_idx[:nnz].contiguous(), fb.val[:nnz].contiguous())
+
+    lb = learned.LearnedFactorBuilder(h, hp, learned.Proposal(h, params, top=4 * cfg["k"]), sic.SIC_FP32_MIXED)
+    lb.run(dp)
+    out["learned"] = solve(csc(lb.fb), 1000)
+    del lb
+    fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
+    fb.run(dp)
+    out["conditional"] = solve(csc(fb), 1000)
+    U, k = hp.n_units, hp.k
+    sel = np.full((U, k), -1, np.int32)
+    cnt = np.zeros(U, np.int32)
+    for g in range(U):
+        c = hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]][:k]
+        sel[g, :len(c)] = c
+        cnt[g] = len(c)
+    fb.sel_idx.copy_(torch.from_numpy(sel.ravel()))
+    fb.sel_count.copy_(torch.from_numpy(cnt))
+    fb.fill(dp)
+    out["knn"] = solve(csc(fb), 1000)
+    out["none"] = solve(None, 300)
+    out["legend"] = "[iterations per right-hand side, max final relative residual, wall ms]; 'none' capped at 300"
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -231,6 +291,10 @@ def main():
     ap.add_argument("--epochs", type=int, default=3)
     ap.add_argument("--case-only", type=int, default=0, metavar="N",
                     help="profiling case: one FP32-mixed supernodal factor build at N points, no timing")
+    ap.add_argument("--case-top", type=int, default=0,
+                    help="with --case-only: keep only the first TOP candidates of each list (the selection "
+                         "kernel of the proposal path)")
+    ap.add_argument("--pcg-n", type=int, default=1 << 16, help="points of the preconditioning comparison (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if ws > 1:
@@ -252,6 +316,8 @@ def main():
     if args.case_only:
         # one FP32-mixed supernodal factor build at the requested size (for ncu captures)
         hp = problem(cfg, cfg["seed"], args.case_only)
+        if args.case_top:
+            hp = truncated(hp, args.case_top)
         h = sic.Handle(local)
         dp = pipeline.DeviceProblem(hp)
         fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
@@ -403,6 +469,10 @@ def main():
                 "unit": "TFLOP/s", "frac": sel_tf / f32_peak, "traffic": None,
                 "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz (derived; measured probe 75 TFLOP/s)"}
 
+    pcg = None
+    if args.pcg_n and rank == 0:
+        pcg = pcg_comparison(h, cfg, params, args.pcg_n)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -443,6 +513,7 @@ def main():
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": 15 * args.steps,
             "clocks": clocks,
+            "pcg": pcg,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -46,24 +46,62 @@ __device__ __forceinline__ T dot_down(T acc, const T* __restrict__ col, long lon
     return (acc + a1) + (a2 + a3);
 }
 
+// Shared-memory variant: factor rows are row-major with a pitch of 4 (mod 32) elements, so
+// that a thread reads its own row, and every thread the broadcast pivot row, with 128-bit
+// loads without bank conflicts.  Workspace variant: column-major [column][row], so that
+// the threads of a warp touch consecutive addresses.
+__host__ __device__ inline long long pitch4(long long x) { return ((x + 27) / 32) * 32 + 4; }
+
 struct AggLayout {
     long long Cm, mm, k;
+    bool rowmajor;
+    __host__ __device__ long long p1() const { return pitch4(k); }
+    __host__ __device__ long long p2() const { return pitch4(mm + k); }
+    __host__ __device__ long long p2t() const { return pitch4(mm); }
     __host__ __device__ long long f1() const { return 0; }
-    __host__ __device__ long long f2c() const { return k * Cm; }
-    __host__ __device__ long long f2t() const { return f2c() + (mm + k) * Cm; }
-    __host__ __device__ long long x() const { return f2t() + mm * mm; }
+    __host__ __device__ long long f2c() const { return rowmajor ? Cm * p1() : k * Cm; }
+    __host__ __device__ long long f2t() const { return f2c() + (rowmajor ? Cm * p2() : (mm + k) * Cm); }
+    __host__ __device__ long long x() const { return f2t() + (rowmajor ? mm * p2t() : mm * mm); }
     __host__ __device__ long long v1() const { return x() + 3 * (Cm + mm); }
     __host__ __device__ long long v2() const { return v1() + Cm; }
-    __host__ __device__ long long size() const { return v2() + Cm; }
+    __host__ __device__ long long size() const { return (v2() + Cm + 3) / 4 * 4; }
 };
 
-inline AggLayout agg_layout(int max_cand, int max_m, int k) {
+inline AggLayout agg_layout(int max_cand, int max_m, int k, bool rowmajor) {
     AggLayout L;
     L.Cm = ((long long)max_cand + 31) / 32 * 32;
     if (L.Cm < 32) L.Cm = 32;
     L.mm = max_m;
     L.k = k;
+    L.rowmajor = rowmajor;
     return L;
+}
+
+// acc - sum_{tau < len} row[tau] * piv[tau] over a contiguous row (shared memory)
+template <typename T>
+__device__ __forceinline__ T dot_row(T acc, const T* __restrict__ row, const T* __restrict__ piv, int len) {
+    T a1 = (T)0, a2 = (T)0, a3 = (T)0;
+    int tau = 0;
+    if constexpr (sizeof(T) == 4) {
+        const float4* r4 = reinterpret_cast<const float4*>(row);
+        const float4* p4 = reinterpret_cast<const float4*>(piv);
+        for (; tau + 4 <= len; tau += 4) {
+            const float4 a = r4[tau >> 2], b = p4[tau >> 2];
+            acc = fmaf(-a.x, b.x, acc);
+            a1 = fmaf(-a.y, b.y, a1);
+            a2 = fmaf(-a.z, b.z, a2);
+            a3 = fmaf(-a.w, b.w, a3);
+        }
+    } else {
+        for (; tau + 4 <= len; tau += 4) {
+            acc = fma(-row[tau], piv[tau], acc);
+            a1 = fma(-row[tau + 1], piv[tau + 1], a1);
+            a2 = fma(-row[tau + 2], piv[tau + 2], a2);
+            a3 = fma(-row[tau + 3], piv[tau + 3], a3);
+        }
+    }
+    for (; tau < len; ++tau) acc = fma(-row[tau], piv[tau], acc);
+    return (acc + a1) + (a2 + a3);
 }
 
 template <typename T, int NT, bool SMEM>
@@ -76,13 +114,18 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     T* base = SMEM ? sm : ws + (long long)blockIdx.x * L.size();
-    T* p1 = SMEM ? sm + L.size() : sm;  // k
-    T* p2 = p1 + k;                      // max_m + k
+    T* p1 = SMEM ? sm + L.size() : sm;       // k (16-byte aligned: L.size() is a multiple of 4)
+    T* p2 = p1 + (k + 3) / 4 * 4;             // max_m + k
     __shared__ T wsc[NW];
     __shared__ int wix[NW];
     __shared__ int s_fail;
 
     const long long Cm = L.Cm, mm = L.mm, ldx = L.Cm + L.mm;
+    const long long P1 = L.p1(), P2 = L.p2(), P2t = L.p2t();
+    // element (row, column) of F1, F2c (candidate rows) and F2t (target rows)
+#define E1(r, c) (SMEM ? F1[(long long)(r) * P1 + (c)] : F1[(long long)(c) * Cm + (r)])
+#define E2(r, c) (SMEM ? F2c[(long long)(r) * P2 + (c)] : F2c[(long long)(c) * Cm + (r)])
+#define E2T(a, c) (SMEM ? F2t[(long long)(a) * P2t + (c)] : F2t[(long long)(c) * mm + (a)])
     T* F1 = base + L.f1();
     T* F2c = base + L.f2c();
     T* F2t = base + L.f2t();
@@ -131,7 +174,7 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
 
         // ---- the target columns of F2 (left-looking Cholesky of the targets) ----
         for (int a = 0; a < m; ++a) {
-            if (tid < a) p2[tid] = F2t[(long long)tid * mm + a];
+            if (tid < a) p2[tid] = E2T(a, tid);
             __syncthreads();
             T dv = diag;
             for (int b = 0; b < a; ++b) dv = fma(-p2[b], p2[b], dv);
@@ -150,9 +193,9 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                 if (i < C) {
                     T dx = X[i] - ax, dy = X[ldx + i] - ay, dz = X[2 * ldx + i] - az;
                     T num = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
-                    num = dot_down(num, F2c + i, Cm, p2, a);
+                    num = SMEM ? dot_row(num, F2c + (long long)i * P2, p2, a) : dot_down(num, F2c + i, Cm, p2, a);
                     const T u = num * rs;
-                    F2c[(long long)a * Cm + i] = u;
+                    E2(i, a) = u;
                     V2[i] = fma(-u, u, V2[i]);
                 } else {
                     const int ta = i - C;
@@ -165,10 +208,10 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                         const long long xt = Cm + ta;
                         T dx = X[xt] - ax, dy = X[ldx + xt] - ay, dz = X[2 * ldx + xt] - az;
                         T num = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
-                        num = dot_down(num, F2t + ta, mm, p2, a);
+                        num = SMEM ? dot_row(num, F2t + (long long)ta * P2t, p2, a) : dot_down(num, F2t + ta, mm, p2, a);
                         u = num * rs;
                     }
-                    F2t[(long long)a * mm + ta] = u;
+                    E2T(ta, a) = u;
                 }
             }
             __syncthreads();
@@ -205,8 +248,8 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                 if (q == 0x7fffffff) break;
                 const T v1q = V1[q], v2q = V2[q];
                 const T qx = X[q], qy = X[ldx + q], qz = X[2 * ldx + q];
-                for (int tau = tid; tau < t; tau += NT) p1[tau] = F1[(long long)tau * Cm + q];
-                for (int tau = tid; tau < m + t; tau += NT) p2[tau] = F2c[(long long)tau * Cm + q];
+                for (int tau = tid; tau < t; tau += NT) p1[tau] = E1(q, tau);
+                for (int tau = tid; tau < m + t; tau += NT) p2[tau] = E2(q, tau);
                 __syncthreads();
                 const T r1 = (T)1 / sic_sqrt(v1q);
                 const T r2 = (T)1 / sic_sqrt(v2q);
@@ -215,11 +258,12 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                     T dx = X[r] - qx, dy = X[ldx + r] - qy, dz = X[2 * ldx + r] - qz;
                     T th = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
                     if (r == q) th += kp.nugget;
-                    const T n1 = dot_down(th, F1 + r, Cm, p1, t);
-                    const T n2 = dot_down(th, F2c + r, Cm, p2, m + t);
+                    const T n1 = SMEM ? dot_row(th, F1 + (long long)r * P1, p1, t) : dot_down(th, F1 + r, Cm, p1, t);
+                    const T n2 = SMEM ? dot_row(th, F2c + (long long)r * P2, p2, m + t)
+                                      : dot_down(th, F2c + r, Cm, p2, m + t);
                     const T u1 = n1 * r1, u2 = n2 * r2;
-                    F1[(long long)t * Cm + r] = u1;
-                    F2c[(long long)(m + t) * Cm + r] = u2;
+                    E1(r, t) = u1;
+                    E2(r, m + t) = u2;
                     if (r == q) {
                         V1[r] = NEG;
                         V2[r] = NEG;
@@ -237,11 +281,15 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
     }
 }
 
+#undef E1
+#undef E2
+#undef E2T
+
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <typename T>
 size_t agg_smem_bytes(const AggLayout& L, bool in_smem) {
-    size_t piv = sizeof(T) * (size_t)(L.k + L.mm + L.k);
+    size_t piv = sizeof(T) * (size_t)((L.k + 3) / 4 * 4 + L.mm + L.k);
     return in_smem ? sizeof(T) * (size_t)L.size() + piv : piv;
 }
 
@@ -270,8 +318,9 @@ int agg_grid_for(sic_handle* h, size_t smem, long long n_grp) {
 template <typename T>
 AggPlan agg_plan(sic_handle* h, long long n_grp, int max_cand, int max_m, int k) {
     AggPlan P;
-    P.L = agg_layout(max_cand, max_m, k);
+    P.L = agg_layout(max_cand, max_m, k, true);
     P.smem = agg_smem_bytes<T>(P.L, true) <= SMEM_LIMIT;
+    if (!P.smem) P.L = agg_layout(max_cand, max_m, k, false);
     P.nt = (max_cand <= 256) ? 256 : 512;
     P.smem_bytes = agg_smem_bytes<T>(P.L, P.smem);
     long long work = n_grp > 0 ? n_grp : 1;

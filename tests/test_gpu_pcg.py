@@ -58,7 +58,7 @@ def _factor_for(env, hp, prec):
 def test_pcg_matches_oracle(env, oracle_lib):
     """FP64 PCG on the device against the oracle's textbook PCG with the oracle's own factor:
     N = 4096, Matern 3/2 with the config-3 spacing ratio, system Theta(nugget 1e-6) + 1e-4 I,
-    preconditioner = supernodal factor (C = 256, k = 32) of that same matrix, 4 right-hand
+    preconditioner = supernodal factor (C = 1024, k = 64) of that same matrix, 4 right-hand
     sides."""
     torch, sic, pipeline, h = env
     oracle = oracle_lib
@@ -66,13 +66,13 @@ def test_pcg_matches_oracle(env, oracle_lib):
     ell = 0.02 * math.sqrt((1 << 20) / n)
     kp = sic.kernel(2, 3, ell, 1.0, 1e-6 + 1e-4)       # the solved matrix, shift folded into the nugget
     okp = oracle.kernel(2, 3, ell, 1.0, 1e-6 + 1e-4)
-    hp = pipeline.prepare_groups(synthetic.points(n, 2, 0), kp, 256, 32, 8, 64)
+    hp = pipeline.prepare_groups(synthetic.points(n, 2, 0), kp, 1024, 64, 8, 64)
     P = hp.pts
     sels = []
     for g in range(len(hp.grp_ptr) - 1):
         g0, g1 = int(hp.grp_ptr[g]), int(hp.grp_ptr[g + 1])
-        cand = oracle.knn_later(P, np.arange(g0, g1), g1, 256)
-        sels.append(oracle.select_multi(okp, P, g0, g1 - g0, cand, 32)["sel"])
+        cand = oracle.knn_later(P, np.arange(g0, g1), g1, 1024)
+        sels.append(oracle.select_multi(okp, P, g0, g1 - g0, cand, 64)["sel"])
     cp, ri, val, _ = oracle.factor_groups(okp, P, hp.grp_ptr, sels)
     L = np.zeros((n, n))
     for c in range(n):
