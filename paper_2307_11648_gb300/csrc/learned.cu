@@ -584,14 +584,7 @@ extern "C" sic_status sic_proposal_score(sic_handle* h, const float* params, con
     if (rows == 0) return SIC_OK;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
-    uint2* W1f = (uint2*)ws;
-    uint2* W2f = W1f + 16 * 32;
-    k_pack_frags<<<2, 256, 0, s>>>(params + OFF_W1, NF, 1, W1f);
-    k_pack_frags<<<16, 256, 0, s>>>(params + OFF_W2, HID, 8, W2f);
-    int grid = persistent_grid(h, k_mlp_infer, 128, 0, (rows + 63) / 64);
-    k_mlp_infer<<<grid, 128, 0, s>>>(feat, rows, W1f, W2f, params, score);
-    SIC_CUDA_TRY(cudaGetLastError());
-    return SIC_OK;
+    return sic_proposal_score_tc(h, params, feat, rows, score, s);
 }
 
 extern "C" sic_status sic_proposal_topk(sic_handle* h, const int64_t* cand_ptr, const int32_t* cand_idx,

@@ -89,3 +89,7 @@ static inline int persistent_grid(const sic_handle* h, K kernel, int threads, si
     if (g < 1) g = 1;
     return (int)g;
 }
+
+// tcgen05 scoring kernel of the proposal network (mlp_tc.cu)
+sic_status sic_proposal_score_tc(sic_handle* h, const float* params, const float* feat, int64_t rows, float* score,
+                                 cudaStream_t s);
