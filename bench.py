@@ -294,6 +294,8 @@ def main():
     ap.add_argument("--case-top", type=int, default=0,
                     help="with --case-only: keep only the first TOP candidates of each list (the selection "
                          "kernel of the proposal path)")
+    ap.add_argument("--case-mlp", action="store_true",
+                    help="with --case-only: run the proposal (untrained network) and select on its top 256")
     ap.add_argument("--pcg-n", type=int, default=1 << 16, help="points of the preconditioning comparison (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
@@ -320,7 +322,10 @@ def main():
             hp = truncated(hp, args.case_top)
         h = sic.Handle(local)
         dp = pipeline.DeviceProblem(hp)
-        fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
+        if args.case_mlp:
+            fb = learned.LearnedFactorBuilder(h, hp, learned.Proposal(h, learned.init_params(0), top=4 * cfg["k"]))
+        else:
+            fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
         fb.run(dp)
         h.sync()
         print(json.dumps({"case": args.case_only, "groups": hp.n_units, "sum_logv": float(fb.sum_logv.cpu()[0])}))
@@ -456,7 +461,7 @@ def main():
         "k_fill (FP64)": {"ms": fill_ms, "achieved_tflops": fill_tf, "peak_tflops": f64_peak,
                           "frac": fill_tf / f64_peak, "unit_peak": "FP64 DFMA"},
         "k_features": {"ms": feat_ms},
-        "k_mlp_infer (BF16 mma.sync)": {"ms": mlp_ms, "achieved_tflops": mlp_tf, "peak_tflops": bf16_peak,
+        "k_mlp_tc (BF16 tcgen05, TMEM)": {"ms": mlp_ms, "achieved_tflops": mlp_tf, "peak_tflops": bf16_peak,
                                         "frac": mlp_tf / bf16_peak, "unit_peak": "measured cuBLAS BF16 (burst)"},
         "top-k": {"ms": topk_ms},
     }

@@ -275,12 +275,11 @@ sic_status sic_proposal_features(sic_handle* h, const double* pts, int64_t n, co
                                  const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr,
                                  const int32_t* cand_idx, float* feat, void* stream);
 
-/* score[rows] = the network applied to feat[rows x 8] with BF16 weights and inputs and
- * FP32 accumulation on the tensor cores (the hidden activations are rounded to BF16 as
- * the second layer's input).  ws: sic_proposal_score_workspace bytes. */
-sic_status sic_proposal_score_workspace(size_t* bytes);
+/* score[rows] = the network applied to feat[rows x 8] on the tcgen05 tensor cores: BF16
+ * weights and inputs, FP32 accumulation in tensor memory, the hidden activations rounded
+ * to BF16 as the second layer's input.  No workspace. */
 sic_status sic_proposal_score(sic_handle* h, const float* params, const float* feat, int64_t rows, float* score,
-                              void* ws, size_t ws_bytes, void* stream);
+                              void* stream);
 
 /* Keeps, per group, the min(top, C) candidates of highest score (ties: earlier in the
  * list), in their original list order.  out_ptr[n_grp+1] receives the CSR offsets,

@@ -3,10 +3,7 @@
 // Section 5.2 runs only on the best `top` of them).
 //
 //   k_features      8 features per (group, candidate), FP32
-//   k_pack_frags    BF16 weight fragments in mma.sync B-operand order
-//   k_mlp_infer     8 -> 128 -> 128 -> 1 with exact GELU; BF16 tensor-core MMAs
-//                   (mma.sync m16n8k16, FP32 accumulate), the first layer's
-//                   accumulators re-used as the second layer's A fragments in registers
+//   (inference)     8 -> 128 -> 128 -> 1 on the tcgen05 tensor cores: mlp_tc.cu
 //   k_topk_*        per group: keep the `top` best-scored candidates, in list order
 //   training        FP32 forward/backward (strided tiled GEMM, split over K with a
 //                   fixed-order reduction), weighted BCE with logits, AdamW
@@ -119,113 +116,6 @@ __global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts
             f[7] = ksum * inv_m * inv_s2;
         }
         __syncthreads();
-    }
-}
-
-// ------------------------------------------------------ tensor-core inference --
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t a0, const uint32_t a1, const uint32_t a2,
-                                         const uint32_t a3, const uint32_t b0, const uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// B fragments of a K x 128 row-major FP32 matrix W (K a multiple of 16 after zero
-// padding of rows >= kval): frag[(kk * 16 + nt) * 32 + lane] = {b0, b1} with
-// b0 = (W[16kk + 2t][8nt + g], W[16kk + 2t + 1][8nt + g]),
-// b1 = (W[16kk + 8 + 2t][8nt + g], W[16kk + 9 + 2t][8nt + g]), g = lane / 4, t = lane % 4.
-__global__ void k_pack_frags(const float* __restrict__ W, int kval, int ktiles, uint2* __restrict__ frag) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ktiles * 16 * 32) return;
-    int lane = i & 31, nt = (i >> 5) & 15, kk = i >> 9;
-    int g = lane >> 2, t = lane & 3, col = 8 * nt + g;
-    auto w = [&](int k) { return (k < kval) ? W[k * HID + col] : 0.0f; };
-    int k0 = 16 * kk + 2 * t;
-    frag[i] = make_uint2(pack_bf16(w(k0), w(k0 + 1)), pack_bf16(w(k0 + 8), w(k0 + 9)));
-}
-
-__global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ X, long long rows,
-                                                   const uint2* __restrict__ W1f, const uint2* __restrict__ W2f,
-                                                   const float* __restrict__ params, float* __restrict__ out) {
-    __shared__ uint2 sW2[8 * 16 * 32];
-    __shared__ uint2 sW1[16 * 32];
-    __shared__ float sb1[HID], sb2[HID], sw3[HID];
-    for (int i = threadIdx.x; i < 8 * 16 * 32; i += blockDim.x) sW2[i] = W2f[i];
-    for (int i = threadIdx.x; i < 16 * 32; i += blockDim.x) sW1[i] = W1f[i];
-    for (int i = threadIdx.x; i < HID; i += blockDim.x) {
-        sb1[i] = params[OFF_B1 + i];
-        sb2[i] = params[OFF_B2 + i];
-        sw3[i] = params[OFF_W3 + i];
-    }
-    const float b3 = params[OFF_B3];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const long long ntiles = (rows + 15) / 16;
-    for (long long tile = (long long)blockIdx.x * 4 + warp; tile < ntiles; tile += (long long)gridDim.x * 4) {
-        const long long r0 = tile * 16 + g, r1 = r0 + 8;
-        float x00 = 0.f, x01 = 0.f, x10 = 0.f, x11 = 0.f;
-        if (r0 < rows) {
-            x00 = X[r0 * NF + 2 * t];
-            x01 = X[r0 * NF + 2 * t + 1];
-        }
-        if (r1 < rows) {
-            x10 = X[r1 * NF + 2 * t];
-            x11 = X[r1 * NF + 2 * t + 1];
-        }
-        const uint32_t a0 = pack_bf16(x00, x01), a1 = pack_bf16(x10, x11);
-        // layer 1 -> GELU -> bf16 A fragments of layer 2
-        uint32_t A2[8][4];
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            float h[2][4];
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int nt = 2 * kk + half;
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                const uint2 b = sW1[nt * 32 + lane];
-                mma16816(acc, a0, a1, 0u, 0u, b.x, b.y);
-                const int c0 = nt * 8 + 2 * t;
-                h[half][0] = gelu_f(acc[0] + sb1[c0]);
-                h[half][1] = gelu_f(acc[1] + sb1[c0 + 1]);
-                h[half][2] = gelu_f(acc[2] + sb1[c0]);
-                h[half][3] = gelu_f(acc[3] + sb1[c0 + 1]);
-            }
-            A2[kk][0] = pack_bf16(h[0][0], h[0][1]);
-            A2[kk][1] = pack_bf16(h[0][2], h[0][3]);
-            A2[kk][2] = pack_bf16(h[1][0], h[1][1]);
-            A2[kk][3] = pack_bf16(h[1][2], h[1][3]);
-        }
-        // layer 2 + GELU + head, one n-tile at a time
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll 4
-        for (int nt = 0; nt < 16; ++nt) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const uint2 b = sW2[(kk * 16 + nt) * 32 + lane];
-                mma16816(acc, A2[kk][0], A2[kk][1], A2[kk][2], A2[kk][3], b.x, b.y);
-            }
-            const int c0 = nt * 8 + 2 * t;
-            s0 += gelu_f(acc[0] + sb2[c0]) * sw3[c0] + gelu_f(acc[1] + sb2[c0 + 1]) * sw3[c0 + 1];
-            s1 += gelu_f(acc[2] + sb2[c0]) * sw3[c0] + gelu_f(acc[3] + sb2[c0 + 1]) * sw3[c0 + 1];
-        }
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-        if (t == 0) {
-            if (r0 < rows) out[r0] = s0 + b3;
-            if (r1 < rows) out[r1] = s1 + b3;
-        }
     }
 }
 
@@ -570,21 +460,12 @@ extern "C" sic_status sic_proposal_features(sic_handle* h, const double* pts, in
     return SIC_OK;
 }
 
-extern "C" sic_status sic_proposal_score_workspace(size_t* bytes) {
-    if (!bytes) return SIC_ERR_INVALID;
-    *bytes = sizeof(uint2) * (size_t)(16 * 32 + 8 * 16 * 32);
-    return SIC_OK;
-}
-
 extern "C" sic_status sic_proposal_score(sic_handle* h, const float* params, const float* feat, int64_t rows,
-                                         float* score, void* ws, size_t ws_bytes, void* stream) {
-    size_t need = 0;
-    sic_proposal_score_workspace(&need);
-    if (!h || !params || !feat || rows < 0 || !score || !ws || ws_bytes < need) return SIC_ERR_INVALID;
+                                         float* score, void* stream) {
+    if (!h || !params || !feat || rows < 0 || !score) return SIC_ERR_INVALID;
     if (rows == 0) return SIC_OK;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
-    cudaStream_t s = (cudaStream_t)stream;
-    return sic_proposal_score_tc(h, params, feat, rows, score, s);
+    return sic_proposal_score_tc(h, params, feat, rows, score, (cudaStream_t)stream);
 }
 
 extern "C" sic_status sic_proposal_topk(sic_handle* h, const int64_t* cand_ptr, const int32_t* cand_idx,

@@ -43,7 +43,6 @@ class Proposal:
         self.h = h
         self.top = top
         self.params = params if isinstance(params, torch.Tensor) else torch.from_numpy(params).to(device)
-        self.ws_score = sic._ws(sic.proposal_score_workspace(), device)
         self.device = device
 
     def buffers(self, hp: pipeline.HostProblem):
@@ -63,7 +62,7 @@ class Proposal:
 
     def score(self, dp, buf, stream=None):
         rows = int(dp.hp.cand_ptr[-1])
-        sic.proposal_score(self.h, self.params, buf["feat"][:rows], buf["score"][:rows], self.ws_score, stream)
+        sic.proposal_score(self.h, self.params, buf["feat"][:rows], buf["score"][:rows], stream)
 
     def topk(self, dp, buf, stream=None):
         sic.proposal_topk(self.h, dp.cand_ptr, dp.cand_idx, buf["score"], self.top, buf["out_ptr"], buf["out_idx"],

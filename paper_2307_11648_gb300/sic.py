@@ -30,7 +30,7 @@ EXPORTS = [
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
     "sic_matern_matvec", "sic_pcg_workspace", "sic_pcg_solve",
-    "sic_mlp_param_count", "sic_proposal_features", "sic_proposal_score_workspace", "sic_proposal_score",
+    "sic_mlp_param_count", "sic_proposal_features", "sic_proposal_score",
     "sic_proposal_topk", "sic_proposal_labels", "sic_mlp_train_workspace", "sic_mlp_grads", "sic_adamw_step",
 ]
 
@@ -94,8 +94,7 @@ def lib():
             "sic_pcg_solve": (st, [vp, vp, i64, pk, d, st, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp, sz, vp]),
             "sic_mlp_param_count": (i32, []),
             "sic_proposal_features": (st, [vp, vp, i64, pk, vp, i64, vp, vp, vp, vp]),
-            "sic_proposal_score_workspace": (st, [C.POINTER(sz)]),
-            "sic_proposal_score": (st, [vp, vp, vp, i64, vp, vp, sz, vp]),
+            "sic_proposal_score": (st, [vp, vp, vp, i64, vp, vp]),
             "sic_proposal_topk": (st, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),
             "sic_proposal_labels": (st, [vp, vp, vp, i64, vp, vp, i32, vp, vp]),
             "sic_mlp_train_workspace": (st, [i64, C.POINTER(sz)]),
@@ -368,18 +367,12 @@ def proposal_features(h: Handle, pts, kp: Kernel, grp_ptr, cand_ptr, cand_idx, f
                                        _stream(stream)), "sic_proposal_features", h)
 
 
-def proposal_score_workspace() -> int:
-    b = C.c_size_t()
-    _check(lib().sic_proposal_score_workspace(C.byref(b)), "sic_proposal_score_workspace")
-    return b.value
-
-
-def proposal_score(h: Handle, params, feat, score, ws, stream=None):
+def proposal_score(h: Handle, params, feat, score, stream=None):
     import torch
     rows = feat.shape[0]
     _check(lib().sic_proposal_score(h.ptr, _dptr(params, torch.float32, "params"), _dptr(feat, torch.float32, "feat"),
-                                    rows, _dptr(score, torch.float32, "score"), _dptr(ws), ws.numel(),
-                                    _stream(stream)), "sic_proposal_score", h)
+                                    rows, _dptr(score, torch.float32, "score"), _stream(stream)),
+           "sic_proposal_score", h)
 
 
 def proposal_topk(h: Handle, cand_ptr, cand_idx, score, top: int, out_ptr, out_idx, stream=None):

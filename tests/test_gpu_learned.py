@@ -96,15 +96,15 @@ def test_grads_and_loss_match_oracle(env, bf16):
 
 
 def test_tensor_core_scores_match_oracle(env):
+    """tcgen05 inference (128-row tiles) against the oracle's forward pass."""
     torch, sic, pipeline, learned, h = env
-    rows = 5000  # not a multiple of 16: ragged last tile
+    rows = 5000  # not a multiple of 128: ragged last tile
     X = (synthetic.normal(8, rows * 8).reshape(rows, 8) * 0.7).astype(np.float32)
     P = learned.init_params(4)
     P[1024:1152] = 0.1
     P[17792] = 0.3
     s = torch.empty(rows, dtype=torch.float32, device="cuda")
-    ws = sic._ws(sic.proposal_score_workspace(), "cuda")
-    sic.proposal_score(h, torch.from_numpy(P).cuda(), torch.from_numpy(X).cuda(), s, ws)
+    sic.proposal_score(h, torch.from_numpy(P).cuda(), torch.from_numpy(X).cuda(), s)
     h.sync()
     ref, _ = OL.forward(_bf16(P), _bf16(X))
     err = np.abs(s.cpu().numpy() - ref).max()
