@@ -309,6 +309,15 @@ sic_status sic_mlp_grads(sic_handle* h, const float* params, const float* feat, 
 sic_status sic_adamw_step(sic_handle* h, float* params, float* m, float* v, const float* grads, int32_t n,
                           int32_t step, float lr, float beta1, float beta2, float eps, float wd, void* stream);
 
+/* ------------------------------------------------------------ self-test -- */
+
+/* Exercises the bounded device wait used by the tensor-core kernels (not part of the
+ * paper): one CTA waits on an mbarrier that nothing arrives at, for at most `cap`
+ * polls (1 <= cap <= 2^24), then writes 0 to out[0] [device] and records
+ * SIC_ERR_TIMEOUT (unit -2) for sic_sync -- the path a kernel takes when an awaited
+ * tensor-core operation never completes; the context stays usable. */
+sic_status sic_selftest_wait_timeout(sic_handle* h, int64_t cap, int32_t* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -232,14 +232,50 @@ __global__ void __launch_bounds__(TC_NT) k_mlp_tc(const float* __restrict__ X, l
     }
 }
 
+// Self-test of the bounded wait: waits on an mbarrier that nothing arrives at, with the
+// given iteration cap, and records SIC_ERR_TIMEOUT when the cap runs out.
+__global__ void k_wait_selftest(long long cap, int* out, DevStatus* st) {
+    __shared__ uint64_t bar;
+    const uint32_t a = smem_u32(&bar);
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+    __syncthreads();
+    bool ok = false;
+    for (long long it = 0; it < cap && !ok; ++it) {
+        uint32_t r;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(r)
+            : "r"(a), "r"(0u)
+            : "memory");
+        ok = r != 0;
+    }
+    if (threadIdx.x == 0) {
+        out[0] = ok ? 1 : 0;
+        if (!ok) record_error(st, SIC_ERR_TIMEOUT, -2);
+    }
+}
+
 }  // namespace
+
+extern "C" sic_status sic_selftest_wait_timeout(sic_handle* h, int64_t cap, int32_t* out, void* stream) {
+    if (!h || !out || cap < 1) return SIC_ERR_INVALID;
+    if (cap > (1LL << 24)) return SIC_ERR_INVALID;  // keep the self-test short
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(cap, out, h->d_status);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
 
 // Scores with the tcgen05 kernel (same contract as sic_proposal_score).
 sic_status sic_proposal_score_tc(sic_handle* h, const float* params, const float* feat, int64_t rows, float* score,
                                  cudaStream_t s) {
-    SIC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TC + 1024));
-    int grid = persistent_grid(h, k_mlp_tc, TC_NT, SMEM_TC + 1024, (rows + 127) / 128);
-    k_mlp_tc<<<grid, TC_NT, SMEM_TC + 1024, s>>>(feat, rows, params, score, h->d_status);
+    SIC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TC));
+    // three CTAs per SM: 3 x (73 KiB + 1 KiB reserved) of shared memory and 3 x 128 of the
+    // 512 TMEM columns; the epilogues of one CTA overlap the MMAs of the others
+    long long tiles = (rows + 127) / 128;
+    long long g = 3LL * h->num_sms;
+    if (tiles < g) g = tiles;
+    k_mlp_tc<<<(unsigned)g, TC_NT, SMEM_TC, s>>>(feat, rows, params, score, h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }

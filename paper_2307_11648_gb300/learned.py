@@ -160,9 +160,23 @@ def training_set(h: sic.Handle, problems, prec=sic.SIC_FP32_MIXED, device="cuda"
     return torch.cat(feats), torch.cat(labels), n_sel
 
 
+def save_checkpoint(path, P, m, v, step, epoch, seed):
+    """Weights, AdamW moments, step and data-order state (the epoch and seed fix the shuffles)."""
+    import torch
+    torch.save({"params": P.cpu(), "m": m.cpu(), "v": v.cpu(), "step": step, "epoch": epoch, "seed": seed}, path)
+
+
 def train(h: sic.Handle, feat, label, params=None, epochs: int = 3, batch: int = 65536, lr: float = 2e-3,
-          wd: float = 1e-4, pos_weight: float = 2.0, seed: int = 0, bf16: bool = True, log=None):
-    """AdamW training of the proposal network with libsic's kernels.  Returns (params, history)."""
+          wd: float = 1e-4, pos_weight: float = 2.0, seed: int = 0, bf16: bool = True, log=None,
+          checkpoint: str | None = None, stop_after_epoch: int | None = None):
+    """AdamW training of the proposal network with libsic's kernels.  Returns (params, history).
+
+    With `checkpoint`, the state is saved after every epoch and, if the file exists at the
+    start, training resumes from it (same result as an uninterrupted run: the per-epoch
+    shuffles depend only on the seed and the epoch).  `stop_after_epoch` ends the run early
+    (used to test resumption)."""
+    import os
+
     import torch
     dev = feat.device
     n = feat.shape[0]
@@ -174,8 +188,16 @@ def train(h: sic.Handle, feat, label, params=None, epochs: int = 3, batch: int =
     ws = sic._ws(sic.mlp_train_workspace(batch), dev)
     hist = []
     step = 0
+    ep0 = 0
+    if checkpoint and os.path.exists(checkpoint):
+        ck = torch.load(checkpoint)
+        P.copy_(ck["params"].to(dev))
+        m.copy_(ck["m"].to(dev))
+        v.copy_(ck["v"].to(dev))
+        step, ep0 = int(ck["step"]), int(ck["epoch"]) + 1
+        assert int(ck["seed"]) == seed
     t0 = time.perf_counter()
-    for ep in range(epochs):
+    for ep in range(ep0, epochs):
         perm = np.argsort(synthetic.uniform(seed + 1000 + ep, 91, n), kind="stable")
         perm_t = torch.from_numpy(perm).to(dev)
         for b0 in range(0, n - batch + 1, batch):
@@ -189,6 +211,11 @@ def train(h: sic.Handle, feat, label, params=None, epochs: int = 3, batch: int =
                 hist.append((step, float(loss.item())))
                 if log:
                     log(f"epoch {ep} step {step} loss {hist[-1][1]:.5f} ({time.perf_counter() - t0:.1f}s)")
+        if checkpoint:
+            h.sync()
+            save_checkpoint(checkpoint, P, m, v, step, ep, seed)
+        if stop_after_epoch is not None and ep >= stop_after_epoch:
+            break
     h.sync()
     hist.append((step, float(loss.item())))
     return P, hist

@@ -29,7 +29,7 @@ EXPORTS = [
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
-    "sic_matern_matvec", "sic_pcg_workspace", "sic_pcg_solve",
+    "sic_matern_matvec", "sic_pcg_workspace", "sic_pcg_solve", "sic_selftest_wait_timeout",
     "sic_mlp_param_count", "sic_proposal_features", "sic_proposal_score",
     "sic_proposal_topk", "sic_proposal_labels", "sic_mlp_train_workspace", "sic_mlp_grads", "sic_adamw_step",
 ]
@@ -90,6 +90,7 @@ def lib():
             "sic_apply_factor_workspace": (st, [i64, i32, st, C.POINTER(sz)]),
             "sic_apply_factor": (st, [vp, i64, vp, vp, vp, st, vp, vp, i32, vp, sz, vp]),
             "sic_matern_matvec": (st, [vp, vp, i64, pk, d, st, vp, vp, i32, vp]),
+            "sic_selftest_wait_timeout": (st, [vp, i64, vp, vp]),
             "sic_pcg_workspace": (st, [i64, i32, C.POINTER(sz)]),
             "sic_pcg_solve": (st, [vp, vp, i64, pk, d, st, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp, sz, vp]),
             "sic_mlp_param_count": (i32, []),
@@ -446,3 +447,9 @@ def pcg_solve(h: Handle, pts, kp: Kernel, shift: float, prec: int, factor, b, x,
                                _dptr(x, torch.float64, "x"), nrhs, float(tol), int(max_iter), _hptr(iters, np.int32),
                                _hptr(relres, np.float64), _dptr(ws), ws.numel(), _stream(stream)), "sic_pcg_solve", h)
     return iters, relres
+
+
+def selftest_wait_timeout(h: Handle, cap: int, out, stream=None):
+    import torch
+    _check(lib().sic_selftest_wait_timeout(h.ptr, int(cap), _dptr(out, torch.int32, "out"), _stream(stream)),
+           "sic_selftest_wait_timeout", h)

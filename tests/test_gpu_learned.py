@@ -235,3 +235,30 @@ def test_learned_proposal_gain(env):
     assert base > 0
     assert gaps["learned"] <= 0.01          # within 1% of plain greedy (the benchmark spec)
     assert hit_mlp / tot >= 0.99
+
+
+def test_training_checkpoint_resume(env, tmp_path):
+    """Training interrupted after epoch 0 and resumed from its checkpoint ends with the same
+    weights as an uninterrupted run (the kernels and the data order are deterministic)."""
+    torch, sic, pipeline, learned, h = env
+    B = 8192
+    X = torch.from_numpy((synthetic.normal(11, 4 * B * 8).reshape(4 * B, 8) * 0.5).astype(np.float32)).cuda()
+    y = torch.from_numpy((synthetic.uniform(12, 3, 4 * B) < 0.1).astype(np.float32)).cuda()
+    full, _ = learned.train(h, X, y, epochs=2, batch=B, seed=5)
+    ck = str(tmp_path / "proposal.pt")
+    learned.train(h, X, y, epochs=2, batch=B, seed=5, checkpoint=ck, stop_after_epoch=0)
+    resumed, _ = learned.train(h, X, y, epochs=2, batch=B, seed=5, checkpoint=ck)
+    assert torch.equal(full, resumed)
+
+
+def test_bounded_wait_reports_timeout(env):
+    """A device wait that nothing satisfies gives up after its cap and reports
+    SIC_ERR_TIMEOUT through sic_sync; the context stays usable afterwards."""
+    torch, sic, pipeline, learned, h = env
+    out = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    sic.selftest_wait_timeout(h, 1000, out)
+    with pytest.raises(sic.SicError) as e:
+        h.sync()
+    assert e.value.code == sic.SIC_ERR_TIMEOUT and int(out.item()) == 0
+    x = torch.ones(4, device="cuda")
+    assert float((x * 2).sum().item()) == 8.0  # the context still works
