@@ -1,15 +1,18 @@
 // KL-optimal fill of the factor (eq. L_col; aggregated form, Appendix A.4), FP64.
 //
-// One warp per unit (a single column, or a group of m consecutive columns sharing
-// the picks S).  With the aggregated set ordered ascending, s = (P_0..P_{m-1}, S
-// sorted), the factor block is L = U^{-T} where U U^T = Theta_{s,s}, U upper
-// triangular.  The warp forms Theta on the reversed order R = reverse(s) in packed
-// lower storage in shared memory, factors it G G^T = Theta_{RR} (left-looking: lane
-// = row, one dot product per entry), and since U = J G J (J the reversal),
-// member a's column is J G^{-T} e_j with j = n-1-a.  The m right-hand sides are
-// solved together (lane = member, up to 32 per batch) by column-oriented back
-// substitution.  v_a = G_jj^2, so logv = 2 log G_jj (eq. inverse_cond).
-// Rows are written diagonal first, then ascending, to the caller's CSC arrays.
+// One CTA of four warps per unit (a single column, or a group of m consecutive
+// columns sharing the picks S).  With the aggregated set ordered ascending,
+// s = (P_0..P_{m-1}, S sorted), the factor block is L = U^{-T} where U U^T =
+// Theta_{s,s}, U upper triangular.  The CTA forms Theta on the reversed order
+// R = reverse(s) in packed lower storage in shared memory (one entry per thread), factors
+// it G G^T = Theta_{RR} (left-looking: thread = row, one dot product per entry; the
+// pivot's thread alone takes sqrt and reciprocal), and since U = J G J (J the reversal),
+// member a's column is J G^{-T} e_j with j = n-1-a: one back substitution per member,
+// one member per warp, the right-hand side in registers.  v_a = G_jj^2, so
+// logv = 2 log G_jj (eq. inverse_cond).  Rows are written diagonal first, then
+// ascending, to the caller's CSC arrays.  Theta entries use the FP64 Matern of
+// matern_d2_fast (table-driven exp, Newton sqrt): this GPU issues two FP64 FMAs per
+// clock per SM, so FP64 instructions are spent on the factorisation.
 //
 // Also here: the nnz count + exclusive scan that builds col_ptr, and the fixed-order
 // two-pass sum of logv (bit-reproducible).
@@ -101,7 +104,8 @@ __global__ void k_scan_add(long long* __restrict__ v, long long n, const long lo
 
 // ------------------------------------------------------------------- the fill --
 
-constexpr int FILL_NT = 128;  // 4 warps per unit
+constexpr int FILL_NT = 128;   // 4 warps per unit
+constexpr int FILL_SLOTS = 6;  // right-hand-side entries per lane: nn <= 192 = 32 * FILL_SLOTS
 
 __device__ __forceinline__ long long pk(int i, int j) { return (long long)i * (i + 1) / 2 + j; }
 
@@ -123,13 +127,14 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
     extern __shared__ double smem_d[];
     const int nmax = k + max_m;
     double* G = smem_d;                                     // packed lower, nmax(nmax+1)/2
-    double* bvec = G + (long long)nmax * (nmax + 1) / 2;    // 4 x nmax, one right-hand side per warp
-    double* rG = bvec + 4 * nmax;                           // 1 / G_jj
+    double* rG = G + (long long)nmax * (nmax + 1) / 2;      // 1 / G_jj
     double* xyz = rG + nmax;                                // 3 x nmax
-    int* pos = reinterpret_cast<int*>(xyz + 3 * nmax);      // nmax
+    double* tab = xyz + 3 * nmax;                           // 2^(j/64), j < 64 (exp_neg_table)
+    int* pos = reinterpret_cast<int*>(tab + 64);            // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    exp_table_fill(tab);
 
     for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         const long long g0 = grp_ptr ? grp_ptr[u] : u;
@@ -175,39 +180,50 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
             const int j = (int)(e - (long long)i * (i + 1) / 2);
             const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j],
                          dz = xyz[2 * nmax + i] - xyz[2 * nmax + j];
-            double v = matern<double>(kp, sqrt(dx * dx + dy * dy + dz * dz));
+            double v = matern_d2_fast(kp, fma(dz, dz, fma(dy, dy, dx * dx)), tab);
             if (i == j) v += kp.nugget;
             G[e] = v;
         }
         __syncthreads();
-        // left-looking Cholesky: column j, thread owns row j + tid (nn <= 192 < 2 * FILL_NT)
+        // left-looking Cholesky: column j, thread owns rows j + tid and j + tid + FILL_NT
+        // (nn <= 192 < 2 * FILL_NT).  The pivot's thread alone takes the square root and
+        // its reciprocal; the others scale their entry once the reciprocal is published.
         for (int j = 0; j < nn; ++j) {
             const long long rj = pk(j, 0);
-            for (int i = j + tid; i < nn; i += FILL_NT) {
-                const long long ri = pk(i, 0);
-                double s0 = G[ri + j], s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                int l = 0;
-                for (; l + 4 <= j; l += 4) {
-                    s0 = fma(-G[ri + l], G[rj + l], s0);
-                    s1 = fma(-G[ri + l + 1], G[rj + l + 1], s1);
-                    s2 = fma(-G[ri + l + 2], G[rj + l + 2], s2);
-                    s3 = fma(-G[ri + l + 3], G[rj + l + 3], s3);
+            double sv[2] = {0.0, 0.0};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = j + tid + h * FILL_NT;
+                if (i < nn) {
+                    const long long ri = pk(i, 0);
+                    double s0 = G[ri + j], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                    int l = 0;
+                    for (; l + 4 <= j; l += 4) {
+                        s0 = fma(-G[ri + l], G[rj + l], s0);
+                        s1 = fma(-G[ri + l + 1], G[rj + l + 1], s1);
+                        s2 = fma(-G[ri + l + 2], G[rj + l + 2], s2);
+                        s3 = fma(-G[ri + l + 3], G[rj + l + 3], s3);
+                    }
+                    for (; l < j; ++l) s0 = fma(-G[ri + l], G[rj + l], s0);
+                    sv[h] = (s0 + s1) + (s2 + s3);
                 }
-                for (; l < j; ++l) s0 = fma(-G[ri + l], G[rj + l], s0);
-                G[ri + j] = (s0 + s1) + (s2 + s3);
+            }
+            if (tid == 0) {
+                if (!(sv[0] > 0.0)) {
+                    s_bad = 1;
+                } else {
+                    const double d = sqrt(sv[0]);
+                    G[rj + j] = d;
+                    rG[j] = 1.0 / d;
+                }
             }
             __syncthreads();
-            const double djj = G[rj + j];
-            if (!(djj > 0.0)) {
-                if (tid == 0) s_bad = 1;
-                break;
-            }
-            const double d = sqrt(djj);
-            const double rd = 1.0 / d;
-            for (int i = j + 1 + tid; i < nn; i += FILL_NT) G[pk(i, j)] *= rd;
-            if (tid == 0) {
-                G[rj + j] = d;
-                rG[j] = rd;
+            if (s_bad) break;
+            const double rd = rG[j];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = j + tid + h * FILL_NT;
+                if (i > j && i < nn) G[pk(i, j)] = sv[h] * rd;
             }
             __syncthreads();
         }
@@ -217,27 +233,46 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
             __syncthreads();
             continue;
         }
-        // member a: solve G^T x = e_jb (jb = nn-1-a), one right-hand side per warp
-        double* b = bvec + warp * nmax;
-        for (int a = warp; a < m; a += 4) {
+        // H = rows of G scaled by their reciprocal pivots (off-diagonal entries), so that
+        // the back substitution G^T x = b reads y_l = b_l and updates b_i -= H_li y_l,
+        // with x_l = y_l / G_ll applied once at the end.
+        for (long long e = tid; e < tri; e += FILL_NT) {
+            const int i = pk_row(e);
+            const int j = (int)(e - (long long)i * (i + 1) / 2);
+            if (j < i) G[e] *= rG[i];
+        }
+        __syncthreads();
+        // member a: solve G^T x = e_jb (jb = nn-1-a), one right-hand side per warp, held in
+        // registers (lane owns entries lane + 32 s)
+        for (int a = warp; a < m; a += FILL_NT / 32) {
             const int jb = nn - 1 - a;
-            for (int i = lane; i <= jb; i += 32) b[i] = (i == jb) ? 1.0 : 0.0;
-            __syncwarp();
-            for (int l = jb; l >= 0; --l) {
-                const double xl = b[l] * rG[l];
-                const long long rl = pk(l, 0);
-                for (int i = lane; i < l; i += 32) b[i] = fma(-G[rl + i], xl, b[i]);
-                __syncwarp();
-                if (lane == 0) b[l] = xl;
-                __syncwarp();
+            double bv[FILL_SLOTS];
+#pragma unroll
+            for (int q = 0; q < FILL_SLOTS; ++q) bv[q] = (lane + 32 * q == jb) ? 1.0 : 0.0;
+#pragma unroll
+            for (int sb = FILL_SLOTS - 1; sb >= 0; --sb) {
+                if (32 * sb > jb) continue;
+                const int top = min(jb, 32 * sb + 31);
+                for (int l = top; l >= 32 * sb; --l) {
+                    const double y = __shfl_sync(0xffffffffu, bv[sb], l & 31);
+                    const long long rl = pk(l, 0);
+#pragma unroll
+                    for (int q = 0; q <= sb; ++q) {
+                        const int i = lane + 32 * q;
+                        if (i < l) bv[q] = fma(-G[rl + i], y, bv[q]);
+                    }
+                }
             }
             const long long c0 = col_ptr[g0 + a];
-            for (int p = lane; p <= jb; p += 32) {
-                row_idx[c0 + p] = pos[jb - p];
-                val[c0 + p] = b[jb - p];
+#pragma unroll
+            for (int q = 0; q < FILL_SLOTS; ++q) {
+                const int i = lane + 32 * q;
+                if (i <= jb) {
+                    row_idx[c0 + jb - i] = pos[i];
+                    val[c0 + jb - i] = bv[q] * rG[i];
+                }
             }
             if (lane == 0) logv[g0 + a] = 2.0 * log(G[pk(jb, jb)]);
-            __syncwarp();
         }
         __syncthreads();
     }
@@ -276,12 +311,39 @@ __global__ void __launch_bounds__(256) k_sum_final(const double* __restrict__ pa
 
 size_t fill_smem_bytes(int k, int max_m) {
     size_t nmax = (size_t)k + (size_t)max_m;
-    return sizeof(double) * (nmax * (nmax + 1) / 2 + 4 * nmax + nmax + 3 * nmax) + sizeof(int) * (nmax + (size_t)k);
+    return sizeof(double) * (nmax * (nmax + 1) / 2 + nmax + 3 * nmax + 64) + sizeof(int) * (nmax + (size_t)k);
+}
+
+__global__ void k_fp64_math(KP<double> kp, const double* __restrict__ x, long long n, double* __restrict__ os,
+                            double* __restrict__ oe, double* __restrict__ ok) {
+    __shared__ double tab[64];
+    exp_table_fill(tab);
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        os[i] = sqrt_newton(v);
+        oe[i] = exp_neg_table(-v, tab);
+        ok[i] = matern_d2_fast(kp, v, tab);
+    }
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- entry points --
+
+extern "C" sic_status sic_selftest_fp64_math(sic_handle* h, const sic_kernel* kp, const double* x, int64_t n,
+                                             double* out_sqrt, double* out_exp, double* out_kernel, void* stream) {
+    if (!h || !sic_valid_kernel(kp) || n < 0 || (n > 0 && (!x || !out_sqrt || !out_exp || !out_kernel)))
+        return SIC_ERR_INVALID;
+    if (n == 0) return SIC_OK;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4LL * h->num_sms) blocks = 4LL * h->num_sms;
+    k_fp64_math<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(make_kp<double>(*kp), x, n, out_sqrt, out_exp,
+                                                                     out_kernel);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
 
 extern "C" sic_status sic_factor_nnz_workspace(int64_t n, size_t* bytes) {
     if (!bytes || n < 0) return SIC_ERR_INVALID;

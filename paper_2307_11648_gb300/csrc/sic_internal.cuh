@@ -60,6 +60,72 @@ __device__ __forceinline__ T matern(const KP<T>& k, T r) {
     return k.s2 * ((T)1 + t + t * t * (T)(1.0 / 3.0)) * e;
 }
 
+// ---- FP64 Matern with few FP64-pipe instructions (GB300 issues 2 DFMA / clk / SM) ----
+//
+// exp(x), x <= 0: table-driven reduction after Tang (ACM TOMS 15(2), 1989).  With
+// k = round(64 x / ln 2) = 64 q + j, x = k ln2/64 + r, |r| <= ln2/128, and
+// exp(x) = 2^q * 2^(j/64) * e^r.  ln2/64 is split into its double rounding and the tail,
+// so r carries ~1e-19 absolute error for |k| < 2^16; e^r - 1 = r + r^2 (1/2 + r/6 + r^2/24
+// + r^3/120 + r^4/720), truncation below 1.3e-20.  The result is formed as T_j + T_j p in
+// one fused operation and scaled by adding q to the exponent field.  Error: the table's
+// rounding plus one final rounding (about 1.5 ulp).  11 FP64 operations.  Arguments below
+// -700 return 0 (exp(-700) ~ 1e-304).  `tab` holds 2^(j/64), j = 0..63 (exp_table_fill).
+__device__ __forceinline__ void exp_table_fill(double* tab) {
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) tab[j] = exp2((double)j * (1.0 / 64.0));
+}
+
+__device__ __forceinline__ double exp_neg_table(double x, const double* __restrict__ tab) {
+    constexpr double SHIFT = 6755399441055744.0;               // 1.5 * 2^52
+    constexpr double INV_L = 92.332482616893656877;            // 64 / ln 2
+    constexpr double L1 = 0.6931471805599453094172321 / 64.0;  // ln2/64, rounded
+    constexpr double L2 = 2.3190468138462996e-17 / 64.0;       // ln2/64 - L1
+    // x < -700 <=> (x negative) high word above that of -700.0 (integer compare, no FP64 op)
+    if ((unsigned)__double2hiint(x) > 0xC085E000u) return 0.0;
+    double kd = fma(x, INV_L, SHIFT);  // k in the low word, two's complement
+    const int k = __double2loint(kd);
+    kd -= SHIFT;
+    double r = fma(-kd, L1, x);
+    r = fma(-kd, L2, r);
+    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+    q = fma(q, r, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+    q = fma(q, r, 0.5);
+    const double p = fma(r * r, q, r);  // e^r - 1
+    const double tj = tab[k & 63];
+    const double e = fma(tj, p, tj);
+    return __hiloint2double(__double2hiint(e) + ((k >> 6) << 20), __double2loint(e));
+}
+
+// sqrt(d2), d2 >= 0: an FP32 reciprocal-square-root seed (from the high word, ~2^-20)
+// refined by two Newton steps on the residual d2 - r^2 with the fixed half-reciprocal h:
+// the relative error goes 2^-20 -> 1.5 * 2^-40 -> ~2^-59, under one rounding of the last
+// fused step.  5 FP64 operations; the range tests are integer compares on the high word.
+// d2 < 2^-120 returns 0 (the square root is below 1e-18); d2 > 2^120 uses sqrt().
+__device__ __forceinline__ double sqrt_newton(double d2) {
+    const unsigned hi = (unsigned)__double2hiint(d2);
+    if (hi < 0x38700000u) return 0.0;  // 2^-120 (and +0)
+    if (hi >= 0x47700000u) return sqrt(d2);  // 2^120
+    const float f = __uint_as_float((hi << 3) - (896u << 23));  // exponent rebased 1023 -> 127
+    const unsigned yb = __float_as_uint(rsqrtf(f));
+    const unsigned yhi = (yb >> 3) + (896u << 20), ylo = yb << 29;
+    const double y = __hiloint2double((int)yhi, (int)ylo);
+    const double h = __hiloint2double((int)(yhi - (1u << 20)), (int)ylo);  // y / 2
+    double r = d2 * y;
+    r = fma(h, fma(-r, r, d2), r);
+    r = fma(h, fma(-r, r, d2), r);
+    return r;
+}
+
+// FP64 Matern from a squared distance with the two routines above (same parameterisation
+// as matern<double>).
+__device__ __forceinline__ double matern_d2_fast(const KP<double>& k, double d2, const double* __restrict__ tab) {
+    const double t = k.c_over_ell * sqrt_newton(d2);
+    const double e = exp_neg_table(-t, tab);
+    if (k.nu_x2 == 1) return k.s2 * e;
+    if (k.nu_x2 == 3) return k.s2 * fma(t, e, e);
+    return k.s2 * fma(fma(t, 1.0 / 3.0, 1.0), t * e, e);
+}
+
 #define SIC_CUDA_TRY(expr)                        \
     do {                                          \
         cudaError_t _e = (expr);                  \

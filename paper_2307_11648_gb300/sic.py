@@ -30,6 +30,7 @@ EXPORTS = [
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
     "sic_matern_matvec", "sic_pcg_workspace", "sic_pcg_solve", "sic_selftest_wait_timeout",
+    "sic_selftest_fp64_math",
     "sic_mlp_param_count", "sic_proposal_features", "sic_proposal_score",
     "sic_proposal_topk", "sic_proposal_labels", "sic_mlp_train_workspace", "sic_mlp_grads", "sic_adamw_step",
 ]
@@ -91,6 +92,7 @@ def lib():
             "sic_apply_factor": (st, [vp, i64, vp, vp, vp, st, vp, vp, i32, vp, sz, vp]),
             "sic_matern_matvec": (st, [vp, vp, i64, pk, d, st, vp, vp, i32, vp]),
             "sic_selftest_wait_timeout": (st, [vp, i64, vp, vp]),
+            "sic_selftest_fp64_math": (st, [vp, pk, vp, i64, vp, vp, vp, vp]),
             "sic_pcg_workspace": (st, [i64, i32, C.POINTER(sz)]),
             "sic_pcg_solve": (st, [vp, vp, i64, pk, d, st, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp, sz, vp]),
             "sic_mlp_param_count": (i32, []),
@@ -453,3 +455,15 @@ def selftest_wait_timeout(h: Handle, cap: int, out, stream=None):
     import torch
     _check(lib().sic_selftest_wait_timeout(h.ptr, int(cap), _dptr(out, torch.int32, "out"), _stream(stream)),
            "sic_selftest_wait_timeout", h)
+
+
+def selftest_fp64_math(h: Handle, kp: Kernel, x, stream=None):
+    """sqrt(x), exp(-x) and the Matern at squared distance x by the fill's FP64 device
+    routines; x is a CUDA float64 tensor, returns three tensors like it."""
+    import torch
+    x = x.contiguous()
+    outs = [torch.empty_like(x) for _ in range(3)]
+    _check(lib().sic_selftest_fp64_math(h.ptr, C.byref(kp), _dptr(x, torch.float64, "x"), x.numel(),
+                                        *[_dptr(o, torch.float64, "out") for o in outs], _stream(stream)),
+           "sic_selftest_fp64_math", h)
+    return outs

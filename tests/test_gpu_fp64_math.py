@@ -1,0 +1,85 @@
+"""The fill's FP64 device routines against CUDA's library functions and the oracle.
+
+  * square root (FP32 seed + two Newton steps): within 1 ulp of the correctly rounded
+    sqrt (torch.sqrt on the device);
+  * exp(-x) (table-driven reduction after Tang, 1989): within 2 ulp of CUDA's exp
+    (torch.exp on the device) and of the host's exp, and 0 below -700;
+  * the Matern at squared distance d2: within (6 + 3t) * 2^-52 relative of the oracle's
+    FP64 Matern (t = sqrt(2 nu) r / ell; the two sides round t differently by up to ~2
+    ulp, and an ulp of t moves exp(-t) by t ulp).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+ULP = 2.0 ** -52
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_11648_gb300 import build
+    build.build()
+    from paper_2307_11648_gb300 import sic
+    return torch, sic, sic.Handle(0)
+
+
+def _inputs(torch):
+    u = synthetic.uniform(71, 0, 200000)
+    x = np.concatenate([
+        np.exp(np.log(1e-36) + u[:50000] * (np.log(1e36) - np.log(1e-36))),  # log-uniform 1e-36 .. 1
+        u[50000:150000] * 40.0,                                              # the Matern range
+        u[150000:] * 750.0,                                                  # up to the cut-off
+        [0.0, 1e-40, 2.0 ** -120, 1.0, 4.0, 699.9, 700.0, 700.5, 1e30, 1e40],
+    ])
+    return torch.tensor(x, dtype=torch.float64, device="cuda"), x
+
+
+def test_sqrt_and_exp_against_cuda(env):
+    torch, sic, h = env
+    kp = sic.kernel(2, 3, 0.1, 1.0, 0.0)
+    xt, x = _inputs(torch)
+    s, e, _ = sic.selftest_fp64_math(h, kp, xt)
+    h.sync()
+    s = s.cpu().numpy()
+    e = e.cpu().numpy()
+    s_ref = torch.sqrt(xt).cpu().numpy()
+    ok = x >= 2.0 ** -120
+    assert np.all(s[~ok] == 0.0)
+    rel = np.abs(s[ok] - s_ref[ok]) / s_ref[ok]
+    print("sqrt max rel err", rel.max() / ULP, "ulp")
+    assert rel.max() <= ULP
+    e_cuda = torch.exp(-xt).cpu().numpy()
+    e_host = np.exp(-x)
+    live = x <= 700.0
+    assert np.all(e[~live] == 0.0)
+    for ref, name in [(e_cuda, "cuda"), (e_host, "host")]:
+        r = np.abs(e[live] - ref[live]) / ref[live]
+        print(f"exp max rel err vs {name}", r.max() / ULP, "ulp")
+        assert r.max() <= 2 * ULP
+
+
+@pytest.mark.parametrize("nu_x2", [1, 3, 5])
+def test_matern_against_oracle(env, oracle_lib, nu_x2):
+    torch, sic, h = env
+    ell, s2 = 0.07, 1.7
+    kp = sic.kernel(3, nu_x2, ell, s2, 0.0)
+    d2 = synthetic.uniform(72, nu_x2, 100000) * (20 * ell) ** 2
+    d2[:3] = [0.0, 1e-30, ell * ell]
+    _, _, kv = sic.selftest_fp64_math(h, kp, torch.tensor(d2, dtype=torch.float64, device="cuda"))
+    h.sync()
+    kv = kv.cpu().numpy()
+    okp = oracle_lib.kernel(3, nu_x2, ell, s2, 0.0)
+    r = np.sqrt(d2)
+    ref = np.array([oracle_lib.matern(okp, v) for v in r])
+    t = math.sqrt(nu_x2) * r / ell
+    err = np.abs(kv - ref) / (ref * (6 + 3 * t) * ULP)
+    print(f"nu={nu_x2}/2 Matern max err / ((6 + 3t) ulp)", err.max())
+    assert err.max() <= 1.0

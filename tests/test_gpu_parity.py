@@ -10,8 +10,11 @@ and a different exp implementation, ~1e-16 relative per operation):
     an absolute rounding of eps32 * variance = 6e-8 * variance, and after up to 64
     downdates the conditional (co)variances carry ~sqrt(64) times that, so scores
     closer than ~1e-6 * variance are not resolved in FP32.  Single-target scores
-    (cov^2 / var) are absolute; multi-target scores (var / var|P) are ratios, so only
-    the relative band applies to them;
+    (cov^2 / var) get that absolute band directly.  Multi-target scores are ratios
+    var|S / var|(P, S) (Section 5.2) of two such variances, so a differing pick is also
+    accepted when the ratios overlap with each variance known to +-FP32_ABS * variance:
+    (v1_c + E) / (v2_c - E) >= (v1_b - E) / (v2_b + E).  This matters where the targets
+    nearly determine a candidate (var|(P, S) ~ 2 * nugget on the finest-scale groups);
   * fill: row indices identical; values max|dL| <= 1e-8 * max|L| per column;
     log v_i to 1e-9 absolute (log v is O(10), so 1e-10 relative);
   * KL sum: 1e-9 relative.
@@ -174,11 +177,12 @@ def test_aggregated_small_full(env, oracle_lib, prec_name):
     P = hp.pts
     stats = ReplayStats()
     band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    var_abs = 0.0 if prec_name == "fp64" else FP32_ABS * kp.variance
     gp = hp.grp_ptr
     for g in range(len(gp) - 1):
         g0, g1 = int(gp[g]), int(gp[g + 1])
         cand = hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]]
-        replay_multi(oracle, okp, P, g0, g1 - g0, cand, hp.k, sels[g], band, stats)
+        replay_multi(oracle, okp, P, g0, g1 - g0, cand, hp.k, sels[g], band, stats, var_abs=var_abs)
     print(prec_name, stats)
     cp, ri, val, logv = fb.csc()
     worst = 0.0
@@ -218,12 +222,13 @@ def test_aggregated_full_size_sampled(env, oracle_lib, prec_name):
     groups = sorted(set(rng.choice(G - 50, 10, replace=False).tolist()) | {G - 40, G - 3, G - 1})
     stats = ReplayStats()
     band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    var_abs = 0.0 if prec_name == "fp64" else FP32_ABS * kp.variance
     cp, ri, val, logv = fb.csc()
     for g in groups:
         g0, g1 = int(gp[g]), int(gp[g + 1])
         cand = oracle.knn_later(P, np.arange(g0, g1), g1, cfg["n_cand"])
         assert cand.tolist() == hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]].tolist()
-        replay_multi(oracle, okp, P, g0, g1 - g0, cand, hp.k, sels[g], band, stats)
+        replay_multi(oracle, okp, P, g0, g1 - g0, cand, hp.k, sels[g], band, stats, var_abs=var_abs)
         for a in range(g1 - g0):
             rows, L, lv = oracle.fill_member(okp, P, g0, g1 - g0, a, sels[g])
             c = g0 + a
@@ -231,6 +236,52 @@ def test_aggregated_full_size_sampled(env, oracle_lib, prec_name):
             assert column_errors(val[cp[c]:cp[c + 1]], L) <= L_TOL
             assert abs(logv[c] - lv) <= LOGV_TOL
     print(prec_name, stats, "sum logv", float(fb.sum_logv.cpu()[0]))
+    assert np.all(np.isfinite(logv))
+
+
+@pytest.mark.parametrize("prec_name", ["fp32", "fp64"])
+def test_aggregated_full_size_top256_sampled(env, oracle_lib, prec_name):
+    """Config-3 workload at full size with every candidate list cut to its 256 nearest
+    entries (the list length the learned proposal hands to the selection; it runs the
+    two-threads-per-candidate shared-memory kernel).  Sampled groups against the oracle,
+    which computes the 256 nearest later points itself."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    cfg = synthetic.PRESETS["cfg3_aggregated"]
+    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"])
+    hp = _cfg3_problem(env)
+    top = 256
+    cnt = np.minimum(np.diff(hp.cand_ptr), top)
+    dptr = np.zeros(len(cnt) + 1, np.int64)
+    dptr[1:] = np.cumsum(cnt)
+    keep = np.repeat(hp.cand_ptr[:-1], cnt) + (np.arange(int(dptr[-1])) - np.repeat(dptr[:-1], cnt))
+    didx = np.ascontiguousarray(hp.cand_idx[keep])
+    dhp = pipeline.HostProblem(hp.pts, hp.kp, hp.k, dptr, didx, hp.grp_ptr, hp.order, hp.ell2)
+    prec = sic.SIC_FP64 if prec_name == "fp64" else sic.SIC_FP32_MIXED
+    fb = _run(env, dhp, prec)
+    sels = fb.sel_lists()
+    okp = _okernel(oracle, kp)
+    P = hp.pts
+    gp = hp.grp_ptr
+    G = len(gp) - 1
+    rng = np.random.default_rng(5)
+    groups = sorted(set(rng.choice(G - 50, 12, replace=False).tolist()) | {0, G - 7, G - 2, G - 1})
+    stats = ReplayStats()
+    band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    var_abs = 0.0 if prec_name == "fp64" else FP32_ABS * kp.variance
+    cp, ri, val, logv = fb.csc()
+    for g in groups:
+        g0, g1 = int(gp[g]), int(gp[g + 1])
+        cand = oracle.knn_later(P, np.arange(g0, g1), g1, top)
+        assert cand.tolist() == didx[dptr[g]:dptr[g + 1]].tolist()
+        replay_multi(oracle, okp, P, g0, g1 - g0, cand, hp.k, sels[g], band, stats, var_abs=var_abs)
+        for a in range(g1 - g0):
+            rows, L, lv = oracle.fill_member(okp, P, g0, g1 - g0, a, sels[g])
+            c = g0 + a
+            assert ri[cp[c]:cp[c + 1]].tolist() == rows.tolist()
+            assert column_errors(val[cp[c]:cp[c + 1]], L) <= L_TOL
+            assert abs(logv[c] - lv) <= LOGV_TOL
+    print(prec_name, "top-256", stats, "sum logv", float(fb.sum_logv.cpu()[0]))
     assert np.all(np.isfinite(logv))
 
 
