@@ -318,13 +318,15 @@ sic_status sic_adamw_step(sic_handle* h, float* params, float* m, float* v, cons
  * tensor-core operation never completes; the context stays usable. */
 sic_status sic_selftest_wait_timeout(sic_handle* h, int64_t cap, int32_t* out, void* stream);
 
-/* Evaluates the FP64 device routines behind the fill's kernel entries (not part of the
- * paper) on n inputs x[i] >= 0 [device]: out_sqrt[i] = sqrt(x[i]) by the Newton-refined
- * square root, out_exp[i] = exp(-x[i]) by the table-driven exponential, and
- * out_kernel[i] = the Matern covariance of *kp (no nugget) at squared distance x[i], all
- * [device, n doubles].  Tests compare them with the library and oracle functions. */
+/* Evaluates the FP64 device routines behind the fill (not part of the paper) on n inputs
+ * x[i] >= 0 [device]: out_sqrt[i] = sqrt(x[i]) and out_rsqrt[i] = 1/sqrt(x[i]) by the
+ * Newton-refined routines (out_rsqrt undefined at x = 0), out_exp[i] = exp(-x[i]) by the
+ * table-driven exponential, and out_kernel[i] = the Matern covariance of *kp (no nugget)
+ * at squared distance x[i], all [device, n doubles].  Tests compare them with the
+ * library and oracle functions. */
 sic_status sic_selftest_fp64_math(sic_handle* h, const sic_kernel* kp, const double* x, int64_t n,
-                                  double* out_sqrt, double* out_exp, double* out_kernel, void* stream);
+                                  double* out_sqrt, double* out_rsqrt, double* out_exp, double* out_kernel,
+                                  void* stream);
 
 #ifdef __cplusplus
 }

@@ -5,8 +5,8 @@
 // s = (P_0..P_{m-1}, S sorted), the factor block is L = U^{-T} where U U^T =
 // Theta_{s,s}, U upper triangular.  The CTA forms Theta on the reversed order
 // R = reverse(s) in packed lower storage in shared memory (one entry per thread), factors
-// it G G^T = Theta_{RR} (left-looking: thread = row, one dot product per entry; the
-// pivot's thread alone takes sqrt and reciprocal), and since U = J G J (J the reversal),
+// it G G^T = Theta_{RR} (right-looking, the trailing update flat over the threads; one
+// thread takes each pivot's square root and reciprocal), and since U = J G J (J the reversal),
 // member a's column is J G^{-T} e_j with j = n-1-a: one back substitution per member,
 // one member per warp, the right-hand side in registers.  v_a = G_jj^2, so
 // logv = 2 log G_jj (eq. inverse_cond).  Rows are written diagonal first, then
@@ -107,14 +107,28 @@ __global__ void k_scan_add(long long* __restrict__ v, long long n, const long lo
 constexpr int FILL_NT = 128;   // 4 warps per unit
 constexpr int FILL_SLOTS = 6;  // right-hand-side entries per lane: nn <= 192 = 32 * FILL_SLOTS
 
-__device__ __forceinline__ long long pk(int i, int j) { return (long long)i * (i + 1) / 2 + j; }
+// Packed lower-triangle index (nn <= 192, so every index fits in 32 bits; 32-bit integer
+// arithmetic and int-to-float conversions stay off the FP64 pipe).
+__device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }
 
 // row i of the packed lower triangle that holds flat entry e (i(i+1)/2 <= e < (i+1)(i+2)/2)
-__device__ __forceinline__ int pk_row(long long e) {
+__device__ __forceinline__ int pk_row(int e) {
     int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-    while ((long long)i * (i + 1) / 2 > e) --i;
-    while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
+    while (i * (i + 1) / 2 > e) --i;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
     return i;
+}
+
+// Pivot of column c from its final Schur complement v: G_cc = sqrt(v) and 1 / G_cc;
+// a non-positive pivot raises *bad.
+__device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* rG, int* bad) {
+    if (!(v > 0.0)) {
+        *bad = 1;
+        return;
+    }
+    const double r = rsqrt_newton(v);
+    G[pk(c, c)] = v * r;
+    rG[c] = r;
 }
 
 __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
@@ -128,7 +142,8 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
     const int nmax = k + max_m;
     double* G = smem_d;                                     // packed lower, nmax(nmax+1)/2
     double* rG = G + (long long)nmax * (nmax + 1) / 2;      // 1 / G_jj
-    double* xyz = rG + nmax;                                // 3 x nmax
+    double* cj = rG + nmax;                                 // the current column of G
+    double* xyz = cj + nmax;                                // 3 x nmax
     double* tab = xyz + 3 * nmax;                           // 2^(j/64), j < 64 (exp_neg_table)
     int* pos = reinterpret_cast<int*>(tab + 64);            // nmax
     int* srt = pos + nmax;                                  // k
@@ -174,10 +189,10 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
         if (tid == 0) s_bad = 0;
         __syncthreads();
         // Theta_RR, packed lower, one flat entry per thread
-        const long long tri = (long long)nn * (nn + 1) / 2;
-        for (long long e = tid; e < tri; e += FILL_NT) {
+        const int tri = nn * (nn + 1) / 2;
+        for (int e = tid; e < tri; e += FILL_NT) {
             const int i = pk_row(e);
-            const int j = (int)(e - (long long)i * (i + 1) / 2);
+            const int j = e - i * (i + 1) / 2;
             const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j],
                          dz = xyz[2 * nmax + i] - xyz[2 * nmax + j];
             double v = matern_d2_fast(kp, fma(dz, dz, fma(dy, dy, dx * dx)), tab);
@@ -185,46 +200,36 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
             G[e] = v;
         }
         __syncthreads();
-        // left-looking Cholesky: column j, thread owns rows j + tid and j + tid + FILL_NT
-        // (nn <= 192 < 2 * FILL_NT).  The pivot's thread alone takes the square root and
-        // its reciprocal; the others scale their entry once the reciprocal is published.
+        // right-looking Cholesky in place on the packed lower triangle: for column j,
+        // G_jj = sqrt(A_jj) (taken, with its reciprocal, by the one thread that last
+        // updated A_jj), G_ij = A_ij / G_jj, then A_il -= G_ij G_lj over the trailing
+        // triangle j < l <= i with one flat entry per thread.  The FP64 units are per SM
+        // sub-partition and charge a warp instruction whatever its active lanes, so the
+        // flat update keeps all four warps equally loaded with full warps.
+        if (tid == 0) fill_pivot(G[0], 0, G, rG, &s_bad);
+        __syncthreads();
         for (int j = 0; j < nn; ++j) {
-            const long long rj = pk(j, 0);
-            double sv[2] = {0.0, 0.0};
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int i = j + tid + h * FILL_NT;
-                if (i < nn) {
-                    const long long ri = pk(i, 0);
-                    double s0 = G[ri + j], s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                    int l = 0;
-                    for (; l + 4 <= j; l += 4) {
-                        s0 = fma(-G[ri + l], G[rj + l], s0);
-                        s1 = fma(-G[ri + l + 1], G[rj + l + 1], s1);
-                        s2 = fma(-G[ri + l + 2], G[rj + l + 2], s2);
-                        s3 = fma(-G[ri + l + 3], G[rj + l + 3], s3);
-                    }
-                    for (; l < j; ++l) s0 = fma(-G[ri + l], G[rj + l], s0);
-                    sv[h] = (s0 + s1) + (s2 + s3);
-                }
-            }
-            if (tid == 0) {
-                if (!(sv[0] > 0.0)) {
-                    s_bad = 1;
-                } else {
-                    const double d = sqrt(sv[0]);
-                    G[rj + j] = d;
-                    rG[j] = 1.0 / d;
-                }
-            }
-            __syncthreads();
             if (s_bad) break;
             const double rd = rG[j];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int i = j + tid + h * FILL_NT;
-                if (i > j && i < nn) G[pk(i, j)] = sv[h] * rd;
+            for (int i = j + 1 + tid; i < nn; i += FILL_NT) {
+                const int a = pk(i, j);
+                const double g = G[a] * rd;
+                G[a] = g;
+                cj[i] = g;
             }
+            __syncthreads();
+            const int nt = nn - 1 - j;
+            const int T = nt * (nt + 1) / 2;
+            double piv = 1.0;
+            for (int e = tid; e < T; e += FILL_NT) {
+                const int ii = pk_row(e);
+                const int i = ii + j + 1, l = e - ii * (ii + 1) / 2 + j + 1;
+                const int a = pk(i, l);
+                const double v = fma(-cj[i], cj[l], G[a]);
+                G[a] = v;
+                if (e == 0) piv = v;
+            }
+            if (tid == 0 && nt > 0) fill_pivot(piv, j + 1, G, rG, &s_bad);
             __syncthreads();
         }
         __syncthreads();
@@ -236,9 +241,9 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
         // H = rows of G scaled by their reciprocal pivots (off-diagonal entries), so that
         // the back substitution G^T x = b reads y_l = b_l and updates b_i -= H_li y_l,
         // with x_l = y_l / G_ll applied once at the end.
-        for (long long e = tid; e < tri; e += FILL_NT) {
+        for (int e = tid; e < tri; e += FILL_NT) {
             const int i = pk_row(e);
-            const int j = (int)(e - (long long)i * (i + 1) / 2);
+            const int j = e - i * (i + 1) / 2;
             if (j < i) G[e] *= rG[i];
         }
         __syncthreads();
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
                 const int top = min(jb, 32 * sb + 31);
                 for (int l = top; l >= 32 * sb; --l) {
                     const double y = __shfl_sync(0xffffffffu, bv[sb], l & 31);
-                    const long long rl = pk(l, 0);
+                    const int rl = pk(l, 0);
 #pragma unroll
                     for (int q = 0; q <= sb; ++q) {
                         const int i = lane + 32 * q;
@@ -311,17 +316,18 @@ __global__ void __launch_bounds__(256) k_sum_final(const double* __restrict__ pa
 
 size_t fill_smem_bytes(int k, int max_m) {
     size_t nmax = (size_t)k + (size_t)max_m;
-    return sizeof(double) * (nmax * (nmax + 1) / 2 + nmax + 3 * nmax + 64) + sizeof(int) * (nmax + (size_t)k);
+    return sizeof(double) * (nmax * (nmax + 1) / 2 + 2 * nmax + 3 * nmax + 64) + sizeof(int) * (nmax + (size_t)k);
 }
 
 __global__ void k_fp64_math(KP<double> kp, const double* __restrict__ x, long long n, double* __restrict__ os,
-                            double* __restrict__ oe, double* __restrict__ ok) {
+                            double* __restrict__ orr, double* __restrict__ oe, double* __restrict__ ok) {
     __shared__ double tab[64];
     exp_table_fill(tab);
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double v = x[i];
         os[i] = sqrt_newton(v);
+        orr[i] = v > 0.0 ? rsqrt_newton(v) : 0.0;
         oe[i] = exp_neg_table(-v, tab);
         ok[i] = matern_d2_fast(kp, v, tab);
     }
@@ -332,15 +338,16 @@ __global__ void k_fp64_math(KP<double> kp, const double* __restrict__ x, long lo
 // ---------------------------------------------------------------- entry points --
 
 extern "C" sic_status sic_selftest_fp64_math(sic_handle* h, const sic_kernel* kp, const double* x, int64_t n,
-                                             double* out_sqrt, double* out_exp, double* out_kernel, void* stream) {
-    if (!h || !sic_valid_kernel(kp) || n < 0 || (n > 0 && (!x || !out_sqrt || !out_exp || !out_kernel)))
+                                             double* out_sqrt, double* out_rsqrt, double* out_exp,
+                                             double* out_kernel, void* stream) {
+    if (!h || !sic_valid_kernel(kp) || n < 0 || (n > 0 && (!x || !out_sqrt || !out_rsqrt || !out_exp || !out_kernel)))
         return SIC_ERR_INVALID;
     if (n == 0) return SIC_OK;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     long long blocks = (n + 255) / 256;
     if (blocks > 4LL * h->num_sms) blocks = 4LL * h->num_sms;
-    k_fp64_math<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(make_kp<double>(*kp), x, n, out_sqrt, out_exp,
-                                                                     out_kernel);
+    k_fp64_math<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(make_kp<double>(*kp), x, n, out_sqrt, out_rsqrt,
+                                                                     out_exp, out_kernel);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }

@@ -1,0 +1,336 @@
+// Supernodal greedy selection with register-resident factor rows (Section 5.2, the
+// Cholesky approach of Appendix C.2), FP32, for up to 256 candidates, m <= 64 targets and
+// k <= 64 picks: the shape of the learned proposal's survivor lists.
+//
+// Thread r owns candidate row r for the whole group.  Its rows of the two partial factors
+// live in registers: F2P[0..m) (targets' columns of F2, i.e. Theta_{r,P} chol(Theta_PP)^-T),
+// F2S[0..t) (the picks' columns of F2) and F1[0..t) (the picks' columns of F1).  A step's
+// left-looking dot products therefore read only the pivot's rows, which every thread
+// reads as the same (broadcast) 16-byte words from a shared-memory mirror of all rows;
+// the mirror is written one entry per row per step.  Register arrays are indexed
+// statically: dot products run over whole 16-element blocks (the entries beyond the
+// current length are zero on both sides) and the new column is written by a
+// block-selected put.
+//
+// Per group: warp 0 factors Theta_PP (FP32, left-looking, lanes own rows); every thread
+// evaluates its Theta_{r,P} and solves for F2P by forward substitution (static loops);
+// then k steps, each with a single block barrier: the warp argmax is one redux over
+// order-preserving score keys (ties: lowest lane = lowest candidate index), the warp
+// winners go to double-buffered shared slots with their V1/V2, and every thread reduces
+// the eight slots itself.  Same scores, exhaustion rule and tie-break as k_select_agg.
+#include "sic_internal.cuh"
+
+namespace {
+
+constexpr int RNT = 256;       // threads = max candidates
+constexpr int RK = 64;         // max picks
+constexpr int RM = 64;         // max targets
+constexpr int RP = RK + 4;     // mirror pitch of F1 and F2S rows (floats)
+constexpr int RPM = RM + 4;    // mirror pitch of F2P rows and of the target factor
+constexpr int LDX = RNT + RM;  // staged coordinates: candidates then targets
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned score_key(float s) {
+    const unsigned b = __float_as_uint(s);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // monotone in s; 0 is below every key
+}
+
+// acc - r . piv over the 16-element blocks that start below len (r is zero from len on,
+// piv is finite everywhere)
+template <int N>
+__device__ __forceinline__ float reg_dot(float acc, const float (&r)[N], const float* __restrict__ piv, int len) {
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int b = 0; b < N / 16; ++b) {
+        if (16 * b < len) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int e = 16 * b + 4 * c;
+                const float4 p = *reinterpret_cast<const float4*>(piv + e);
+                acc = fmaf(-r[e], p.x, acc);
+                a1 = fmaf(-r[e + 1], p.y, a1);
+                a2 = fmaf(-r[e + 2], p.z, a2);
+                a3 = fmaf(-r[e + 3], p.w, a3);
+            }
+        }
+    }
+    return (acc + a1) + (a2 + a3);
+}
+
+// r[idx] = v for a run-time idx: the 4-element block that holds it is found by a uniform
+// compare per block (blocks expanded by template recursion), the element by predicated
+// moves in inline PTX; both keep every array index static, so the arrays stay in
+// registers instead of local memory
+__device__ __forceinline__ void put_if(float& x, int idx, int e, float v) {
+    asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %1, %2;\n\t@p mov.f32 %0, %3;\n\t}" : "+f"(x) : "r"(idx), "r"(e), "f"(v));
+}
+
+template <int C, int N>
+__device__ __forceinline__ void reg_put_from(float (&r)[N], int idx, float v) {
+    if constexpr (C < N / 4) {
+        if (C == (idx >> 2)) {
+            put_if(r[4 * C], idx, 4 * C, v);
+            put_if(r[4 * C + 1], idx, 4 * C + 1, v);
+            put_if(r[4 * C + 2], idx, 4 * C + 2, v);
+            put_if(r[4 * C + 3], idx, 4 * C + 3, v);
+        }
+        reg_put_from<C + 1>(r, idx, v);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void reg_put(float (&r)[N], int idx, float v) {
+    reg_put_from<0>(r, idx, v);
+}
+
+__global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
+    const double* __restrict__ pts, long long n, int dim, KP<float> kp, float floor_,
+    const long long* __restrict__ grp_ptr, long long n_grp, const long long* __restrict__ cand_ptr,
+    const int32_t* __restrict__ cand_idx, int k, int32_t* __restrict__ sel_idx, int32_t* __restrict__ sel_count,
+    DevStatus* st) {
+    extern __shared__ __align__(16) float smf[];
+    float* F1m = smf;                 // [RNT][RP]
+    float* F2Sm = F1m + RNT * RP;     // [RNT][RP]
+    float* F2Pm = F2Sm + RNT * RP;    // [RNT][RPM]
+    float* X = F2Pm + RNT * RPM;      // [3][LDX]
+    float* Lp = F1m;                  // [RM][RPM] chol(Theta_PP), overlays F1m before the steps
+    float* rLp = F1m + RM * RPM;      // [RM] reciprocal diagonal of Lp
+    __shared__ unsigned pkey[2][RNT / 32];
+    __shared__ int pidx[2][RNT / 32];
+    __shared__ float pv1[2][RNT / 32], pv2[2][RNT / 32];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float NEG = -INFINITY;
+    const float diag = kp.s2 + kp.nugget;
+
+    for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
+        const long long g0 = grp_ptr[g];
+        const int m = (int)(grp_ptr[g + 1] - g0);
+        const long long b0 = cand_ptr[g];
+        const int C = (int)(cand_ptr[g + 1] - b0);
+        if (m < 1 || m > RM || C < 0 || C > RNT || g0 < 0 || g0 + m > n) {
+            if (tid == 0) {
+                record_error(st, SIC_ERR_INVALID, g);
+                sel_count[g] = 0;
+            }
+            for (int q = tid; q < k; q += RNT) sel_idx[g * k + q] = -1;
+            continue;
+        }
+        // ---- stage coordinates relative to the first member (differences formed in FP64)
+        double org[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) org[d] = pts[g0 * dim + d];
+        bool live = false;
+        if (tid < C) {
+            long long p = cand_idx[b0 + tid];
+            live = true;
+            if (p < g0 + m || p >= n) {  // candidates must lie after the group
+                record_error(st, SIC_ERR_INVALID, g);
+                p = g0;
+                live = false;
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) X[d * LDX + tid] = (d < dim) ? (float)(pts[p * dim + d] - org[d]) : 0.f;
+        }
+        if (tid < m) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                X[d * LDX + RNT + tid] = (d < dim) ? (float)(pts[(g0 + tid) * dim + d] - org[d]) : 0.f;
+        }
+        // zero this thread's pick mirrors except F1m (which holds Lp until the steps)
+#pragma unroll
+        for (int c = 0; c < RP / 4; ++c)
+            *reinterpret_cast<float4*>(F2Sm + tid * RP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tid < RM) {
+#pragma unroll
+            for (int c = 0; c < RPM / 4; ++c)
+                *reinterpret_cast<float4*>(Lp + tid * RPM + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (tid == 0) s_fail = 0;
+        __syncthreads();
+        const float xr = live ? X[tid] : 0.f, yr = live ? X[LDX + tid] : 0.f, zr = live ? X[2 * LDX + tid] : 0.f;
+
+        // ---- Theta_{r,P} of the own row (kept in F2P until the forward substitution)
+        float F2P[RM];
+#pragma unroll
+        for (int a = 0; a < RM; ++a) {
+            F2P[a] = 0.f;
+            if (live && a < m) {
+                const float dx = xr - X[RNT + a], dy = yr - X[LDX + RNT + a], dz = zr - X[2 * LDX + RNT + a];
+                F2P[a] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+            }
+        }
+        // ---- Lp = chol(Theta_PP) by warp 0, left-looking, lane owns rows lane and lane + 32
+        if (warp == 0) {
+            for (int j = 0; j < m; ++j) {
+                const float xj = X[RNT + j], yj = X[LDX + RNT + j], zj = X[2 * LDX + RNT + j];
+                float sv[2] = {0.f, 0.f};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = lane + 32 * h;
+                    if (i >= j && i < m) {
+                        const float dx = X[RNT + i] - xj, dy = X[LDX + RNT + i] - yj, dz = X[2 * LDX + RNT + i] - zj;
+                        float th = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                        if (i == j) th += kp.nugget;
+                        const float* ri = Lp + i * RPM;
+                        const float* rj = Lp + j * RPM;
+                        float s0 = th, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                        int l = 0;
+                        for (; l + 4 <= j; l += 4) {
+                            const float4 a = *reinterpret_cast<const float4*>(ri + l);
+                            const float4 b = *reinterpret_cast<const float4*>(rj + l);
+                            s0 = fmaf(-a.x, b.x, s0);
+                            s1 = fmaf(-a.y, b.y, s1);
+                            s2 = fmaf(-a.z, b.z, s2);
+                            s3 = fmaf(-a.w, b.w, s3);
+                        }
+                        for (; l < j; ++l) s0 = fmaf(-ri[l], rj[l], s0);
+                        sv[h] = (s0 + s1) + (s2 + s3);
+                    }
+                }
+                const float sjj = __shfl_sync(FULL, j < 32 ? sv[0] : sv[1], j & 31);
+                if (!(sjj > 0.f)) {
+                    if (lane == 0) {
+                        record_error(st, SIC_ERR_NOT_PD, g);
+                        s_fail = 1;
+                    }
+                    break;
+                }
+                const float d = sqrtf(sjj), rd = 1.f / d;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = lane + 32 * h;
+                    if (i > j && i < m) Lp[i * RPM + j] = sv[h] * rd;
+                }
+                if (lane == 0) {
+                    Lp[j * RPM + j] = d;
+                    rLp[j] = rd;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (s_fail) {
+            if (tid == 0) sel_count[g] = 0;
+            for (int q = tid; q < k; q += RNT) sel_idx[g * k + q] = -1;
+            __syncthreads();
+            continue;
+        }
+        // ---- F2P = Lp^-1 Theta_{P,r} (forward substitution, in place) and V2 = Theta_rr|P
+        float V1 = live ? diag : NEG, V2 = live ? diag : NEG;
+        if (live) {
+#pragma unroll
+            for (int a = 0; a < RM; ++a) {
+                if (a < m) {
+                    const float* la = Lp + a * RPM;
+                    float s0 = F2P[a], s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+                    for (int c = 0; c + 4 <= a; c += 4) {
+                        const float4 l4 = *reinterpret_cast<const float4*>(la + c);
+                        s0 = fmaf(-F2P[c], l4.x, s0);
+                        s1 = fmaf(-F2P[c + 1], l4.y, s1);
+                        s2 = fmaf(-F2P[c + 2], l4.z, s2);
+                        s3 = fmaf(-F2P[c + 3], l4.w, s3);
+                    }
+#pragma unroll
+                    for (int c = a & ~3; c < a; ++c) s0 = fmaf(-F2P[c], la[c], s0);
+                    const float u = ((s0 + s1) + (s2 + s3)) * rLp[a];
+                    F2P[a] = u;
+                    V2 = fmaf(-u, u, V2);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < RM / 4; ++c)
+            *reinterpret_cast<float4*>(F2Pm + tid * RPM + 4 * c) =
+                make_float4(F2P[4 * c], F2P[4 * c + 1], F2P[4 * c + 2], F2P[4 * c + 3]);
+        if (tid < RNT) {  // the tail of the pitch
+            *reinterpret_cast<float4*>(F2Pm + tid * RPM + RM) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();  // Lp is no longer read: F1m becomes the F1 mirror
+#pragma unroll
+        for (int c = 0; c < RP / 4; ++c)
+            *reinterpret_cast<float4*>(F1m + tid * RP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+        float F1[RK], F2S[RK];
+#pragma unroll
+        for (int c = 0; c < RK; ++c) {
+            F1[c] = 0.f;
+            F2S[c] = 0.f;
+        }
+        __syncthreads();
+
+        // ---- the greedy steps
+        int t = 0;
+        for (; t < k; ++t) {
+            const int buf = t & 1;
+            const unsigned key = (V2 >= floor_) ? score_key(V1 / V2) : 0u;
+            const unsigned wmax = __reduce_max_sync(FULL, key);
+            const unsigned hit = __ballot_sync(FULL, key == wmax);
+            if (lane == __ffs(hit) - 1) {  // the warp's best row (lowest lane among equal keys)
+                pkey[buf][warp] = wmax;
+                pidx[buf][warp] = tid;
+                pv1[buf][warp] = V1;
+                pv2[buf][warp] = V2;
+            }
+            __syncthreads();
+            unsigned bk = pkey[buf][0];
+            int bw = 0;
+#pragma unroll
+            for (int w = 1; w < RNT / 32; ++w) {
+                const unsigned kw = pkey[buf][w];
+                if (kw > bk) {
+                    bk = kw;
+                    bw = w;
+                }
+            }
+            if (bk == 0u) break;
+            const int q = pidx[buf][bw];
+            const float r1 = 1.f / sqrtf(pv1[buf][bw]);
+            const float r2 = 1.f / sqrtf(pv2[buf][bw]);
+            if (V2 != NEG) {
+                const float dx = xr - X[q], dy = yr - X[LDX + q], dz = zr - X[2 * LDX + q];
+                float th = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                if (tid == q) th += kp.nugget;
+                const float n1 = reg_dot(th, F1, F1m + q * RP, t);
+                float n2 = reg_dot(th, F2P, F2Pm + q * RPM, m);
+                n2 = reg_dot(n2, F2S, F2Sm + q * RP, t);
+                const float u1 = n1 * r1, u2 = n2 * r2;
+                reg_put(F1, t, u1);
+                reg_put(F2S, t, u2);
+                F1m[tid * RP + t] = u1;
+                F2Sm[tid * RP + t] = u2;
+                if (tid == q) {
+                    V1 = NEG;
+                    V2 = NEG;
+                } else {
+                    V1 = fmaf(-u1, u1, V1);
+                    V2 = fmaf(-u2, u2, V2);
+                }
+            }
+            if (tid == 0) sel_idx[g * k + t] = cand_idx[b0 + q];
+        }
+        if (tid == 0) sel_count[g] = t;
+        for (int q = t + tid; q < k; q += RNT) sel_idx[g * k + q] = -1;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+bool agg_reg_applies(sic_precision prec, int max_cand, int max_m, int k) {
+    return prec == SIC_FP32_MIXED && max_cand <= RNT && max_m <= RM && k <= RK;
+}
+
+sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
+                          const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx,
+                          int k, int32_t* sel_idx, int32_t* sel_count, cudaStream_t s) {
+    const size_t smem = sizeof(float) * ((size_t)RNT * RP * 2 + (size_t)RNT * RPM + 3 * (size_t)LDX);
+    SIC_CUDA_TRY(cudaFuncSetAttribute(k_select_agg_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = persistent_grid(h, k_select_agg_reg, RNT, smem, n_grp > 0 ? n_grp : 1);
+    k_select_agg_reg<<<grid, RNT, smem, s>>>(pts, n, kp->dim, make_kp<float>(*kp), (float)sic_floor_of(kp),
+                                             (const long long*)grp_ptr, n_grp, (const long long*)cand_ptr, cand_idx,
+                                             k, sel_idx, sel_count, h->d_status);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}

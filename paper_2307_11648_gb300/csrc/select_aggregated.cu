@@ -1,4 +1,6 @@
 // Supernodal greedy selection (Section 5.2, multiple targets sharing one selection).
+// (FP32 with at most 256 candidates, m <= 64 and k <= 64 goes to the register-resident
+// kernel of select_agg_reg.cu.)
 //
 // One CTA owns one group at a time over a persistent grid.  The two partial Cholesky
 // factors of the paper's Cholesky approach (Appendix C.2) live in shared memory when
@@ -342,7 +344,9 @@ extern "C" sic_status sic_select_aggregated_workspace(sic_handle* h, int64_t n_g
     if (!h || !bytes || n_grp < 0 || max_cand < 0 || max_m < 1 || k < 1) return SIC_ERR_INVALID;
     if (max_m > 64 || max_cand > 4096 || k > 128) return SIC_ERR_UNSUPPORTED;
     if (cudaSetDevice(h->device) != cudaSuccess) return SIC_ERR_CUDA;
-    if (prec == SIC_FP64)
+    if (agg_reg_applies(prec, max_cand, max_m, k))
+        *bytes = 0;
+    else if (prec == SIC_FP64)
         *bytes = agg_plan<double>(h, n_grp, max_cand, max_m, k).ws_bytes;
     else if (prec == SIC_FP32_MIXED)
         *bytes = agg_plan<float>(h, n_grp, max_cand, max_m, k).ws_bytes;
@@ -390,6 +394,8 @@ extern "C" sic_status sic_select_aggregated(sic_handle* h, const double* pts, in
     if (max_cand > 0 && !cand_idx) return SIC_ERR_INVALID;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
+    if (agg_reg_applies(prec, max_cand, max_m, k))
+        return launch_agg_reg(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, k, sel_idx, sel_count, s);
     if (prec == SIC_FP64)
         return launch_agg<double>(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, sel_idx,
                                   sel_count, ws, ws_bytes, s);

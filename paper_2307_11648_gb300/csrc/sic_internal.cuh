@@ -116,6 +116,21 @@ __device__ __forceinline__ double sqrt_newton(double d2) {
     return r;
 }
 
+// 1/sqrt(x), x > 0, in FP64: the FP32 seed of sqrt_newton refined by two Newton steps
+// y <- y (3/2 - (x/2) y^2) (relative error 2^-20 -> ~2^-39 -> ~2^-77, then rounding:
+// about 2 ulp).  7 FP64 operations; x outside [2^-120, 2^120) uses 1 / sqrt(x).
+__device__ __forceinline__ double rsqrt_newton(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x);
+    if (hi < 0x38700000u || hi >= 0x47700000u) return 1.0 / sqrt(x);
+    const float f = __uint_as_float((hi << 3) - (896u << 23));
+    const unsigned yb = __float_as_uint(rsqrtf(f));
+    double y = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return y;
+}
+
 // FP64 Matern from a squared distance with the two routines above (same parameterisation
 // as matern<double>).
 __device__ __forceinline__ double matern_d2_fast(const KP<double>& k, double d2, const double* __restrict__ tab) {
@@ -155,6 +170,13 @@ static inline int persistent_grid(const sic_handle* h, K kernel, int threads, si
     if (g < 1) g = 1;
     return (int)g;
 }
+
+// register-resident FP32 supernodal selection (select_agg_reg.cu): used by
+// sic_select_aggregated when agg_reg_applies; needs no workspace
+bool agg_reg_applies(sic_precision prec, int max_cand, int max_m, int k);
+sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
+                          const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx,
+                          int k, int32_t* sel_idx, int32_t* sel_count, cudaStream_t s);
 
 // tcgen05 scoring kernel of the proposal network (mlp_tc.cu)
 sic_status sic_proposal_score_tc(sic_handle* h, const float* params, const float* feat, int64_t rows, float* score,

@@ -92,7 +92,7 @@ def lib():
             "sic_apply_factor": (st, [vp, i64, vp, vp, vp, st, vp, vp, i32, vp, sz, vp]),
             "sic_matern_matvec": (st, [vp, vp, i64, pk, d, st, vp, vp, i32, vp]),
             "sic_selftest_wait_timeout": (st, [vp, i64, vp, vp]),
-            "sic_selftest_fp64_math": (st, [vp, pk, vp, i64, vp, vp, vp, vp]),
+            "sic_selftest_fp64_math": (st, [vp, pk, vp, i64, vp, vp, vp, vp, vp]),
             "sic_pcg_workspace": (st, [i64, i32, C.POINTER(sz)]),
             "sic_pcg_solve": (st, [vp, vp, i64, pk, d, st, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp, sz, vp]),
             "sic_mlp_param_count": (i32, []),
@@ -458,11 +458,11 @@ def selftest_wait_timeout(h: Handle, cap: int, out, stream=None):
 
 
 def selftest_fp64_math(h: Handle, kp: Kernel, x, stream=None):
-    """sqrt(x), exp(-x) and the Matern at squared distance x by the fill's FP64 device
-    routines; x is a CUDA float64 tensor, returns three tensors like it."""
+    """sqrt(x), 1/sqrt(x), exp(-x) and the Matern at squared distance x by the fill's FP64
+    device routines; x is a CUDA float64 tensor, returns four tensors like it."""
     import torch
     x = x.contiguous()
-    outs = [torch.empty_like(x) for _ in range(3)]
+    outs = [torch.empty_like(x) for _ in range(4)]
     _check(lib().sic_selftest_fp64_math(h.ptr, C.byref(kp), _dptr(x, torch.float64, "x"), x.numel(),
                                         *[_dptr(o, torch.float64, "out") for o in outs], _stream(stream)),
            "sic_selftest_fp64_math", h)

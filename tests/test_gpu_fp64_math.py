@@ -1,7 +1,7 @@
 """The fill's FP64 device routines against CUDA's library functions and the oracle.
 
   * square root (FP32 seed + two Newton steps): within 1 ulp of the correctly rounded
-    sqrt (torch.sqrt on the device);
+    sqrt (torch.sqrt on the device); reciprocal square root: within 2 ulp of 1/sqrt;
   * exp(-x) (table-driven reduction after Tang, 1989): within 2 ulp of CUDA's exp
     (torch.exp on the device) and of the host's exp, and 0 below -700;
   * the Matern at squared distance d2: within (6 + 3t) * 2^-52 relative of the oracle's
@@ -46,9 +46,10 @@ def test_sqrt_and_exp_against_cuda(env):
     torch, sic, h = env
     kp = sic.kernel(2, 3, 0.1, 1.0, 0.0)
     xt, x = _inputs(torch)
-    s, e, _ = sic.selftest_fp64_math(h, kp, xt)
+    s, rs, e, _ = sic.selftest_fp64_math(h, kp, xt)
     h.sync()
     s = s.cpu().numpy()
+    rs = rs.cpu().numpy()
     e = e.cpu().numpy()
     s_ref = torch.sqrt(xt).cpu().numpy()
     ok = x >= 2.0 ** -120
@@ -56,6 +57,11 @@ def test_sqrt_and_exp_against_cuda(env):
     rel = np.abs(s[ok] - s_ref[ok]) / s_ref[ok]
     print("sqrt max rel err", rel.max() / ULP, "ulp")
     assert rel.max() <= ULP
+    pos = x > 0
+    r_ref = (1.0 / torch.sqrt(xt)).cpu().numpy()
+    rrel = np.abs(rs[pos] - r_ref[pos]) / r_ref[pos]
+    print("rsqrt max rel err", rrel.max() / ULP, "ulp")
+    assert rrel.max() <= 2 * ULP
     e_cuda = torch.exp(-xt).cpu().numpy()
     e_host = np.exp(-x)
     live = x <= 700.0
@@ -73,7 +79,7 @@ def test_matern_against_oracle(env, oracle_lib, nu_x2):
     kp = sic.kernel(3, nu_x2, ell, s2, 0.0)
     d2 = synthetic.uniform(72, nu_x2, 100000) * (20 * ell) ** 2
     d2[:3] = [0.0, 1e-30, ell * ell]
-    _, _, kv = sic.selftest_fp64_math(h, kp, torch.tensor(d2, dtype=torch.float64, device="cuda"))
+    _, _, _, kv = sic.selftest_fp64_math(h, kp, torch.tensor(d2, dtype=torch.float64, device="cuda"))
     h.sync()
     kv = kv.cpu().numpy()
     okp = oracle_lib.kernel(3, nu_x2, ell, s2, 0.0)
