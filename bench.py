@@ -44,6 +44,10 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 FFMA_PER_SM_CLK = 128   # FP32 FMA lanes per SM per clock
 DFMA_PER_SM_CLK = 2     # FP64 FMA per SM per clock on GB300 (1.26 TFLOP/s nominal at 2070 MHz)
+# kernels of one learned step: k_features, k_mlp_tc, k_topk_counts + k_scan_one_block +
+# k_topk_compact, k_select_agg_reg, k_nnz_count + k_scan_tile + k_scan_partials +
+# k_scan_add, k_fill + k_sum_tiles + k_sum_final (plus one memset node)
+LAUNCHES_PER_STEP = 13
 
 
 # ------------------------------------------------------------- clocks ---
@@ -60,6 +64,7 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        self.lines = []
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -380,7 +385,19 @@ def main():
         [lambda: pr.features(dp, lb.buf), lambda: pr.score(dp, lb.buf), lambda: pr.topk(dp, lb.buf),
          lambda: lb.fb.select(rdp), lambda: lb.fb.fill(rdp)], args.steps, args.warmup, sampler)
     prop_ms = feat_ms + mlp_ms + topk_ms
-    t_step = max_over_ranks(t_ms, ws)
+    eager_ms = max_over_ranks(t_ms, ws)
+    # the same step captured once in a CUDA graph and replayed (one graph launch per step):
+    # the headline time
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        lb.run(dp)
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        lb.run(dp)
+    g_ms, _, clocks = timed([graph.replay], args.steps, args.warmup, sampler)
+    t_step = max_over_ranks(g_ms, ws)
     value = ws * N / (t_step * 1e-3)
     S = {"learned_fp32": float(lb.sum_logv.cpu()[0])}
     nnz = int(lb.col_ptr[-1].item())
@@ -508,6 +525,9 @@ def main():
                            "select_ms": p32_sel, "fill_ms": p32_fill},
             "distance_top256_fp32": {"value": ws * N / (d_ms * 1e-3), "unit": "columns/s", "ms_per_step": d_ms},
             "speedup_vs_fp64_plain": p64_ms / t_step,
+            "timing": "CUDA graph of the whole step, replayed; phases_ms from the same launches issued "
+                      "eagerly with events between phases",
+            "eager_ms_per_step": eager_ms,
             "phases_ms": {"features": feat_ms, "mlp": mlp_ms, "topk": topk_ms, "select": sel_ms,
                           "fill_and_kl": fill_ms},
             "setup_s": {"prep_host": prep_s, "train_proposal": train_s, "train_selections": n_sel,
@@ -516,7 +536,7 @@ def main():
             "roofline": roof,
             "e2e": {"value": ws * N / (e2e_ms * 1e-3), "unit": "columns/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": 15 * args.steps,
+            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clocks,
             "pcg": pcg,
             "cpu_baseline": cpu,
