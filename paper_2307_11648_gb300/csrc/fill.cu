@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
     double* rG = G + (long long)nmax * (nmax + 1) / 2;      // 1 / G_jj
     double* cj = rG + nmax;                                 // the current column of G
     double* xyz = cj + nmax;                                // 3 x nmax
-    double* tab = xyz + 3 * nmax;                           // 2^(j/64), j < 64 (exp_neg_table)
-    int* pos = reinterpret_cast<int*>(tab + 64);            // nmax
+    double* tab = xyz + 3 * nmax;                           // 2^(j/256) (exp_neg_table)
+    int* pos = reinterpret_cast<int*>(tab + EXP_TAB);       // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -193,9 +193,13 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
         for (int e = tid; e < tri; e += FILL_NT) {
             const int i = pk_row(e);
             const int j = e - i * (i + 1) / 2;
-            const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j],
-                         dz = xyz[2 * nmax + i] - xyz[2 * nmax + j];
-            double v = matern_d2_fast(kp, fma(dz, dz, fma(dy, dy, dx * dx)), tab);
+            const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j];
+            double d2 = fma(dy, dy, dx * dx);
+            if (dim == 3) {
+                const double dz = xyz[2 * nmax + i] - xyz[2 * nmax + j];
+                d2 = fma(dz, dz, d2);
+            }
+            double v = matern_d2_fast(kp, d2, tab);
             if (i == j) v += kp.nugget;
             G[e] = v;
         }
@@ -220,8 +224,11 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
             __syncthreads();
             const int nt = nn - 1 - j;
             const int T = nt * (nt + 1) / 2;
+            // entries are dealt from thread 32 (j mod 4) on, so that the next pivot (entry 0)
+            // falls to each warp in turn and the warps' FP64 work stays equal
+            const int e0 = (tid - 32 * (j & 3)) & (FILL_NT - 1);
             double piv = 1.0;
-            for (int e = tid; e < T; e += FILL_NT) {
+            for (int e = e0; e < T; e += FILL_NT) {
                 const int ii = pk_row(e);
                 const int i = ii + j + 1, l = e - ii * (ii + 1) / 2 + j + 1;
                 const int a = pk(i, l);
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
                 G[a] = v;
                 if (e == 0) piv = v;
             }
-            if (tid == 0 && nt > 0) fill_pivot(piv, j + 1, G, rG, &s_bad);
+            if (e0 == 0 && nt > 0) fill_pivot(piv, j + 1, G, rG, &s_bad);
             __syncthreads();
         }
         __syncthreads();
@@ -316,12 +323,12 @@ __global__ void __launch_bounds__(256) k_sum_final(const double* __restrict__ pa
 
 size_t fill_smem_bytes(int k, int max_m) {
     size_t nmax = (size_t)k + (size_t)max_m;
-    return sizeof(double) * (nmax * (nmax + 1) / 2 + 2 * nmax + 3 * nmax + 64) + sizeof(int) * (nmax + (size_t)k);
+    return sizeof(double) * (nmax * (nmax + 1) / 2 + 2 * nmax + 3 * nmax + EXP_TAB) + sizeof(int) * (nmax + (size_t)k);
 }
 
 __global__ void k_fp64_math(KP<double> kp, const double* __restrict__ x, long long n, double* __restrict__ os,
                             double* __restrict__ orr, double* __restrict__ oe, double* __restrict__ ok) {
-    __shared__ double tab[64];
+    __shared__ double tab[EXP_TAB];
     exp_table_fill(tab);
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {

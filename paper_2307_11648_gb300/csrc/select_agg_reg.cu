@@ -8,9 +8,10 @@
 // left-looking dot products therefore read only the pivot's rows, which every thread
 // reads as the same (broadcast) 16-byte words from a shared-memory mirror of all rows;
 // the mirror is written one entry per row per step.  Register arrays are indexed
-// statically: dot products run over whole 16-element blocks (the entries beyond the
-// current length are zero on both sides) and the new column is written by a
-// block-selected put.
+// statically: the k steps run as four blocks of 16 with the block index a compile-time
+// constant, so the dot products over F1 and F2S run over whole 16-element blocks (entries
+// beyond the current length are zero on both sides) and the new column is written by
+// predicated moves into one block.
 //
 // Per group: warp 0 factors Theta_PP (FP32, left-looking, lanes own rows); every thread
 // evaluates its Theta_{r,P} and solves for F2P by forward substitution (static loops);
@@ -18,6 +19,8 @@
 // order-preserving score keys (ties: lowest lane = lowest candidate index), the warp
 // winners go to double-buffered shared slots with their V1/V2, and every thread reduces
 // the eight slots itself.  Same scores, exhaustion rule and tie-break as k_select_agg.
+#include <type_traits>
+
 #include "sic_internal.cuh"
 
 namespace {
@@ -57,30 +60,26 @@ __device__ __forceinline__ float reg_dot(float acc, const float (&r)[N], const f
     return (acc + a1) + (a2 + a3);
 }
 
-// r[idx] = v for a run-time idx: the 4-element block that holds it is found by a uniform
-// compare per block (blocks expanded by template recursion), the element by predicated
-// moves in inline PTX; both keep every array index static, so the arrays stay in
-// registers instead of local memory
+// acc - r . piv over the first NB 16-element blocks (static)
+template <int NB, int N>
+__device__ __forceinline__ float dot_blocks(float acc, const float (&r)[N], const float* __restrict__ piv) {
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16 * NB; e += 4) {
+        const float4 p = *reinterpret_cast<const float4*>(piv + e);
+        acc = fmaf(-r[e], p.x, acc);
+        a1 = fmaf(-r[e + 1], p.y, a1);
+        a2 = fmaf(-r[e + 2], p.z, a2);
+        a3 = fmaf(-r[e + 3], p.w, a3);
+    }
+    return (acc + a1) + (a2 + a3);
+}
+
+// x = v when idx == e, by a predicated move in inline PTX: with e static this keeps every
+// register-array index static (a C++ select on a run-time index lets the compiler turn a
+// series of them into one indexed store, which moves the array to local memory)
 __device__ __forceinline__ void put_if(float& x, int idx, int e, float v) {
     asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %1, %2;\n\t@p mov.f32 %0, %3;\n\t}" : "+f"(x) : "r"(idx), "r"(e), "f"(v));
-}
-
-template <int C, int N>
-__device__ __forceinline__ void reg_put_from(float (&r)[N], int idx, float v) {
-    if constexpr (C < N / 4) {
-        if (C == (idx >> 2)) {
-            put_if(r[4 * C], idx, 4 * C, v);
-            put_if(r[4 * C + 1], idx, 4 * C + 1, v);
-            put_if(r[4 * C + 2], idx, 4 * C + 2, v);
-            put_if(r[4 * C + 3], idx, 4 * C + 3, v);
-        }
-        reg_put_from<C + 1>(r, idx, v);
-    }
-}
-
-template <int N>
-__device__ __forceinline__ void reg_put(float (&r)[N], int idx, float v) {
-    reg_put_from<0>(r, idx, v);
 }
 
 __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
@@ -95,7 +94,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
     float* X = F2Pm + RNT * RPM;      // [3][LDX]
     float* Lp = F1m;                  // [RM][RPM] chol(Theta_PP), overlays F1m before the steps
     float* rLp = F1m + RM * RPM;      // [RM] reciprocal diagonal of Lp
-    __shared__ unsigned pkey[2][RNT / 32];
+    __shared__ __align__(16) unsigned pkey[2][RNT / 32];
     __shared__ int pidx[2][RNT / 32];
     __shared__ float pv1[2][RNT / 32], pv2[2][RNT / 32];
     __shared__ int s_fail;
@@ -260,56 +259,71 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         }
         __syncthreads();
 
-        // ---- the greedy steps
+        // ---- the greedy steps, in four blocks of 16: within block TB the step t = 16 TB + tt
+        // appends entry t, so the dot products over F1 and F2S run over the blocks 0..TB
+        // (entries from t on are zero) and the put touches block TB only -- all statically
         int t = 0;
-        for (; t < k; ++t) {
-            const int buf = t & 1;
-            const unsigned key = (V2 >= floor_) ? score_key(V1 / V2) : 0u;
-            const unsigned wmax = __reduce_max_sync(FULL, key);
-            const unsigned hit = __ballot_sync(FULL, key == wmax);
-            if (lane == __ffs(hit) - 1) {  // the warp's best row (lowest lane among equal keys)
-                pkey[buf][warp] = wmax;
-                pidx[buf][warp] = tid;
-                pv1[buf][warp] = V1;
-                pv2[buf][warp] = V2;
-            }
-            __syncthreads();
-            unsigned bk = pkey[buf][0];
-            int bw = 0;
+        auto steps = [&](auto tbc) -> bool {  // false once the selection has ended
+            constexpr int TB = decltype(tbc)::value;
+            for (int tt = 0; tt < 16; ++tt, ++t) {
+                if (t >= k) return false;
+                const int buf = t & 1;
+                const unsigned key = (V2 >= floor_) ? score_key(V1 / V2) : 0u;
+                const unsigned wmax = __reduce_max_sync(FULL, key);
+                const unsigned hit = __ballot_sync(FULL, key == wmax);
+                if (lane == __ffs(hit) - 1) {  // the warp's best row (lowest lane among equal keys)
+                    pkey[buf][warp] = wmax;
+                    pidx[buf][warp] = tid;
+                    pv1[buf][warp] = V1;
+                    pv2[buf][warp] = V2;
+                }
+                __syncthreads();
+                const uint4 k0 = *reinterpret_cast<const uint4*>(&pkey[buf][0]);
+                const uint4 k1 = *reinterpret_cast<const uint4*>(&pkey[buf][4]);
+                const unsigned kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+                unsigned bk = kk[0];
+                int bw = 0;
 #pragma unroll
-            for (int w = 1; w < RNT / 32; ++w) {
-                const unsigned kw = pkey[buf][w];
-                if (kw > bk) {
-                    bk = kw;
-                    bw = w;
+                for (int w = 1; w < RNT / 32; ++w) {
+                    if (kk[w] > bk) {
+                        bk = kk[w];
+                        bw = w;
+                    }
                 }
-            }
-            if (bk == 0u) break;
-            const int q = pidx[buf][bw];
-            const float r1 = 1.f / sqrtf(pv1[buf][bw]);
-            const float r2 = 1.f / sqrtf(pv2[buf][bw]);
-            if (V2 != NEG) {
-                const float dx = xr - X[q], dy = yr - X[LDX + q], dz = zr - X[2 * LDX + q];
-                float th = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
-                if (tid == q) th += kp.nugget;
-                const float n1 = reg_dot(th, F1, F1m + q * RP, t);
-                float n2 = reg_dot(th, F2P, F2Pm + q * RPM, m);
-                n2 = reg_dot(n2, F2S, F2Sm + q * RP, t);
-                const float u1 = n1 * r1, u2 = n2 * r2;
-                reg_put(F1, t, u1);
-                reg_put(F2S, t, u2);
-                F1m[tid * RP + t] = u1;
-                F2Sm[tid * RP + t] = u2;
-                if (tid == q) {
-                    V1 = NEG;
-                    V2 = NEG;
-                } else {
-                    V1 = fmaf(-u1, u1, V1);
-                    V2 = fmaf(-u2, u2, V2);
+                if (bk == 0u) return false;
+                const int q = pidx[buf][bw];
+                const float r1 = 1.f / sqrtf(pv1[buf][bw]);
+                const float r2 = 1.f / sqrtf(pv2[buf][bw]);
+                if (V2 != NEG) {
+                    const float dx = xr - X[q], dy = yr - X[LDX + q], dz = zr - X[2 * LDX + q];
+                    float th = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                    if (tid == q) th += kp.nugget;
+                    const float n1 = dot_blocks<TB + 1>(th, F1, F1m + q * RP);
+                    float n2 = reg_dot(th, F2P, F2Pm + q * RPM, m);
+                    n2 = dot_blocks<TB + 1>(n2, F2S, F2Sm + q * RP);
+                    const float u1 = n1 * r1, u2 = n2 * r2;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        put_if(F1[16 * TB + e], tt, e, u1);
+                        put_if(F2S[16 * TB + e], tt, e, u2);
+                    }
+                    F1m[tid * RP + t] = u1;
+                    F2Sm[tid * RP + t] = u2;
+                    if (tid == q) {
+                        V1 = NEG;
+                        V2 = NEG;
+                    } else {
+                        V1 = fmaf(-u1, u1, V1);
+                        V2 = fmaf(-u2, u2, V2);
+                    }
                 }
+                if (tid == 0) sel_idx[g * k + t] = cand_idx[b0 + q];
             }
-            if (tid == 0) sel_idx[g * k + t] = cand_idx[b0 + q];
-        }
+            return true;
+        };
+        if (steps(std::integral_constant<int, 0>{}) && steps(std::integral_constant<int, 1>{}) &&
+            steps(std::integral_constant<int, 2>{}))
+            steps(std::integral_constant<int, 3>{});
         if (tid == 0) sel_count[g] = t;
         for (int q = t + tid; q < k; q += RNT) sel_idx[g * k + q] = -1;
         __syncthreads();

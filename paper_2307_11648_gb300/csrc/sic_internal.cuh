@@ -63,22 +63,24 @@ __device__ __forceinline__ T matern(const KP<T>& k, T r) {
 // ---- FP64 Matern with few FP64-pipe instructions (GB300 issues 2 DFMA / clk / SM) ----
 //
 // exp(x), x <= 0: table-driven reduction after Tang (ACM TOMS 15(2), 1989).  With
-// k = round(64 x / ln 2) = 64 q + j, x = k ln2/64 + r, |r| <= ln2/128, and
-// exp(x) = 2^q * 2^(j/64) * e^r.  ln2/64 is split into its double rounding and the tail,
-// so r carries ~1e-19 absolute error for |k| < 2^16; e^r - 1 = r + r^2 (1/2 + r/6 + r^2/24
-// + r^3/120 + r^4/720), truncation below 1.3e-20.  The result is formed as T_j + T_j p in
-// one fused operation and scaled by adding q to the exponent field.  Error: the table's
-// rounding plus one final rounding (about 1.5 ulp).  11 FP64 operations.  Arguments below
-// -700 return 0 (exp(-700) ~ 1e-304).  `tab` holds 2^(j/64), j = 0..63 (exp_table_fill).
+// k = round(256 x / ln 2) = 256 q + j, x = k ln2/256 + r, |r| <= ln2/512, and
+// exp(x) = 2^q * 2^(j/256) * e^r.  ln2/256 is split into its double rounding and the tail,
+// so r carries ~1e-19 absolute error for |k| < 2^18; e^r - 1 = r + r^2 (1/2 + r/6 + r^2/24),
+// truncation below 4e-17.  The result is formed as T_j + T_j p in one fused operation and
+// scaled by adding q to the exponent field.  Error: the table's rounding plus one final
+// rounding (about 1.5 ulp).  9 FP64 operations.  Arguments below -700 return 0
+// (exp(-700) ~ 1e-304).  `tab` holds 2^(j/256), j = 0..255 (exp_table_fill).
+constexpr int EXP_TAB = 256;
+
 __device__ __forceinline__ void exp_table_fill(double* tab) {
-    for (int j = threadIdx.x; j < 64; j += blockDim.x) tab[j] = exp2((double)j * (1.0 / 64.0));
+    for (int j = threadIdx.x; j < EXP_TAB; j += blockDim.x) tab[j] = exp2((double)j * (1.0 / EXP_TAB));
 }
 
 __device__ __forceinline__ double exp_neg_table(double x, const double* __restrict__ tab) {
-    constexpr double SHIFT = 6755399441055744.0;               // 1.5 * 2^52
-    constexpr double INV_L = 92.332482616893656877;            // 64 / ln 2
-    constexpr double L1 = 0.6931471805599453094172321 / 64.0;  // ln2/64, rounded
-    constexpr double L2 = 2.3190468138462996e-17 / 64.0;       // ln2/64 - L1
+    constexpr double SHIFT = 6755399441055744.0;                // 1.5 * 2^52
+    constexpr double INV_L = 369.32993046757463228;             // 256 / ln 2
+    constexpr double L1 = 0.6931471805599453094172321 / 256.0;  // ln2/256, rounded
+    constexpr double L2 = 2.3190468138462996e-17 / 256.0;       // ln2/256 - L1
     // x < -700 <=> (x negative) high word above that of -700.0 (integer compare, no FP64 op)
     if ((unsigned)__double2hiint(x) > 0xC085E000u) return 0.0;
     double kd = fma(x, INV_L, SHIFT);  // k in the low word, two's complement
@@ -86,14 +88,12 @@ __device__ __forceinline__ double exp_neg_table(double x, const double* __restri
     kd -= SHIFT;
     double r = fma(-kd, L1, x);
     r = fma(-kd, L2, r);
-    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-    q = fma(q, r, 1.0 / 24.0);
-    q = fma(q, r, 1.0 / 6.0);
+    double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     q = fma(q, r, 0.5);
     const double p = fma(r * r, q, r);  // e^r - 1
-    const double tj = tab[k & 63];
+    const double tj = tab[k & (EXP_TAB - 1)];
     const double e = fma(tj, p, tj);
-    return __hiloint2double(__double2hiint(e) + ((k >> 6) << 20), __double2loint(e));
+    return __hiloint2double(__double2hiint(e) + ((k >> 8) << 20), __double2loint(e));
 }
 
 // sqrt(d2), d2 >= 0: an FP32 reciprocal-square-root seed (from the high word, ~2^-20)
