@@ -106,6 +106,7 @@ __global__ void k_scan_add(long long* __restrict__ v, long long n, const long lo
 
 constexpr int FILL_NT = 128;   // 4 warps per unit
 constexpr int FILL_SLOTS = 6;  // right-hand-side entries per lane: nn <= 192 = 32 * FILL_SLOTS
+constexpr int FILL_M_SPLIT = 32;  // groups of at most this size run in their own launch
 
 // Packed lower-triangle index (nn <= 192, so every index fits in 32 bits; 32-bit integer
 // arithmetic and int-to-float conversions stay off the FP64 pipe).
@@ -135,11 +136,12 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
                                                   const long long* __restrict__ grp_ptr, long long n_units,
                                                   const int32_t* __restrict__ sel_idx,
                                                   const int32_t* __restrict__ sel_count, int k, int max_m,
+                                                  int m_lo, int m_hi,
                                                   long long n, const long long* __restrict__ col_ptr,
                                                   int32_t* __restrict__ row_idx, double* __restrict__ val,
                                                   double* __restrict__ logv, DevStatus* st) {
     extern __shared__ double smem_d[];
-    const int nmax = k + max_m;
+    const int nmax = k + m_hi;  // shared memory is laid out for this launch's size class
     double* G = smem_d;                                     // packed lower, nmax(nmax+1)/2
     double* rG = G + (long long)nmax * (nmax + 1) / 2;      // 1 / G_jj
     double* cj = rG + nmax;                                 // the current column of G
@@ -156,9 +158,10 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
         const int m = grp_ptr ? (int)(grp_ptr[u + 1] - g0) : 1;
         const int cnt = sel_count[u];
         if (m < 1 || m > max_m || cnt < 0 || cnt > k || g0 < 0 || g0 + m > n) {
-            if (tid == 0) record_error(st, SIC_ERR_INVALID, u);
+            if (tid == 0 && m_lo == 1) record_error(st, SIC_ERR_INVALID, u);  // reported by the first class
             continue;
         }
+        if (m < m_lo || m > m_hi) continue;  // another launch's size class
         const int nn = cnt + m;
         // picks sorted ascending by rank; they must be distinct positions after the unit,
         // and col_ptr must match the pattern
@@ -411,12 +414,21 @@ extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t
     if (!ws || ws_bytes < need) return SIC_ERR_INVALID;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
-    size_t sm = fill_smem_bytes(k, max_m);
-    if (sm > 227 * 1024) return SIC_ERR_UNSUPPORTED;
-    SIC_CUDA_TRY(cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int grid = persistent_grid(h, k_fill, FILL_NT, sm, n_grp);
-    k_fill<<<grid, FILL_NT, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp, sel_idx,
-                                sel_count, k, max_m, n, (const long long*)col_ptr, row_idx, val, logv, h->d_status);
+    if (fill_smem_bytes(k, max_m) > 227 * 1024) return SIC_ERR_UNSUPPORTED;
+    // two size classes when the groups can be large: the shared-memory layout (and so the
+    // CTAs per SM) of each launch fits its own largest group, so the many small groups run
+    // at higher occupancy; each launch skips the other's groups
+    const int split = (max_m > FILL_M_SPLIT) ? FILL_M_SPLIT : max_m;
+    for (int c = 0; c < 2; ++c) {
+        const int lo = c == 0 ? 1 : split + 1, hi = c == 0 ? split : max_m;
+        if (lo > hi) break;
+        const size_t sm = fill_smem_bytes(k, hi);
+        SIC_CUDA_TRY(cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const int grid = persistent_grid(h, k_fill, FILL_NT, sm, n_grp);
+        k_fill<<<grid, FILL_NT, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp,
+                                         sel_idx, sel_count, k, max_m, lo, hi, n, (const long long*)col_ptr, row_idx,
+                                         val, logv, h->d_status);
+    }
     long long nb = (n + SUM_TILE - 1) / SUM_TILE;
     k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n, (double*)ws);
     k_sum_final<<<1, 256, 0, s>>>((const double*)ws, nb, sum_logv);

@@ -75,11 +75,14 @@ __device__ __forceinline__ float dot_blocks(float acc, const float (&r)[N], cons
     return (acc + a1) + (a2 + a3);
 }
 
-// x = v when idx == e, by a predicated move in inline PTX: with e static this keeps every
-// register-array index static (a C++ select on a run-time index lets the compiler turn a
-// series of them into one indexed store, which moves the array to local memory)
-__device__ __forceinline__ void put_if(float& x, int idx, int e, float v) {
-    asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %1, %2;\n\t@p mov.f32 %0, %3;\n\t}" : "+f"(x) : "r"(idx), "r"(e), "f"(v));
+// x = u and y = v when idx == e, by predicated moves in inline PTX (one compare for both):
+// with e static this keeps every register-array index static (a C++ select on a run-time
+// index lets the compiler turn a series of them into one indexed store, which moves the
+// array to local memory)
+__device__ __forceinline__ void put2_if(float& x, float& y, int idx, int e, float u, float v) {
+    asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\t@p mov.f32 %0, %4;\n\t@p mov.f32 %1, %5;\n\t}"
+        : "+f"(x), "+f"(y)
+        : "r"(idx), "r"(e), "f"(u), "f"(v));
 }
 
 __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
@@ -292,8 +295,8 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                 }
                 if (bk == 0u) return false;
                 const int q = pidx[buf][bw];
-                const float r1 = 1.f / sqrtf(pv1[buf][bw]);
-                const float r2 = 1.f / sqrtf(pv2[buf][bw]);
+                const float r1 = rsqrtf(pv1[buf][bw]);
+                const float r2 = rsqrtf(pv2[buf][bw]);
                 if (V2 != NEG) {
                     const float dx = xr - X[q], dy = yr - X[LDX + q], dz = zr - X[2 * LDX + q];
                     float th = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
@@ -303,10 +306,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                     n2 = dot_blocks<TB + 1>(n2, F2S, F2Sm + q * RP);
                     const float u1 = n1 * r1, u2 = n2 * r2;
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        put_if(F1[16 * TB + e], tt, e, u1);
-                        put_if(F2S[16 * TB + e], tt, e, u2);
-                    }
+                    for (int e = 0; e < 16; ++e) put2_if(F1[16 * TB + e], F2S[16 * TB + e], tt, e, u1, u2);
                     F1m[tid * RP + t] = u1;
                     F2Sm[tid * RP + t] = u2;
                     if (tid == q) {
