@@ -1,6 +1,6 @@
 // KL-optimal fill of the factor (eq. L_col; aggregated form, Appendix A.4), FP64.
 //
-// One CTA of four warps per unit (a single column, or a group of m consecutive
+// One CTA of four worker warps (plus a pivot warp) per unit (a single column, or a group of m consecutive
 // columns sharing the picks S).  With the aggregated set ordered ascending,
 // s = (P_0..P_{m-1}, S sorted), the factor block is L = U^{-T} where U U^T =
 // Theta_{s,s}, U upper triangular.  The CTA forms Theta on the reversed order
@@ -104,7 +104,9 @@ __global__ void k_scan_add(long long* __restrict__ v, long long n, const long lo
 
 // ------------------------------------------------------------------- the fill --
 
-constexpr int FILL_NT = 128;   // 4 warps per unit
+constexpr int FILL_NT = 128;   // 4 worker warps per unit
+constexpr int FILL_PIVOT = FILL_NT;         // lane 0 of a fifth warp takes the Cholesky pivots
+constexpr int FILL_BLOCK = FILL_NT + 32;
 constexpr int FILL_SLOTS = 6;  // right-hand-side entries per lane: nn <= 192 = 32 * FILL_SLOTS
 constexpr int FILL_M_SPLIT = 32;  // groups of at most this size run in their own launch
 
@@ -132,7 +134,7 @@ __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* r
     rG[c] = r;
 }
 
-__global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
+__global__ void __launch_bounds__(FILL_BLOCK) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
                                                   const long long* __restrict__ grp_ptr, long long n_units,
                                                   const int32_t* __restrict__ sel_idx,
                                                   const int32_t* __restrict__ sel_count, int k, int max_m,
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool worker = tid < FILL_NT;  // the pivot warp joins only the barriers and the pivots
     exp_table_fill(tab);
 
     for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
         // picks sorted ascending by rank; they must be distinct positions after the unit,
         // and col_ptr must match the pattern
         bool bad = false;
-        for (int i = tid; i < cnt; i += FILL_NT) {
+        for (int i = worker ? tid : cnt; i < cnt; i += FILL_NT) {
             const int v = sel_idx[u * k + i];
             int rank = 0, same = 0;
             for (int j = 0; j < cnt; ++j) {
@@ -177,14 +180,14 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
             if (v < g0 + m || v >= n || same != 1) bad = true;
             else srt[rank] = v;
         }
-        for (int a = tid; a < m; a += FILL_NT)
+        for (int a = worker ? tid : m; a < m; a += FILL_NT)
             if (col_ptr[g0 + a + 1] - col_ptr[g0 + a] != (long long)(m - a + cnt)) bad = true;
         if (__syncthreads_or(bad)) {
             if (tid == 0) record_error(st, SIC_ERR_INVALID, u);
             continue;
         }
         // R order: picks descending, then members descending
-        for (int i = tid; i < nn; i += FILL_NT) {
+        for (int i = worker ? tid : nn; i < nn; i += FILL_NT) {
             const int p = (i < cnt) ? srt[cnt - 1 - i] : (int)(g0 + m - 1 - (i - cnt));
             pos[i] = p;
             for (int d = 0; d < 3; ++d) xyz[d * nmax + i] = (d < dim) ? pts[(long long)p * dim + d] : 0.0;
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
         __syncthreads();
         // Theta_RR, packed lower, one flat entry per thread
         const int tri = nn * (nn + 1) / 2;
-        for (int e = tid; e < tri; e += FILL_NT) {
+        for (int e = worker ? tid : tri; e < tri; e += FILL_NT) {
             const int i = pk_row(e);
             const int j = e - i * (i + 1) / 2;
             const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j];
@@ -208,17 +211,18 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
         }
         __syncthreads();
         // right-looking Cholesky in place on the packed lower triangle: for column j,
-        // G_jj = sqrt(A_jj) (taken, with its reciprocal, by the one thread that last
-        // updated A_jj), G_ij = A_ij / G_jj, then A_il -= G_ij G_lj over the trailing
-        // triangle j < l <= i with one flat entry per thread.  The FP64 units are per SM
-        // sub-partition and charge a warp instruction whatever its active lanes, so the
-        // flat update keeps all four warps equally loaded with full warps.
-        if (tid == 0) fill_pivot(G[0], 0, G, rG, &s_bad);
+        // G_jj = sqrt(A_jj), G_ij = A_ij / G_jj, then A_il -= G_ij G_lj over the trailing
+        // triangle j < l <= i with one flat entry per worker thread.  The FP64 units are per
+        // SM sub-partition and charge a warp instruction whatever its active lanes, so the
+        // flat update keeps the four worker warps equally loaded with full warps.  The next
+        // pivot (its diagonal update, square root and reciprocal: a chain of dependent FP64
+        // operations) is taken by the pivot warp while the workers update the rest.
+        if (tid == FILL_PIVOT) fill_pivot(G[0], 0, G, rG, &s_bad);
         __syncthreads();
         for (int j = 0; j < nn; ++j) {
             if (s_bad) break;
             const double rd = rG[j];
-            for (int i = j + 1 + tid; i < nn; i += FILL_NT) {
+            for (int i = worker ? j + 1 + tid : nn; i < nn; i += FILL_NT) {
                 const int a = pk(i, j);
                 const double g = G[a] * rd;
                 G[a] = g;
@@ -227,19 +231,17 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
             __syncthreads();
             const int nt = nn - 1 - j;
             const int T = nt * (nt + 1) / 2;
-            // entries are dealt from thread 32 (j mod 4) on, so that the next pivot (entry 0)
-            // falls to each warp in turn and the warps' FP64 work stays equal
-            const int e0 = (tid - 32 * (j & 3)) & (FILL_NT - 1);
-            double piv = 1.0;
-            for (int e = e0; e < T; e += FILL_NT) {
-                const int ii = pk_row(e);
-                const int i = ii + j + 1, l = e - ii * (ii + 1) / 2 + j + 1;
-                const int a = pk(i, l);
-                const double v = fma(-cj[i], cj[l], G[a]);
-                G[a] = v;
-                if (e == 0) piv = v;
+            if (worker) {
+                for (int e = tid + 1; e < T; e += FILL_NT) {  // entry 0, A_{j+1,j+1}, is the pivot warp's
+                    const int ii = pk_row(e);
+                    const int i = ii + j + 1, l = e - ii * (ii + 1) / 2 + j + 1;
+                    const int a = pk(i, l);
+                    G[a] = fma(-cj[i], cj[l], G[a]);
+                }
+            } else if (tid == FILL_PIVOT && nt > 0) {
+                const int a = pk(j + 1, j + 1);
+                fill_pivot(fma(-cj[j + 1], cj[j + 1], G[a]), j + 1, G, rG, &s_bad);
             }
-            if (e0 == 0 && nt > 0) fill_pivot(piv, j + 1, G, rG, &s_bad);
             __syncthreads();
         }
         __syncthreads();
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
         // H = rows of G scaled by their reciprocal pivots (off-diagonal entries), so that
         // the back substitution G^T x = b reads y_l = b_l and updates b_i -= H_li y_l,
         // with x_l = y_l / G_ll applied once at the end.
-        for (int e = tid; e < tri; e += FILL_NT) {
+        for (int e = worker ? tid : tri; e < tri; e += FILL_NT) {
             const int i = pk_row(e);
             const int j = e - i * (i + 1) / 2;
             if (j < i) G[e] *= rG[i];
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(FILL_NT) k_fill(const double* __restrict__ pts
         __syncthreads();
         // member a: solve G^T x = e_jb (jb = nn-1-a), one right-hand side per warp, held in
         // registers (lane owns entries lane + 32 s)
-        for (int a = warp; a < m; a += FILL_NT / 32) {
+        for (int a = worker ? warp : m; a < m; a += FILL_NT / 32) {
             const int jb = nn - 1 - a;
             double bv[FILL_SLOTS];
 #pragma unroll
@@ -424,8 +426,8 @@ extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t
         if (lo > hi) break;
         const size_t sm = fill_smem_bytes(k, hi);
         SIC_CUDA_TRY(cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        const int grid = persistent_grid(h, k_fill, FILL_NT, sm, n_grp);
-        k_fill<<<grid, FILL_NT, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp,
+        const int grid = persistent_grid(h, k_fill, FILL_BLOCK, sm, n_grp);
+        k_fill<<<grid, FILL_BLOCK, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp,
                                          sel_idx, sel_count, k, max_m, lo, hi, n, (const long long*)col_ptr, row_idx,
                                          val, logv, h->d_status);
     }
