@@ -8,7 +8,7 @@
 // it G G^T = Theta_{RR} (right-looking, the trailing update flat over the threads; one
 // thread takes each pivot's square root and reciprocal), and since U = J G J (J the reversal),
 // member a's column is J G^{-T} e_j with j = n-1-a: one back substitution per member,
-// one member per warp, the right-hand side in registers.  v_a = G_jj^2, so
+// one member per half-warp, the right-hand side in registers.  v_a = G_jj^2, so
 // logv = 2 log G_jj (eq. inverse_cond).  Rows are written diagonal first, then
 // ascending, to the caller's CSC arrays.  Theta entries use the FP64 Matern of
 // matern_d2_fast (table-driven exp, Newton sqrt): this GPU issues two FP64 FMAs per
@@ -107,7 +107,7 @@ __global__ void k_scan_add(long long* __restrict__ v, long long n, const long lo
 constexpr int FILL_NT = 128;   // 4 worker warps per unit
 constexpr int FILL_PIVOT = FILL_NT;         // lane 0 of a fifth warp takes the Cholesky pivots
 constexpr int FILL_BLOCK = FILL_NT + 32;
-constexpr int FILL_SLOTS = 6;  // right-hand-side entries per lane: nn <= 192 = 32 * FILL_SLOTS
+constexpr int FILL_HSLOTS = 12;  // right-hand-side entries per half-warp lane: nn <= 192 = 16 * FILL_HSLOTS
 constexpr int FILL_M_SPLIT = 32;  // groups of at most this size run in their own launch
 
 // Packed lower-triangle index (nn <= 192, so every index fits in 32 bits; 32-bit integer
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(FILL_BLOCK) k_fill(const double* __restrict__ 
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool worker = tid < FILL_NT;  // the pivot warp joins only the barriers and the pivots
-    exp_table_fill(tab);
+    exp_table_fill(tab, kp.s2);
 
     for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         const long long g0 = grp_ptr ? grp_ptr[u] : u;
@@ -259,38 +259,49 @@ __global__ void __launch_bounds__(FILL_BLOCK) k_fill(const double* __restrict__ 
             if (j < i) G[e] *= rG[i];
         }
         __syncthreads();
-        // member a: solve G^T x = e_jb (jb = nn-1-a), one right-hand side per warp, held in
-        // registers (lane owns entries lane + 32 s)
-        for (int a = worker ? warp : m; a < m; a += FILL_NT / 32) {
-            const int jb = nn - 1 - a;
-            double bv[FILL_SLOTS];
+        // member a: solve G^T x = e_jb (jb = nn-1-a).  Members go in pairs (2p, 2p+1), one pair
+        // per warp, one member per half-warp; the right-hand side lives in registers (lane
+        // h*16 + r of half h owns entries r + 16 q).  The two members' jb differ by one, so
+        // each warp instruction serves both, in 16-lane instead of 32-lane granularity.
+        const int npairs = (m + 1) / 2;
+        const int half = lane >> 4, hl = lane & 15;
+        for (int p = worker ? warp : npairs; p < npairs; p += FILL_NT / 32) {
+            const int a = 2 * p + half;
+            const bool has = a < m;
+            const int jb = has ? nn - 1 - a : -1;
+            const int jtop = nn - 1 - 2 * p;
+            double bv[FILL_HSLOTS];
 #pragma unroll
-            for (int q = 0; q < FILL_SLOTS; ++q) bv[q] = (lane + 32 * q == jb) ? 1.0 : 0.0;
+            for (int q = 0; q < FILL_HSLOTS; ++q) bv[q] = (hl + 16 * q == jb) ? 1.0 : 0.0;
 #pragma unroll
-            for (int sb = FILL_SLOTS - 1; sb >= 0; --sb) {
-                if (32 * sb > jb) continue;
-                const int top = min(jb, 32 * sb + 31);
-                for (int l = top; l >= 32 * sb; --l) {
-                    const double y = __shfl_sync(0xffffffffu, bv[sb], l & 31);
+            for (int sb = FILL_HSLOTS - 1; sb >= 0; --sb) {
+                if (16 * sb > jtop) continue;
+                const int top = min(jtop, 16 * sb + 15);
+                for (int l = top; l >= 16 * sb; --l) {
+                    const double y = __shfl_sync(0xffffffffu, bv[sb], (lane & 16) | (l & 15));
                     const int rl = pk(l, 0);
 #pragma unroll
                     for (int q = 0; q <= sb; ++q) {
-                        const int i = lane + 32 * q;
+                        const int i = hl + 16 * q;
                         if (i < l) bv[q] = fma(-G[rl + i], y, bv[q]);
                     }
                 }
             }
-            const long long c0 = col_ptr[g0 + a];
+            if (has) {
+                const long long c0 = col_ptr[g0 + a];
 #pragma unroll
-            for (int q = 0; q < FILL_SLOTS; ++q) {
-                const int i = lane + 32 * q;
-                if (i <= jb) {
-                    row_idx[c0 + jb - i] = pos[i];
-                    val[c0 + jb - i] = bv[q] * rG[i];
+                for (int q = 0; q < FILL_HSLOTS; ++q) {
+                    const int i = hl + 16 * q;
+                    if (i <= jb) {
+                        row_idx[c0 + jb - i] = pos[i];
+                        val[c0 + jb - i] = bv[q] * rG[i];
+                    }
                 }
             }
-            if (lane == 0) logv[g0 + a] = 2.0 * log(G[pk(jb, jb)]);
         }
+        // log v of every member, one member per thread (the FP64 log once per lane instead of
+        // once per warp)
+        for (int a = worker ? tid : m; a < m; a += FILL_NT) logv[g0 + a] = 2.0 * log(G[pk(nn - 1 - a, nn - 1 - a)]);
         __syncthreads();
     }
 }
@@ -333,15 +344,16 @@ size_t fill_smem_bytes(int k, int max_m) {
 
 __global__ void k_fp64_math(KP<double> kp, const double* __restrict__ x, long long n, double* __restrict__ os,
                             double* __restrict__ orr, double* __restrict__ oe, double* __restrict__ ok) {
-    __shared__ double tab[EXP_TAB];
+    __shared__ double tab[EXP_TAB], tab_s2[EXP_TAB];
     exp_table_fill(tab);
+    exp_table_fill(tab_s2, kp.s2);
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double v = x[i];
         os[i] = sqrt_newton(v);
         orr[i] = v > 0.0 ? rsqrt_newton(v) : 0.0;
         oe[i] = exp_neg_table(-v, tab);
-        ok[i] = matern_d2_fast(kp, v, tab);
+        ok[i] = matern_d2_fast(kp, v, tab_s2);
     }
 }
 

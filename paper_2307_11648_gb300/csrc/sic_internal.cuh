@@ -69,11 +69,12 @@ __device__ __forceinline__ T matern(const KP<T>& k, T r) {
 // truncation below 4e-17.  The result is formed as T_j + T_j p in one fused operation and
 // scaled by adding q to the exponent field.  Error: the table's rounding plus one final
 // rounding (about 1.5 ulp).  9 FP64 operations.  Arguments below -700 return 0
-// (exp(-700) ~ 1e-304).  `tab` holds 2^(j/256), j = 0..255 (exp_table_fill).
+// (exp(-700) ~ 1e-304).  `tab` holds scale * 2^(j/256), j = 0..255 (exp_table_fill), so the
+// routine returns scale * exp(x) (the Matern fill folds the variance in this way).
 constexpr int EXP_TAB = 256;
 
-__device__ __forceinline__ void exp_table_fill(double* tab) {
-    for (int j = threadIdx.x; j < EXP_TAB; j += blockDim.x) tab[j] = exp2((double)j * (1.0 / EXP_TAB));
+__device__ __forceinline__ void exp_table_fill(double* tab, double scale = 1.0) {
+    for (int j = threadIdx.x; j < EXP_TAB; j += blockDim.x) tab[j] = scale * exp2((double)j * (1.0 / EXP_TAB));
 }
 
 __device__ __forceinline__ double exp_neg_table(double x, const double* __restrict__ tab) {
@@ -132,13 +133,13 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
 }
 
 // FP64 Matern from a squared distance with the two routines above (same parameterisation
-// as matern<double>).
-__device__ __forceinline__ double matern_d2_fast(const KP<double>& k, double d2, const double* __restrict__ tab) {
+// as matern<double>); `tab_s2` is the exp table filled with scale = the variance.
+__device__ __forceinline__ double matern_d2_fast(const KP<double>& k, double d2, const double* __restrict__ tab_s2) {
     const double t = k.c_over_ell * sqrt_newton(d2);
-    const double e = exp_neg_table(-t, tab);
-    if (k.nu_x2 == 1) return k.s2 * e;
-    if (k.nu_x2 == 3) return k.s2 * fma(t, e, e);
-    return k.s2 * fma(fma(t, 1.0 / 3.0, 1.0), t * e, e);
+    const double e = exp_neg_table(-t, tab_s2);  // s2 exp(-t)
+    if (k.nu_x2 == 1) return e;
+    if (k.nu_x2 == 3) return fma(t, e, e);
+    return fma(fma(t, 1.0 / 3.0, 1.0), t * e, e);
 }
 
 #define SIC_CUDA_TRY(expr)                        \
