@@ -9,9 +9,9 @@
 // reads as the same (broadcast) 16-byte words from a shared-memory mirror of all rows;
 // the mirror is written one entry per row per step.  Register arrays are indexed
 // statically: the k steps run as four blocks of 16 with the block index a compile-time
-// constant, so the dot products over F1 and F2S run over whole 16-element blocks (entries
-// beyond the current length are zero on both sides) and the new column is written by
-// predicated moves into one block.
+// constant; the dot products over F1 and F2S take the completed blocks from registers and
+// the current block from the own row's mirror (entries beyond the current length are zero
+// on both sides), and a completed block moves from the mirror into registers.
 //
 // Per group: warp 0 factors Theta_PP (FP32, left-looking, lanes own rows); every thread
 // evaluates its Theta_{r,P} and solves for F2P by forward substitution (static loops);
@@ -75,14 +75,19 @@ __device__ __forceinline__ float dot_blocks(float acc, const float (&r)[N], cons
     return (acc + a1) + (a2 + a3);
 }
 
-// x = u and y = v when idx == e, by predicated moves in inline PTX (one compare for both):
-// with e static this keeps every register-array index static (a C++ select on a run-time
-// index lets the compiler turn a series of them into one indexed store, which moves the
-// array to local memory)
-__device__ __forceinline__ void put2_if(float& x, float& y, int idx, int e, float u, float v) {
-    asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\t@p mov.f32 %0, %4;\n\t@p mov.f32 %1, %5;\n\t}"
-        : "+f"(x), "+f"(y)
-        : "r"(idx), "r"(e), "f"(u), "f"(v));
+// acc - own . piv over one 16-element block, both read from shared memory
+__device__ __forceinline__ float dot_mirror(float acc, const float* __restrict__ own, const float* __restrict__ piv) {
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float4 r = *reinterpret_cast<const float4*>(own + 4 * c);
+        const float4 p = *reinterpret_cast<const float4*>(piv + 4 * c);
+        acc = fmaf(-r.x, p.x, acc);
+        a1 = fmaf(-r.y, p.y, a1);
+        a2 = fmaf(-r.z, p.z, a2);
+        a3 = fmaf(-r.w, p.w, a3);
+    }
+    return (acc + a1) + (a2 + a3);
 }
 
 __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
@@ -301,12 +306,14 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                     const float dx = xr - X[q], dy = yr - X[LDX + q], dz = zr - X[2 * LDX + q];
                     float th = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
                     if (tid == q) th += kp.nugget;
-                    const float n1 = dot_blocks<TB + 1>(th, F1, F1m + q * RP);
+                    // blocks 0..TB-1 from registers, the current block TB from the own row's
+                    // mirror (its entries from tt on are still zero)
+                    float n1 = dot_blocks<TB>(th, F1, F1m + q * RP);
+                    n1 = dot_mirror(n1, F1m + tid * RP + 16 * TB, F1m + q * RP + 16 * TB);
                     float n2 = reg_dot(th, F2P, F2Pm + q * RPM, m);
-                    n2 = dot_blocks<TB + 1>(n2, F2S, F2Sm + q * RP);
+                    n2 = dot_blocks<TB>(n2, F2S, F2Sm + q * RP);
+                    n2 = dot_mirror(n2, F2Sm + tid * RP + 16 * TB, F2Sm + q * RP + 16 * TB);
                     const float u1 = n1 * r1, u2 = n2 * r2;
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) put2_if(F1[16 * TB + e], F2S[16 * TB + e], tt, e, u1, u2);
                     F1m[tid * RP + t] = u1;
                     F2Sm[tid * RP + t] = u2;
                     if (tid == q) {
@@ -318,6 +325,20 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                     }
                 }
                 if (tid == 0) sel_idx[g * k + t] = cand_idx[b0 + q];
+            }
+            // block TB is complete: move the own row's entries into registers
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float4 a = *reinterpret_cast<const float4*>(F1m + tid * RP + 16 * TB + 4 * c);
+                const float4 b = *reinterpret_cast<const float4*>(F2Sm + tid * RP + 16 * TB + 4 * c);
+                F1[16 * TB + 4 * c] = a.x;
+                F1[16 * TB + 4 * c + 1] = a.y;
+                F1[16 * TB + 4 * c + 2] = a.z;
+                F1[16 * TB + 4 * c + 3] = a.w;
+                F2S[16 * TB + 4 * c] = b.x;
+                F2S[16 * TB + 4 * c + 1] = b.y;
+                F2S[16 * TB + 4 * c + 2] = b.z;
+                F2S[16 * TB + 4 * c + 3] = b.w;
             }
             return true;
         };
