@@ -281,7 +281,16 @@ def test_aggregated_full_size_top256_sampled(env, oracle_lib, prec_name):
             assert ri[cp[c]:cp[c + 1]].tolist() == rows.tolist()
             assert column_errors(val[cp[c]:cp[c + 1]], L) <= L_TOL
             assert abs(logv[c] - lv) <= LOGV_TOL
-    print(prec_name, "top-256", stats, "sum logv", float(fb.sum_logv.cpu()[0]))
+    # T4 on the device's output: every sampled member column is Theta-normalised,
+    # L_{s,i}^T Theta_{s,s} L_{s,i} = 1 (eq. L_col), with Theta from the oracle
+    worst = 0.0
+    for g in groups:
+        for c in range(int(gp[g]), int(gp[g + 1])):
+            rows = ri[cp[c]:cp[c + 1]]
+            v = val[cp[c]:cp[c + 1]]
+            worst = max(worst, abs(float(v @ oracle.theta_matrix(okp, P, rows) @ v) - 1.0))
+    assert worst <= 1e-8, worst
+    print(prec_name, "top-256", stats, "sum logv", float(fb.sum_logv.cpu()[0]), "T4 worst", worst)
     assert np.all(np.isfinite(logv))
 
 
