@@ -304,7 +304,8 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                 const float r2 = rsqrtf(pv2[buf][bw]);
                 if (V2 != NEG) {
                     const float dx = xr - X[q], dy = yr - X[LDX + q], dz = zr - X[2 * LDX + q];
-                    float th = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    float th = matern<float>(kp, d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
                     if (tid == q) th += kp.nugget;
                     // blocks 0..TB-1 from registers, the current block TB from the own row's
                     // mirror (its entries from tt on are still zero)
