@@ -49,6 +49,10 @@ DFMA_PER_SM_CLK = 2     # FP64 FMA per SM per clock on GB300 (1.26 TFLOP/s nomin
 # k_scan_add, k_fill x 2 (two group-size classes) + k_sum_tiles + k_sum_final (plus one
 # memset node)
 LAUNCHES_PER_STEP = 14
+# DRAM read + write bytes of the two k_fill launches of one learned step at N = 2^19
+# (22,423 supernodes), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
+FILL_DRAM_BYTES_N2E19 = 17.430016e6 + 261.050112e6 + 9.671168e6 + 122.095616e6
+FILL_GROUPS_N2E19 = 22423
 
 
 # ------------------------------------------------------------- clocks ---
@@ -520,9 +524,15 @@ def main():
         "top-k": {"ms": topk_ms},
     }
     if fill_ms >= sel_ms:
-        roof = {"bound": "alu", "kernel": "k_fill (FP64 fill)", "achieved": fill_tf, "peak": f64_peak,
-                "unit": "TFLOP/s", "frac": fill_tf / f64_peak, "traffic": None,
-                "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (derived; measured probe 1.20 TFLOP/s)"}
+        # DRAM bytes of the two k_fill launches measured at N = 2^19, scaled by the supernode
+        # count; the algorithmic bytes are the factor written (row index + value per nonzero),
+        # col_ptr and log v, the points and the picks read
+        traffic = FILL_DRAM_BYTES_N2E19 * hp.n_units / FILL_GROUPS_N2E19
+        roof = {"bound": "alu", "kernel": "k_fill (FP64 fill, both launches)", "achieved": fill_tf,
+                "peak": f64_peak, "unit": "TFLOP/s", "frac": fill_tf / f64_peak, "traffic": traffic,
+                "traffic_algorithmic": nnz * 12.0 + N * (8.0 + 8.0 + 8.0 * hp.pts.shape[1]) + hp.n_units * hp.k * 4.0,
+                "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (derived from unit counts; a DFMA "
+                               "throughput kernel saturates at 1.6 FMA/clk/SM = 1.0 TFLOP/s)"}
     else:
         roof = {"bound": "alu", "kernel": "k_select_agg<float>", "achieved": sel_tf, "peak": f32_peak,
                 "unit": "TFLOP/s", "frac": sel_tf / f32_peak, "traffic": None,

@@ -128,6 +128,14 @@ sic_status sic_prep_candidates_groups(const double* pts, int64_t n, int32_t dim,
                                       int64_t n_grp, int32_t n_cand, int64_t* cand_ptr, int32_t* cand_idx,
                                       int32_t n_threads);
 
+/* Candidates for directed GP regression (Section 3): pts holds the n_targets target
+ * points first, then the training points.  For each target i < n_targets, the n_cand
+ * training positions (>= n_targets) nearest to it, sorted by (distance, position), go
+ * to cand_idx[cand_ptr[i] .. cand_ptr[i+1]) (fewer if there are fewer training points).
+ * cand_ptr[n_targets + 1], cand_idx[n_targets * n_cand].  [host] */
+sic_status sic_prep_candidates_targets(const double* pts, int64_t n, int32_t dim, int64_t n_targets,
+                                       int32_t n_cand, int64_t* cand_ptr, int32_t* cand_idx, int32_t n_threads);
+
 /* ---------------------------------------------------------- selection [device] -- */
 
 /* Directed GP selection (Section 3): pick up to k of the n training points x_train
@@ -308,6 +316,24 @@ sic_status sic_mlp_grads(sic_handle* h, const float* params, const float* feat, 
  * on n parameters: m, v are the moment buffers [device]. */
 sic_status sic_adamw_step(sic_handle* h, float* params, float* m, float* v, const float* grads, int32_t n,
                           int32_t step, float lr, float beta1, float beta2, float eps, float wd, void* stream);
+
+/* ------------------------------------------------- directed GP regression -- */
+
+/* Posterior of the latent process at targets[t] (positions of pts) given the
+ * observations y at its picks sel_idx[t * k .. t * k + sel_count[t]) (Section 3, the
+ * prediction step after the directed selection; e.g. picks from sic_select_columns on
+ * candidates from sic_prep_candidates_targets):
+ *   mean[t] = Theta_{t,I} Theta_{I,I}^{-1} y_I,
+ *   var[t]  = variance - Theta_{t,I} Theta_{I,I}^{-1} Theta_{I,t}
+ * in FP64; the nugget (observation noise) sits on the diagonal of Theta_{I,I} only.
+ * pts [device, n x dim], targets [device, n_targets] (NULL: t), sel_idx, sel_count
+ * [device], y [device, n; only picked positions are read], mean, var [device,
+ * n_targets].  1 <= k <= 128.  A pick outside [0, n) or equal to the target, or a
+ * count outside [0, k], records SIC_ERR_INVALID; a non-positive pivot (repeated picks)
+ * SIC_ERR_NOT_PD (the target's outputs are NaN).  No workspace. */
+sic_status sic_gp_predict(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp, const int32_t* targets,
+                          int64_t n_targets, const int32_t* sel_idx, const int32_t* sel_count, int32_t k,
+                          const double* y, double* mean, double* var, void* stream);
 
 /* ------------------------------------------------------------ self-test -- */
 

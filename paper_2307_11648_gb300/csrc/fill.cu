@@ -1,7 +1,8 @@
 // KL-optimal fill of the factor (eq. L_col; aggregated form, Appendix A.4), FP64.
 //
-// One CTA of four worker warps (plus a pivot warp) per unit (a single column, or a group of m consecutive
-// columns sharing the picks S).  With the aggregated set ordered ascending,
+// One CTA of four (small groups) or eight (large groups) worker warps plus a pivot warp
+// per unit (a single column, or a group of m consecutive columns sharing the picks S).
+// With the aggregated set ordered ascending,
 // s = (P_0..P_{m-1}, S sorted), the factor block is L = U^{-T} where U U^T =
 // Theta_{s,s}, U upper triangular.  The CTA forms Theta on the reversed order
 // R = reverse(s) in packed lower storage in shared memory (one entry per thread), factors
@@ -104,9 +105,8 @@ __global__ void k_scan_add(long long* __restrict__ v, long long n, const long lo
 
 // ------------------------------------------------------------------- the fill --
 
-constexpr int FILL_NT = 128;   // 4 worker warps per unit
-constexpr int FILL_PIVOT = FILL_NT;         // lane 0 of a fifth warp takes the Cholesky pivots
-constexpr int FILL_BLOCK = FILL_NT + 32;
+// worker threads per unit: 128 for the small-group launch, 256 for the large groups (more
+// warps in flight where fewer CTAs fit per SM); lane 0 of one more warp takes the pivots
 constexpr int FILL_HSLOTS = 12;  // right-hand-side entries per half-warp lane: nn <= 192 = 16 * FILL_HSLOTS
 constexpr int FILL_M_SPLIT = 32;  // groups of at most this size run in their own launch
 
@@ -134,7 +134,8 @@ __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* r
     rG[c] = r;
 }
 
-__global__ void __launch_bounds__(FILL_BLOCK) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
+template <int FILL_NT>
+__global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
                                                   const long long* __restrict__ grp_ptr, long long n_units,
                                                   const int32_t* __restrict__ sel_idx,
                                                   const int32_t* __restrict__ sel_count, int k, int max_m,
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(FILL_BLOCK) k_fill(const double* __restrict__ 
         // flat update keeps the four worker warps equally loaded with full warps.  The next
         // pivot (its diagonal update, square root and reciprocal: a chain of dependent FP64
         // operations) is taken by the pivot warp while the workers update the rest.
-        if (tid == FILL_PIVOT) fill_pivot(G[0], 0, G, rG, &s_bad);
+        if (tid == FILL_NT) fill_pivot(G[0], 0, G, rG, &s_bad);
         __syncthreads();
         for (int j = 0; j < nn; ++j) {
             if (s_bad) break;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(FILL_BLOCK) k_fill(const double* __restrict__ 
                     const int a = pk(i, l);
                     G[a] = fma(-cj[i], cj[l], G[a]);
                 }
-            } else if (tid == FILL_PIVOT && nt > 0) {
+            } else if (tid == FILL_NT && nt > 0) {
                 const int a = pk(j + 1, j + 1);
                 fill_pivot(fma(-cj[j + 1], cj[j + 1], G[a]), j + 1, G, rG, &s_bad);
             }
@@ -437,11 +438,13 @@ extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t
         const int lo = c == 0 ? 1 : split + 1, hi = c == 0 ? split : max_m;
         if (lo > hi) break;
         const size_t sm = fill_smem_bytes(k, hi);
-        SIC_CUDA_TRY(cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        const int grid = persistent_grid(h, k_fill, FILL_BLOCK, sm, n_grp);
-        k_fill<<<grid, FILL_BLOCK, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp,
-                                         sel_idx, sel_count, k, max_m, lo, hi, n, (const long long*)col_ptr, row_idx,
-                                         val, logv, h->d_status);
+        auto kern = (c == 0) ? k_fill<128> : k_fill<256>;
+        const int block = (c == 0 ? 128 : 256) + 32;
+        SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const int grid = persistent_grid(h, kern, block, sm, n_grp);
+        kern<<<grid, block, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp, sel_idx,
+                                     sel_count, k, max_m, lo, hi, n, (const long long*)col_ptr, row_idx, val, logv,
+                                     h->d_status);
     }
     long long nb = (n + SUM_TILE - 1) / SUM_TILE;
     k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n, (double*)ws);

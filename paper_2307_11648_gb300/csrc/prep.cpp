@@ -317,6 +317,30 @@ extern "C" sic_status sic_prep_candidates_columns(const double* pts, int64_t n, 
     return SIC_OK;
 }
 
+extern "C" sic_status sic_prep_candidates_targets(const double* pts, int64_t n, int32_t dim, int64_t n_targets,
+                                                  int32_t n_cand, int64_t* cand_ptr, int32_t* cand_idx,
+                                                  int32_t n_threads) {
+    if (!pts || !cand_ptr || !cand_idx || n < 1 || dim < 1 || dim > 3 || n_cand < 0 || n_targets < 0 ||
+        n_targets > n)
+        return SIC_ERR_INVALID;
+    cand_ptr[0] = 0;
+    if (n_targets == 0) return SIC_OK;
+    SuffixGrids sg;
+    sg.build(pts, n, dim, std::max<int64_t>(256, n - n_targets), n_threads);
+    std::vector<int32_t> cnt(n_targets, 0);
+    parallel_for(n_targets, n_threads, 256, [&](int64_t i) {
+        thread_local std::vector<KeyPos> buf;
+        int64_t t = i;
+        cnt[i] = knn_query(pts, n, dim, sg, &t, 1, n_targets, n_cand, cand_idx + i * (int64_t)n_cand, buf);
+    });
+    for (int64_t i = 0; i < n_targets; ++i) {
+        int64_t src = i * (int64_t)n_cand, dst = cand_ptr[i];
+        if (dst != src) std::copy(cand_idx + src, cand_idx + src + cnt[i], cand_idx + dst);
+        cand_ptr[i + 1] = dst + cnt[i];
+    }
+    return SIC_OK;
+}
+
 extern "C" sic_status sic_prep_groups(const double* pts, const double* ell2, int64_t n, int32_t dim, int32_t K,
                                       double lambda, int32_t mmin, int32_t mmax, int64_t* members,
                                       int64_t* grp_ptr, int64_t* n_grp, int32_t n_threads) {

@@ -24,6 +24,7 @@ SIC_OP_L, SIC_OP_LT, SIC_OP_LLT = 0, 1, 2
 EXPORTS = [
     "sic_create", "sic_destroy", "sic_sync", "sic_last_error_unit", "sic_status_string", "sic_exhaustion_floor",
     "sic_prep_maximin", "sic_prep_candidates_columns", "sic_prep_groups", "sic_prep_candidates_groups",
+    "sic_prep_candidates_targets", "sic_gp_predict",
     "sic_select_single_workspace", "sic_select_single", "sic_select_columns",
     "sic_select_aggregated_workspace", "sic_select_aggregated",
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
@@ -75,6 +76,8 @@ def lib():
             "sic_exhaustion_floor": (d, [pk]),
             "sic_prep_maximin": (st, [vp, i64, i32, vp, vp, i32]),
             "sic_prep_candidates_columns": (st, [vp, i64, i32, i32, vp, vp, i32]),
+            "sic_prep_candidates_targets": (st, [vp, i64, i32, i64, i32, vp, vp, i32]),
+            "sic_gp_predict": (st, [vp, vp, i64, pk, vp, i64, vp, vp, i32, vp, vp, vp, vp]),
             "sic_prep_groups": (st, [vp, vp, i64, i32, i32, d, i32, i32, vp, vp, vp, i32]),
             "sic_prep_candidates_groups": (st, [vp, i64, i32, vp, i64, i32, vp, vp, i32]),
             "sic_select_single_workspace": (st, [i64, i32, st, C.POINTER(sz)]),
@@ -205,6 +208,18 @@ def prep_candidates_columns(pts: np.ndarray, n_cand: int, n_threads: int = 0):
     idx = np.empty(max(1, n * n_cand), np.int32)
     _check(lib().sic_prep_candidates_columns(_hptr(pts, np.float64), n, dim, n_cand, _hptr(ptr, np.int64),
                                              _hptr(idx, np.int32), n_threads), "sic_prep_candidates_columns")
+    return ptr, idx[:ptr[-1]].copy()
+
+
+def prep_candidates_targets(pts: np.ndarray, n_targets: int, n_cand: int, n_threads: int = 0):
+    """pts: targets first, then training points.  Returns (cand_ptr, cand_idx)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    n, dim = pts.shape
+    ptr = np.empty(n_targets + 1, np.int64)
+    idx = np.empty(max(1, n_targets * n_cand), np.int32)
+    _check(lib().sic_prep_candidates_targets(_hptr(pts, np.float64), n, dim, n_targets, n_cand,
+                                             _hptr(ptr, np.int64), _hptr(idx, np.int32), n_threads),
+           "sic_prep_candidates_targets")
     return ptr, idx[:ptr[-1]].copy()
 
 
@@ -467,3 +482,14 @@ def selftest_fp64_math(h: Handle, kp: Kernel, x, stream=None):
                                         *[_dptr(o, torch.float64, "out") for o in outs], _stream(stream)),
            "sic_selftest_fp64_math", h)
     return outs
+
+
+def gp_predict(h: Handle, pts, kp: Kernel, targets, sel_idx, sel_count, k: int, y, mean, var, stream=None):
+    """Posterior mean and variance at `targets` (CUDA tensors; targets may be None)."""
+    import torch
+    n_t = mean.numel()
+    _check(lib().sic_gp_predict(h.ptr, _dptr(pts, torch.float64, "pts"), pts.shape[0], C.byref(kp),
+                                None if targets is None else _dptr(targets, torch.int32, "targets"), n_t,
+                                _dptr(sel_idx, torch.int32, "sel_idx"), _dptr(sel_count, torch.int32, "sel_count"),
+                                int(k), _dptr(y, torch.float64, "y"), _dptr(mean, torch.float64, "mean"),
+                                _dptr(var, torch.float64, "var"), _stream(stream)), "sic_gp_predict", h)
