@@ -45,10 +45,10 @@ SM_MAX_MHZ = 2070.0
 FFMA_PER_SM_CLK = 128   # FP32 FMA lanes per SM per clock
 DFMA_PER_SM_CLK = 2     # FP64 FMA per SM per clock on GB300 (1.26 TFLOP/s nominal at 2070 MHz)
 # kernels of one learned step: k_features, k_mlp_tc, k_topk_counts + k_scan_one_block +
-# k_topk_compact, k_select_agg_reg, k_nnz_count + k_scan_tile + k_scan_partials +
-# k_scan_add, k_fill x 2 (two group-size classes) + k_sum_tiles + k_sum_final (plus one
-# memset node)
-LAUNCHES_PER_STEP = 14
+# k_topk_compact, k_agg_target_chol + k_select_agg_reg, k_nnz_count + k_scan_tile +
+# k_scan_partials + k_scan_add, k_fill x 2 (two group-size classes) + k_sum_tiles +
+# k_sum_final (plus one memset node)
+LAUNCHES_PER_STEP = 15
 # DRAM read + write bytes of the two k_fill launches of one learned step at N = 2^19
 # (22,423 supernodes), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
 FILL_DRAM_BYTES_N2E19 = 17.430016e6 + 261.050112e6 + 9.671168e6 + 122.095616e6

@@ -13,8 +13,9 @@
 // the current block from the own row's mirror (entries beyond the current length are zero
 // on both sides), and a completed block moves from the mirror into registers.
 //
-// Per group: warp 0 factors Theta_PP (FP32, left-looking, lanes own rows); every thread
-// evaluates its Theta_{r,P} and solves for F2P by forward substitution (static loops);
+// Per group: the targets' factor chol(Theta_PP) comes from a separate launch over all
+// groups (FP32, one warp per group) through the workspace; every thread evaluates its
+// Theta_{r,P} and solves for F2P by forward substitution (static loops);
 // then k steps, each with a single block barrier: the warp argmax is one redux over
 // order-preserving score keys (ties: lowest lane = lowest candidate index), the warp
 // winners go to double-buffered shared slots with their V1/V2, and every thread reduces
@@ -32,6 +33,11 @@ constexpr int RP = RK + 4;     // mirror pitch of F1 and F2S rows (floats)
 constexpr int RPM = RM + 4;    // mirror pitch of F2P rows and of the target factor
 constexpr int LDX = RNT + RM;  // staged coordinates: candidates then targets
 constexpr unsigned FULL = 0xffffffffu;
+// workspace slot of one group: chol(Theta_PP) packed by rows (RM (RM + 1) / 2), its reciprocal
+// diagonal (RM) and a failure flag
+constexpr int LP_PACKED = RM * (RM + 1) / 2;
+constexpr int LP_SLOT = LP_PACKED + RM + 4;
+constexpr int LP_WARPS = 2;  // groups per CTA in the targets' Cholesky kernel (36 KB static smem)
 
 __device__ __forceinline__ unsigned score_key(float s) {
     const unsigned b = __float_as_uint(s);
@@ -90,11 +96,89 @@ __device__ __forceinline__ float dot_mirror(float acc, const float* __restrict__
     return (acc + a1) + (a2 + a3);
 }
 
+// The targets' Cholesky factor Lp = chol(Theta_PP) of every group, FP32, one warp per
+// group (left-looking, lane owns rows lane and lane + 32), from the same FP32 coordinates
+// relative to the first member that the selection kernel stages.  Runs as its own
+// launch over all groups at once, ahead of the latency-bound selection.
+__global__ void __launch_bounds__(32 * LP_WARPS) k_agg_target_chol(const double* __restrict__ pts, long long n,
+                                                                    int dim, KP<float> kp,
+                                                                    const long long* __restrict__ grp_ptr,
+                                                                    long long n_grp, float* __restrict__ ws) {
+    __shared__ __align__(16) float lsm[LP_WARPS][RM * RPM + 3 * RM];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float* Lp = lsm[w];
+    float* XP = Lp + RM * RPM;
+    for (long long g = (long long)blockIdx.x * LP_WARPS + w; g < n_grp; g += (long long)gridDim.x * LP_WARPS) {
+        const long long g0 = grp_ptr[g];
+        const int m = (int)(grp_ptr[g + 1] - g0);
+        float* out = ws + g * (long long)LP_SLOT;
+        if (m < 1 || m > RM || g0 < 0 || g0 + m > n) {
+            if (lane == 0) out[LP_PACKED + RM] = 1.f;  // reported by the selection kernel
+            continue;
+        }
+        double org[3] = {0.0, 0.0, 0.0};
+        for (int d = 0; d < dim; ++d) org[d] = pts[g0 * dim + d];
+        for (int a = lane; a < m; a += 32)
+            for (int d = 0; d < 3; ++d) XP[d * RM + a] = (d < dim) ? (float)(pts[(g0 + a) * dim + d] - org[d]) : 0.f;
+        __syncwarp();
+        bool ok = true;
+        for (int j = 0; j < m; ++j) {
+            const float xj = XP[j], yj = XP[RM + j], zj = XP[2 * RM + j];
+            float sv[2] = {0.f, 0.f};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                if (i >= j && i < m) {
+                    const float dx = XP[i] - xj, dy = XP[RM + i] - yj, dz = XP[2 * RM + i] - zj;
+                    float th = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                    if (i == j) th += kp.nugget;
+                    const float* ri = Lp + i * RPM;
+                    const float* rj = Lp + j * RPM;
+                    float s0 = th, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                    int l = 0;
+                    for (; l + 4 <= j; l += 4) {
+                        const float4 a = *reinterpret_cast<const float4*>(ri + l);
+                        const float4 b = *reinterpret_cast<const float4*>(rj + l);
+                        s0 = fmaf(-a.x, b.x, s0);
+                        s1 = fmaf(-a.y, b.y, s1);
+                        s2 = fmaf(-a.z, b.z, s2);
+                        s3 = fmaf(-a.w, b.w, s3);
+                    }
+                    for (; l < j; ++l) s0 = fmaf(-ri[l], rj[l], s0);
+                    sv[h] = (s0 + s1) + (s2 + s3);
+                }
+            }
+            const float sjj = __shfl_sync(FULL, j < 32 ? sv[0] : sv[1], j & 31);
+            if (!(sjj > 0.f)) {
+                ok = false;
+                break;
+            }
+            const float d = sqrtf(sjj), rd = 1.f / d;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                if (i > j && i < m) {
+                    Lp[i * RPM + j] = sv[h] * rd;
+                    out[i * (i + 1) / 2 + j] = sv[h] * rd;
+                }
+            }
+            if (lane == 0) {
+                Lp[j * RPM + j] = d;
+                out[j * (j + 1) / 2 + j] = d;
+                out[LP_PACKED + j] = rd;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) out[LP_PACKED + RM] = ok ? 0.f : 2.f;
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
     const double* __restrict__ pts, long long n, int dim, KP<float> kp, float floor_,
     const long long* __restrict__ grp_ptr, long long n_grp, const long long* __restrict__ cand_ptr,
     const int32_t* __restrict__ cand_idx, int k, int32_t* __restrict__ sel_idx, int32_t* __restrict__ sel_count,
-    DevStatus* st) {
+    const float* __restrict__ lp_ws, DevStatus* st) {
     extern __shared__ __align__(16) float smf[];
     float* F1m = smf;                 // [RNT][RP]
     float* F2Sm = F1m + RNT * RP;     // [RNT][RP]
@@ -168,53 +252,23 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                 F2P[a] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
             }
         }
-        // ---- Lp = chol(Theta_PP) by warp 0, left-looking, lane owns rows lane and lane + 32
-        if (warp == 0) {
-            for (int j = 0; j < m; ++j) {
-                const float xj = X[RNT + j], yj = X[LDX + RNT + j], zj = X[2 * LDX + RNT + j];
-                float sv[2] = {0.f, 0.f};
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = lane + 32 * h;
-                    if (i >= j && i < m) {
-                        const float dx = X[RNT + i] - xj, dy = X[LDX + RNT + i] - yj, dz = X[2 * LDX + RNT + i] - zj;
-                        float th = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
-                        if (i == j) th += kp.nugget;
-                        const float* ri = Lp + i * RPM;
-                        const float* rj = Lp + j * RPM;
-                        float s0 = th, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                        int l = 0;
-                        for (; l + 4 <= j; l += 4) {
-                            const float4 a = *reinterpret_cast<const float4*>(ri + l);
-                            const float4 b = *reinterpret_cast<const float4*>(rj + l);
-                            s0 = fmaf(-a.x, b.x, s0);
-                            s1 = fmaf(-a.y, b.y, s1);
-                            s2 = fmaf(-a.z, b.z, s2);
-                            s3 = fmaf(-a.w, b.w, s3);
-                        }
-                        for (; l < j; ++l) s0 = fmaf(-ri[l], rj[l], s0);
-                        sv[h] = (s0 + s1) + (s2 + s3);
-                    }
+        // ---- Lp = chol(Theta_PP) and its reciprocal diagonal from the targets' Cholesky launch
+        {
+            const float* src = lp_ws + g * (long long)LP_SLOT;
+            const int tri = m * (m + 1) / 2;
+            for (int e = tid; e < tri; e += RNT) {
+                int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                while (i * (i + 1) / 2 > e) --i;
+                while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                Lp[i * RPM + (e - i * (i + 1) / 2)] = src[e];
+            }
+            if (tid < m) rLp[tid] = src[LP_PACKED + tid];
+            if (tid == 0) {
+                const float f = src[LP_PACKED + RM];
+                if (f != 0.f) {
+                    record_error(st, f == 2.f ? SIC_ERR_NOT_PD : SIC_ERR_INVALID, g);
+                    s_fail = 1;
                 }
-                const float sjj = __shfl_sync(FULL, j < 32 ? sv[0] : sv[1], j & 31);
-                if (!(sjj > 0.f)) {
-                    if (lane == 0) {
-                        record_error(st, SIC_ERR_NOT_PD, g);
-                        s_fail = 1;
-                    }
-                    break;
-                }
-                const float d = sqrtf(sjj), rd = 1.f / d;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = lane + 32 * h;
-                    if (i > j && i < m) Lp[i * RPM + j] = sv[h] * rd;
-                }
-                if (lane == 0) {
-                    Lp[j * RPM + j] = d;
-                    rLp[j] = rd;
-                }
-                __syncwarp();
             }
         }
         __syncthreads();
@@ -358,15 +412,22 @@ bool agg_reg_applies(sic_precision prec, int max_cand, int max_m, int k) {
     return prec == SIC_FP32_MIXED && max_cand <= RNT && max_m <= RM && k <= RK;
 }
 
+size_t agg_reg_workspace(long long n_grp) { return sizeof(float) * (size_t)LP_SLOT * (size_t)(n_grp > 0 ? n_grp : 1); }
+
 sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
                           const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx,
-                          int k, int32_t* sel_idx, int32_t* sel_count, cudaStream_t s) {
+                          int k, int32_t* sel_idx, int32_t* sel_count, void* ws, size_t ws_bytes, cudaStream_t s) {
+    if (!ws || ws_bytes < agg_reg_workspace(n_grp)) return SIC_ERR_INVALID;
+    const KP<float> kpf = make_kp<float>(*kp);
+    const int lgrid = persistent_grid(h, k_agg_target_chol, 32 * LP_WARPS, 0, (n_grp + LP_WARPS - 1) / LP_WARPS);
+    k_agg_target_chol<<<lgrid, 32 * LP_WARPS, 0, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp,
+                                                       (float*)ws);
     const size_t smem = sizeof(float) * ((size_t)RNT * RP * 2 + (size_t)RNT * RPM + 3 * (size_t)LDX);
     SIC_CUDA_TRY(cudaFuncSetAttribute(k_select_agg_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = persistent_grid(h, k_select_agg_reg, RNT, smem, n_grp > 0 ? n_grp : 1);
-    k_select_agg_reg<<<grid, RNT, smem, s>>>(pts, n, kp->dim, make_kp<float>(*kp), (float)sic_floor_of(kp),
+    k_select_agg_reg<<<grid, RNT, smem, s>>>(pts, n, kp->dim, kpf, (float)sic_floor_of(kp),
                                              (const long long*)grp_ptr, n_grp, (const long long*)cand_ptr, cand_idx,
-                                             k, sel_idx, sel_count, h->d_status);
+                                             k, sel_idx, sel_count, (const float*)ws, h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }

@@ -345,7 +345,7 @@ extern "C" sic_status sic_select_aggregated_workspace(sic_handle* h, int64_t n_g
     if (max_m > 64 || max_cand > 4096 || k > 128) return SIC_ERR_UNSUPPORTED;
     if (cudaSetDevice(h->device) != cudaSuccess) return SIC_ERR_CUDA;
     if (agg_reg_applies(prec, max_cand, max_m, k))
-        *bytes = 0;
+        *bytes = agg_reg_workspace(n_grp);
     else if (prec == SIC_FP64)
         *bytes = agg_plan<double>(h, n_grp, max_cand, max_m, k).ws_bytes;
     else if (prec == SIC_FP32_MIXED)
@@ -395,7 +395,8 @@ extern "C" sic_status sic_select_aggregated(sic_handle* h, const double* pts, in
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (agg_reg_applies(prec, max_cand, max_m, k))
-        return launch_agg_reg(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, k, sel_idx, sel_count, s);
+        return launch_agg_reg(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, k, sel_idx, sel_count, ws, ws_bytes,
+                              s);
     if (prec == SIC_FP64)
         return launch_agg<double>(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, sel_idx,
                                   sel_count, ws, ws_bytes, s);
