@@ -6,11 +6,11 @@
 // s = (P_0..P_{m-1}, S sorted), the factor block is L = U^{-T} where U U^T =
 // Theta_{s,s}, U upper triangular.  The CTA forms Theta on the reversed order
 // R = reverse(s) in packed lower storage in shared memory (one entry per thread), factors
-// it G G^T = Theta_{RR} (right-looking, the trailing update flat over the threads; one
-// thread takes each pivot's square root and reciprocal), and since U = J G J (J the reversal),
-// member a's column is J G^{-T} e_j with j = n-1-a: one back substitution per member,
-// one member per half-warp, the right-hand side in registers.  v_a = G_jj^2, so
-// logv = 2 log G_jj (eq. inverse_cond).  Rows are written diagonal first, then
+// it Theta_{RR} = L D L^T = G G^T with G = L D^{1/2} (right-looking, the trailing update
+// flat over the threads; one thread takes each pivot's reciprocal; no square roots), and
+// since U = J G J (J the reversal), member a's column is J G^{-T} e_j = d_j^{-1/2} J L^{-T} e_j
+// with j = n-1-a: one back substitution per member, one member per half-warp, the
+// right-hand side in registers.  v_a = G_jj^2 = d_j, so logv = log d_j (eq. inverse_cond).  Rows are written diagonal first, then
 // ascending, to the caller's CSC arrays.  Theta entries use the FP64 Matern of
 // matern_d2_fast (table-driven exp, Newton sqrt): this GPU issues two FP64 FMAs per
 // clock per SM, so FP64 instructions are spent on the factorisation.
@@ -122,15 +122,29 @@ __device__ __forceinline__ int pk_row(int e) {
     return i;
 }
 
-// Pivot of column c from its final Schur complement v: G_cc = sqrt(v) and 1 / G_cc;
-// a non-positive pivot raises *bad.
+// Pivot of column c of the LDL^T factorisation from its final Schur complement v: D_cc = v
+// (kept on the diagonal) and 1 / v (an FP32 reciprocal seed refined by two Newton steps:
+// relative error 2^-23 -> 2^-46 -> ~2^-92, four FP64 operations); a non-positive pivot
+// raises *bad.  The range test reads the bits (no FP64 compare).
 __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* rG, int* bad) {
-    if (!(v > 0.0)) {
+    const long long vb = __double_as_longlong(v);
+    if (vb <= 0 || vb >= 0x7ff0000000000000LL) {  // not in (+0, +inf): non-positive, infinite or NaN
         *bad = 1;
         return;
     }
-    const double r = rsqrt_newton(v);
-    G[pk(c, c)] = v * r;
+    double r;
+    const unsigned hi = (unsigned)__double2hiint(v);
+    if (hi < 0x38700000u || hi >= 0x47700000u) {
+        r = 1.0 / v;
+    } else {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__uint_as_float((hi << 3) - (896u << 23))));
+        const unsigned yb = __float_as_uint(y);
+        r = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
+        r = fma(r, fma(-v, r, 1.0), r);
+        r = fma(r, fma(-v, r, 1.0), r);
+    }
+    G[pk(c, c)] = v;
     rG[c] = r;
 }
 
@@ -147,8 +161,9 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
     const int nmax = k + m_hi;  // shared memory is laid out for this launch's size class
     double* G = smem_d;                                     // packed lower, nmax(nmax+1)/2
     double* rG = G + (long long)nmax * (nmax + 1) / 2;      // 1 / G_jj
-    double* cj = rG + nmax;                                 // the current column of G
-    double* xyz = cj + nmax;                                // 3 x nmax
+    double* cj = rG + nmax;                                 // the current column of L
+    double* cu = cj + nmax;                                 // the same column before scaling by 1/d_j
+    double* xyz = cu + nmax;                                // 3 x nmax
     double* tab = xyz + 3 * nmax;                           // 2^(j/256) (exp_neg_table)
     int* pos = reinterpret_cast<int*>(tab + EXP_TAB);       // nmax
     int* srt = pos + nmax;                                  // k
@@ -211,13 +226,14 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
             G[e] = v;
         }
         __syncthreads();
-        // right-looking Cholesky in place on the packed lower triangle: for column j,
-        // G_jj = sqrt(A_jj), G_ij = A_ij / G_jj, then A_il -= G_ij G_lj over the trailing
-        // triangle j < l <= i with one flat entry per worker thread.  The FP64 units are per
-        // SM sub-partition and charge a warp instruction whatever its active lanes, so the
-        // flat update keeps the four worker warps equally loaded with full warps.  The next
-        // pivot (its diagonal update, square root and reciprocal: a chain of dependent FP64
-        // operations) is taken by the pivot warp while the workers update the rest.
+        // right-looking LDL^T factorisation Theta_RR = L D L^T in place on the packed lower
+        // triangle (no square roots: G = L D^{1/2} is never formed): for column j, d_j = A_jj,
+        // L_ij = A_ij / d_j, then A_il -= L_ij A_lj over the trailing triangle j < l <= i with
+        // one flat entry per worker thread.  The FP64 units are per SM sub-partition and charge
+        // a warp instruction whatever its active lanes, so the flat update keeps the worker
+        // warps equally loaded with full warps.  The next pivot (its diagonal update and
+        // reciprocal, a chain of dependent FP64 operations) is taken by the pivot warp while
+        // the workers update the rest.
         if (tid == FILL_NT) fill_pivot(G[0], 0, G, rG, &s_bad);
         __syncthreads();
         for (int j = 0; j < nn; ++j) {
@@ -225,9 +241,11 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
             const double rd = rG[j];
             for (int i = worker ? j + 1 + tid : nn; i < nn; i += FILL_NT) {
                 const int a = pk(i, j);
-                const double g = G[a] * rd;
-                G[a] = g;
-                cj[i] = g;
+                const double uv = G[a];
+                const double l = uv * rd;
+                G[a] = l;
+                cj[i] = l;
+                cu[i] = uv;
             }
             __syncthreads();
             const int nt = nn - 1 - j;
@@ -237,11 +255,11 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
                     const int ii = pk_row(e);
                     const int i = ii + j + 1, l = e - ii * (ii + 1) / 2 + j + 1;
                     const int a = pk(i, l);
-                    G[a] = fma(-cj[i], cj[l], G[a]);
+                    G[a] = fma(-cj[i], cu[l], G[a]);
                 }
             } else if (tid == FILL_NT && nt > 0) {
                 const int a = pk(j + 1, j + 1);
-                fill_pivot(fma(-cj[j + 1], cj[j + 1], G[a]), j + 1, G, rG, &s_bad);
+                fill_pivot(fma(-cj[j + 1], cu[j + 1], G[a]), j + 1, G, rG, &s_bad);
             }
             __syncthreads();
         }
@@ -251,19 +269,12 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
             __syncthreads();
             continue;
         }
-        // H = rows of G scaled by their reciprocal pivots (off-diagonal entries), so that
-        // the back substitution G^T x = b reads y_l = b_l and updates b_i -= H_li y_l,
-        // with x_l = y_l / G_ll applied once at the end.
-        for (int e = worker ? tid : tri; e < tri; e += FILL_NT) {
-            const int i = pk_row(e);
-            const int j = e - i * (i + 1) / 2;
-            if (j < i) G[e] *= rG[i];
-        }
-        __syncthreads();
-        // member a: solve G^T x = e_jb (jb = nn-1-a).  Members go in pairs (2p, 2p+1), one pair
-        // per warp, one member per half-warp; the right-hand side lives in registers (lane
-        // h*16 + r of half h owns entries r + 16 q).  The two members' jb differ by one, so
-        // each warp instruction serves both, in 16-lane instead of 32-lane granularity.
+        // member a: with G = L D^{1/2}, G^-T e_jb = d_jb^{-1/2} L^-T e_jb (jb = nn-1-a): a
+        // back substitution with the unit upper L^T, scaled once.  Members go in pairs
+        // (2p, 2p+1), one pair per warp, one member per half-warp; the right-hand side lives in
+        // registers (lane h*16 + r of half h owns entries r + 16 q).  The two members' jb
+        // differ by one, so each warp instruction serves both, in 16-lane instead of 32-lane
+        // granularity.
         const int npairs = (m + 1) / 2;
         const int half = lane >> 4, hl = lane & 15;
         for (int p = worker ? warp : npairs; p < npairs; p += FILL_NT / 32) {
@@ -290,19 +301,20 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
             }
             if (has) {
                 const long long c0 = col_ptr[g0 + a];
+                const double sc = rsqrt_newton(G[pk(jb, jb)]);
 #pragma unroll
                 for (int q = 0; q < FILL_HSLOTS; ++q) {
                     const int i = hl + 16 * q;
                     if (i <= jb) {
                         row_idx[c0 + jb - i] = pos[i];
-                        val[c0 + jb - i] = bv[q] * rG[i];
+                        val[c0 + jb - i] = bv[q] * sc;
                     }
                 }
             }
         }
         // log v of every member, one member per thread (the FP64 log once per lane instead of
         // once per warp)
-        for (int a = worker ? tid : m; a < m; a += FILL_NT) logv[g0 + a] = 2.0 * log(G[pk(nn - 1 - a, nn - 1 - a)]);
+        for (int a = worker ? tid : m; a < m; a += FILL_NT) logv[g0 + a] = log(G[pk(nn - 1 - a, nn - 1 - a)]);
         __syncthreads();
     }
 }
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(256) k_sum_final(const double* __restrict__ pa
 
 size_t fill_smem_bytes(int k, int max_m) {
     size_t nmax = (size_t)k + (size_t)max_m;
-    return sizeof(double) * (nmax * (nmax + 1) / 2 + 2 * nmax + 3 * nmax + EXP_TAB) + sizeof(int) * (nmax + (size_t)k);
+    return sizeof(double) * (nmax * (nmax + 1) / 2 + 3 * nmax + 3 * nmax + EXP_TAB) + sizeof(int) * (nmax + (size_t)k);
 }
 
 __global__ void k_fp64_math(KP<double> kp, const double* __restrict__ x, long long n, double* __restrict__ os,
