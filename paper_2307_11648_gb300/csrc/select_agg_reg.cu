@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
             for (int tt = 0; tt < 16; ++tt, ++t) {
                 if (t >= k) return false;
                 const int buf = t & 1;
-                const unsigned key = (V2 >= floor_) ? score_key(V1 / V2) : 0u;
+                const unsigned key = (V2 >= floor_) ? score_key(__fdividef(V1, V2)) : 0u;
                 const unsigned wmax = __reduce_max_sync(FULL, key);
                 const unsigned hit = __ballot_sync(FULL, key == wmax);
                 if (lane == __ffs(hit) - 1) {  // the warp's best row (lowest lane among equal keys)
