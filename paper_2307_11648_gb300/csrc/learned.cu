@@ -163,68 +163,116 @@ __device__ __forceinline__ unsigned long long topk_key(float s, int r) {
     return ((unsigned long long)u << 32) | (unsigned int)(0x7fffffff - r);
 }
 
-__global__ void __launch_bounds__(512) k_topk_compact(const long long* __restrict__ cand_ptr,
-                                                      const int32_t* __restrict__ cand_idx,
-                                                      const float* __restrict__ score, long long n_grp, int top,
-                                                      const long long* __restrict__ out_ptr,
-                                                      int32_t* __restrict__ out_idx, DevStatus* st) {
-    __shared__ unsigned long long key[4096];
-    __shared__ unsigned long long thr;
-    __shared__ int warp_cnt[16];
+// Per-group top-k by radix selection: the threshold key T (the top-th largest 32-bit
+// order-preserving score key) is found digit by digit (4 passes of 8 bits, each a shared
+// histogram of the keys that match the digits chosen so far and a one-warp scan from the
+// top bin); then the list is compacted in order, keeping keys > T and, among keys == T,
+// the first `need` in list order -- the same set as sorting by (score desc, position asc).
+constexpr int TOPK_NT = 512;
+constexpr int TOPK_KPT = 4096 / TOPK_NT;  // keys per thread
+
+__global__ void __launch_bounds__(TOPK_NT) k_topk_compact(const long long* __restrict__ cand_ptr,
+                                                          const int32_t* __restrict__ cand_idx,
+                                                          const float* __restrict__ score, long long n_grp, int top,
+                                                          const long long* __restrict__ out_ptr,
+                                                          int32_t* __restrict__ out_idx, DevStatus* st) {
+    __shared__ unsigned hist[256];
+    __shared__ unsigned s_digit, s_need;
+    __shared__ int warp_a[TOPK_NT / 32], warp_b[TOPK_NT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
         const long long b0 = cand_ptr[g];
         const int C = (int)(cand_ptr[g + 1] - b0);
         const long long o0 = out_ptr[g];
         if (C <= top) {
-            for (int r = threadIdx.x; r < C; r += blockDim.x) out_idx[o0 + r] = cand_idx[b0 + r];
+            for (int r = tid; r < C; r += TOPK_NT) out_idx[o0 + r] = cand_idx[b0 + r];
             continue;
         }
         if (C > 4096) {
-            if (threadIdx.x == 0) record_error(st, SIC_ERR_UNSUPPORTED, g);
+            if (tid == 0) record_error(st, SIC_ERR_UNSUPPORTED, g);
             continue;
         }
-        int P = 1;
-        while (P < C) P <<= 1;
-        for (int r = threadIdx.x; r < P; r += blockDim.x) key[r] = (r < C) ? topk_key(score[b0 + r], r) : 0ull;
-        __syncthreads();
-        // bitonic sort, descending
-        for (int size = 2; size <= P; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
-                    int lo = 2 * i - (i & (stride - 1));
-                    int hi = lo + stride;
-                    bool desc = ((lo & size) == 0);
-                    unsigned long long a = key[lo], b = key[hi];
-                    if ((a < b) == desc) {
-                        key[lo] = b;
-                        key[hi] = a;
+        unsigned key[TOPK_KPT];
+#pragma unroll
+        for (int q = 0; q < TOPK_KPT; ++q) {
+            const int r = tid + q * TOPK_NT;
+            key[q] = (r < C) ? (unsigned)(topk_key(score[b0 + r], r) >> 32) : 0u;
+        }
+        unsigned prefix = 0, mask = 0, need = (unsigned)top;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            if (tid < 256) hist[tid] = 0;
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < TOPK_KPT; ++q) {
+                const int r = tid + q * TOPK_NT;
+                if (r < C && (key[q] & mask) == prefix) atomicAdd(&hist[(key[q] >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (warp == 0) {  // bins from the top: lane l holds bins 255 - 8l - i, i < 8
+                unsigned c[8], sum = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    c[i] = hist[255 - 8 * lane - i];
+                    sum += c[i];
+                }
+                unsigned incl = sum;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += o;
+                }
+                const unsigned excl = incl - sum;
+                if (excl < need && need <= incl) {
+                    unsigned run = excl;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (run + c[i] >= need) {
+                            s_digit = 255u - 8u * lane - i;
+                            s_need = need - run;
+                            break;
+                        }
+                        run += c[i];
                     }
                 }
-                __syncthreads();
             }
+            __syncthreads();
+            prefix |= s_digit << shift;
+            mask |= 255u << shift;
+            need = s_need;
+            __syncthreads();
         }
-        if (threadIdx.x == 0) thr = key[top - 1];
-        __syncthreads();
-        const unsigned long long th = thr;
-        // compaction in list order: chunks of 512 with a block prefix count
-        int base = 0;
-        for (int c0 = 0; c0 < C; c0 += blockDim.x) {
-            const int r = c0 + threadIdx.x;
-            const bool keep = r < C && topk_key(score[b0 + r], r) >= th;
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) warp_cnt[warp] = __popc(bal);
+        // compaction in list order: keys > T, then the first `need` keys == T
+        const unsigned T = prefix;
+        int base = 0, eq_run = 0;
+#pragma unroll
+        for (int q = 0; q < TOPK_KPT; ++q) {
+            if (q * TOPK_NT >= C) break;
+            const int r = tid + q * TOPK_NT;
+            const bool in = r < C;
+            const bool eq = in && key[q] == T;
+            const unsigned beq = __ballot_sync(0xffffffffu, eq);
+            if (lane == 0) warp_a[warp] = __popc(beq);
+            __syncthreads();
+            int eq_before = eq_run, eq_total = 0;
+            for (int w = 0; w < TOPK_NT / 32; ++w) {
+                if (w < warp) eq_before += warp_a[w];
+                eq_total += warp_a[w];
+            }
+            eq_before += __popc(beq & ((1u << lane) - 1u));
+            const bool keep = in && (key[q] > T || (eq && eq_before < (int)need));
+            const unsigned bk = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) warp_b[warp] = __popc(bk);
             __syncthreads();
             int before = 0, total = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                if (w < warp) before += warp_cnt[w];
-                total += warp_cnt[w];
+            for (int w = 0; w < TOPK_NT / 32; ++w) {
+                if (w < warp) before += warp_b[w];
+                total += warp_b[w];
             }
-            if (keep) out_idx[o0 + base + before + __popc(bal & ((1u << lane) - 1u))] = cand_idx[b0 + r];
+            if (keep) out_idx[o0 + base + before + __popc(bk & ((1u << lane) - 1u))] = cand_idx[b0 + r];
             base += total;
+            eq_run += eq_total;
             __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -479,8 +527,8 @@ extern "C" sic_status sic_proposal_topk(sic_handle* h, const int64_t* cand_ptr, 
     k_topk_counts<<<(unsigned)((n_grp + 255) / 256), 256, 0, s>>>((const long long*)cand_ptr, n_grp, top,
                                                                     (long long*)out_ptr);
     k_scan_one_block<<<1, 1024, 0, s>>>((long long*)out_ptr, n_grp);
-    int grid = persistent_grid(h, k_topk_compact, 512, 0, n_grp);
-    k_topk_compact<<<grid, 512, 0, s>>>((const long long*)cand_ptr, cand_idx, score, n_grp, top,
+    int grid = persistent_grid(h, k_topk_compact, TOPK_NT, 0, n_grp);
+    k_topk_compact<<<grid, TOPK_NT, 0, s>>>((const long long*)cand_ptr, cand_idx, score, n_grp, top,
                                         (const long long*)out_ptr, out_idx, h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
