@@ -51,7 +51,7 @@ DFMA_PER_SM_CLK = 2     # FP64 FMA per SM per clock on GB300 (1.26 TFLOP/s nomin
 LAUNCHES_PER_STEP = 15
 # DRAM read + write bytes of the two k_fill launches of one learned step at N = 2^19
 # (22,423 supernodes), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
-FILL_DRAM_BYTES_N2E19 = 17.430016e6 + 261.050112e6 + 9.671168e6 + 122.095616e6
+FILL_DRAM_BYTES_N2E19 = 17.650944e6 + 259.233280e6 + 9.646848e6 + 124.519680e6
 FILL_GROUPS_N2E19 = 22423
 
 

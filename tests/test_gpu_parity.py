@@ -421,3 +421,46 @@ def test_errors_reported_by_sync(env):
     with pytest.raises(sic.SicError) as e:
         h.sync()
     assert e.value.code == sic.SIC_ERR_NOT_PD and e.value.unit == 5
+
+
+def test_supernodal_fp32_errors_reported_by_sync(env):
+    """The FP32 supernodal path for short candidate lists (targets' factors in their own
+    launch, register-resident selection) reports through sic_sync: a candidate inside its
+    own group (invalid), a group larger than the stated max_m (invalid), and coincident
+    targets without a nugget (the targets' factor is singular)."""
+    torch, sic, pipeline, h = env
+    kp = sic.kernel(2, 3, 0.05, 1.0, 1e-6)
+    hp = pipeline.prepare_groups(synthetic.points(4096, 2, 12), kp, 128, 16, mmin=4, mmax=32)
+    g = 10
+    g0 = int(hp.grp_ptr[g])
+
+    def run(hp_, max_m=None):
+        dp = pipeline.DeviceProblem(hp_)
+        fb = pipeline.FactorBuilder(h, hp_, sic.SIC_FP32_MIXED)
+        mm = hp_.max_m if max_m is None else max_m
+        ws = sic._ws(sic.select_aggregated_workspace(h, hp_.n_units, hp_.max_cand, mm, hp_.k, sic.SIC_FP32_MIXED),
+                     "cuda")
+        sic.select_aggregated(h, dp.pts, hp_.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, hp_.max_cand, mm, hp_.k,
+                              sic.SIC_FP32_MIXED, fb.sel_idx, fb.sel_count, ws)
+
+    run(hp)
+    h.sync()  # the clean problem runs without error
+    bad = pipeline.HostProblem(hp.pts, hp.kp, hp.k, hp.cand_ptr, hp.cand_idx.copy(), hp.grp_ptr, hp.order, hp.ell2)
+    bad.cand_idx[hp.cand_ptr[g]] = g0  # a member of the group itself
+    run(bad)
+    with pytest.raises(sic.SicError) as e:
+        h.sync()
+    assert e.value.code == sic.SIC_ERR_INVALID and e.value.unit == g
+    m_big = int(np.argmax(np.diff(hp.grp_ptr)))
+    run(hp, max_m=int(np.diff(hp.grp_ptr)[m_big]) - 1)
+    with pytest.raises(sic.SicError) as e:
+        h.sync()
+    assert e.value.code == sic.SIC_ERR_INVALID
+    kp0 = sic.kernel(2, 3, 0.05, 1.0, 0.0)
+    P = hp.pts.copy()
+    P[g0 + 1] = P[g0]  # two coincident members: Theta_PP singular without a nugget
+    sing = pipeline.HostProblem(P, kp0, hp.k, hp.cand_ptr, hp.cand_idx, hp.grp_ptr, hp.order, hp.ell2)
+    run(sing)
+    with pytest.raises(sic.SicError) as e:
+        h.sync()
+    assert e.value.code == sic.SIC_ERR_NOT_PD and e.value.unit == g
