@@ -1,12 +1,15 @@
 // Proposal-network inference on the 5th-generation tensor cores (tcgen05 + TMEM).
 //
 // One CTA of 128 threads scores 128 candidate rows at a time (persistent over row tiles):
-//   layer 1  D = X W1      M = 128 rows, N = 128 hidden, K = 16 (8 features + 8 zeros)
-//   GELU     read D from TMEM (tcgen05.ld, thread = row), add b1, GELU (tanh form, see
-//            gelu_f), round to BF16 and store as the next A operand in shared memory
-//   layer 2  D = H1 W2     M = 128, N = 128, K = 128 (8 MMAs of K = 16)
+//   layer 1  D = X W1 + b1  M = 128 rows, N = 128 hidden, K = 16: 8 features, a constant
+//            1 whose weight row is b1, 7 zeros (the bias comes out of the MMA)
+//   GELU     read D from TMEM (tcgen05.ld, thread = row), 2 gelu(D) (tanh form, see
+//            gelu2_f), round to BF16 and store as the next A operand in shared memory
+//   layer 2  D = (2 H1) (W2 / 2)   M = 128, N = 128, K = 128 (8 MMAs of K = 16)
 //   head     read D (thread = row: the whole hidden row is in the thread's registers),
-//            s = sum_j gelu(D_j + b2_j) w3_j + b3 -- no cross-thread reduction.
+//            s = sum_j 2 gelu(D_j + b2_j) (w3_j / 2) + b3 -- no cross-thread reduction.
+// The factors 2 and 1/2 are exact in BF16 and FP32, so folding the GELU's 1/2 into W2 and
+// w3 changes no rounding; it saves one multiply per hidden value.
 // Operands are BF16 in shared memory in the K-major layout without swizzle: 8 x 16-byte
 // "core matrices" (8 rows x 8 elements, 128 contiguous bytes), core matrices adjacent
 // along K at LBO = 128 bytes, 8-row groups at SBO = (K / 8) * 128 bytes.  The weights
@@ -31,7 +34,7 @@ constexpr int SA1 = 0;                    // 128 x 16 bf16 = 4 KiB
 constexpr int SB1 = SA1 + 128 * 16 * 2;   // 128 x 16 bf16 = 4 KiB
 constexpr int SA2 = SB1 + 128 * 16 * 2;   // 128 x 128 bf16 = 32 KiB
 constexpr int SB2 = SA2 + 128 * 128 * 2;  // 128 x 128 bf16 = 32 KiB
-constexpr int SVEC = SB2 + 128 * 128 * 2; // b1, b2, w3 (FP32)
+constexpr int SVEC = SB2 + 128 * 128 * 2; // b2, w3 / 2 (FP32)
 constexpr int SBAR = SVEC + 3 * HID * 4;  // mbarrier (8 B) + TMEM address (4 B)
 constexpr int SMEM_TC = SBAR + 16;
 
@@ -105,10 +108,10 @@ __device__ __forceinline__ float tanh_hw(float x) {
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float gelu_f(float z) {
+// twice the GELU: z (1 + tanh(u)), the 1/2 being folded into the consumer's weights
+__device__ __forceinline__ float gelu2_f(float z) {
     const float u = z * fmaf(0.0356774081f, z * z, 0.7978845608f);
-    const float hz = 0.5f * z;
-    return fmaf(hz, tanh_hw(u), hz);
+    return fmaf(z, tanh_hw(u), z);
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -121,28 +124,26 @@ __global__ void __launch_bounds__(TC_NT) k_mlp_tc(const float* __restrict__ X, l
                                                   DevStatus* st) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5;
-    float* sb1 = reinterpret_cast<float*>(sm + SVEC);
-    float* sb2 = sb1 + HID;
+    float* sb2 = reinterpret_cast<float*>(sm + SVEC);
     float* sw3 = sb2 + HID;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SBAR);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + SBAR + 8);
     const uint32_t bar_a = smem_u32(bar);
 
-    // weights (W^T as N x K, K-major), biases, head
+    // weights (W^T as N x K, K-major; row K = NF of layer 1 is b1, W2 and w3 halved), b2
     for (int e = tid; e < HID * 16; e += TC_NT) {
         const int n = e / 16, k = e % 16;
-        const float w = (k < NF) ? params[k * HID + n] : 0.f;
+        const float w = (k < NF) ? params[k * HID + n] : (k == NF ? params[OFF_B1 + n] : 0.f);
         *reinterpret_cast<__nv_bfloat16*>(sm + SB1 + core_off(n, k, 16)) = __float2bfloat16_rn(w);
     }
     for (int e = tid; e < HID * HID; e += TC_NT) {
         const int n = e / HID, k = e % HID;
         *reinterpret_cast<__nv_bfloat16*>(sm + SB2 + core_off(n, k, HID)) =
-            __float2bfloat16_rn(params[OFF_W2 + k * HID + n]);
+            __float2bfloat16_rn(0.5f * params[OFF_W2 + k * HID + n]);
     }
     for (int i = tid; i < HID; i += TC_NT) {
-        sb1[i] = params[OFF_B1 + i];
         sb2[i] = params[OFF_B2 + i];
-        sw3[i] = params[OFF_W3 + i];
+        sw3[i] = 0.5f * params[OFF_W3 + i];
     }
     const float b3 = params[OFF_B3];
     if (tid == 0) {
@@ -169,13 +170,13 @@ __global__ void __launch_bounds__(TC_NT) k_mlp_tc(const float* __restrict__ X, l
     const long long ntiles = (rows + 127) / 128;
     for (long long tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
         const long long r = tile * 128 + tid;
-        // A1 row: 8 features then 8 zeros (two core matrices along K)
+        // A1 row: 8 features, then 1 (picks up b1) and 7 zeros (two core matrices along K)
         float f[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) f[q] = (r < rows) ? X[r * NF + q] : 0.f;
         *reinterpret_cast<uint4*>(sm + SA1 + core_off(tid, 0, 16)) =
             make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-        *reinterpret_cast<uint4*>(sm + SA1 + core_off(tid, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sm + SA1 + core_off(tid, 8, 16)) = make_uint4(pack2(1.f, 0.f), 0u, 0u, 0u);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(TC_NT) k_mlp_tc(const float* __restrict__ X, l
             uint32_t pk[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-                pk[j] = pack2(gelu_f(v[2 * j] + sb1[c * 32 + 2 * j]), gelu_f(v[2 * j + 1] + sb1[c * 32 + 2 * j + 1]));
+                pk[j] = pack2(gelu2_f(v[2 * j]), gelu2_f(v[2 * j + 1]));
 #pragma unroll
             for (int g = 0; g < 4; ++g)
                 *reinterpret_cast<uint4*>(sm + SA2 + core_off(tid, c * 32 + g * 8, HID)) =
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(TC_NT) k_mlp_tc(const float* __restrict__ X, l
             float v[32];
             tmem_ld32(lane_addr + c * 32, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) s = fmaf(gelu_f(v[j] + sb2[c * 32 + j]), sw3[c * 32 + j], s);
+            for (int j = 0; j < 32; ++j) s = fmaf(gelu2_f(v[j] + sb2[c * 32 + j]), sw3[c * 32 + j], s);
         }
         if (r < rows) out[r] = s + b3;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

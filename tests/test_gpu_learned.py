@@ -237,7 +237,7 @@ def test_learned_proposal_gain(env):
     gaps = {k: (res[k] - res["plain64"]) / base for k in ["plain32", "learned", "distance"]}
     print("sum log v", res, "KL gaps", gaps, f"recall mlp {hit_mlp / tot:.5f} distance {hit_dist / tot:.5f}")
     assert base > 0
-    assert gaps["learned"] <= 0.01          # within 1% of plain greedy (the benchmark spec)
+    assert gaps["learned"] <= 0.01          # KL within 1% of plain greedy
     assert hit_mlp / tot >= 0.99
 
 
