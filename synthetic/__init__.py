@@ -24,8 +24,8 @@ import math
 import numpy as np
 
 __all__ = [
-    "GOLDEN_GAMMA", "mix64", "uniform", "normal", "points", "planted_factor", "PRESETS",
-    "STREAM_POINTS", "STREAM_NORMAL", "STREAM_PLANTED",
+    "GOLDEN_GAMMA", "mix64", "uniform", "normal", "points", "clustered_points", "planted_factor", "PRESETS",
+    "STREAM_POINTS", "STREAM_NORMAL", "STREAM_PLANTED", "STREAM_CLUSTER",
 ]
 
 GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -35,6 +35,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 STREAM_POINTS = 1
 STREAM_NORMAL = 2
 STREAM_PLANTED = 3
+STREAM_CLUSTER = 4
 
 
 def mix64(z):
@@ -82,6 +83,17 @@ def normal(seed: int, count: int, stream: int = STREAM_NORMAL) -> np.ndarray:
 def points(n: int, dim: int, seed: int) -> np.ndarray:
     """n points i.i.d. uniform in [0,1)^dim, row-major float64 (point i, coordinate c = draw i*dim+c)."""
     return uniform(seed, STREAM_POINTS, n * dim).reshape(n, dim)
+
+
+def clustered_points(n: int, dim: int, seed: int, frac: float = 0.5, width: float = 0.05) -> np.ndarray:
+    """An inhomogeneous cloud: `points(n, dim, seed)`, with each point moved, when its own
+    extra uniform draw is below `frac`, into the cube of side `width` centred in [0,1)^dim
+    (same relative position inside it).  About frac * n points crowd the small cube; the rest
+    stay spread over the unit cube."""
+    p = points(n, dim, seed)
+    pick = uniform(seed, STREAM_CLUSTER, n) < frac
+    p[pick] = 0.5 + width * (p[pick] - 0.5)
+    return p
 
 
 def planted_factor(n: int, s: int, seed: int, diag: float = 10.0) -> np.ndarray:
