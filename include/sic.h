@@ -178,6 +178,52 @@ sic_status sic_select_aggregated(sic_handle* h, const double* pts, int64_t n, co
                                  sic_precision prec, int32_t* sel_idx, int32_t* sel_count, void* ws,
                                  size_t ws_bytes, void* stream);
 
+/* ------------------------------------- global allocation of nonzeros [device] -- */
+/*
+ * Section 5.4: instead of k picks everywhere, a budget of off-diagonal nonzeros goes to
+ * whichever unit (column or supernode) lowers the KL divergence most per nonzero.  The
+ * paper keeps every unit's best candidate in a priority queue; here each unit first runs
+ * its local greedy for up to k picks, reporting the exact decrease of each pick, and
+ * sic_allocate_global then keeps a prefix of every unit's picks.  The prefixes equal
+ * what the queue would pop (a unit's candidates change only when the unit itself gains
+ * an entry, so its picks come in its local order; a pick is popped once the running
+ * minimum of its unit's decreases up to it is the largest left).
+ *
+ * sic_select_columns_gain / sic_select_aggregated_gain: as sic_select_columns /
+ * sic_select_aggregated, plus gain[n_units * k] [device, FP64]: gain[u * k + t] is the
+ * decrease per nonzero of 2 KL by pick t (t < sel_count[u]; later entries untouched):
+ *   column (Section 5.4.1, eq. global_obj): log(v_t / v_{t+1}), v_t the target's
+ *     conditional variance after t picks, i.e. -log(1 - corr^2) of the pick;
+ *   supernode of m members (Section 5.4.2): log(Theta_{jj|I} / Theta_{jj|I,P}) / m for
+ *     the pick j (the change of logdet Theta_{PP|I}; the pick adds m nonzeros).
+ * In SIC_FP32_MIXED the ratio comes from the FP32 selection state, the logarithm in FP64.
+ */
+sic_status sic_select_columns_gain(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                   const int32_t* targets, int64_t n_cols, const int64_t* cand_ptr,
+                                   const int32_t* cand_idx, int32_t max_cand, int32_t k, sic_precision prec,
+                                   int32_t* sel_idx, int32_t* sel_count, double* gain, void* stream);
+sic_status sic_select_aggregated_gain(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                      const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr,
+                                      const int32_t* cand_idx, int32_t max_cand, int32_t max_m, int32_t k,
+                                      sic_precision prec, int32_t* sel_idx, int32_t* sel_count, double* gain,
+                                      void* ws, size_t ws_bytes, void* stream);
+
+/* Global greedy allocation (Section 5.4) of `budget` off-diagonal nonzeros over n_units
+ * units with the gains above.  A pick of unit u costs m_u nonzeros (m_u = grp_ptr[u+1] -
+ * grp_ptr[u]; 1 for every unit when grp_ptr is NULL).  Picks are taken in the queue's
+ * order -- largest running minimum of the unit's gains first, equal keys by lower unit,
+ * then earlier pick -- until the first pick whose cost exceeds what is left of the budget.
+ * out_count[n_units] [device] receives the number of leading picks kept per unit
+ * (<= sel_count[u]); the pattern is sel_idx[u * k .. u * k + out_count[u]), to be passed
+ * as sel_count to sic_factor_nnz and sic_build_factor.  gain, sel_count, grp_ptr
+ * [device]; budget >= 0; 1 <= k <= 128.  A sel_count outside [0, k] or a NaN gain is
+ * reported by sic_sync as SIC_ERR_INVALID (that unit is then treated as empty, or the
+ * NaN as -infinity).  Needs sic_allocate_global_workspace bytes of ws. */
+sic_status sic_allocate_global_workspace(int64_t n_units, int32_t k, size_t* bytes);
+sic_status sic_allocate_global(sic_handle* h, int64_t n_units, const int64_t* grp_ptr, const double* gain,
+                               const int32_t* sel_count, int32_t k, int64_t budget, int32_t* out_count, void* ws,
+                               size_t ws_bytes, void* stream);
+
 /* ----------------------------------------------------------- the factor [device] -- */
 
 /* Column pointers of the factor for a selection.  Without groups (grp_ptr NULL,
@@ -189,14 +235,6 @@ sic_status sic_factor_nnz_workspace(int64_t n, size_t* bytes);
 sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, const int32_t* sel_count,
                           int64_t n, int64_t* col_ptr, void* ws, size_t ws_bytes, void* stream);
 
-/* KL-optimal fill (eq. L_col; aggregated form of Appendix A.4) in FP64 for the
- * pattern sel_idx / sel_count (k picks per column or group, as returned by the
- * selection calls; any order).  Writes row_idx / val at col_ptr (from
- * sic_factor_nnz), logv[n] = log Theta_{ii | s_i \ i} and *sum_logv (one FP64 on the
- * device, summed in a fixed order so that repeated runs agree bit for bit).  The KL
- * divergence of the factor is (sum_logv - logdet Theta) / 2 (eq. obj_chol).
- * grp_ptr NULL means single columns (n_grp = n).  max_m bounds the group size (1
- * without groups, <= 64).  Needs sic_build_factor_workspace bytes of ws. */
 /* Allocation-free variant of sic_factor_nnz (the paper has no counterpart; it is a
  * convenience of this library).  For callers that cannot allocate device memory --
  * for example code running inside a host framework that has reserved the device's
@@ -214,6 +252,15 @@ sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, 
  * from several threads -- race on it and must be serialised by the caller. */
 sic_status sic_factor_nnz_noalloc(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, const int32_t* sel_count,
                                   int64_t n, int64_t* col_ptr, void* stream);
+
+/* KL-optimal fill (eq. L_col; aggregated form of Appendix A.4) in FP64 for the
+ * pattern sel_idx / sel_count (k picks per column or group, as returned by the
+ * selection calls; any order).  Writes row_idx / val at col_ptr (from
+ * sic_factor_nnz), logv[n] = log Theta_{ii | s_i \ i} and *sum_logv (one FP64 on the
+ * device, summed in a fixed order so that repeated runs agree bit for bit).  The KL
+ * divergence of the factor is (sum_logv - logdet Theta) / 2 (eq. obj_chol).
+ * grp_ptr NULL means single columns (n_grp = n).  max_m bounds the group size (1
+ * without groups, <= 64).  Needs sic_build_factor_workspace bytes of ws. */
 
 sic_status sic_build_factor_workspace(int64_t n, size_t* bytes);
 sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
     const double* __restrict__ pts, long long n, int dim, KP<float> kp, float floor_,
     const long long* __restrict__ grp_ptr, long long n_grp, const long long* __restrict__ cand_ptr,
     const int32_t* __restrict__ cand_idx, int k, int max_m, int32_t* __restrict__ sel_idx,
-    int32_t* __restrict__ sel_count, const float* __restrict__ lp_ws, DevStatus* st) {
+    int32_t* __restrict__ sel_count, const float* __restrict__ lp_ws, double* __restrict__ gain, DevStatus* st) {
     extern __shared__ __align__(16) float smf[];
     float* F1m = smf;                 // [RNT][RP]
     float* F2Sm = F1m + RNT * RP;     // [RNT][RP]
@@ -379,7 +379,11 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                         V2 = fmaf(-u2, u2, V2);
                     }
                 }
-                if (tid == 0) sel_idx[g * k + t] = cand_idx[b0 + q];
+                if (tid == 0) {
+                    sel_idx[g * k + t] = cand_idx[b0 + q];
+                    // decrease of logdet Theta_{PP|I} per nonzero (Section 5.4.2)
+                    if (gain) gain[g * k + t] = log((double)pv1[buf][bw] / (double)pv2[buf][bw]) / m;
+                }
             }
             // block TB is complete: move the own row's entries into registers
 #pragma unroll
@@ -416,8 +420,8 @@ size_t agg_reg_workspace(long long n_grp) { return sizeof(float) * (size_t)LP_SL
 
 sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
                           const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx,
-                          int max_m, int k, int32_t* sel_idx, int32_t* sel_count, void* ws, size_t ws_bytes,
-                          cudaStream_t s) {
+                          int max_m, int k, int32_t* sel_idx, int32_t* sel_count, double* gain, void* ws,
+                          size_t ws_bytes, cudaStream_t s) {
     if (!ws || ws_bytes < agg_reg_workspace(n_grp)) return SIC_ERR_INVALID;
     const KP<float> kpf = make_kp<float>(*kp);
     const int lgrid = persistent_grid(h, k_agg_target_chol, 32 * LP_WARPS, 0, (n_grp + LP_WARPS - 1) / LP_WARPS);
@@ -428,7 +432,7 @@ sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const s
     const int grid = persistent_grid(h, k_select_agg_reg, RNT, smem, n_grp > 0 ? n_grp : 1);
     k_select_agg_reg<<<grid, RNT, smem, s>>>(pts, n, kp->dim, kpf, (float)sic_floor_of(kp),
                                              (const long long*)grp_ptr, n_grp, (const long long*)cand_ptr, cand_idx,
-                                             k, max_m, sel_idx, sel_count, (const float*)ws, h->d_status);
+                                             k, max_m, sel_idx, sel_count, (const float*)ws, gain, h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }

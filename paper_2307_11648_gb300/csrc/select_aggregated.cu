@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
     const double* __restrict__ pts, long long n, int dim, KP<T> kp, T floor_, const long long* __restrict__ grp_ptr,
     long long n_grp, const long long* __restrict__ cand_ptr, const int32_t* __restrict__ cand_idx, int max_cand,
     int max_m, int k, int32_t* __restrict__ sel_idx, int32_t* __restrict__ sel_count, T* __restrict__ ws,
-    AggLayout L, DevStatus* st) {
+    AggLayout L, double* __restrict__ gain, DevStatus* st) {
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -274,7 +274,11 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                         V2[r] = fma(-u2, u2, V2[r]);
                     }
                 }
-                if (tid == 0) sel_idx[g * k + t] = cand_idx[b0 + q];
+                if (tid == 0) {
+                    sel_idx[g * k + t] = cand_idx[b0 + q];
+                    // decrease of logdet Theta_{PP|I} per nonzero (Section 5.4.2)
+                    if (gain) gain[g * k + t] = log((double)v1q / (double)v2q) / m;
+                }
             }
         }
         if (tid == 0) sel_count[g] = t;
@@ -359,7 +363,8 @@ namespace {
 template <typename T>
 sic_status launch_agg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp, const int64_t* grp_ptr,
                       int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx, int max_cand, int max_m, int k,
-                      int32_t* sel_idx, int32_t* sel_count, void* ws, size_t ws_bytes, cudaStream_t s) {
+                      int32_t* sel_idx, int32_t* sel_count, double* gain, void* ws, size_t ws_bytes,
+                      cudaStream_t s) {
     AggPlan P = agg_plan<T>(h, n_grp, max_cand, max_m, k);
     if (P.ws_bytes > 0 && (!ws || ws_bytes < P.ws_bytes)) return SIC_ERR_INVALID;
     KP<T> kpt = make_kp<T>(*kp);
@@ -369,7 +374,7 @@ sic_status launch_agg(sic_handle* h, const double* pts, long long n, const sic_k
 #define SIC_AGG_LAUNCH(NTV, SM)                                                                                   \
     k_select_agg<T, NTV, SM><<<P.grid, NTV, P.smem_bytes, s>>>(pts, n, kp->dim, kpt, fl, gp, n_grp, cp, cand_idx, \
                                                                max_cand, max_m, k, sel_idx, sel_count, (T*)ws,    \
-                                                               P.L, h->d_status)
+                                                               P.L, gain, h->d_status)
     if (P.nt == 256) {
         if (P.smem) SIC_AGG_LAUNCH(256, true); else SIC_AGG_LAUNCH(256, false);
     } else {
@@ -381,11 +386,12 @@ sic_status launch_agg(sic_handle* h, const double* pts, long long n, const sic_k
 }
 }  // namespace
 
-extern "C" sic_status sic_select_aggregated(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
-                                            const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr,
-                                            const int32_t* cand_idx, int32_t max_cand, int32_t max_m, int32_t k,
-                                            sic_precision prec, int32_t* sel_idx, int32_t* sel_count, void* ws,
-                                            size_t ws_bytes, void* stream) {
+extern "C" sic_status sic_select_aggregated_gain(sic_handle* h, const double* pts, int64_t n,
+                                                 const sic_kernel* kp, const int64_t* grp_ptr, int64_t n_grp,
+                                                 const int64_t* cand_ptr, const int32_t* cand_idx, int32_t max_cand,
+                                                 int32_t max_m, int32_t k, sic_precision prec, int32_t* sel_idx,
+                                                 int32_t* sel_count, double* gain, void* ws, size_t ws_bytes,
+                                                 void* stream) {
     if (!h || !pts || !sic_valid_kernel(kp) || !grp_ptr || !cand_ptr || !sel_idx || !sel_count || n < 1 ||
         n_grp < 0 || max_cand < 0 || max_m < 1 || k < 1)
         return SIC_ERR_INVALID;
@@ -395,13 +401,22 @@ extern "C" sic_status sic_select_aggregated(sic_handle* h, const double* pts, in
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (agg_reg_applies(prec, max_cand, max_m, k))
-        return launch_agg_reg(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_m, k, sel_idx, sel_count, ws,
-                              ws_bytes, s);
+        return launch_agg_reg(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_m, k, sel_idx, sel_count, gain,
+                              ws, ws_bytes, s);
     if (prec == SIC_FP64)
         return launch_agg<double>(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, sel_idx,
-                                  sel_count, ws, ws_bytes, s);
+                                  sel_count, gain, ws, ws_bytes, s);
     if (prec == SIC_FP32_MIXED)
         return launch_agg<float>(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, sel_idx,
-                                 sel_count, ws, ws_bytes, s);
+                                 sel_count, gain, ws, ws_bytes, s);
     return SIC_ERR_INVALID;
+}
+
+extern "C" sic_status sic_select_aggregated(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                            const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr,
+                                            const int32_t* cand_idx, int32_t max_cand, int32_t max_m, int32_t k,
+                                            sic_precision prec, int32_t* sel_idx, int32_t* sel_count, void* ws,
+                                            size_t ws_bytes, void* stream) {
+    return sic_select_aggregated_gain(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, prec,
+                                      sel_idx, sel_count, nullptr, ws, ws_bytes, stream);
 }

@@ -17,6 +17,9 @@
 //   (eq. cond_select; the target's own row of the factor is never stored).
 // FP32 mode works in coordinates relative to the target (formed in FP64) so that
 // candidate-to-candidate differences keep their digits.
+// With `gain` non-null, thread 0 also carries the target's variance v_t in FP64
+// (v_{t+1} = v_t - u_t^2) and writes the pick's decrease of 2 KL, log(v_t / v_{t+1})
+// (Section 5.4.1: minus the log of one minus the squared conditional correlation).
 #include "sic_internal.cuh"
 
 namespace {
@@ -40,7 +43,8 @@ template <typename T, int KMAX, int ROWS>
 __global__ void __launch_bounds__(NT) k_select_columns(
     const double* __restrict__ pts, long long n, int dim, KP<T> kp, T floor_, const int32_t* __restrict__ targets,
     long long n_cols, const long long* __restrict__ cand_ptr, const int32_t* __restrict__ cand_idx,
-    int max_cand, int k, int32_t* __restrict__ sel_idx, int32_t* __restrict__ sel_count, DevStatus* st) {
+    int max_cand, int k, int32_t* __restrict__ sel_idx, int32_t* __restrict__ sel_count, double v0,
+    double* __restrict__ gain, DevStatus* st) {
     __shared__ Slot<T, KMAX> slot[2][NW];
     __shared__ T wscore[2][NW];
     __shared__ int widx[2][NW];
@@ -101,6 +105,7 @@ __global__ void __launch_bounds__(NT) k_select_columns(
                 cov[r] = matern<T>(kp, sic_sqrt(d2));
             }
         }
+        double vt = v0;  // target variance (thread 0, gains only)
         int t = 0;
         for (; t < k; ++t) {
             const int buf = t & 1;
@@ -201,7 +206,14 @@ __global__ void __launch_bounds__(NT) k_select_columns(
                 if (row == gi) live[r] = false;
                 }
             }
-            if (tid == 0) sel_idx[c * k + t] = cand_idx[b0 + gi];
+            if (tid == 0) {
+                sel_idx[c * k + t] = cand_idx[b0 + gi];
+                if (gain) {
+                    const double un = vt - (double)ut * (double)ut;
+                    gain[c * k + t] = log(vt / un);
+                    vt = un;
+                }
+            }
         }
         if (tid == 0) sel_count[c] = t;
         for (int q = t + tid; q < k; q += NT) sel_idx[c * k + q] = -1;
@@ -212,23 +224,24 @@ __global__ void __launch_bounds__(NT) k_select_columns(
 template <typename T, int KMAX, int ROWS>
 sic_status launch_cols(sic_handle* h, const double* pts, long long n, int dim, const sic_kernel* kp, const int32_t* targets,
                        long long n_cols, const int64_t* cand_ptr, const int32_t* cand_idx, int max_cand, int k,
-                       int32_t* sel_idx, int32_t* sel_count, cudaStream_t s) {
+                       int32_t* sel_idx, int32_t* sel_count, double* gain, cudaStream_t s) {
     auto kern = k_select_columns<T, KMAX, ROWS>;
     int grid = persistent_grid(h, kern, NT, 0, n_cols);
     KP<T> p = make_kp<T>(*kp);
     kern<<<grid, NT, 0, s>>>(pts, n, dim, p, (T)sic_floor_of(kp), targets, n_cols, (const long long*)cand_ptr,
-                             cand_idx, max_cand, k, sel_idx, sel_count, h->d_status);
+                             cand_idx, max_cand, k, sel_idx, sel_count, kp->variance + kp->nugget, gain,
+                             h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }
 
 }  // namespace
 
-extern "C" sic_status sic_select_columns(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
-                                         const int32_t* targets, int64_t n_cols, const int64_t* cand_ptr,
-                                         const int32_t* cand_idx, int32_t max_cand, int32_t k,
-                                         sic_precision prec, int32_t* sel_idx, int32_t* sel_count,
-                                         void* stream) {
+extern "C" sic_status sic_select_columns_gain(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                              const int32_t* targets, int64_t n_cols, const int64_t* cand_ptr,
+                                              const int32_t* cand_idx, int32_t max_cand, int32_t k,
+                                              sic_precision prec, int32_t* sel_idx, int32_t* sel_count,
+                                              double* gain, void* stream) {
     if (!h || !pts || !sic_valid_kernel(kp) || !cand_ptr || !sel_idx || !sel_count || n < 1 || n_cols < 0)
         return SIC_ERR_INVALID;
     if (k < 1 || max_cand < 0 || (n_cols > 0 && !cand_idx)) return SIC_ERR_INVALID;
@@ -240,23 +253,32 @@ extern "C" sic_status sic_select_columns(sic_handle* h, const double* pts, int64
     const int kb = (k <= 16) ? 16 : (k <= 32 ? 32 : 64);
     const int rows = (max_cand <= 256) ? 1 : (max_cand <= 512 ? 2 : 4);
     if (prec == SIC_FP64) {
-        if (kb == 16 && rows == 1) return launch_cols<double, 16, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 16 && rows == 2) return launch_cols<double, 16, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 16 && rows == 4) return launch_cols<double, 16, 4>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 32 && rows == 1) return launch_cols<double, 32, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 32 && rows == 2) return launch_cols<double, 32, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 64 && rows == 1) return launch_cols<double, 64, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
+        if (kb == 16 && rows == 1) return launch_cols<double, 16, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 16 && rows == 2) return launch_cols<double, 16, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 16 && rows == 4) return launch_cols<double, 16, 4>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 32 && rows == 1) return launch_cols<double, 32, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 32 && rows == 2) return launch_cols<double, 32, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 64 && rows == 1) return launch_cols<double, 64, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
         return SIC_ERR_UNSUPPORTED;
     } else if (prec == SIC_FP32_MIXED) {
-        if (kb == 16 && rows == 1) return launch_cols<float, 16, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 16 && rows == 2) return launch_cols<float, 16, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 16 && rows == 4) return launch_cols<float, 16, 4>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 32 && rows == 1) return launch_cols<float, 32, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 32 && rows == 2) return launch_cols<float, 32, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 32 && rows == 4) return launch_cols<float, 32, 4>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 64 && rows == 1) return launch_cols<float, 64, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
-        if (kb == 64 && rows == 2) return launch_cols<float, 64, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, s);
+        if (kb == 16 && rows == 1) return launch_cols<float, 16, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 16 && rows == 2) return launch_cols<float, 16, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 16 && rows == 4) return launch_cols<float, 16, 4>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 32 && rows == 1) return launch_cols<float, 32, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 32 && rows == 2) return launch_cols<float, 32, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 32 && rows == 4) return launch_cols<float, 32, 4>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 64 && rows == 1) return launch_cols<float, 64, 1>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
+        if (kb == 64 && rows == 2) return launch_cols<float, 64, 2>(h, pts, n, dim, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count, gain, s);
         return SIC_ERR_UNSUPPORTED;
     }
     return SIC_ERR_INVALID;
+}
+
+extern "C" sic_status sic_select_columns(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                         const int32_t* targets, int64_t n_cols, const int64_t* cand_ptr,
+                                         const int32_t* cand_idx, int32_t max_cand, int32_t k,
+                                         sic_precision prec, int32_t* sel_idx, int32_t* sel_count,
+                                         void* stream) {
+    return sic_select_columns_gain(h, pts, n, kp, targets, n_cols, cand_ptr, cand_idx, max_cand, k, prec, sel_idx,
+                                   sel_count, nullptr, stream);
 }

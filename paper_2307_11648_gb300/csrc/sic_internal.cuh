@@ -178,8 +178,8 @@ bool agg_reg_applies(sic_precision prec, int max_cand, int max_m, int k);
 size_t agg_reg_workspace(long long n_grp);
 sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
                           const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx,
-                          int max_m, int k, int32_t* sel_idx, int32_t* sel_count, void* ws, size_t ws_bytes,
-                          cudaStream_t s);
+                          int max_m, int k, int32_t* sel_idx, int32_t* sel_count, double* gain, void* ws,
+                          size_t ws_bytes, cudaStream_t s);
 
 // tcgen05 scoring kernel of the proposal network (mlp_tc.cu)
 sic_status sic_proposal_score_tc(sic_handle* h, const float* params, const float* feat, int64_t rows, float* score,

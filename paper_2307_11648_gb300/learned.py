@@ -85,15 +85,16 @@ def reduced_problem(hp: pipeline.HostProblem, top: int) -> pipeline.HostProblem:
 
 
 class LearnedFactorBuilder:
-    """proposal (features -> MLP -> top-k) -> exact greedy on the survivors -> FP64 fill."""
+    """proposal (features -> MLP -> top-k) -> exact greedy on the survivors -> FP64 fill
+    (with a nonzero budget: the global greedy allocation before the fill)."""
 
     def __init__(self, h: sic.Handle, hp: pipeline.HostProblem, proposal: Proposal, prec=sic.SIC_FP32_MIXED,
-                 device="cuda"):
+                 device="cuda", budget: int | None = None):
         import torch
         self.h, self.hp, self.proposal = h, hp, proposal
         self.buf = proposal.buffers(hp)
         self.rhp = reduced_problem(hp, proposal.top)
-        self.fb = pipeline.FactorBuilder(h, self.rhp, prec, device)
+        self.fb = pipeline.FactorBuilder(h, self.rhp, prec, device, budget=budget)
         self.rdp = None
 
     def _reduced_device(self, dp):

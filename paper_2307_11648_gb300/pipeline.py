@@ -6,7 +6,9 @@ scratch buffers and issues, on one stream, the sequence
 
     select (per column or per supernode) -> nnz scan -> FP64 fill + sum of log v
 
-every step of which is a libsic kernel.  Buffers are allocated once, so a build can
+every step of which is a libsic kernel.  With a nonzero budget (Section 5.4) the
+selection also reports each pick's KL decrease and the global greedy allocation keeps
+a prefix of every unit's picks before the fill.  Buffers are allocated once, so a build can
 be replayed (and captured in a CUDA graph) without allocation.
 """
 from __future__ import annotations
@@ -85,15 +87,27 @@ class DeviceProblem:
 
 
 class FactorBuilder:
-    """Preallocated outputs + scratch for building the factor of one problem."""
+    """Preallocated outputs + scratch for building the factor of one problem.
 
-    def __init__(self, h: sic.Handle, hp: HostProblem, prec: int, device="cuda", nnz_cap: int | None = None):
+    budget=None: every unit keeps its (up to) k greedy picks.  budget=B: at most B
+    off-diagonal nonzeros shared out by the global greedy allocation (a supernode's pick
+    costs one nonzero per member); `local_count` then holds the local greedy's counts and
+    `sel_count` the allocated ones, which the fill uses."""
+
+    def __init__(self, h: sic.Handle, hp: HostProblem, prec: int, device="cuda", nnz_cap: int | None = None,
+                 budget: int | None = None):
         import torch
-        self.h, self.hp, self.prec = h, hp, prec
+        self.h, self.hp, self.prec, self.budget = h, hp, prec, budget
         n, U, k = hp.n, hp.n_units, hp.k
         dev = device
         self.sel_idx = torch.empty(U * k, dtype=torch.int32, device=dev)
         self.sel_count = torch.empty(U, dtype=torch.int32, device=dev)
+        self.local_count = self.sel_count
+        self.gain = None
+        if budget is not None:
+            self.local_count = torch.empty(U, dtype=torch.int32, device=dev)
+            self.gain = torch.empty(U * k, dtype=torch.float64, device=dev)
+            self.ws_alloc = sic._ws(sic.allocate_global_workspace(U, k), dev)
         self.col_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
         # capacity: every column holds at most (its group's later members) + k + 1 entries
         if nnz_cap is None:
@@ -115,13 +129,25 @@ class FactorBuilder:
         self.ws_fill = sic._ws(sic.build_factor_workspace(n), dev)
 
     def select(self, dp: DeviceProblem, stream=None):
+        self.select_local(dp, stream)
+        if self.budget is not None:
+            self.allocate(dp, stream)
+
+    def select_local(self, dp: DeviceProblem, stream=None):
+        """Every unit's greedy picks (and, with a budget, their KL decreases)."""
         hp = self.hp
         if hp.grp_ptr is None:
             sic.select_columns(self.h, dp.pts, hp.kp, dp.cand_ptr, dp.cand_idx, hp.max_cand, hp.k, self.prec,
-                               self.sel_idx, self.sel_count, stream=stream)
+                               self.sel_idx, self.local_count, stream=stream, gain=self.gain)
         else:
             sic.select_aggregated(self.h, dp.pts, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, hp.max_cand, hp.max_m,
-                                  hp.k, self.prec, self.sel_idx, self.sel_count, self.ws_sel, stream=stream)
+                                  hp.k, self.prec, self.sel_idx, self.local_count, self.ws_sel, stream=stream,
+                                  gain=self.gain)
+
+    def allocate(self, dp: DeviceProblem, stream=None):
+        """Global greedy allocation of the budget over the units' picks (Section 5.4)."""
+        sic.allocate_global(self.h, self.gain, self.local_count, self.hp.k, self.budget, self.sel_count,
+                            self.ws_alloc, grp_ptr=dp.grp_ptr, stream=stream)
 
     def fill(self, dp: DeviceProblem, stream=None):
         hp = self.hp

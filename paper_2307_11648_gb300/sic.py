@@ -27,6 +27,7 @@ EXPORTS = [
     "sic_prep_candidates_targets", "sic_gp_predict",
     "sic_select_single_workspace", "sic_select_single", "sic_select_columns",
     "sic_select_aggregated_workspace", "sic_select_aggregated",
+    "sic_select_columns_gain", "sic_select_aggregated_gain", "sic_allocate_global_workspace", "sic_allocate_global",
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
@@ -86,6 +87,11 @@ def lib():
             "sic_select_aggregated_workspace": (st, [vp, i64, i32, i32, i32, st, C.POINTER(sz)]),
             "sic_select_aggregated": (st, [vp, vp, i64, pk, vp, i64, vp, vp, i32, i32, i32, st, vp, vp, vp, sz,
                                            vp]),
+            "sic_select_columns_gain": (st, [vp, vp, i64, pk, vp, i64, vp, vp, i32, i32, st, vp, vp, vp, vp]),
+            "sic_select_aggregated_gain": (st, [vp, vp, i64, pk, vp, i64, vp, vp, i32, i32, i32, st, vp, vp, vp,
+                                                vp, sz, vp]),
+            "sic_allocate_global_workspace": (st, [i64, i32, C.POINTER(sz)]),
+            "sic_allocate_global": (st, [vp, i64, vp, vp, vp, i32, i64, vp, vp, sz, vp]),
             "sic_factor_nnz_workspace": (st, [i64, C.POINTER(sz)]),
             "sic_factor_nnz": (st, [vp, vp, i64, vp, i64, vp, vp, sz, vp]),
             "sic_factor_nnz_noalloc": (st, [vp, vp, i64, vp, i64, vp, vp]),
@@ -275,16 +281,19 @@ def select_single(h: Handle, x_train, x_target, kp: Kernel, k: int, prec: int, o
 
 
 def select_columns(h: Handle, pts, kp: Kernel, cand_ptr, cand_idx, max_cand: int, k: int, prec: int, sel_idx,
-                   sel_count, targets=None, stream=None):
+                   sel_count, targets=None, stream=None, gain=None):
+    """sic_select_columns, or sic_select_columns_gain when `gain` (n_cols x k FP64) is given."""
     import torch
     n = pts.shape[0]
     n_cols = targets.numel() if targets is not None else n
-    _check(lib().sic_select_columns(h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp),
-                                    _dptr(targets, torch.int32, "targets"), n_cols,
-                                    _dptr(cand_ptr, torch.int64, "cand_ptr"), _dptr(cand_idx, torch.int32, "cand_idx"),
-                                    max_cand, k, prec, _dptr(sel_idx, torch.int32, "sel_idx"),
-                                    _dptr(sel_count, torch.int32, "sel_count"), _stream(stream)),
-           "sic_select_columns", h)
+    args = [h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp), _dptr(targets, torch.int32, "targets"), n_cols,
+            _dptr(cand_ptr, torch.int64, "cand_ptr"), _dptr(cand_idx, torch.int32, "cand_idx"), max_cand, k, prec,
+            _dptr(sel_idx, torch.int32, "sel_idx"), _dptr(sel_count, torch.int32, "sel_count")]
+    if gain is None:
+        _check(lib().sic_select_columns(*args, _stream(stream)), "sic_select_columns", h)
+    else:
+        _check(lib().sic_select_columns_gain(*args, _dptr(gain, torch.float64, "gain"), _stream(stream)),
+               "sic_select_columns_gain", h)
 
 
 def select_aggregated_workspace(h: Handle, n_grp: int, max_cand: int, max_m: int, k: int, prec: int) -> int:
@@ -295,17 +304,35 @@ def select_aggregated_workspace(h: Handle, n_grp: int, max_cand: int, max_m: int
 
 
 def select_aggregated(h: Handle, pts, kp: Kernel, grp_ptr, cand_ptr, cand_idx, max_cand: int, max_m: int, k: int,
-                      prec: int, sel_idx, sel_count, ws, stream=None):
+                      prec: int, sel_idx, sel_count, ws, stream=None, gain=None):
+    """sic_select_aggregated, or sic_select_aggregated_gain when `gain` (n_grp x k FP64) is given."""
     import torch
     n = pts.shape[0]
     n_grp = grp_ptr.numel() - 1
-    _check(lib().sic_select_aggregated(h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp),
-                                       _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp,
-                                       _dptr(cand_ptr, torch.int64, "cand_ptr"),
-                                       _dptr(cand_idx, torch.int32, "cand_idx"), max_cand, max_m, k, prec,
-                                       _dptr(sel_idx, torch.int32, "sel_idx"),
-                                       _dptr(sel_count, torch.int32, "sel_count"), _dptr(ws), ws.numel(),
-                                       _stream(stream)), "sic_select_aggregated", h)
+    args = [h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp), _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp,
+            _dptr(cand_ptr, torch.int64, "cand_ptr"), _dptr(cand_idx, torch.int32, "cand_idx"), max_cand, max_m, k,
+            prec, _dptr(sel_idx, torch.int32, "sel_idx"), _dptr(sel_count, torch.int32, "sel_count")]
+    if gain is None:
+        _check(lib().sic_select_aggregated(*args, _dptr(ws), ws.numel(), _stream(stream)), "sic_select_aggregated", h)
+    else:
+        _check(lib().sic_select_aggregated_gain(*args, _dptr(gain, torch.float64, "gain"), _dptr(ws), ws.numel(),
+                                                _stream(stream)), "sic_select_aggregated_gain", h)
+
+
+def allocate_global_workspace(n_units: int, k: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sic_allocate_global_workspace(n_units, k, C.byref(b)), "sic_allocate_global_workspace")
+    return b.value
+
+
+def allocate_global(h: Handle, gain, sel_count, k: int, budget: int, out_count, ws, grp_ptr=None, stream=None):
+    """Global greedy allocation of `budget` nonzeros (Section 5.4): out_count[u] leading picks of unit u."""
+    import torch
+    n_units = sel_count.numel()
+    _check(lib().sic_allocate_global(h.ptr, n_units, _dptr(grp_ptr, torch.int64, "grp_ptr"),
+                                     _dptr(gain, torch.float64, "gain"), _dptr(sel_count, torch.int32, "sel_count"),
+                                     k, int(budget), _dptr(out_count, torch.int32, "out_count"), _dptr(ws),
+                                     ws.numel(), _stream(stream)), "sic_allocate_global", h)
 
 
 # ------------------------------------------------------------- the factor --
