@@ -22,6 +22,7 @@ sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -53,6 +54,14 @@ LAUNCHES_PER_STEP = 15
 # (22,423 supernodes), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
 FILL_DRAM_BYTES_N2E19 = 17.650944e6 + 259.233280e6 + 9.646848e6 + 124.519680e6
 FILL_GROUPS_N2E19 = 22423
+
+
+def measured_peak(key: str, fallback: float) -> float:
+    """A peak from MEASURED_PEAKS.json (copy bandwidth, cuBLAS BF16), else the stated fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except Exception:
+        return fallback
 
 
 # ------------------------------------------------------------- clocks ---
@@ -438,8 +447,45 @@ def main():
     S["distance_fp32"] = float(fd.sum_logv.cpu()[0])
     del fd, ddp
     torch.cuda.empty_cache()
+    # ---- global greedy allocation of nonzeros (Section 5.4): the learned step with the
+    # nonzeros of 48 picks per supernode shared out by the global greedy (at most 64 per
+    # supernode), against 48 picks everywhere
+    kb = 3 * cfg["k"] // 4
+    sizes = np.diff(hp.grp_ptr)
+    budget = int(sizes.sum()) * kb
+    lbg = learned.LearnedFactorBuilder(h, hp, proposal, sic.SIC_FP32_MIXED, budget=budget)
+    grdp = lbg._reduced_device(dp)
+    gstep_ms, (gprop_ms, gsel_ms, galloc_ms, gfill_ms), _ = timed(
+        [lambda: lbg.propose(dp), lambda: lbg.fb.select_local(grdp), lambda: lbg.fb.allocate(grdp),
+         lambda: lbg.fb.fill(grdp)], args.steps, args.warmup)
+    S["learned_global_48"] = float(lbg.sum_logv.cpu()[0])
+    gcnt = lbg.fb.sel_count.cpu().numpy()
+    kept = int(np.dot(gcnt, sizes))
+    del lbg
+    lbe = learned.LearnedFactorBuilder(h, dataclasses.replace(hp, k=kb), proposal, sic.SIC_FP32_MIXED)
+    lbe.run(dp)
+    h.sync()
+    S["learned_even_48"] = float(lbe.sum_logv.cpu()[0])
+    del lbe
+    torch.cuda.empty_cache()
+    # algorithmic bytes of the allocation: every decrease read once, the counts read and
+    # written, the group offsets read
+    U = hp.n_units
+    alloc_bytes = U * cfg["k"] * 8.0 + U * (4.0 + 4.0 + 8.0)
+    hbm_peak = measured_peak("hbm_gbs", 6800.0)
+    global_alloc = {
+        "budget_nonzeros": budget, "kept_nonzeros": kept,
+        "picks_per_group_min_max": [int(gcnt.min()), int(gcnt.max())],
+        "ms_per_step": gstep_ms, "phases_ms": {"proposal": gprop_ms, "select_with_decreases": gsel_ms,
+                                               "allocate": galloc_ms, "fill_and_kl": gfill_ms},
+        "allocate_roofline": {"bound": "hbm", "achieved": alloc_bytes / (galloc_ms * 1e-3) / 1e9,
+                              "peak": hbm_peak, "unit": "GB/s",
+                              "frac": alloc_bytes / (galloc_ms * 1e-3) / 1e9 / hbm_peak,
+                              "algorithmic_bytes": alloc_bytes},
+    }
     base = S["plain_fp64"] - S["reference_2k"]
-    kl_gap = {k: (S[k] - S["plain_fp64"]) / base for k in ["learned_fp32", "plain_fp32", "distance_fp32"]}
+    kl_gap = {k: (S[k] - S["plain_fp64"]) / base for k in ["learned_fp32", "plain_fp32", "distance_fp32",
+                                                           "learned_global_48", "learned_even_48"]}
 
     # ---- end to end through the C-ABI with host buffers (pinned), copies in the region.
     # Every step copies its inputs host->device and its factor device->host.  Two device
@@ -509,10 +555,7 @@ def main():
     sel_tf = select_flops(rp.grp_ptr, rp.cand_ptr, hp.k) / (sel_ms * 1e-3) / 1e12
     rows = float(hp.cand_ptr[-1])
     mlp_tf = rows * 2.0 * (16 * 128 + 128 * 128 + 128) / (mlp_ms * 1e-3) / 1e12  # layer 1 padded to K = 16
-    try:
-        bf16_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
-    except Exception:
-        bf16_peak = 1900.0
+    bf16_peak = measured_peak("bf16_tflops", 1900.0)
     fill_tf = fill_flops(hp.grp_ptr, sel_count_learned) / (fill_ms * 1e-3) / 1e12
     kernels = {
         "k_select_agg<float> (256 candidates)": {"ms": sel_ms, "achieved_tflops": sel_tf, "peak_tflops": f32_peak,
@@ -589,6 +632,7 @@ def main():
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clocks,
             "pcg": pcg,
+            "global_allocation": global_alloc,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
