@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
     __shared__ __align__(16) unsigned pkey[2][RNT / 32];
     __shared__ int pidx[2][RNT / 32];
     __shared__ float pv1[2][RNT / 32], pv2[2][RNT / 32];
+    __shared__ float gv1[RK], gv2[RK];  // the picks' two conditional variances (gains only)
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float NEG = -INFINITY;
@@ -381,8 +382,10 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                 }
                 if (tid == 0) {
                     sel_idx[g * k + t] = cand_idx[b0 + q];
-                    // decrease of logdet Theta_{PP|I} per nonzero (Section 5.4.2)
-                    if (gain) gain[g * k + t] = log((double)pv1[buf][bw] / (double)pv2[buf][bw]) / m;
+                    if (gain) {
+                        gv1[t] = pv1[buf][bw];
+                        gv2[t] = pv2[buf][bw];
+                    }
                 }
             }
             // block TB is complete: move the own row's entries into registers
@@ -404,6 +407,11 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         if (steps(std::integral_constant<int, 0>{}) && steps(std::integral_constant<int, 1>{}) &&
             steps(std::integral_constant<int, 2>{}))
             steps(std::integral_constant<int, 3>{});
+        if (gain) {
+            // decreases of logdet Theta_{PP|I} per nonzero (Section 5.4.2), off the step chain
+            __syncthreads();
+            for (int q = tid; q < t; q += RNT) gain[g * k + q] = log((double)gv1[q] / (double)gv2[q]) / m;
+        }
         if (tid == 0) sel_count[g] = t;
         for (int q = t + tid; q < k; q += RNT) sel_idx[g * k + q] = -1;
         __syncthreads();

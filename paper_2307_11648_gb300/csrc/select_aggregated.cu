@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
     __shared__ T wsc[NW];
     __shared__ int wix[NW];
     __shared__ int s_fail;
+    __shared__ double gv1[128], gv2[128];  // the picks' two conditional variances (gains only)
 
     const long long Cm = L.Cm, mm = L.mm, ldx = L.Cm + L.mm;
     const long long P1 = L.p1(), P2 = L.p2(), P2t = L.p2t();
@@ -276,10 +277,17 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                 }
                 if (tid == 0) {
                     sel_idx[g * k + t] = cand_idx[b0 + q];
-                    // decrease of logdet Theta_{PP|I} per nonzero (Section 5.4.2)
-                    if (gain) gain[g * k + t] = log((double)v1q / (double)v2q) / m;
+                    if (gain) {
+                        gv1[t] = (double)v1q;
+                        gv2[t] = (double)v2q;
+                    }
                 }
             }
+        }
+        if (gain) {
+            // decreases of logdet Theta_{PP|I} per nonzero (Section 5.4.2), off the step chain
+            __syncthreads();
+            for (int q = tid; q < t; q += NT) gain[g * k + q] = log(gv1[q] / gv2[q]) / m;
         }
         if (tid == 0) sel_count[g] = t;
         for (int q = t + tid; q < k; q += NT) sel_idx[g * k + q] = -1;
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
 #undef E2
 #undef E2T
 
-constexpr size_t SMEM_LIMIT = 227 * 1024;
+constexpr size_t SMEM_LIMIT = 227 * 1024 - 4096;  // dynamic part; the static arrays take < 4 KB
 
 template <typename T>
 size_t agg_smem_bytes(const AggLayout& L, bool in_smem) {

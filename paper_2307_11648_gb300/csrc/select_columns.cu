@@ -18,8 +18,10 @@
 // FP32 mode works in coordinates relative to the target (formed in FP64) so that
 // candidate-to-candidate differences keep their digits.
 // With `gain` non-null, thread 0 also carries the target's variance v_t in FP64
-// (v_{t+1} = v_t - u_t^2) and writes the pick's decrease of 2 KL, log(v_t / v_{t+1})
-// (Section 5.4.1: minus the log of one minus the squared conditional correlation).
+// (v_{t+1} = v_t - u_t^2, kept at or above the exhaustion floor: the target's own nugget is
+// never explained) and, after the column's last step, the threads write the picks'
+// decreases of 2 KL, log(v_t / v_{t+1}) (Section 5.4.1: minus the log of one minus the
+// squared conditional correlation) -- the logarithms stay off the step chain.
 #include "sic_internal.cuh"
 
 namespace {
@@ -44,10 +46,11 @@ __global__ void __launch_bounds__(NT) k_select_columns(
     const double* __restrict__ pts, long long n, int dim, KP<T> kp, T floor_, const int32_t* __restrict__ targets,
     long long n_cols, const long long* __restrict__ cand_ptr, const int32_t* __restrict__ cand_idx,
     int max_cand, int k, int32_t* __restrict__ sel_idx, int32_t* __restrict__ sel_count, double v0,
-    double* __restrict__ gain, DevStatus* st) {
+    double vfloor, double* __restrict__ gain, DevStatus* st) {
     __shared__ Slot<T, KMAX> slot[2][NW];
     __shared__ T wscore[2][NW];
     __shared__ int widx[2][NW];
+    __shared__ double gv[KMAX + 1];  // target variance before each pick (gains only)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T NEG = -INFINITY;
@@ -209,11 +212,15 @@ __global__ void __launch_bounds__(NT) k_select_columns(
             if (tid == 0) {
                 sel_idx[c * k + t] = cand_idx[b0 + gi];
                 if (gain) {
-                    const double un = vt - (double)ut * (double)ut;
-                    gain[c * k + t] = log(vt / un);
-                    vt = un;
+                    gv[t] = vt;
+                    vt = fmax(vt - (double)ut * (double)ut, vfloor);
+                    gv[t + 1] = vt;
                 }
             }
+        }
+        if (gain) {
+            __syncthreads();
+            for (int q = tid; q < t; q += NT) gain[c * k + q] = log(gv[q] / gv[q + 1]);
         }
         if (tid == 0) sel_count[c] = t;
         for (int q = t + tid; q < k; q += NT) sel_idx[c * k + q] = -1;
@@ -229,8 +236,8 @@ sic_status launch_cols(sic_handle* h, const double* pts, long long n, int dim, c
     int grid = persistent_grid(h, kern, NT, 0, n_cols);
     KP<T> p = make_kp<T>(*kp);
     kern<<<grid, NT, 0, s>>>(pts, n, dim, p, (T)sic_floor_of(kp), targets, n_cols, (const long long*)cand_ptr,
-                             cand_idx, max_cand, k, sel_idx, sel_count, kp->variance + kp->nugget, gain,
-                             h->d_status);
+                             cand_idx, max_cand, k, sel_idx, sel_count, kp->variance + kp->nugget,
+                             sic_floor_of(kp), gain, h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }
