@@ -10,8 +10,8 @@ Two layers:
     single- and multiple-target greedy selections in the paper's Cholesky form,
     the KL-optimal fill by dense solves, and a CSC product;
   * numpy code in this file: the naive re-factorising greedy forms, exhaustive
-    subset search, dense log-determinants, the reverse-Cholesky aggregated fill and
-    the KL assembly.  numpy's Cholesky / slogdet serve as library primitives.
+    subset search, dense log-determinants, the picks' FP64 conditional variances,
+    the reverse-Cholesky aggregated fill and the KL assembly.  numpy's Cholesky / slogdet serve as library primitives.
 
 Parity pins for each function live in tests/test_oracle_pins.py.
 """
@@ -321,6 +321,24 @@ def select_multi_naive(kp: Kernel, pts, g0: int, m: int, cand, k: int, floor=Non
         S.append(best_j)
         vals.append(best_v)
     return np.array(S, np.int32), np.array(vals)
+
+
+def pivot_variances(kp: Kernel, pts, P, picks):
+    """FP64 side state of a selection: for the t-th pick q_t of a unit with targets P,
+    (var1[t], var2[t]) = (Theta_{q_t q_t | q_0..q_t-1}, Theta_{q_t q_t | q_0..q_t-1, P}),
+    the pivot's conditional variance without and with the targets, each by one dense
+    Schur complement (the plain definition of a conditional variance).  The pick's
+    decrease of logdet Theta_{PP|I} is log(var1 / var2) (eq. greedy_mult)."""
+    P = [int(x) for x in P]
+    picks = [int(x) for x in picks]
+    var1 = np.zeros(len(picks))
+    var2 = np.zeros(len(picks))
+    for t, q in enumerate(picks):
+        for out, cond in ((var1, picks[:t]), (var2, P + picks[:t])):
+            K = theta_matrix(kp, pts, cond + [q])
+            c = len(cond)
+            out[t] = K[c, c] - (K[:c, c] @ np.linalg.solve(K[:c, :c], K[:c, c]) if c else 0.0)
+    return var1, var2
 
 
 def brute_force_subset(kp: Kernel, pts, target: int, cand, k: int):

@@ -377,3 +377,51 @@ def test_pcg_oracle_textbook_properties():
     x2, it2, _ = pcg(A2, b[:20].repeat(2), Minv=M, tol=1e-12)
     assert np.allclose(x2, np.linalg.solve(A2, b[:20].repeat(2)), rtol=1e-9)
     assert it2 <= 40
+
+
+# ------------------------------------------------- FP64 side state (pivots) --
+
+def test_pivot_variances_match_cholesky_greedy(oracle_lib):
+    """The dense Schur complements agree with the Cholesky-form greedy's own quantities:
+    var1 / var2 of each pick is the multiple-target score of that pick (eq. greedy_mult),
+    and for one target the decrease log(var1 / var2) is log(v_t / v_t+1) of the target's
+    variance (the two sides of the determinant lemma)."""
+    oracle = oracle_lib
+    pts, _ = _ordered(oracle, 400, 2, 21)
+    kp = oracle.kernel(2, 3, 0.2, 1.0, 1e-6)
+    gptr, gidx = oracle.group_candidates(pts, np.array([0, 5, 9], np.int64), 40)
+    for g, (g0, m) in enumerate([(0, 5), (5, 4)]):
+        cand = gidx[gptr[g]:gptr[g + 1]]
+        r = oracle.select_multi(kp, pts, g0, m, cand, 12)
+        v1, v2 = oracle.pivot_variances(kp, pts, range(g0, g0 + m), r["sel"])
+        np.testing.assert_allclose(v1 / v2, r["chosen"], rtol=1e-9)
+    cptr, cidx = oracle.column_candidates(pts, 40)
+    for i in [0, 17, 150]:
+        cand = cidx[cptr[i]:cptr[i + 1]]
+        r = oracle.select_single(kp, pts, i, cand, 12)
+        v1, v2 = oracle.pivot_variances(kp, pts, [i], r["sel"])
+        np.testing.assert_allclose(np.log(v1 / v2), np.log(r["vtar"][:-1] / r["vtar"][1:]), rtol=1e-8)
+
+
+def test_pivot_variances_ou_closed_form(oracle_lib):
+    """Exponential kernel on a line (Ornstein-Uhlenbeck, Markov): a pick's variance given
+    earlier picks depends only on its nearest earlier picks on each side --
+    sigma^2 (1 - e^{-2d/ell}) beyond the outermost pick at distance d, and the bridge
+    variance sigma^2 (1 - e^{-2a/ell})(1 - e^{-2b/ell}) / (1 - e^{-2(a+b)/ell}) between
+    picks at distances a and b; the first pick has the full variance."""
+    oracle = oracle_lib
+    ell = 0.3
+    kp = oracle.kernel(1, 1, ell, 2.0, 0.0)
+    pts = np.array([[0.0], [0.55], [0.1], [0.9], [0.3]])
+    picks = [1, 2, 3, 4]
+    v1, v2 = oracle.pivot_variances(kp, pts, [0], picks)
+    e = lambda d: 1.0 - math.exp(-2.0 * d / ell)
+    bridge = lambda a, b: 2.0 * e(a) * e(b) / e(a + b)
+    assert v1[0] == pytest.approx(2.0, rel=1e-12)
+    assert v1[1] == pytest.approx(2.0 * e(0.45), rel=1e-10)      # 0.1 beyond 0.55
+    assert v1[2] == pytest.approx(2.0 * e(0.35), rel=1e-10)      # 0.9 beyond 0.55
+    assert v1[3] == pytest.approx(bridge(0.2, 0.25), rel=1e-10)  # 0.3 between 0.1 and 0.55
+    # with the target at 0 as well
+    assert v2[0] == pytest.approx(2.0 * e(0.55), rel=1e-10)
+    assert v2[1] == pytest.approx(bridge(0.1, 0.45), rel=1e-10)  # 0.1 between 0 and 0.55
+    assert v2[3] == pytest.approx(bridge(0.2, 0.25), rel=1e-10)
