@@ -208,6 +208,26 @@ sic_status sic_select_aggregated_gain(sic_handle* h, const double* pts, int64_t 
                                       sic_precision prec, int32_t* sel_idx, int32_t* sel_count, double* gain,
                                       void* ws, size_t ws_bytes, void* stream);
 
+/* FP64 side state of a selection (the FP32 path's FP64 pivot conditional variances):
+ * for the picks q_0, q_1, ... of every unit (sel_idx[u * k .. u * k + sel_count[u]), in
+ * pick order, as returned by the selection calls in either precision) it computes in FP64
+ *   pvar[u * k + t]   = Theta_{q_t q_t | q_0..q_t-1}        (conditioned on earlier picks),
+ *   pvar_p[u * k + t] = Theta_{q_t q_t | P, q_0..q_t-1}     (and on the unit's targets P),
+ *   gain[u * k + t]   = log(pvar / pvar_p) / m              (the pick's exact decrease of
+ *                                                          logdet Theta_{PP|I} per nonzero,
+ *                                                          eq. greedy_mult / eq. global_obj),
+ * from LDL^T factorisations of Theta_SS and of Theta over [P; S] (their pivots are these
+ * conditional variances; eq. cond_select).  Units: supernodes grp_ptr[u] .. grp_ptr[u+1]-1
+ * (1 <= m <= max_m <= 64), or with grp_ptr NULL single columns targeting targets[u] (u
+ * when NULL; max_m must be 1).  1 <= k <= 128.  Any of pvar, pvar_p, gain may be NULL (not
+ * all); entries from sel_count[u] on are untouched.  A pick outside [0, n) or a unit
+ * outside its bounds is reported by sic_sync as SIC_ERR_INVALID, a repeated pick (a
+ * singular Theta_SS) as SIC_ERR_NOT_PD; that unit's entries are then NaN.  [device] */
+sic_status sic_side_state_fp64(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                               const int64_t* grp_ptr, const int32_t* targets, int64_t n_units, int32_t max_m,
+                               const int32_t* sel_idx, const int32_t* sel_count, int32_t k, double* pvar,
+                               double* pvar_p, double* gain, void* stream);
+
 /* Global greedy allocation (Section 5.4) of `budget` off-diagonal nonzeros over n_units
  * units with the gains above.  A pick of unit u costs m_u nonzeros (m_u = grp_ptr[u+1] -
  * grp_ptr[u]; 1 for every unit when grp_ptr is NULL).  Picks are taken in the queue's

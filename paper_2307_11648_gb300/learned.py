@@ -89,12 +89,12 @@ class LearnedFactorBuilder:
     (with a nonzero budget: the global greedy allocation before the fill)."""
 
     def __init__(self, h: sic.Handle, hp: pipeline.HostProblem, proposal: Proposal, prec=sic.SIC_FP32_MIXED,
-                 device="cuda", budget: int | None = None):
+                 device="cuda", budget: int | None = None, side_fp64: bool = False):
         import torch
         self.h, self.hp, self.proposal = h, hp, proposal
         self.buf = proposal.buffers(hp)
         self.rhp = reduced_problem(hp, proposal.top)
-        self.fb = pipeline.FactorBuilder(h, self.rhp, prec, device, budget=budget)
+        self.fb = pipeline.FactorBuilder(h, self.rhp, prec, device, budget=budget, side_fp64=side_fp64)
         self.rdp = None
 
     def _reduced_device(self, dp):

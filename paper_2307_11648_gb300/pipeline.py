@@ -92,12 +92,14 @@ class FactorBuilder:
     budget=None: every unit keeps its (up to) k greedy picks.  budget=B: at most B
     off-diagonal nonzeros shared out by the global greedy allocation (a supernode's pick
     costs one nonzero per member); `local_count` then holds the local greedy's counts and
-    `sel_count` the allocated ones, which the fill uses."""
+    `sel_count` the allocated ones, which the fill uses.  side_fp64=True takes the picks'
+    decreases from the FP64 side state (exact in FP64 whatever the selection's precision)
+    instead of from the selection's own arithmetic."""
 
     def __init__(self, h: sic.Handle, hp: HostProblem, prec: int, device="cuda", nnz_cap: int | None = None,
-                 budget: int | None = None):
+                 budget: int | None = None, side_fp64: bool = False):
         import torch
-        self.h, self.hp, self.prec, self.budget = h, hp, prec, budget
+        self.h, self.hp, self.prec, self.budget, self.side_fp64 = h, hp, prec, budget, side_fp64
         n, U, k = hp.n, hp.n_units, hp.k
         dev = device
         self.sel_idx = torch.empty(U * k, dtype=torch.int32, device=dev)
@@ -137,12 +139,22 @@ class FactorBuilder:
         """Every unit's greedy picks (and, with a budget, their KL decreases)."""
         hp = self.hp
         if hp.grp_ptr is None:
+        own = None if self.side_fp64 else self.gain
+        if hp.grp_ptr is None:
             sic.select_columns(self.h, dp.pts, hp.kp, dp.cand_ptr, dp.cand_idx, hp.max_cand, hp.k, self.prec,
-                               self.sel_idx, self.local_count, stream=stream, gain=self.gain)
+                               self.sel_idx, self.local_count, stream=stream, gain=own)
         else:
             sic.select_aggregated(self.h, dp.pts, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, hp.max_cand, hp.max_m,
                                   hp.k, self.prec, self.sel_idx, self.local_count, self.ws_sel, stream=stream,
-                                  gain=self.gain)
+                                  gain=own)
+        if self.gain is not None and self.side_fp64:
+            self.side_state(dp, stream)
+
+    def side_state(self, dp: DeviceProblem, stream=None):
+        """The picks' exact FP64 decreases (sic_side_state_fp64) into `gain`."""
+        hp = self.hp
+        sic.side_state_fp64(self.h, dp.pts, hp.kp, self.sel_idx, self.local_count, hp.k, grp_ptr=dp.grp_ptr,
+                            max_m=hp.max_m, gain=self.gain, stream=stream)
 
     def allocate(self, dp: DeviceProblem, stream=None):
         """Global greedy allocation of the budget over the units' picks (Section 5.4)."""

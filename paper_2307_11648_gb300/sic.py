@@ -28,6 +28,7 @@ EXPORTS = [
     "sic_select_single_workspace", "sic_select_single", "sic_select_columns",
     "sic_select_aggregated_workspace", "sic_select_aggregated",
     "sic_select_columns_gain", "sic_select_aggregated_gain", "sic_allocate_global_workspace", "sic_allocate_global",
+    "sic_side_state_fp64",
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
@@ -91,6 +92,7 @@ def lib():
             "sic_select_aggregated_gain": (st, [vp, vp, i64, pk, vp, i64, vp, vp, i32, i32, i32, st, vp, vp, vp,
                                                 vp, sz, vp]),
             "sic_allocate_global_workspace": (st, [i64, i32, C.POINTER(sz)]),
+            "sic_side_state_fp64": (st, [vp, vp, i64, pk, vp, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp]),
             "sic_allocate_global": (st, [vp, i64, vp, vp, vp, i32, i64, vp, vp, sz, vp]),
             "sic_factor_nnz_workspace": (st, [i64, C.POINTER(sz)]),
             "sic_factor_nnz": (st, [vp, vp, i64, vp, i64, vp, vp, sz, vp]),
@@ -317,6 +319,21 @@ def select_aggregated(h: Handle, pts, kp: Kernel, grp_ptr, cand_ptr, cand_idx, m
     else:
         _check(lib().sic_select_aggregated_gain(*args, _dptr(gain, torch.float64, "gain"), _dptr(ws), ws.numel(),
                                                 _stream(stream)), "sic_select_aggregated_gain", h)
+
+
+def side_state_fp64(h: Handle, pts, kp: Kernel, sel_idx, sel_count, k: int, grp_ptr=None, max_m: int = 1,
+                    targets=None, pvar=None, pvar_p=None, gain=None, stream=None):
+    """FP64 conditional variances of the picks without / with the unit's targets and their
+    exact decreases per nonzero (sic_side_state_fp64); outputs are n_units x k FP64."""
+    import torch
+    n = pts.shape[0]
+    n_units = sel_count.numel()
+    _check(lib().sic_side_state_fp64(h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp),
+                                     _dptr(grp_ptr, torch.int64, "grp_ptr"), _dptr(targets, torch.int32, "targets"),
+                                     n_units, max_m, _dptr(sel_idx, torch.int32, "sel_idx"),
+                                     _dptr(sel_count, torch.int32, "sel_count"), k,
+                                     _dptr(pvar, torch.float64, "pvar"), _dptr(pvar_p, torch.float64, "pvar_p"),
+                                     _dptr(gain, torch.float64, "gain"), _stream(stream)), "sic_side_state_fp64", h)
 
 
 def allocate_global_workspace(n_units: int, k: int) -> int:
