@@ -13,8 +13,11 @@ Tolerances:
     the running-minimum keys of the picks in question lie within 1e-9 relative of the
     queue's cut key (a near-tie at the cut that FP64 rounding may decide either way);
   * FP32 selections: the allocation is valid (within budget, a prefix of every unit's
-    picks, no dropped pick ranked above a kept one) and the factor's sum of log v is within
-    1e-5 relative of the FP64 path's (FP32 and FP64 selections differ by ~1e-6 of it).
+    picks, no dropped pick ranked above a kept one).  With the decreases taken from the
+    FP64 side state, the factor's sum of log v is within 1e-5 relative of the FP64 path's
+    (FP32 and FP64 selections differ by ~1e-6 of it); with the FP32 selection's own
+    decreases only within 1e-3 (on a clustered cloud the FP32 conditional variances near the
+    nugget carry errors of several percent, which misrank picks at the cut).
 """
 import dataclasses
 import math
@@ -286,8 +289,9 @@ def test_groups_global_fp32_valid_and_close_to_fp64(env, clustered):
     B = int(32 * sizes.sum())
     dp = pipeline.DeviceProblem(hp)
     res = {}
-    for name, prec in [("fp32", sic.SIC_FP32_MIXED), ("fp64", sic.SIC_FP64)]:
-        fb = pipeline.FactorBuilder(h, hp, prec, budget=B)
+    for name, prec, side in [("fp32", sic.SIC_FP32_MIXED, False), ("fp32_side", sic.SIC_FP32_MIXED, True),
+                             ("fp64", sic.SIC_FP64, False)]:
+        fb = pipeline.FactorBuilder(h, hp, prec, budget=B, side_fp64=side)
         fb.run(dp)
         h.sync()
         gain = fb.gain.view(-1, hp.k).cpu().numpy()
@@ -298,9 +302,11 @@ def test_groups_global_fp32_valid_and_close_to_fp64(env, clustered):
     even.run(dp)
     h.sync()
     s_even = float(even.sum_logv.cpu()[0])
-    print(f"clustered={clustered}: sum log v global fp32 {res['fp32']:.3f} fp64 {res['fp64']:.3f} even(32) {s_even:.3f}")
-    assert res["fp32"] == pytest.approx(res["fp64"], rel=1e-5)
-    assert res["fp32"] < s_even
+    print(f"clustered={clustered}: sum log v global fp32 {res['fp32']:.3f} fp32 + FP64 side state "
+          f"{res['fp32_side']:.3f} fp64 {res['fp64']:.3f} even(32) {s_even:.3f}")
+    assert res["fp32_side"] == pytest.approx(res["fp64"], rel=1e-5)
+    assert res["fp32"] == pytest.approx(res["fp64"], rel=1e-3)
+    assert max(res.values()) < s_even
 
 
 @pytest.mark.parametrize("clustered", [False, True])
