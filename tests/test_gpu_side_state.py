@@ -144,8 +144,8 @@ def test_side_state_errors_reported(env):
     torch, sic, pipeline, h = env
     kp = sic.kernel(2, 3, 0.1, 1.0, 1e-8)
     pts = synthetic.points(300, 2, 3)
-    with pytest.raises(sic.SicError):  # a repeated pick: Theta_SS is singular
-        _run_side(env, pts, kp, [np.array([5, 9, 5], np.int32)], [3], 4)
+    with pytest.raises(sic.SicError):  # a repeated pick without nugget: Theta_SS is singular
+        _run_side(env, pts, sic.kernel(2, 3, 0.1, 1.0, 0.0), [np.array([5, 5], np.int32)], [2], 4)
     with pytest.raises(sic.SicError):  # a pick outside the points
         _run_side(env, pts, kp, [np.array([5, 300], np.int32)], [2], 4)
     with pytest.raises(sic.SicError):  # a count above k
