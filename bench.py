@@ -462,6 +462,13 @@ def main():
     gcnt = lbg.fb.sel_count.cpu().numpy()
     kept = int(np.dot(gcnt, sizes))
     del lbg
+    # the same with the decreases from the FP64 side state of the FP32 picks
+    lbs = learned.LearnedFactorBuilder(h, hp, proposal, sic.SIC_FP32_MIXED, budget=budget, side_fp64=True)
+    srdp = lbs._reduced_device(dp)
+    sstep_ms, _, _ = timed([lambda: lbs.run(dp)], args.steps, args.warmup)
+    side_ms, _, _ = timed([lambda: lbs.fb.side_state(srdp)], args.steps, 1)
+    S["learned_global_48_side_fp64"] = float(lbs.sum_logv.cpu()[0])
+    del lbs
     lbe = learned.LearnedFactorBuilder(h, dataclasses.replace(hp, k=kb), proposal, sic.SIC_FP32_MIXED)
     lbe.run(dp)
     h.sync()
@@ -478,6 +485,7 @@ def main():
         "picks_per_group_min_max": [int(gcnt.min()), int(gcnt.max())],
         "ms_per_step": gstep_ms, "phases_ms": {"proposal": gprop_ms, "select_with_decreases": gsel_ms,
                                                "allocate": galloc_ms, "fill_and_kl": gfill_ms},
+        "with_side_state_fp64": {"ms_per_step": sstep_ms, "side_state_ms": side_ms},
         "allocate_roofline": {"bound": "hbm", "achieved": alloc_bytes / (galloc_ms * 1e-3) / 1e9,
                               "peak": hbm_peak, "unit": "GB/s",
                               "frac": alloc_bytes / (galloc_ms * 1e-3) / 1e9 / hbm_peak,
@@ -485,7 +493,8 @@ def main():
     }
     base = S["plain_fp64"] - S["reference_2k"]
     kl_gap = {k: (S[k] - S["plain_fp64"]) / base for k in ["learned_fp32", "plain_fp32", "distance_fp32",
-                                                           "learned_global_48", "learned_even_48"]}
+                                                           "learned_global_48", "learned_global_48_side_fp64",
+                                                           "learned_even_48"]}
 
     # ---- end to end through the C-ABI with host buffers (pinned), copies in the region.
     # Every step copies its inputs host->device and its factor device->host.  Two device
