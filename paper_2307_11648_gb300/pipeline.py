@@ -138,7 +138,6 @@ class FactorBuilder:
     def select_local(self, dp: DeviceProblem, stream=None):
         """Every unit's greedy picks (and, with a budget, their KL decreases)."""
         hp = self.hp
-        if hp.grp_ptr is None:
         own = None if self.side_fp64 else self.gain
         if hp.grp_ptr is None:
             sic.select_columns(self.h, dp.pts, hp.kp, dp.cand_ptr, dp.cand_idx, hp.max_cand, hp.k, self.prec,

@@ -88,3 +88,16 @@ def test_prep_grid_points_and_ties(sic, oracle_lib):
     p1, i1 = sic.prep_candidates_columns(P, 30)
     p2, i2 = oracle.column_candidates(P, 30)
     assert np.array_equal(i1, i2)
+
+
+def test_package_modules_import():
+    """Every module of the package and bench.py parse and import on a host without a GPU
+    (the library itself is only loaded on first use)."""
+    import ast
+    import importlib
+    import os
+    for mod in ["sic", "pipeline", "learned", "gp", "build"]:
+        importlib.import_module(f"paper_2307_11648_gb300.{mod}")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for f in ["bench.py", "__graft_entry__.py"]:
+        ast.parse(open(os.path.join(root, f)).read())
