@@ -128,6 +128,17 @@ sic_status sic_prep_candidates_groups(const double* pts, int64_t n, int32_t dim,
                                       int64_t n_grp, int32_t n_cand, int64_t* cand_ptr, int32_t* cand_idx,
                                       int32_t n_threads);
 
+/* Candidate lists of nonadjacent groups for partial selection (Section 5.1.1): group g's
+ * members are the positions members[grp_ptr[g] .. grp_ptr[g+1]) (ascending, any spacing:
+ * e.g. the `members` output of sic_prep_groups, in the original elimination order); its
+ * candidates are the n_cand points after its first member, other than its members, whose
+ * least squared distance to a member is smallest, sorted by (that distance, position) --
+ * so some lie between members and condition only the members before them.  cand_idx must
+ * hold n_grp * n_cand entries.  [host] */
+sic_status sic_prep_candidates_partial(const double* pts, int64_t n, int32_t dim, const int64_t* members,
+                                       const int64_t* grp_ptr, int64_t n_grp, int32_t n_cand, int64_t* cand_ptr,
+                                       int32_t* cand_idx, int32_t n_threads);
+
 /* Candidates for directed GP regression (Section 3): pts holds the n_targets target
  * points first, then the training points.  For each target i < n_targets, the n_cand
  * training positions (>= n_targets) nearest to it, sorted by (distance, position), go
@@ -177,6 +188,35 @@ sic_status sic_select_aggregated(sic_handle* h, const double* pts, int64_t n, co
                                  const int32_t* cand_idx, int32_t max_cand, int32_t max_m, int32_t k,
                                  sic_precision prec, int32_t* sel_idx, int32_t* sel_count, void* ws,
                                  size_t ws_bytes, void* stream);
+
+/* Partial selection for nonadjacent groups (Section 5.2 "Partial selection", Appendix
+ * C.3): group g's targets are members[grp_ptr[g] .. grp_ptr[g+1]) (ascending positions,
+ * 1 <= m <= max_m <= 64), its candidates cand_idx[cand_ptr[g] .. cand_ptr[g+1]) (count <=
+ * max_cand, each after the group's first member); a candidate conditions only the
+ * members before it.  Greedy on sum_i log Theta_{ii | s_i \ i} over the members (eq.
+ * partial_kl), s_i = later members and picks after i, with the Cholesky factor of the
+ * targets and picks (columns latest first) updated by insertion and in-place rank-one
+ * downdate.  Ties: the earliest candidate; a candidate is exhausted when its variance
+ * given every member and pick is below sic_exhaustion_floor.  sel_idx[n_grp * k],
+ * sel_count[n_grp] as in sic_select_aggregated; gain (n_grp * k FP64, may be NULL) the
+ * pick's decrease of the objective per nonzero (per member it conditions; Section 5.4.2).
+ * The factor lives in shared memory: (max_cand + max_m) * (max_m + k + 1) values plus
+ * small arrays must fit in ~223 KB (SIC_ERR_UNSUPPORTED otherwise), e.g. FP32 with
+ * 256 candidates and FP64 with 128, at max_m = k = 64.  1 <= k <= 128.  [device] */
+sic_status sic_select_partial(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                              const int64_t* grp_ptr, const int64_t* members, int64_t n_grp, const int64_t* cand_ptr,
+                              const int32_t* cand_idx, int32_t max_cand, int32_t max_m, int32_t k,
+                              sic_precision prec, int32_t* sel_idx, int32_t* sel_count, double* gain, void* stream);
+
+/* The pattern of a partial selection as single-column lists for the fill: member i of
+ * group g gets col_sel[i * kc ..] = the later members of g, then g's picks after i, and
+ * col_count[i] their number (kc >= max_m - 1 + k; a longer list is cut and reported as
+ * SIC_ERR_INVALID).  The factor then follows from sic_factor_nnz / sic_build_factor with
+ * grp_ptr NULL, max_m 1 and k = kc (each column's KL-optimal values, eq. L_col).  Columns
+ * of positions in no group are not written.  [device] */
+sic_status sic_partial_columns(sic_handle* h, int64_t n, const int64_t* grp_ptr, const int64_t* members,
+                               int64_t n_grp, const int32_t* sel_idx, const int32_t* sel_count, int32_t k,
+                               int32_t kc, int32_t* col_sel, int32_t* col_count, void* stream);
 
 /* ------------------------------------- global allocation of nonzeros [device] -- */
 /*

@@ -412,3 +412,44 @@ extern "C" sic_status sic_prep_candidates_groups(const double* pts, int64_t n, i
     }
     return SIC_OK;
 }
+
+extern "C" sic_status sic_prep_candidates_partial(const double* pts, int64_t n, int32_t dim, const int64_t* members,
+                                                  const int64_t* grp_ptr, int64_t n_grp, int32_t n_cand,
+                                                  int64_t* cand_ptr, int32_t* cand_idx, int32_t n_threads) {
+    if (!pts || !members || !grp_ptr || !cand_ptr || !cand_idx || n < 1 || dim < 1 || dim > 3 || n_grp < 1 ||
+        n_cand < 0)
+        return SIC_ERR_INVALID;
+    for (int64_t g = 0; g < n_grp; ++g) {
+        if (grp_ptr[g + 1] <= grp_ptr[g]) return SIC_ERR_INVALID;
+        for (int64_t a = grp_ptr[g]; a < grp_ptr[g + 1]; ++a)
+            if (members[a] < 0 || members[a] >= n || (a > grp_ptr[g] && members[a] <= members[a - 1]))
+                return SIC_ERR_INVALID;  // positions in range, ascending within a group
+    }
+    SuffixGrids sg;
+    sg.build(pts, n, dim, std::max<int64_t>(256, 4LL * n_cand), n_threads);
+    std::vector<int32_t> cnt(n_grp, 0);
+    parallel_for(n_grp, n_threads, 16, [&](int64_t g) {
+        thread_local std::vector<KeyPos> buf;
+        thread_local std::vector<int32_t> nb;
+        const int64_t a = grp_ptr[g], b = grp_ptr[g + 1];
+        const int m = (int)(b - a);
+        nb.resize((size_t)n_cand + m);
+        // nearest (to any member) points after the first member; the other members among
+        // them are dropped (they enter every earlier member's column by themselves)
+        int32_t got = knn_query(pts, n, dim, sg, members + a, m, members[a] + 1, n_cand + m - 1, nb.data(), buf);
+        int32_t w = 0;
+        int32_t* out = cand_idx + g * (int64_t)n_cand;
+        for (int32_t q = 0; q < got && w < n_cand; ++q) {
+            if (std::binary_search(members + a, members + b, (int64_t)nb[q])) continue;
+            out[w++] = nb[q];
+        }
+        cnt[g] = w;
+    });
+    cand_ptr[0] = 0;
+    for (int64_t g = 0; g < n_grp; ++g) {
+        int64_t src = g * (int64_t)n_cand, dst = cand_ptr[g];
+        if (dst != src) std::copy(cand_idx + src, cand_idx + src + cnt[g], cand_idx + dst);
+        cand_ptr[g + 1] = dst + cnt[g];
+    }
+    return SIC_OK;
+}

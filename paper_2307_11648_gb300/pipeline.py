@@ -30,6 +30,7 @@ class HostProblem:
     grp_ptr: np.ndarray | None = None  # int64, groups + 1 (None: single columns)
     order: np.ndarray | None = None    # old point index per position (for reference)
     ell2: np.ndarray | None = None
+    members: np.ndarray | None = None  # nonadjacent groups: member positions (grp_ptr indexes it)
 
     @property
     def n(self):
@@ -46,6 +47,11 @@ class HostProblem:
     @property
     def max_m(self):
         return 1 if self.grp_ptr is None else int(np.max(np.diff(self.grp_ptr)))
+
+    @property
+    def kc(self):
+        """Longest single-column list of a nonadjacent-group pattern: later members + picks."""
+        return self.max_m - 1 + self.k
 
     def h2d_bytes(self):
         b = self.pts.nbytes + self.cand_ptr.nbytes + self.cand_idx.nbytes
@@ -74,6 +80,18 @@ def prepare_groups(points: np.ndarray, kp: sic.Kernel, n_cand: int, k: int, mmin
     return HostProblem(P2, kp, k, ptr, idx, gp, order[members], ell2[members])
 
 
+def prepare_partial(points: np.ndarray, kp: sic.Kernel, n_cand: int, k: int, mmin: int = 8, mmax: int = 64,
+                    lam: float = 1.5, n_threads: int = 0) -> HostProblem:
+    """Reverse-maximin order and the Section 6.1 groups kept where they fall in the ordering
+    (nonadjacent, no renumbering), with candidates after each group's first member
+    (Section 5.1.1): the input of partial selection."""
+    order, ell2 = sic.prep_maximin(points, n_threads)
+    P = np.ascontiguousarray(points[order])
+    members, gp = sic.prep_groups(P, ell2, 2 * k, lam, mmin, mmax, n_threads)
+    ptr, idx = sic.prep_candidates_partial(P, members, gp, n_cand, n_threads)
+    return HostProblem(P, kp, k, ptr, idx, gp, order, ell2, members)
+
+
 class DeviceProblem:
     def __init__(self, hp: HostProblem, device="cuda"):
         import torch
@@ -84,6 +102,7 @@ class DeviceProblem:
         idx = hp.cand_idx if hp.cand_idx.size else np.zeros(1, np.int32)  # never a NULL pointer
         self.cand_idx = torch.from_numpy(idx).to(device)
         self.grp_ptr = torch.from_numpy(hp.grp_ptr).to(device) if hp.grp_ptr is not None else None
+        self.members = torch.from_numpy(hp.members).to(device) if hp.members is not None else None
 
 
 class FactorBuilder:
@@ -179,3 +198,51 @@ class FactorBuilder:
         cp = self.col_ptr.cpu().numpy()
         nnz = int(cp[-1])
         return cp, self.row_idx[:nnz].cpu().numpy(), self.val[:nnz].cpu().numpy(), self.logv.cpu().numpy()
+
+
+class PartialFactorBuilder:
+    """Nonadjacent groups: partial selection (Section 5.2, Appendix C.3), the pattern expanded
+    to single-column lists, and the FP64 fill of each column (eq. L_col)."""
+
+    def __init__(self, h: sic.Handle, hp: HostProblem, prec: int, device="cuda"):
+        import torch
+        assert hp.members is not None and hp.grp_ptr is not None
+        self.h, self.hp, self.prec = h, hp, prec
+        n, G, k, kc = hp.n, hp.n_units, hp.k, hp.kc
+        dev = device
+        self.sel_idx = torch.empty(G * k, dtype=torch.int32, device=dev)
+        self.sel_count = torch.empty(G, dtype=torch.int32, device=dev)
+        self.gain = torch.empty(G * k, dtype=torch.float64, device=dev)
+        self.col_sel = torch.empty(n * kc, dtype=torch.int32, device=dev)
+        self.col_count = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.col_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        m = np.diff(hp.grp_ptr)
+        self.nnz_cap = int(np.sum(m * (m + 1) // 2 + m * k))
+        self.row_idx = torch.empty(self.nnz_cap, dtype=torch.int32, device=dev)
+        self.val = torch.empty(self.nnz_cap, dtype=torch.float64, device=dev)
+        self.logv = torch.empty(n, dtype=torch.float64, device=dev)
+        self.sum_logv = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.ws_nnz = sic._ws(sic.factor_nnz_workspace(n), dev)
+        self.ws_fill = sic._ws(sic.build_factor_workspace(n), dev)
+
+    def select(self, dp: DeviceProblem, stream=None):
+        hp = self.hp
+        sic.select_partial(self.h, dp.pts, hp.kp, dp.grp_ptr, dp.members, dp.cand_ptr, dp.cand_idx, hp.max_cand,
+                           hp.max_m, hp.k, self.prec, self.sel_idx, self.sel_count, gain=self.gain, stream=stream)
+
+    def fill(self, dp: DeviceProblem, stream=None):
+        hp = self.hp
+        sic.partial_columns(self.h, hp.n, dp.grp_ptr, dp.members, self.sel_idx, self.sel_count, hp.k, hp.kc,
+                            self.col_sel, self.col_count, stream=stream)
+        sic.factor_nnz(self.h, None, self.col_count, hp.n, self.col_ptr, self.ws_nnz, stream=stream)
+        sic.build_factor(self.h, dp.pts, hp.kp, None, 1, self.col_sel, self.col_count, hp.kc, self.col_ptr,
+                         self.row_idx, self.val, self.logv, self.sum_logv, self.ws_fill, stream=stream)
+
+    def run(self, dp: DeviceProblem, stream=None):
+        self.select(dp, stream)
+        self.fill(dp, stream)
+
+    def sel_lists(self):
+        si = self.sel_idx.view(-1, self.hp.k).cpu().numpy()
+        sc = self.sel_count.cpu().numpy()
+        return [si[u, :sc[u]].copy() for u in range(len(sc))]

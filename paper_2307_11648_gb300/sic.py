@@ -28,7 +28,7 @@ EXPORTS = [
     "sic_select_single_workspace", "sic_select_single", "sic_select_columns",
     "sic_select_aggregated_workspace", "sic_select_aggregated",
     "sic_select_columns_gain", "sic_select_aggregated_gain", "sic_allocate_global_workspace", "sic_allocate_global",
-    "sic_side_state_fp64",
+    "sic_side_state_fp64", "sic_prep_candidates_partial", "sic_select_partial", "sic_partial_columns",
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
@@ -93,6 +93,9 @@ def lib():
                                                 vp, sz, vp]),
             "sic_allocate_global_workspace": (st, [i64, i32, C.POINTER(sz)]),
             "sic_side_state_fp64": (st, [vp, vp, i64, pk, vp, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp]),
+            "sic_prep_candidates_partial": (st, [vp, i64, i32, vp, vp, i64, i32, vp, vp, i32]),
+            "sic_select_partial": (st, [vp, vp, i64, pk, vp, vp, i64, vp, vp, i32, i32, i32, st, vp, vp, vp, vp]),
+            "sic_partial_columns": (st, [vp, i64, vp, vp, i64, vp, vp, i32, i32, vp, vp, vp]),
             "sic_allocate_global": (st, [vp, i64, vp, vp, vp, i32, i64, vp, vp, sz, vp]),
             "sic_factor_nnz_workspace": (st, [i64, C.POINTER(sz)]),
             "sic_factor_nnz": (st, [vp, vp, i64, vp, i64, vp, vp, sz, vp]),
@@ -319,6 +322,46 @@ def select_aggregated(h: Handle, pts, kp: Kernel, grp_ptr, cand_ptr, cand_idx, m
     else:
         _check(lib().sic_select_aggregated_gain(*args, _dptr(gain, torch.float64, "gain"), _dptr(ws), ws.numel(),
                                                 _stream(stream)), "sic_select_aggregated_gain", h)
+
+
+def prep_candidates_partial(pts: np.ndarray, members: np.ndarray, grp_ptr: np.ndarray, n_cand: int,
+                            n_threads: int = 0):
+    """Host: candidates of nonadjacent groups (sic_prep_candidates_partial) -> (cand_ptr, cand_idx)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    members = np.ascontiguousarray(members, dtype=np.int64)
+    grp_ptr = np.ascontiguousarray(grp_ptr, dtype=np.int64)
+    n_grp = len(grp_ptr) - 1
+    ptr = np.zeros(n_grp + 1, np.int64)
+    idx = np.zeros(max(n_grp * n_cand, 1), np.int32)
+    _check(lib().sic_prep_candidates_partial(_hptr(pts, np.float64), pts.shape[0], pts.shape[1],
+                                             _hptr(members, np.int64), _hptr(grp_ptr, np.int64), n_grp, n_cand,
+                                             _hptr(ptr, np.int64), _hptr(idx, np.int32), n_threads),
+           "sic_prep_candidates_partial")
+    return ptr, idx[:ptr[-1]].copy()
+
+
+def select_partial(h: Handle, pts, kp: Kernel, grp_ptr, members, cand_ptr, cand_idx, max_cand: int, max_m: int,
+                   k: int, prec: int, sel_idx, sel_count, gain=None, stream=None):
+    """Partial selection for nonadjacent groups (sic_select_partial)."""
+    import torch
+    _check(lib().sic_select_partial(h.ptr, _dptr(pts, torch.float64, "pts"), pts.shape[0], C.byref(kp),
+                                    _dptr(grp_ptr, torch.int64, "grp_ptr"), _dptr(members, torch.int64, "members"),
+                                    grp_ptr.numel() - 1, _dptr(cand_ptr, torch.int64, "cand_ptr"),
+                                    _dptr(cand_idx, torch.int32, "cand_idx"), max_cand, max_m, k, prec,
+                                    _dptr(sel_idx, torch.int32, "sel_idx"), _dptr(sel_count, torch.int32, "sel_count"),
+                                    _dptr(gain, torch.float64, "gain"), _stream(stream)), "sic_select_partial", h)
+
+
+def partial_columns(h: Handle, n: int, grp_ptr, members, sel_idx, sel_count, k: int, kc: int, col_sel, col_count,
+                    stream=None):
+    """Single-column lists of a partial selection for the fill (sic_partial_columns)."""
+    import torch
+    _check(lib().sic_partial_columns(h.ptr, n, _dptr(grp_ptr, torch.int64, "grp_ptr"),
+                                     _dptr(members, torch.int64, "members"), grp_ptr.numel() - 1,
+                                     _dptr(sel_idx, torch.int32, "sel_idx"), _dptr(sel_count, torch.int32, "sel_count"),
+                                     k, kc, _dptr(col_sel, torch.int32, "col_sel"),
+                                     _dptr(col_count, torch.int32, "col_count"), _stream(stream)),
+           "sic_partial_columns", h)
 
 
 def side_state_fp64(h: Handle, pts, kp: Kernel, sel_idx, sel_count, k: int, grp_ptr=None, max_m: int = 1,

@@ -101,3 +101,25 @@ def test_package_modules_import():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     for f in ["bench.py", "__graft_entry__.py"]:
         ast.parse(open(os.path.join(root, f)).read())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_prep_candidates_partial_brute_force(sic, oracle_lib, seed):
+    """Candidates of nonadjacent groups: the n_cand points after the first member, members
+    excluded, by (least squared distance to a member, position) -- checked by brute force on
+    the groups of the Section 6.1 rule kept in the original ordering."""
+    oracle = oracle_lib
+    pts = synthetic.points(1500, 2, 40 + seed)
+    order, ell2 = sic.prep_maximin(pts)
+    P = np.ascontiguousarray(pts[order])
+    members, gp = sic.prep_groups(P, ell2, 32, 1.5, 4, 32)
+    ptr, idx = sic.prep_candidates_partial(P, members, gp, 40)
+    nonadjacent = 0
+    for g in range(len(gp) - 1):
+        mem = members[gp[g]:gp[g + 1]]
+        nonadjacent += int(mem[-1] - mem[0] + 1 != len(mem))
+        d = ((P[:, None, :] - P[None, mem, :]) ** 2).sum(-1).min(1)
+        ok = [j for j in range(len(P)) if j > mem[0] and j not in set(mem.tolist())]
+        want = sorted(ok, key=lambda j: (d[j], j))[:40]
+        assert idx[ptr[g]:ptr[g + 1]].tolist() == want, g
+    assert nonadjacent > 0
