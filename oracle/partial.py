@@ -40,11 +40,12 @@ import numpy as np
 from . import exhaustion_floor, theta_matrix
 
 
-def select_partial(kp, pts, P, cand, k: int, floor=None):
+def select_partial(kp, pts, P, cand, k: int, floor=None, forced=None):
     """Greedy partial selection for the targets P (positions, any order) from the candidate
-    positions `cand`.  Returns dict(sel, decrease, L, order): the picks, each pick's decrease
-    of the objective, and the final factor (rows: candidates then targets; columns in the
-    order `order`, latest position first)."""
+    positions `cand`.  forced[t] >= 0 replays a pick given as an index into cand.  Returns
+    dict(sel, decrease, best, chosen, L, order): the picks, each pick's decrease of the
+    objective (= chosen), the largest decrease at each step (best), and the final factor
+    (rows: candidates then targets; columns in the order `order`, latest position first)."""
     P = sorted(int(x) for x in P)
     cand = [int(x) for x in cand]
     floor = exhaustion_floor(kp) if floor is None else floor
@@ -75,7 +76,8 @@ def select_partial(kp, pts, P, cand, k: int, floor=None):
             lee = new[e, c]
             rr = math.sqrt(lee * lee - x[e] * x[e])
             cth, sth = rr / lee, x[e] / lee
-            below = [y for y in range(C + m) if y not in order[:c + 1] and y != r]
+            above = set(order[:c + 1])
+            below = [y for y in range(C + m) if y not in above and y != r]
             col = (new[below, c] - sth * x[below]) / cth
             x[below] = cth * x[below] - sth * col
             new[below, c] = col
@@ -86,9 +88,10 @@ def select_partial(kp, pts, P, cand, k: int, floor=None):
 
     for r in range(C, C + m):             # the targets first
         insert(r)
-    sel, dec = [], []
-    for _ in range(k):
+    sel, dec, bests = [], [], []
+    for t in range(k):
         best, best_r = None, -1
+        scores = {}
         for j in range(C):
             if taken[j]:
                 continue
@@ -102,15 +105,21 @@ def select_partial(kp, pts, P, cand, k: int, floor=None):
                 v -= L[j, c] ** 2
             if v < floor:
                 continue
+            scores[j] = score
             if best is None or score > best:
                 best, best_r = score, j
         if best_r < 0:
             break
-        taken[best_r] = True
-        insert(best_r)
-        sel.append(rows[best_r])
-        dec.append(best)
-    return dict(sel=np.array(sel, np.int32), decrease=np.array(dec), L=L, order=[rows[e] for e in order])
+        q = best_r
+        if forced is not None and t < len(forced) and forced[t] >= 0:
+            q = int(forced[t])
+        taken[q] = True
+        insert(q)
+        sel.append(rows[q])
+        dec.append(scores.get(q, -math.inf))
+        bests.append(best)
+    return dict(sel=np.array(sel, np.int32), decrease=np.array(dec), best=np.array(bests), chosen=np.array(dec),
+                L=L, order=[rows[e] for e in order])
 
 
 def objective(kp, pts, P, S) -> float:

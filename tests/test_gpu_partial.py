@@ -1,0 +1,166 @@
+"""GPU partial selection for nonadjacent groups (Section 5.2, Appendix C.3) against the oracle.
+
+Tolerances follow the parity tests: FP64 picks identical except at near-ties of the
+oracle's scores within 1e-10 relative (oracle replay); FP32 picks within 2e-2 relative or
+1e-6 sigma^2 absolute of the oracle's best decrease; the decreases of agreeing FP64 picks to
+1e-9 relative plus 1e-12; the fill of the resulting pattern as in the parity tests (rows
+identical, values 1e-8 of the column's largest, log v to 1e-9).
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from parity import ReplayStats, _replay, column_errors
+
+pytestmark = pytest.mark.gpu
+
+TIE_BAND = 1e-10
+FP32_BAND, FP32_ABS = 2e-2, 1e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_11648_gb300 import build
+    build.build()
+    from paper_2307_11648_gb300 import pipeline, sic
+    return torch, sic, pipeline, sic.Handle(0)
+
+
+def _okernel(oracle, kp):
+    return oracle.kernel(kp.dim, kp.nu_x2, kp.length_scale, kp.variance, kp.nugget)
+
+
+def _problem(env, n, seed, n_cand, k, mmin=4, mmax=16):
+    torch, sic, pipeline, h = env
+    kp = sic.kernel(2, 3, 0.1, 1.0, 1e-6)
+    return kp, pipeline.prepare_partial(synthetic.points(n, 2, seed), kp, n_cand, k, mmin, mmax)
+
+
+def _replay_partial(oracle, okp, hp, g, gpu_sel, band, stats, abs_band=0.0):
+    from oracle import partial
+    mem = hp.members[hp.grp_ptr[g]:hp.grp_ptr[g + 1]]
+    cand = hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]]
+
+    def run(forced):
+        return partial.select_partial(okp, hp.pts, mem, cand, hp.k, forced=forced if forced else None)
+    _replay(run, gpu_sel, cand, band, stats, f"group {g}", abs_band)
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_partial_selection_matches_oracle(env, oracle_lib, prec_name):
+    """N = 4096, groups of 4-16 members kept where the ordering puts them, 48 candidates
+    (some between members), up to 12 picks; a sample of groups replayed by the oracle."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    from oracle import partial
+    kp, hp = _problem(env, 4096, 5, 48, 12)
+    prec = sic.SIC_FP64 if prec_name == "fp64" else sic.SIC_FP32_MIXED
+    dp = pipeline.DeviceProblem(hp)
+    fb = pipeline.PartialFactorBuilder(h, hp, prec)
+    fb.select(dp)
+    h.sync()
+    sels = fb.sel_lists()
+    gain = fb.gain.view(-1, hp.k).cpu().numpy()
+    okp = _okernel(oracle, kp)
+    G = hp.n_units
+    between = sum(int(any(hp.members[hp.grp_ptr[g]] < q < hp.members[hp.grp_ptr[g + 1] - 1] for q in sels[g]))
+                  for g in range(G))
+    assert between > 0  # picks between members: the case partial selection exists for
+    stats = ReplayStats()
+    band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    ab = 0.0 if prec_name == "fp64" else FP32_ABS * kp.variance
+    same = 0
+    sample = range(0, G, max(1, G // 40))
+    for g in sample:
+        _replay_partial(oracle, okp, hp, g, sels[g], band, stats, ab)
+        if prec_name == "fp64":
+            mem = hp.members[hp.grp_ptr[g]:hp.grp_ptr[g + 1]]
+            r = partial.select_partial(okp, hp.pts, mem, hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]], hp.k)
+            if np.array_equal(r["sel"], sels[g]):
+                same += 1
+                ncond = [sum(int(i < q) for i in mem) for q in r["sel"]]
+                np.testing.assert_allclose(gain[g, :len(sels[g])], r["decrease"] / np.maximum(ncond, 1),
+                                           rtol=1e-9, atol=1e-12, err_msg=str(g))
+    print(prec_name, f"groups {G}, with picks between members {between}; replay {stats}")
+    if prec_name == "fp64":
+        assert same >= len(sample) - 2
+
+
+def test_partial_fill_matches_oracle(env, oracle_lib):
+    """The pattern of a partial selection (member i: later members + picks after i) filled
+    column by column in FP64, against the oracle's dense per-column fill."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    kp, hp = _problem(env, 4096, 6, 48, 12)
+    dp = pipeline.DeviceProblem(hp)
+    fb = pipeline.PartialFactorBuilder(h, hp, sic.SIC_FP64)
+    fb.run(dp)
+    h.sync()
+    okp = _okernel(oracle, kp)
+    sels = fb.sel_lists()
+    cp = fb.col_ptr.cpu().numpy()
+    nnz = int(cp[-1])
+    ri, val, logv = fb.row_idx[:nnz].cpu().numpy(), fb.val[:nnz].cpu().numpy(), fb.logv.cpu().numpy()
+    col = {}
+    for g in range(hp.n_units):
+        mem = hp.members[hp.grp_ptr[g]:hp.grp_ptr[g + 1]].tolist()
+        for a, i in enumerate(mem):
+            col[i] = mem[a + 1:] + [int(q) for q in sels[g] if q > i]
+    assert sorted(col) == list(range(hp.n))
+    worst = 0.0
+    for i in range(0, hp.n, 7):
+        rows, L, lv = oracle.fill_column(okp, hp.pts, i, col[i])
+        a, b = cp[i], cp[i + 1]
+        assert ri[a:b].tolist() == rows.tolist(), i
+        e = column_errors(val[a:b], L)
+        worst = max(worst, e)
+        assert e <= 1e-8, (i, e)
+        assert abs(logv[i] - lv) <= 1e-9, i
+    assert nnz == sum(1 + len(v) for v in col.values())
+    print(f"fill: nnz {nnz}, worst column error {worst:.2e}")
+
+
+def test_partial_beats_renumbered_groups(env):
+    """The paper's observation behind partial selection: keeping the groups where the
+    ordering puts them (candidates between members allowed, partial selection) gives a lower
+    KL than renumbering them to be consecutive (every candidate after the group,
+    multiple-target selection), at the same k.  sum log v differences equal 2 KL
+    differences (logdet Theta does not depend on the ordering).  N = 2^16."""
+    torch, sic, pipeline, h = env
+    kp = sic.kernel(2, 3, 0.05, 1.0, 1e-6)
+    pts = synthetic.points(1 << 16, 2, 9)
+    k, C = 32, 128
+    hp_p = pipeline.prepare_partial(pts, kp, C, k, 8, 32)
+    hp_a = pipeline.prepare_groups(pts, kp, C, k, 8, 32)
+    res = {}
+    for name, hp, B in [("partial", hp_p, pipeline.PartialFactorBuilder),
+                        ("renumbered", hp_a, pipeline.FactorBuilder)]:
+        dp = pipeline.DeviceProblem(hp)
+        fb = B(h, hp, sic.SIC_FP32_MIXED)
+        fb.run(dp)
+        h.sync()
+        res[name] = (float(fb.sum_logv.cpu()[0]), int(fb.col_ptr[-1].item()))
+    print("sum log v, nnz:", res)
+    assert res["partial"][0] < res["renumbered"][0]
+
+
+def test_partial_errors_reported(env):
+    torch, sic, pipeline, h = env
+    kp, hp = _problem(env, 600, 7, 24, 8)
+    dp = pipeline.DeviceProblem(hp)
+    bad = dp.cand_idx.clone()
+    g0 = int(hp.members[hp.grp_ptr[1]])
+    bad[int(hp.cand_ptr[1])] = g0  # a candidate at the group's first member
+    fb = pipeline.PartialFactorBuilder(h, hp, sic.SIC_FP64)
+    sic.select_partial(h, dp.pts, kp, dp.grp_ptr, dp.members, dp.cand_ptr, bad, hp.max_cand, hp.max_m, hp.k,
+                       sic.SIC_FP64, fb.sel_idx, fb.sel_count)
+    with pytest.raises(sic.SicError):
+        h.sync()
+    with pytest.raises(sic.SicError):  # the factor cannot fit in shared memory
+        sic.select_partial(h, dp.pts, kp, dp.grp_ptr, dp.members, dp.cand_ptr, dp.cand_idx, 4000, hp.max_m, hp.k,
+                           sic.SIC_FP64, fb.sel_idx, fb.sel_count)
+    fb.run(dp)
+    h.sync()
