@@ -37,7 +37,8 @@ def _run_side(env, pts, kp, sel, cnt, k, grp_ptr=None, max_m=1):
     U = len(cnt)
     si = np.full((U, k), -1, np.int32)
     for u in range(U):
-        si[u, :cnt[u]] = sel[u][:cnt[u]]
+        c = min(cnt[u], k, len(sel[u]))
+        si[u, :c] = sel[u][:c]
     d = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
     out = [torch.full((U * k,), -1.0, dtype=torch.float64, device="cuda") for _ in range(3)]
     sic.side_state_fp64(h, d(pts, np.float64), kp, d(si.reshape(-1), np.int32), d(np.asarray(cnt), np.int32), k,
