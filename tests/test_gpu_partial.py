@@ -6,6 +6,8 @@ oracle's scores within 1e-10 relative (oracle replay); FP32 picks within 2e-2 re
 1e-9 relative plus 1e-12; the fill of the resulting pattern as in the parity tests (rows
 identical, values 1e-8 of the column's largest, log v to 1e-9).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -123,28 +125,38 @@ def test_partial_fill_matches_oracle(env, oracle_lib):
     print(f"fill: nnz {nnz}, worst column error {worst:.2e}")
 
 
-def test_partial_beats_renumbered_groups(env):
-    """The paper's observation behind partial selection: keeping the groups where the
-    ordering puts them (candidates between members allowed, partial selection) gives a lower
-    KL than renumbering them to be consecutive (every candidate after the group,
-    multiple-target selection), at the same k.  sum log v differences equal 2 KL
-    differences (logdet Theta does not depend on the ordering).  N = 2^16."""
+def test_partial_beats_candidates_after_the_group(env):
+    """The paper's observation behind partial selection: with the groups where the ordering
+    puts them, forcing every candidate to lie after the whole group (so that the
+    multiple-target selection applies) drops the candidates between members and gives a
+    higher KL than partial selection over all of them -- here with fewer nonzeros, too.
+    Renumbering the groups to be consecutive (this library's supernodal path) is reported
+    beside them.  sum log v differences are 2 KL differences (logdet Theta does not depend on
+    the ordering).  N = 2^16, k = 32, 128 candidates, groups of 8-32."""
     torch, sic, pipeline, h = env
     kp = sic.kernel(2, 3, 0.05, 1.0, 1e-6)
     pts = synthetic.points(1 << 16, 2, 9)
     k, C = 32, 128
-    hp_p = pipeline.prepare_partial(pts, kp, C, k, 8, 32)
-    hp_a = pipeline.prepare_groups(pts, kp, C, k, 8, 32)
+    hp = pipeline.prepare_partial(pts, kp, C, k, 8, 32)
+    ptr, idx = [0], []
+    for g in range(hp.n_units):
+        last = hp.members[hp.grp_ptr[g + 1] - 1]
+        idx += [int(j) for j in hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]] if j > last]
+        ptr.append(len(idx))
+    hp_after = dataclasses.replace(hp, cand_ptr=np.array(ptr, np.int64), cand_idx=np.array(idx, np.int32))
+    hp_renum = pipeline.prepare_groups(pts, kp, C, k, 8, 32)
     res = {}
-    for name, hp, B in [("partial", hp_p, pipeline.PartialFactorBuilder),
-                        ("renumbered", hp_a, pipeline.FactorBuilder)]:
-        dp = pipeline.DeviceProblem(hp)
-        fb = B(h, hp, sic.SIC_FP32_MIXED)
+    for name, p, B in [("partial", hp, pipeline.PartialFactorBuilder),
+                       ("after_the_group", hp_after, pipeline.PartialFactorBuilder),
+                       ("renumbered", hp_renum, pipeline.FactorBuilder)]:
+        dp = pipeline.DeviceProblem(p)
+        fb = B(h, p, sic.SIC_FP32_MIXED)
         fb.run(dp)
         h.sync()
         res[name] = (float(fb.sum_logv.cpu()[0]), int(fb.col_ptr[-1].item()))
     print("sum log v, nnz:", res)
-    assert res["partial"][0] < res["renumbered"][0]
+    assert res["partial"][0] < res["after_the_group"][0] - 100.0
+    assert res["partial"][1] <= res["after_the_group"][1]
 
 
 def test_partial_errors_reported(env):
