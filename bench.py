@@ -316,6 +316,8 @@ def main():
     ap.add_argument("--case-mlp", action="store_true",
                     help="with --case-only: run the proposal (untrained network) and select on its top 256")
     ap.add_argument("--pcg-n", type=int, default=1 << 16, help="points of the preconditioning comparison (0: skip)")
+    ap.add_argument("--partial-n", type=int, default=1 << 18,
+                    help="points of the partial-selection (nonadjacent groups) measurement (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if ws > 1:
@@ -491,6 +493,21 @@ def main():
                               "frac": alloc_bytes / (galloc_ms * 1e-3) / 1e9 / hbm_peak,
                               "algorithmic_bytes": alloc_bytes},
     }
+    # ---- partial selection for nonadjacent groups (Section 5.2): groups kept where the ordering
+    # puts them, 256 candidates after each group's first member, FP32 selection, per-column fill
+    partial = None
+    if args.partial_n:
+        php = pipeline.prepare_partial(synthetic.points(args.partial_n, 2, cfg["seed"] + rank), hp.kp, 256, cfg["k"],
+                                       cfg["m_min"], cfg["m_max"])
+        pdp = pipeline.DeviceProblem(php)
+        pfb = pipeline.PartialFactorBuilder(h, php, sic.SIC_FP32_MIXED)
+        p_ms, (psel_ms, pfill_ms), _ = timed([lambda: pfb.select(pdp), lambda: pfb.fill(pdp)], 2, 1)
+        partial = {"n": args.partial_n, "groups": php.n_units, "candidates": 256, "k": cfg["k"],
+                   "ms_per_step": p_ms, "select_ms": psel_ms, "fill_ms": pfill_ms,
+                   "columns_per_s": args.partial_n / (p_ms * 1e-3), "sum_logv": float(pfb.sum_logv.cpu()[0]),
+                   "nnz": int(pfb.col_ptr[-1].item())}
+        del pfb, pdp, php
+        torch.cuda.empty_cache()
     base = S["plain_fp64"] - S["reference_2k"]
     kl_gap = {k: (S[k] - S["plain_fp64"]) / base for k in ["learned_fp32", "plain_fp32", "distance_fp32",
                                                            "learned_global_48", "learned_global_48_side_fp64",
@@ -642,6 +659,7 @@ def main():
             "clocks": clocks,
             "pcg": pcg,
             "global_allocation": global_alloc,
+            "partial_selection": partial,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -18,8 +18,9 @@
 //   insert   the pick q goes to its place p (the number of columns of later points): the
 //            columns before p stay; the new column is Theta_{:,q | first p} / sqrt(Theta_{qq |
 //            first p}) by left-looking; the columns from p on are downdated in place by it
-//            column by column (eq. chol_partial_update): one thread forms each column's
-//            rotation, every row below the pivot applies it.
+//            column by column (eq. chol_partial_update): every thread forms the column's
+//            rotation from the pivot row, every row below the pivot applies it (one barrier
+//            per column).
 // Columns live in physical slots in insertion order; `ordr/ords/opos` map the logical
 // (latest-first) order to the pivot row, the slot and the target position (INT_MAX for a
 // pick).  One CTA per group (persistent), L in shared memory, rows spread over the threads.
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
     int* ordr = rank + Lay.R;                         // [W] pivot row of logical column c
     int* ords = ordr + Lay.W;                         // [W] physical slot of logical column c
     int* opos = ords + Lay.W;                         // [W] target position of column c (INT_MAX: a pick)
-    __shared__ T s_rs, s_d, s_cth, s_sth;
+    __shared__ T s_rs, s_d;
     __shared__ int s_p, s_fail;
     __shared__ T wkey[PT_NT / 32];
     __shared__ int widx[PT_NT / 32];
@@ -146,23 +147,30 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
                 xv[r] = (r == q) ? (T)0 : u;
             }
             __syncthreads();
+            // one barrier per column: every thread forms the column's rotation from the pivot
+            // row's entry and downdate value (final since the previous column's pass), the rows
+            // below apply it; the pivot row's new diagonal is stored one pass later (by the
+            // thread that owns the row), when no thread reads the old one any more
+            bool bad = false;
+            int pend = -1;  // element (row * PP + slot) whose new diagonal waits
+            T pend_v = (T)0;
             for (int c = p; c < ncol; ++c) {
-                const int e = ordr[c], s = ords[c];
-                if (tid == 0) {
-                    const T lee = Lm[e * PP + s], xe = xv[e];
-                    const T rr2 = fma(-xe, xe, lee * lee);
-                    if (!(rr2 > (T)0) || !(lee > (T)0)) s_fail = 2;
-                    const T rr = sic_sqrt(rr2 > (T)0 ? rr2 : (T)0);
-                    s_cth = rr / lee;
-                    s_sth = xe / lee;
-                    Lm[e * PP + s] = rr;
+                if (pend >= 0) {
+                    Lm[pend] = pend_v;
+                    pend = -1;
                 }
-                __syncthreads();
-                if (s_fail) return false;
-                const T cth = s_cth, sth = s_sth, icth = (T)1 / cth;
+                const int e = ordr[c], s = ords[c];
+                const T lee = Lm[e * PP + s], xe = xv[e];
+                const T rr2 = fma(-xe, xe, lee * lee);
+                bad = bad || !(rr2 > (T)0) || !(lee > (T)0);
+                const T rr = sic_sqrt(rr2 > (T)0 ? rr2 : (T)0);
+                const T cth = rr / lee, sth = xe / lee, icth = lee / rr;
                 for (int r = tid; r < R; r += PT_NT) {
                     const int rk = rank[r];
-                    if (r != q && (rk < 0 || rk > c)) {
+                    if (r == e) {
+                        pend = r * PP + s;
+                        pend_v = rr;
+                    } else if (r != q && (rk < 0 || rk > c)) {
                         const T xr = xv[r];
                         const T nl = (Lm[r * PP + s] - sth * xr) * icth;
                         Lm[r * PP + s] = nl;
@@ -171,6 +179,10 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
                 }
                 __syncthreads();
             }
+            if (pend >= 0) Lm[pend] = pend_v;
+            if (bad && tid == 0) s_fail = 2;
+            __syncthreads();
+            if (s_fail) return false;
             // row q now holds a pivot: nothing in the columns after its own
             for (int c = p + tid; c < ncol; c += PT_NT) Lm[q * PP + ords[c]] = (T)0;
             __syncthreads();
