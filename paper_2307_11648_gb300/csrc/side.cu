@@ -35,6 +35,7 @@ __device__ __forceinline__ int tri_row(int e) {
 
 struct SideLayout {
     int nmax, k;
+    int dec;  // 1: the packed-triangle decode table follows the doubles (when it fits)
     __host__ __device__ int tab() const { return 0; }
     __host__ __device__ int A() const { return EXP_TAB; }
     __host__ __device__ int B() const { return A() + nmax * (nmax + 1) / 2; }
@@ -43,7 +44,12 @@ struct SideLayout {
     __host__ __device__ int clB() const { return clA() + nmax; }
     __host__ __device__ int rdA() const { return clB() + k; }
     __host__ __device__ int rdB() const { return rdA() + nmax; }
-    __host__ __device__ int size() const { return rdB() + k; }
+    __host__ __device__ int size() const { return rdB() + k; }  // doubles
+    // then the decode table of the packed triangle: entry e -> (row << 8) | column
+    __host__ __device__ int tri() const { return nmax * (nmax + 1) / 2; }
+    __host__ __device__ size_t bytes() const {
+        return sizeof(double) * (size_t)size() + (dec ? sizeof(uint16_t) * (size_t)tri() : 0);
+    }
 };
 
 __global__ void __launch_bounds__(SIDE_NT) k_side(const double* __restrict__ pts, long long n, int dim,
@@ -63,11 +69,28 @@ __global__ void __launch_bounds__(SIDE_NT) k_side(const double* __restrict__ pts
     double* clB = sm + L.clB();
     double* rdA = sm + L.rdA();
     double* rdB = sm + L.rdB();
+    uint16_t* dec = reinterpret_cast<uint16_t*>(sm + L.size());  // packed-triangle decode table
     __shared__ int s_bad;  // 1: invalid unit or pick, 2: a pivot not positive
     const int tid = threadIdx.x, NMAX = L.nmax;
     const double diag = kp.s2 + kp.nugget;
     const double NaN = __longlong_as_double(0x7ff8000000000000LL);
     exp_table_fill(tab, kp.s2);
+    if (L.dec)
+        for (int e = threadIdx.x; e < L.tri(); e += blockDim.x) {
+            const int r = tri_row(e);
+            dec[e] = (uint16_t)((r << 8) | (e - r * (r + 1) / 2));
+        }
+    // row and column of packed-triangle element e: from the table, else by the square root
+    auto decode = [&](int e, int& r, int& c) {
+        if (L.dec) {
+            const unsigned v = dec[e];
+            r = (int)(v >> 8);
+            c = (int)(v & 255u);
+        } else {
+            r = tri_row(e);
+            c = e - r * (r + 1) / 2;
+        }
+    };
 
     for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         long long p0;
@@ -99,7 +122,8 @@ __global__ void __launch_bounds__(SIDE_NT) k_side(const double* __restrict__ pts
             // Theta over [P; S] (packed lower) and a copy of its S block
             const int tri = nn * (nn + 1) / 2;
             for (int e = tid; e < tri; e += SIDE_NT) {
-                const int a = tri_row(e), b = e - a * (a + 1) / 2;
+                int a, b;
+                decode(e, a, b);
                 double v = diag;
                 if (a != b) {
                     const double dx = xyz[a] - xyz[b], dy = xyz[NMAX + a] - xyz[NMAX + b],
@@ -126,7 +150,8 @@ __global__ void __launch_bounds__(SIDE_NT) k_side(const double* __restrict__ pts
                 for (int e = tid; e < eA + eB; e += SIDE_NT) {
                     const bool inA = e < eA;
                     const int f = inA ? e : e - eA;
-                    const int r = tri_row(f), c = f - r * (r + 1) / 2;
+                    int r, c;
+                    decode(f, r, c);
                     const int a = j + 1 + r, b = j + 1 + c;
                     double* M = inA ? A : B;
                     const double* cl = inA ? clA : clB;
@@ -173,7 +198,9 @@ extern "C" sic_status sic_side_state_fp64(sic_handle* h, const double* pts, int6
     SideLayout L;
     L.nmax = max_m + k;
     L.k = k;
-    const size_t smem = sizeof(double) * (size_t)L.size();
+    L.dec = 1;
+    if (L.bytes() > 227 * 1024 - 1024) L.dec = 0;
+    const size_t smem = L.bytes();
     if (smem > 227 * 1024 - 1024) return SIC_ERR_UNSUPPORTED;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     if (smem > 48 * 1024)
