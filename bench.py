@@ -316,6 +316,11 @@ def main():
     ap.add_argument("--case-mlp", action="store_true",
                     help="with --case-only: run the proposal (untrained network) and select on its top 256")
     ap.add_argument("--pcg-n", type=int, default=1 << 16, help="points of the preconditioning comparison (0: skip)")
+    ap.add_argument("--case-global", action="store_true",
+                    help="with --case-only: the learned step with a budget of 48 picks per supernode on average, "
+                         "decreases from the FP64 side state, global allocation")
+    ap.add_argument("--case-partial", action="store_true",
+                    help="with --case-only: partial selection of nonadjacent groups (256 candidates) and its fill")
     ap.add_argument("--partial-n", type=int, default=1 << 18,
                     help="points of the partial-selection (nonadjacent groups) measurement (0: skip)")
     args = ap.parse_args()
@@ -336,6 +341,16 @@ def main():
     build.build()
     torch.cuda.set_device(local)
     cfg = synthetic.PRESETS[WORKLOAD]
+    if args.case_only and args.case_partial:
+        h = sic.Handle(local)
+        php = pipeline.prepare_partial(synthetic.points(args.case_only, 2, cfg["seed"]), sic.kernel(
+            2, cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"]), 256, cfg["k"], cfg["m_min"],
+            cfg["m_max"])
+        fb = pipeline.PartialFactorBuilder(h, php, sic.SIC_FP32_MIXED)
+        fb.run(pipeline.DeviceProblem(php))
+        h.sync()
+        print(json.dumps({"case": args.case_only, "groups": php.n_units, "sum_logv": float(fb.sum_logv.cpu()[0])}))
+        return
     if args.case_only:
         # one FP32-mixed supernodal factor build at the requested size (for ncu captures)
         hp = problem(cfg, cfg["seed"], args.case_only)
@@ -343,7 +358,11 @@ def main():
             hp = truncated(hp, args.case_top)
         h = sic.Handle(local)
         dp = pipeline.DeviceProblem(hp)
-        if args.case_mlp:
+        if args.case_global:
+            fb = learned.LearnedFactorBuilder(h, hp, learned.Proposal(h, learned.init_params(0), top=4 * cfg["k"]),
+                                              budget=int(np.diff(hp.grp_ptr).sum()) * (3 * cfg["k"] // 4),
+                                              side_fp64=True)
+        elif args.case_mlp:
             fb = learned.LearnedFactorBuilder(h, hp, learned.Proposal(h, learned.init_params(0), top=4 * cfg["k"]))
         else:
             fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
