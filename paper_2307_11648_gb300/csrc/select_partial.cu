@@ -30,7 +30,10 @@
 
 namespace {
 
-constexpr int PT_NT = 256;
+constexpr int PT_NT = 512;
+
+__device__ __forceinline__ float pt_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double pt_div(double a, double b) { return a / b; }
 
 struct PtLayout {
     int R, W, P;  // rows (candidates + targets), columns (targets + picks), row pitch (odd)
@@ -114,18 +117,32 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
         // inserts row q's point: place p, left-looking column into slot ncol, in-place
         // downdate of the columns from p on; false (uniformly) when a pivot is not positive
         auto insert = [&](int q) -> bool {
-            if (tid == 0) {
+            if (warp == 0) {
+                // its place: binary search of the columns (positions descending)
                 int p = 0;
-                while (p < ncol && pos[ordr[p]] > pos[q]) ++p;
-                T d = diag;
-                for (int c = 0; c < p; ++c) {
-                    const T l = Lm[q * PP + ords[c]];
-                    d = fma(-l, l, d);
+                if (lane == 0) {
+                    int lo = 0, hi = ncol;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pos[ordr[mid]] > pos[q]) lo = mid + 1; else hi = mid;
+                    }
+                    p = lo;
                 }
-                s_p = p;
-                s_d = d;
-                if (!(d > (T)0)) s_fail = 2;
-                s_rs = (d > (T)0) ? (T)1 / sic_sqrt(d) : (T)0;
+                p = __shfl_sync(0xffffffffu, p, 0);
+                T part = (T)0;
+                for (int c = lane; c < p; c += 32) {
+                    const T l = Lm[q * PP + ords[c]];
+                    part = fma(l, l, part);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+                if (lane == 0) {
+                    const T d = diag - part;  // Theta_{qq | first p}
+                    s_p = p;
+                    s_d = d;
+                    if (!(d > (T)0)) s_fail = 2;
+                    s_rs = (d > (T)0) ? (T)1 / sic_sqrt(d) : (T)0;
+                }
             }
             __syncthreads();
             if (s_fail) return false;
@@ -183,15 +200,23 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
             if (bad && tid == 0) s_fail = 2;
             __syncthreads();
             if (s_fail) return false;
-            // row q now holds a pivot: nothing in the columns after its own
+            // row q now holds a pivot: nothing in the columns after its own; the column maps
+            // shift one place from p on (each thread carries one entry across the barrier)
             for (int c = p + tid; c < ncol; c += PT_NT) Lm[q * PP + ords[c]] = (T)0;
+            const int cm = p + 1 + tid;  // the new index of the entry this thread moves
+            int mr = 0, ms = 0, mp = 0;
+            if (cm <= ncol) {
+                mr = ordr[cm - 1];
+                ms = ords[cm - 1];
+                mp = opos[cm - 1];
+            }
             __syncthreads();
+            if (cm <= ncol) {
+                ordr[cm] = mr;
+                ords[cm] = ms;
+                opos[cm] = mp;
+            }
             if (tid == 0) {
-                for (int c = ncol; c > p; --c) {
-                    ordr[c] = ordr[c - 1];
-                    ords[c] = ords[c - 1];
-                    opos[c] = opos[c - 1];
-                }
                 ordr[p] = q;
                 ords[p] = ncol;
                 opos[p] = (q >= C) ? pos[q] : INT_MAX;
@@ -219,7 +244,7 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
                 for (int c = 0; c < ncol; ++c) {
                     const T l = Lm[j * PP + ords[c]];
                     const T vn = fma(-l, l, v);
-                    if (opos[c] < pj) pr = pr * vn / v;  // a target j conditions (eq. obj_partial)
+                    if (opos[c] < pj) pr = pt_div(pr * vn, v);  // a target j conditions (eq. obj_partial)
                     v = vn;                              // eq. partial_induct
                 }
                 if (v >= floor_ && (pr < bk || (pr == bk && j < bi))) {
@@ -250,9 +275,9 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
                     q = widx[w];
                 }
             if (q == INT_MAX) break;
+            // the targets the pick conditions (its nonzeros)
+            const int nc = __syncthreads_count(tid < ncol && opos[tid] < pos[q]);
             if (tid == 0) {
-                int nc = 0;
-                for (int c = 0; c < ncol; ++c) nc += opos[c] < pos[q];
                 gprod[t] = (double)gk;
                 gcnd[t] = nc;
                 sel_idx[g * k + t] = pos[q];
