@@ -208,15 +208,31 @@ sic_status sic_select_partial(sic_handle* h, const double* pts, int64_t n, const
                               const int32_t* cand_idx, int32_t max_cand, int32_t max_m, int32_t k,
                               sic_precision prec, int32_t* sel_idx, int32_t* sel_count, double* gain, void* stream);
 
-/* The pattern of a partial selection as single-column lists for the fill: member i of
- * group g gets col_sel[i * kc ..] = the later members of g, then g's picks after i, and
- * col_count[i] their number (kc >= max_m - 1 + k; a longer list is cut and reported as
- * SIC_ERR_INVALID).  The factor then follows from sic_factor_nnz / sic_build_factor with
- * grp_ptr NULL, max_m 1 and k = kc (each column's KL-optimal values, eq. L_col).  Columns
- * of positions in no group are not written.  [device] */
+/* The pattern of a partial selection as single-column lists: member i of group g gets
+ * col_sel[i * kc ..] = the later members of g, then g's picks after i, and col_count[i] their
+ * number (kc >= max_m - 1 + k; a longer list is cut and reported as SIC_ERR_INVALID).  With
+ * col_sel NULL only col_count is written (the input of sic_factor_nnz with grp_ptr NULL for
+ * sic_build_factor_partial).  The lists also suit sic_build_factor with grp_ptr NULL, max_m
+ * 1 and k = kc (one factorisation per column).  Columns of positions in no group are not
+ * written.  [device] */
 sic_status sic_partial_columns(sic_handle* h, int64_t n, const int64_t* grp_ptr, const int64_t* members,
                                int64_t n_grp, const int32_t* sel_idx, const int32_t* sel_count, int32_t k,
                                int32_t kc, int32_t* col_sel, int32_t* col_count, void* stream);
+
+/* KL-optimal FP64 fill of a partial-selection pattern, aggregated per group (Section 5.1.1,
+ * Appendix A.4): the group's members and picks sorted from the latest position to the
+ * earliest make every member's set a leading block, so one LDL^T of Theta over them serves
+ * all members (member u_a: L_S^T x = e_a d_a^{-1/2} over the leading block, log v = log
+ * d_a).  col_ptr from sic_factor_nnz (grp_ptr NULL) on the counts of sic_partial_columns;
+ * row_idx / val / logv / *sum_logv as in sic_build_factor.  Positions of a group's union
+ * must be distinct and its picks after its first member (else SIC_ERR_INVALID by
+ * sic_sync).  max_m <= 64, k <= 128, (max_m + k) <= 192.  ws: sic_build_factor_workspace(n)
+ * bytes.  [device] */
+sic_status sic_build_factor_partial(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                    const int64_t* grp_ptr, const int64_t* members, int64_t n_grp, int32_t max_m,
+                                    const int32_t* sel_idx, const int32_t* sel_count, int32_t k,
+                                    const int64_t* col_ptr, int32_t* row_idx, double* val, double* logv,
+                                    double* sum_logv, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------- global allocation of nonzeros [device] -- */
 /*

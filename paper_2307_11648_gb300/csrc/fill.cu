@@ -418,6 +418,15 @@ extern "C" sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int6
     return SIC_OK;
 }
 
+// sum of log v in a fixed order (two launches), shared with the partial-pattern fill
+sic_status launch_sum_logv(const double* logv, long long n, double* sum_logv, void* ws, cudaStream_t s) {
+    long long nb = (n + SUM_TILE - 1) / SUM_TILE;
+    k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n, (double*)ws);
+    k_sum_final<<<1, 256, 0, s>>>((const double*)ws, nb, sum_logv);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
+
 extern "C" sic_status sic_build_factor_workspace(int64_t n, size_t* bytes) {
     if (!bytes || n < 0) return SIC_ERR_INVALID;
     long long nb = (n + SUM_TILE - 1) / SUM_TILE;

@@ -319,6 +319,12 @@ __global__ void k_partial_columns(long long n, const long long* __restrict__ grp
                 record_error(st, SIC_ERR_INVALID, g);
                 continue;
             }
+            if (!col_sel) {  // counts only
+                int w = (int)(a1 - a - 1);
+                for (int t = 0; t < cnt; ++t) w += sel_idx[g * k + t] > i;
+                col_count[i] = w;
+                continue;
+            }
             int w = 0;
             int32_t* out = col_sel + i * kc;
             for (long long b = a + 1; b < a1 && w < kc; ++b) out[w++] = (int32_t)members[b];
@@ -378,8 +384,7 @@ extern "C" sic_status sic_select_partial(sic_handle* h, const double* pts, int64
 extern "C" sic_status sic_partial_columns(sic_handle* h, int64_t n, const int64_t* grp_ptr, const int64_t* members,
                                           int64_t n_grp, const int32_t* sel_idx, const int32_t* sel_count, int32_t k,
                                           int32_t kc, int32_t* col_sel, int32_t* col_count, void* stream) {
-    if (!h || n < 1 || n_grp < 0 || k < 1 || kc < 1 || !grp_ptr || !members || !sel_idx || !sel_count || !col_sel ||
-        !col_count)
+    if (!h || n < 1 || n_grp < 0 || k < 1 || kc < 1 || !grp_ptr || !members || !sel_idx || !sel_count || !col_count)
         return SIC_ERR_INVALID;
     if (n_grp == 0) return SIC_OK;
     SIC_CUDA_TRY(cudaSetDevice(h->device));

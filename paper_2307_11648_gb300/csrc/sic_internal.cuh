@@ -181,6 +181,9 @@ sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const s
                           int max_m, int k, int32_t* sel_idx, int32_t* sel_count, double* gain, void* ws,
                           size_t ws_bytes, cudaStream_t s);
 
+// fixed-order sum of log v (fill.cu); ws holds sic_build_factor_workspace(n) bytes
+sic_status launch_sum_logv(const double* logv, long long n, double* sum_logv, void* ws, cudaStream_t s);
+
 // tcgen05 scoring kernel of the proposal network (mlp_tc.cu)
 sic_status sic_proposal_score_tc(sic_handle* h, const float* params, const float* feat, int64_t rows, float* score,
                                  cudaStream_t s);

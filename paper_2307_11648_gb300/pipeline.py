@@ -201,19 +201,20 @@ class FactorBuilder:
 
 
 class PartialFactorBuilder:
-    """Nonadjacent groups: partial selection (Section 5.2, Appendix C.3), the pattern expanded
-    to single-column lists, and the FP64 fill of each column (eq. L_col)."""
+    """Nonadjacent groups: partial selection (Section 5.2, Appendix C.3) and the KL-optimal
+    FP64 fill of its pattern -- aggregated per group (one LDL^T of the group's members and
+    picks, latest first) or, with per_column=True, one factorisation per column."""
 
-    def __init__(self, h: sic.Handle, hp: HostProblem, prec: int, device="cuda"):
+    def __init__(self, h: sic.Handle, hp: HostProblem, prec: int, device="cuda", per_column: bool = False):
         import torch
         assert hp.members is not None and hp.grp_ptr is not None
-        self.h, self.hp, self.prec = h, hp, prec
+        self.h, self.hp, self.prec, self.per_column = h, hp, prec, per_column
         n, G, k, kc = hp.n, hp.n_units, hp.k, hp.kc
         dev = device
         self.sel_idx = torch.empty(G * k, dtype=torch.int32, device=dev)
         self.sel_count = torch.empty(G, dtype=torch.int32, device=dev)
         self.gain = torch.empty(G * k, dtype=torch.float64, device=dev)
-        self.col_sel = torch.empty(n * kc, dtype=torch.int32, device=dev)
+        self.col_sel = torch.empty(n * kc if per_column else 1, dtype=torch.int32, device=dev)
         self.col_count = torch.zeros(n, dtype=torch.int32, device=dev)
         self.col_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
         m = np.diff(hp.grp_ptr)
@@ -232,11 +233,19 @@ class PartialFactorBuilder:
 
     def fill(self, dp: DeviceProblem, stream=None):
         hp = self.hp
+        if self.per_column:
+            sic.partial_columns(self.h, hp.n, dp.grp_ptr, dp.members, self.sel_idx, self.sel_count, hp.k, hp.kc,
+                                self.col_sel, self.col_count, stream=stream)
+            sic.factor_nnz(self.h, None, self.col_count, hp.n, self.col_ptr, self.ws_nnz, stream=stream)
+            sic.build_factor(self.h, dp.pts, hp.kp, None, 1, self.col_sel, self.col_count, hp.kc, self.col_ptr,
+                             self.row_idx, self.val, self.logv, self.sum_logv, self.ws_fill, stream=stream)
+            return
         sic.partial_columns(self.h, hp.n, dp.grp_ptr, dp.members, self.sel_idx, self.sel_count, hp.k, hp.kc,
-                            self.col_sel, self.col_count, stream=stream)
+                            None, self.col_count, stream=stream)
         sic.factor_nnz(self.h, None, self.col_count, hp.n, self.col_ptr, self.ws_nnz, stream=stream)
-        sic.build_factor(self.h, dp.pts, hp.kp, None, 1, self.col_sel, self.col_count, hp.kc, self.col_ptr,
-                         self.row_idx, self.val, self.logv, self.sum_logv, self.ws_fill, stream=stream)
+        sic.build_factor_partial(self.h, dp.pts, hp.kp, dp.grp_ptr, dp.members, hp.max_m, self.sel_idx,
+                                 self.sel_count, hp.k, self.col_ptr, self.row_idx, self.val, self.logv,
+                                 self.sum_logv, self.ws_fill, stream=stream)
 
     def run(self, dp: DeviceProblem, stream=None):
         self.select(dp, stream)

@@ -29,6 +29,7 @@ EXPORTS = [
     "sic_select_aggregated_workspace", "sic_select_aggregated",
     "sic_select_columns_gain", "sic_select_aggregated_gain", "sic_allocate_global_workspace", "sic_allocate_global",
     "sic_side_state_fp64", "sic_prep_candidates_partial", "sic_select_partial", "sic_partial_columns",
+    "sic_build_factor_partial",
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
@@ -96,6 +97,8 @@ def lib():
             "sic_prep_candidates_partial": (st, [vp, i64, i32, vp, vp, i64, i32, vp, vp, i32]),
             "sic_select_partial": (st, [vp, vp, i64, pk, vp, vp, i64, vp, vp, i32, i32, i32, st, vp, vp, vp, vp]),
             "sic_partial_columns": (st, [vp, i64, vp, vp, i64, vp, vp, i32, i32, vp, vp, vp]),
+            "sic_build_factor_partial": (st, [vp, vp, i64, pk, vp, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp,
+                                              sz, vp]),
             "sic_allocate_global": (st, [vp, i64, vp, vp, vp, i32, i64, vp, vp, sz, vp]),
             "sic_factor_nnz_workspace": (st, [i64, C.POINTER(sz)]),
             "sic_factor_nnz": (st, [vp, vp, i64, vp, i64, vp, vp, sz, vp]),
@@ -362,6 +365,21 @@ def partial_columns(h: Handle, n: int, grp_ptr, members, sel_idx, sel_count, k: 
                                      k, kc, _dptr(col_sel, torch.int32, "col_sel"),
                                      _dptr(col_count, torch.int32, "col_count"), _stream(stream)),
            "sic_partial_columns", h)
+
+
+def build_factor_partial(h: Handle, pts, kp: Kernel, grp_ptr, members, max_m: int, sel_idx, sel_count, k: int,
+                         col_ptr, row_idx, val, logv, sum_logv, ws, stream=None):
+    """Aggregated FP64 fill of a partial-selection pattern (sic_build_factor_partial)."""
+    import torch
+    _check(lib().sic_build_factor_partial(h.ptr, _dptr(pts, torch.float64, "pts"), pts.shape[0], C.byref(kp),
+                                          _dptr(grp_ptr, torch.int64, "grp_ptr"),
+                                          _dptr(members, torch.int64, "members"), grp_ptr.numel() - 1, max_m,
+                                          _dptr(sel_idx, torch.int32, "sel_idx"),
+                                          _dptr(sel_count, torch.int32, "sel_count"), k,
+                                          _dptr(col_ptr, torch.int64, "col_ptr"), _dptr(row_idx, torch.int32, "row_idx"),
+                                          _dptr(val, torch.float64, "val"), _dptr(logv, torch.float64, "logv"),
+                                          _dptr(sum_logv, torch.float64, "sum_logv"), _dptr(ws), ws.numel(),
+                                          _stream(stream)), "sic_build_factor_partial", h)
 
 
 def side_state_fp64(h: Handle, pts, kp: Kernel, sel_idx, sel_count, k: int, grp_ptr=None, max_m: int = 1,

@@ -91,14 +91,16 @@ def test_partial_selection_matches_oracle(env, oracle_lib, prec_name):
         assert same >= len(sample) - 2
 
 
-def test_partial_fill_matches_oracle(env, oracle_lib):
-    """The pattern of a partial selection (member i: later members + picks after i) filled
-    column by column in FP64, against the oracle's dense per-column fill."""
+@pytest.mark.parametrize("per_column", [False, True])
+def test_partial_fill_matches_oracle(env, oracle_lib, per_column):
+    """The pattern of a partial selection (member i: later members + picks after i) filled in
+    FP64 -- aggregated per group (one LDL^T of the group's members and picks) and column by
+    column from the expanded lists -- against the oracle's dense per-column fill."""
     torch, sic, pipeline, h = env
     oracle = oracle_lib
     kp, hp = _problem(env, 4096, 6, 48, 12)
     dp = pipeline.DeviceProblem(hp)
-    fb = pipeline.PartialFactorBuilder(h, hp, sic.SIC_FP64)
+    fb = pipeline.PartialFactorBuilder(h, hp, sic.SIC_FP64, per_column=per_column)
     fb.run(dp)
     h.sync()
     okp = _okernel(oracle, kp)
@@ -122,7 +124,9 @@ def test_partial_fill_matches_oracle(env, oracle_lib):
         assert e <= 1e-8, (i, e)
         assert abs(logv[i] - lv) <= 1e-9, i
     assert nnz == sum(1 + len(v) for v in col.values())
-    print(f"fill: nnz {nnz}, worst column error {worst:.2e}")
+    _, _, _, ologv = oracle.factor_columns(okp, hp.pts, [np.array(col[i], np.int32) for i in range(hp.n)])
+    assert float(fb.sum_logv.cpu()[0]) == pytest.approx(float(ologv.sum()), rel=1e-9)
+    print(f"fill (per column {per_column}): nnz {nnz}, worst column error {worst:.2e}")
 
 
 def test_partial_beats_candidates_after_the_group(env):
