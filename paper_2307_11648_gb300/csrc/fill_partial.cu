@@ -20,7 +20,7 @@
 
 namespace {
 
-constexpr int FP_NT = 128;
+constexpr int FP_NT = 256;
 
 __device__ __forceinline__ int fpk(int a, int b) { return a * (a + 1) / 2 + b; }
 

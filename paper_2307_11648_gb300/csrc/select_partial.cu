@@ -18,9 +18,9 @@
 //   insert   the pick q goes to its place p (the number of columns of later points): the
 //            columns before p stay; the new column is Theta_{:,q | first p} / sqrt(Theta_{qq |
 //            first p}) by left-looking; the columns from p on are downdated in place by it
-//            column by column (eq. chol_partial_update): every thread forms the column's
-//            rotation from the pivot row, every row below the pivot applies it (one barrier
-//            per column).
+//            column by column (eq. chol_partial_update): one warp forms the rotations in order
+//            from the pivot rows (the targets and picks), then every candidate row applies them
+//            all, with one barrier in between.
 // Columns live in physical slots in insertion order; `ordr/ords/opos` map the logical
 // (latest-first) order to the pivot row, the slot and the target position (INT_MAX for a
 // pick).  One CTA per group (persistent), L in shared memory, rows spread over the threads.
@@ -38,7 +38,7 @@ __device__ __forceinline__ double pt_div(double a, double b) { return a / b; }
 struct PtLayout {
     int R, W, P;  // rows (candidates + targets), columns (targets + picks), row pitch (odd)
     __host__ __device__ size_t bytes(size_t tsz) const {
-        return tsz * ((size_t)R * P + 4 * (size_t)R) + sizeof(int) * (2 * (size_t)R + 3 * (size_t)W);
+        return tsz * ((size_t)R * P + 4 * (size_t)R + 3 * (size_t)W) + sizeof(int) * (2 * (size_t)R + 3 * (size_t)W);
     }
 };
 
@@ -52,7 +52,10 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
     T* Lm = reinterpret_cast<T*>(smraw);              // [R][P]
     T* X = Lm + (size_t)Lay.R * Lay.P;                // [3][R] coordinates
     T* xv = X + 3 * Lay.R;                            // [R] downdate vector
-    int* pos = reinterpret_cast<int*>(xv + Lay.R);    // [R] positions
+    T* rc = xv + Lay.R;                               // [W] rotation of logical column c: cos,
+    T* rsn = rc + Lay.W;                              //     sin,
+    T* ric = rsn + Lay.W;                             //     1 / cos
+    int* pos = reinterpret_cast<int*>(ric + Lay.W);   // [R] positions
     int* rank = pos + Lay.R;                          // [R] logical column of an element row, -1 otherwise
     int* ordr = rank + Lay.R;                         // [W] pivot row of logical column c
     int* ords = ordr + Lay.W;                         // [W] physical slot of logical column c
@@ -164,42 +167,52 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
                 xv[r] = (r == q) ? (T)0 : u;
             }
             __syncthreads();
-            // one barrier per column: every thread forms the column's rotation from the pivot
-            // row's entry and downdate value (final since the previous column's pass), the rows
-            // below apply it; the pivot row's new diagonal is stored one pass later (by the
-            // thread that owns the row), when no thread reads the old one any more
-            bool bad = false;
-            int pend = -1;  // element (row * PP + slot) whose new diagonal waits
-            T pend_v = (T)0;
-            for (int c = p; c < ncol; ++c) {
-                if (pend >= 0) {
-                    Lm[pend] = pend_v;
-                    pend = -1;
-                }
-                const int e = ordr[c], s = ords[c];
-                const T lee = Lm[e * PP + s], xe = xv[e];
-                const T rr2 = fma(-xe, xe, lee * lee);
-                bad = bad || !(rr2 > (T)0) || !(lee > (T)0);
-                const T rr = sic_sqrt(rr2 > (T)0 ? rr2 : (T)0);
-                const T cth = rr / lee, sth = xe / lee, icth = lee / rr;
-                for (int r = tid; r < R; r += PT_NT) {
-                    const int rk = rank[r];
-                    if (r == e) {
-                        pend = r * PP + s;
-                        pend_v = rr;
-                    } else if (r != q && (rk < 0 || rk > c)) {
+            // the downdate of the columns from p on, in two phases.  (1) Warp 0 forms the
+            // columns' rotations in order from the pivot rows alone -- the rows of the targets and
+            // picks at earlier positions than q, which are the pivots of those same columns --
+            // each lane carrying a few of those rows; the rotations go to shared memory.  (2)
+            // Every other row below (the candidates) applies them in order, with no barrier
+            // between columns.
+            if (warp == 0) {
+                bool bad = false;
+                for (int c = p; c < ncol; ++c) {
+                    const int e = ordr[c], s = ords[c];
+                    const T lee = Lm[e * PP + s], xe = xv[e];
+                    const T rr2 = fma(-xe, xe, lee * lee);
+                    bad = bad || !(rr2 > (T)0) || !(lee > (T)0);
+                    const T rr = sic_sqrt(rr2 > (T)0 ? rr2 : (T)0);
+                    const T cth = rr / lee, sth = xe / lee, icth = lee / rr;
+                    __syncwarp();  // every lane has read the pivot's entries
+                    if (lane == 0) {
+                        rc[c] = cth;
+                        rsn[c] = sth;
+                        ric[c] = icth;
+                        Lm[e * PP + s] = rr;
+                    }
+                    for (int c2 = c + 1 + lane; c2 < ncol; c2 += 32) {
+                        const int r = ordr[c2];
                         const T xr = xv[r];
                         const T nl = (Lm[r * PP + s] - sth * xr) * icth;
                         Lm[r * PP + s] = nl;
                         xv[r] = cth * xr - sth * nl;
                     }
+                    __syncwarp();  // the next pivot row is final
                 }
-                __syncthreads();
+                if (bad && lane == 0) s_fail = 2;
             }
-            if (pend >= 0) Lm[pend] = pend_v;
-            if (bad && tid == 0) s_fail = 2;
             __syncthreads();
             if (s_fail) return false;
+            for (int r = tid; r < R; r += PT_NT) {
+                if (rank[r] >= 0 || r == q) continue;
+                T xr = xv[r];
+                for (int c = p; c < ncol; ++c) {
+                    const int s = ords[c];
+                    const T nl = (Lm[r * PP + s] - rsn[c] * xr) * ric[c];
+                    Lm[r * PP + s] = nl;
+                    xr = rc[c] * xr - rsn[c] * nl;
+                }
+            }
+            __syncthreads();
             // row q now holds a pivot: nothing in the columns after its own; the column maps
             // shift one place from p on (each thread carries one entry across the barrier)
             for (int c = p + tid; c < ncol; c += PT_NT) Lm[q * PP + ords[c]] = (T)0;

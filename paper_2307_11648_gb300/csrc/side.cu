@@ -21,7 +21,7 @@
 
 namespace {
 
-constexpr int SIDE_NT = 128;
+constexpr int SIDE_NT = 256;
 
 __device__ __forceinline__ int spk(int a, int b) { return a * (a + 1) / 2 + b; }
 
