@@ -9,7 +9,7 @@
 // x_r = -sum_{c = r+1..a} L_cr x_c;  log Theta_{u_a u_a | s \ u_a} = log d_a.  One LDL^T per
 // group serves every member, as in the consecutive-group fill, instead of one per column.
 //
-// One CTA of 128 threads per group (persistent): the union sorted by rank counting, Theta in
+// One CTA of 256 threads per group (persistent): the union sorted by rank counting, Theta in
 // packed lower storage (FP64 Matern from the table-driven exp), a right-looking LDL^T flat over
 // the CTA (two barriers per pivot, the next pivot's reciprocal formed by the thread that
 // produces it), then one warp per member for the back substitution (lanes own rows, the

@@ -11,7 +11,7 @@
 // them (eq. cond_select), so var1 is the diagonal D of the LDL^T of Theta_SS (S in pick
 // order) and var2 the diagonal of the LDL^T of Theta over [P; S] at the picks' rows.
 //
-// One CTA of 128 threads per unit (persistent): Theta over [P; S] is built once in packed
+// One CTA of 256 threads per unit (persistent): Theta over [P; S] is built once in packed
 // lower storage (FP64 Matern from the table-driven exp of the fill), its trailing S
 // block copied; both factorisations run right-looking, flat over the CTA so that every
 // warp carries FP64 work, and share each pivot's two barriers: (1) the column of
