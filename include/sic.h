@@ -339,6 +339,27 @@ sic_status sic_factor_nnz_noalloc(sic_handle* h, const int64_t* grp_ptr, int64_t
  * without groups, <= 64).  Needs sic_build_factor_workspace bytes of ws. */
 
 sic_status sic_build_factor_workspace(int64_t n, size_t* bytes);
+/* Autotuned variant (this library's launch tuning; the paper has no counterpart): the same
+ * arguments and results as sic_build_factor, but it runs the fill once per candidate split of
+ * the group-size classes (groups of <= split members in the 4-worker launch, larger in the
+ * 8-worker one; candidates 8 .. 64 capped at max_m), times each with CUDA events on `stream`
+ * (synchronising it; not for stream capture), keeps the fastest in the handle for this
+ * (k, max_m) -- later sic_build_factor calls with the same k and max_m use it -- and leaves
+ * the outputs of that configuration (they do not depend on the split).  *best_split [host]
+ * receives the choice (may be NULL).  sic_tune_save / sic_tune_load write and read the
+ * handle's table as text ("op a b value ms" per line, op 1 = this split, a = k, b = max_m);
+ * a line that does not parse is skipped and reported as SIC_ERR_INVALID.  sic_tune_count /
+ * sic_tune_entry list the table.  [device / host] */
+sic_status sic_tune_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                 const int64_t* grp_ptr, int64_t n_grp, int32_t max_m, const int32_t* sel_idx,
+                                 const int32_t* sel_count, int32_t k, const int64_t* col_ptr, int32_t* row_idx,
+                                 double* val, double* logv, double* sum_logv, void* ws, size_t ws_bytes,
+                                 void* stream, int32_t* best_split);
+sic_status sic_tune_save(const sic_handle* h, const char* path);
+sic_status sic_tune_load(sic_handle* h, const char* path);
+int32_t sic_tune_count(const sic_handle* h);
+sic_status sic_tune_entry(const sic_handle* h, int32_t i, int32_t* op, int32_t* a, int32_t* b, int32_t* value,
+                          float* ms);
 sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
                             const int64_t* grp_ptr, int64_t n_grp, int32_t max_m, const int32_t* sel_idx,
                             const int32_t* sel_count, int32_t k, const int64_t* col_ptr, int32_t* row_idx,

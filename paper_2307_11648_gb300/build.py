@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsic.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "select_columns.cu", "select_aggregated.cu", "select_agg_reg.cu", "select_single.cu", "fill.cu", "apply.cu", "learned.cu", "mlp_tc.cu", "pcg.cu", "gp.cu", "allocate.cu", "side.cu", "select_partial.cu", "fill_partial.cu"]
+CU_SOURCES = ["api.cu", "select_columns.cu", "select_aggregated.cu", "select_agg_reg.cu", "select_single.cu", "fill.cu", "apply.cu", "learned.cu", "mlp_tc.cu", "pcg.cu", "gp.cu", "allocate.cu", "side.cu", "select_partial.cu", "fill_partial.cu", "tune.cu"]
 CXX_SOURCES = ["prep.cpp"]
 
 

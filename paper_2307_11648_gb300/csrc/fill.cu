@@ -454,7 +454,10 @@ extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t
     // two size classes when the groups can be large: the shared-memory layout (and so the
     // CTAs per SM) of each launch fits its own largest group, so the many small groups run
     // at higher occupancy; each launch skips the other's groups
-    const int split = (max_m > FILL_M_SPLIT) ? FILL_M_SPLIT : max_m;
+    // the size-class split: tuned for this (k, max_m) by sic_tune_build_factor, else FILL_M_SPLIT
+    int split = tune_get(h, TUNE_FILL_SPLIT, k, max_m, FILL_M_SPLIT);
+    if (split > max_m) split = max_m;
+    if (split < 1) split = 1;
     for (int c = 0; c < 2; ++c) {
         const int lo = c == 0 ? 1 : split + 1, hi = c == 0 ? split : max_m;
         if (lo > hi) break;

@@ -14,12 +14,27 @@ struct DevStatus {
     long long unit;
 };
 
+// One tuned launch choice: op (what is tuned), a bucket key (a, b), the chosen value and its
+// measured time.  The handle keeps a small table (sic_tune_* in tune.cpp).
+struct TuneEntry {
+    int32_t op, a, b, value;
+    float ms;
+};
+constexpr int TUNE_MAX = 64;
+constexpr int TUNE_FILL_SPLIT = 1;  // k_fill size classes: groups of <= value members in the first launch
+
 struct sic_handle {
     int device;
     int num_sms;
     DevStatus* d_status;  // one word in device memory, owned by the handle
     long long last_unit;
+    int n_tune;
+    TuneEntry tune[TUNE_MAX];
 };
+
+// tuned value for (op, a, b), or `fallback` (tune.cpp)
+int tune_get(const sic_handle* h, int op, int a, int b, int fallback);
+void tune_put(sic_handle* h, int op, int a, int b, int value, float ms);
 
 __device__ __forceinline__ void record_error(DevStatus* st, int code, long long unit) {
     if (atomicCAS(&st->code, 0, code) == 0) st->unit = unit;

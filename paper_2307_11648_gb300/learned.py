@@ -121,6 +121,11 @@ class LearnedFactorBuilder:
         self.select(dp, stream)
         self.fill(dp, stream)
 
+    def tune(self, dp, stream=None) -> int:
+        """Propose, then tune the fill's launch split on the reduced problem (kept in the handle)."""
+        self.propose(dp, stream)
+        return self.fb.tune(self._reduced_device(dp), stream)
+
     @property
     def sum_logv(self):
         return self.fb.sum_logv

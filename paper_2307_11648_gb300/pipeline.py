@@ -189,6 +189,16 @@ class FactorBuilder:
         self.select(dp, stream)
         self.fill(dp, stream)
 
+    def tune(self, dp: DeviceProblem, stream=None) -> int:
+        """Select, then tune the fill's launch split on this problem (kept in the handle for
+        later fills with the same k and group bound); returns the chosen split."""
+        hp = self.hp
+        self.select(dp, stream)
+        sic.factor_nnz(self.h, dp.grp_ptr, self.sel_count, hp.n, self.col_ptr, self.ws_nnz, stream=stream)
+        return sic.tune_build_factor(self.h, dp.pts, hp.kp, dp.grp_ptr, hp.max_m, self.sel_idx, self.sel_count, hp.k,
+                                     self.col_ptr, self.row_idx, self.val, self.logv, self.sum_logv, self.ws_fill,
+                                     stream=stream)
+
     def sel_lists(self):
         si = self.sel_idx.view(-1, self.hp.k).cpu().numpy()
         sc = self.sel_count.cpu().numpy()

@@ -29,7 +29,8 @@ EXPORTS = [
     "sic_select_aggregated_workspace", "sic_select_aggregated",
     "sic_select_columns_gain", "sic_select_aggregated_gain", "sic_allocate_global_workspace", "sic_allocate_global",
     "sic_side_state_fp64", "sic_prep_candidates_partial", "sic_select_partial", "sic_partial_columns",
-    "sic_build_factor_partial",
+    "sic_build_factor_partial", "sic_tune_build_factor", "sic_tune_save", "sic_tune_load", "sic_tune_count",
+    "sic_tune_entry",
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
     "sic_build_factor",
     "sic_apply_factor_workspace", "sic_apply_factor",
@@ -104,6 +105,13 @@ def lib():
             "sic_factor_nnz": (st, [vp, vp, i64, vp, i64, vp, vp, sz, vp]),
             "sic_factor_nnz_noalloc": (st, [vp, vp, i64, vp, i64, vp, vp]),
             "sic_build_factor_workspace": (st, [i64, C.POINTER(sz)]),
+            "sic_tune_build_factor": (st, [vp, vp, i64, pk, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, sz,
+                                           vp, C.POINTER(i32)]),
+            "sic_tune_save": (st, [vp, C.c_char_p]),
+            "sic_tune_load": (st, [vp, C.c_char_p]),
+            "sic_tune_count": (i32, [vp]),
+            "sic_tune_entry": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                    C.POINTER(C.c_float)]),
             "sic_build_factor": (st, [vp, vp, i64, pk, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
             "sic_apply_factor_workspace": (st, [i64, i32, st, C.POINTER(sz)]),
             "sic_apply_factor": (st, [vp, i64, vp, vp, vp, st, vp, vp, i32, vp, sz, vp]),
@@ -365,6 +373,43 @@ def partial_columns(h: Handle, n: int, grp_ptr, members, sel_idx, sel_count, k: 
                                      k, kc, _dptr(col_sel, torch.int32, "col_sel"),
                                      _dptr(col_count, torch.int32, "col_count"), _stream(stream)),
            "sic_partial_columns", h)
+
+
+def tune_build_factor(h: Handle, pts, kp: Kernel, grp_ptr, max_m: int, sel_idx, sel_count, k: int, col_ptr,
+                      row_idx, val, logv, sum_logv, ws, stream=None) -> int:
+    """sic_tune_build_factor: the fill with its group-size split tuned (and kept in the handle)."""
+    import torch
+    n = pts.shape[0]
+    n_grp = grp_ptr.numel() - 1 if grp_ptr is not None else n
+    best = C.c_int32(0)
+    _check(lib().sic_tune_build_factor(h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp),
+                                       _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp, max_m,
+                                       _dptr(sel_idx, torch.int32, "sel_idx"),
+                                       _dptr(sel_count, torch.int32, "sel_count"), k,
+                                       _dptr(col_ptr, torch.int64, "col_ptr"), _dptr(row_idx, torch.int32, "row_idx"),
+                                       _dptr(val, torch.float64, "val"), _dptr(logv, torch.float64, "logv"),
+                                       _dptr(sum_logv, torch.float64, "sum_logv"), _dptr(ws), ws.numel(),
+                                       _stream(stream), C.byref(best)), "sic_tune_build_factor", h)
+    return best.value
+
+
+def tune_save(h: Handle, path: str):
+    _check(lib().sic_tune_save(h.ptr, str(path).encode()), "sic_tune_save")
+
+
+def tune_load(h: Handle, path: str):
+    _check(lib().sic_tune_load(h.ptr, str(path).encode()), "sic_tune_load")
+
+
+def tune_table(h: Handle):
+    """The handle's tuned choices as a list of (op, a, b, value, ms)."""
+    out = []
+    for i in range(lib().sic_tune_count(h.ptr)):
+        v = [C.c_int32() for _ in range(4)]
+        ms = C.c_float()
+        _check(lib().sic_tune_entry(h.ptr, i, *[C.byref(x) for x in v], C.byref(ms)), "sic_tune_entry")
+        out.append((v[0].value, v[1].value, v[2].value, v[3].value, ms.value))
+    return out
 
 
 def build_factor_partial(h: Handle, pts, kp: Kernel, grp_ptr, members, max_m: int, sel_idx, sel_count, k: int,
