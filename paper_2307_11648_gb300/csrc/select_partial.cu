@@ -35,6 +35,28 @@ constexpr int PT_NT = 512;
 __device__ __forceinline__ float pt_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double pt_div(double a, double b) { return a / b; }
 
+// A column's rotation from its pivot entry lee and downdate value xe: the new pivot
+// rr = sqrt(lee^2 - xe^2), cos = rr / lee, sin = xe / lee and 1 / cos.  FP32 takes one fast
+// reciprocal and one reciprocal square root (it sits on the insertion's serial chain); FP64
+// divides exactly.
+__device__ __forceinline__ bool pt_rot(float lee, float xe, float& rr, float& cth, float& sth, float& icth) {
+    const float rr2 = fmaf(-xe, xe, lee * lee);
+    const float irr = rsqrtf(rr2), ilee = __fdividef(1.f, lee);
+    rr = rr2 * irr;
+    cth = rr * ilee;
+    sth = xe * ilee;
+    icth = lee * irr;
+    return rr2 > 0.f && lee > 0.f;
+}
+__device__ __forceinline__ bool pt_rot(double lee, double xe, double& rr, double& cth, double& sth, double& icth) {
+    const double rr2 = fma(-xe, xe, lee * lee);
+    rr = sqrt(rr2 > 0.0 ? rr2 : 0.0);
+    cth = rr / lee;
+    sth = xe / lee;
+    icth = lee / rr;
+    return rr2 > 0.0 && lee > 0.0;
+}
+
 struct PtLayout {
     int R, W, P;  // rows (candidates + targets), columns (targets + picks), row pitch (odd)
     __host__ __device__ size_t bytes(size_t tsz) const {
@@ -177,11 +199,8 @@ __global__ void __launch_bounds__(PT_NT, 1) k_select_partial(
                 bool bad = false;
                 for (int c = p; c < ncol; ++c) {
                     const int e = ordr[c], s = ords[c];
-                    const T lee = Lm[e * PP + s], xe = xv[e];
-                    const T rr2 = fma(-xe, xe, lee * lee);
-                    bad = bad || !(rr2 > (T)0) || !(lee > (T)0);
-                    const T rr = sic_sqrt(rr2 > (T)0 ? rr2 : (T)0);
-                    const T cth = rr / lee, sth = xe / lee, icth = lee / rr;
+                    T rr, cth, sth, icth;
+                    bad = !pt_rot(Lm[e * PP + s], xv[e], rr, cth, sth, icth) || bad;
                     __syncwarp();  // every lane has read the pivot's entries
                     if (lane == 0) {
                         rc[c] = cth;
