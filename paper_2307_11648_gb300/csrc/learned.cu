@@ -475,8 +475,19 @@ TrainWs train_ws(long long B) {
     return w;
 }
 
+// the training GEMMs: 128-wide products in BF16 on the tensor cores (gemm_tc) when `tc`, the
+// rest (and everything in the FP32 mode) in the CUDA-core tiled GEMM; K-splits summed in a
+// fixed order either way
 void gemm(cudaStream_t s, int M, int N, int K, const float* A, long long sam, long long sak, const float* B,
-          long long sbk, long long sbn, float* C, int nz, float* part) {
+          long long sbk, long long sbn, float* C, int nz, float* part, sic_handle* tc = nullptr) {
+    if (tc && N == HID) {
+        gemm_tc(tc, s, M, K, A, sam, sak, B, sbk, sbn, nz == 1 ? C : part, nz);
+        if (nz > 1) {
+            long long len = (long long)M * N;
+            k_sum_splits<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(part, nz, len, C);
+        }
+        return;
+    }
     int kchunk = (K + nz - 1) / nz;
     kchunk = (kchunk + 15) / 16 * 16;
     dim3 grid((N + 63) / 64, (M + 63) / 64, nz);
@@ -576,10 +587,11 @@ extern "C" sic_status sic_mlp_grads(sic_handle* h, const float* params, const fl
     const unsigned ew = (unsigned)((B * HID + 255) / 256);
     k_round_params<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, q, NPARAM, bf16);
     k_round_rows<<<(unsigned)((B * NF + 255) / 256), 256, 0, s>>>(feat, xr, B * NF, bf16);
-    // forward
-    gemm(s, (int)B, HID, NF, xr, NF, 1, q + OFF_W1, HID, 1, Z1, 1, part);
+    // forward (with bf16: the 128-wide products on the tensor cores, operands in BF16)
+    sic_handle* tc = bf16 ? h : nullptr;
+    gemm(s, (int)B, HID, NF, xr, NF, 1, q + OFF_W1, HID, 1, Z1, 1, part, tc);
     k_bias_gelu<<<ew, 256, 0, s>>>(Z1, H1, q + OFF_B1, B, bf16);
-    gemm(s, (int)B, HID, HID, H1, HID, 1, q + OFF_W2, HID, 1, Z2, 1, part);
+    gemm(s, (int)B, HID, HID, H1, HID, 1, q + OFF_W2, HID, 1, Z2, 1, part, tc);
     k_bias_gelu<<<ew, 256, 0, s>>>(Z2, H2, q + OFF_B2, B, 0);
     k_head<<<(unsigned)((B + 3) / 4), 128, 0, s>>>(H2, q + OFF_W3, q + OFF_B3, label, B, pos_weight, score, dS,
                                                    lrow);
@@ -590,13 +602,13 @@ extern "C" sic_status sic_mlp_grads(sic_handle* h, const float* params, const fl
     // dZ2 into H2's storage (H2 is no longer needed)
     k_dz2<<<ew, 256, 0, s>>>(dS, q + OFF_W3, Z2, H2, B);
     float* dZ2 = H2;
-    gemm(s, HID, HID, (int)B, H1, 1, HID, dZ2, HID, 1, grads + OFF_W2, L.nz, part);
+    gemm(s, HID, HID, (int)B, H1, 1, HID, dZ2, HID, 1, grads + OFF_W2, L.nz, part, tc);
     k_colsum<<<1, 128, 0, s>>>(dZ2, B, HID, grads + OFF_B2);
     // dH1 = dZ2 W2^T  -> into Z2's storage, then dZ1 = dH1 .* gelu'(Z1)
-    gemm(s, (int)B, HID, HID, dZ2, HID, 1, q + OFF_W2, 1, HID, Z2, 1, part);
+    gemm(s, (int)B, HID, HID, dZ2, HID, 1, q + OFF_W2, 1, HID, Z2, 1, part, tc);
     float* dZ1 = Z2;
     k_mul_dgelu<<<ew, 256, 0, s>>>(dZ1, Z1, B * HID);
-    gemm(s, NF, HID, (int)B, xr, 1, NF, dZ1, HID, 1, grads + OFF_W1, L.nz, part);
+    gemm(s, NF, HID, (int)B, xr, 1, NF, dZ1, HID, 1, grads + OFF_W1, L.nz, part, tc);
     k_colsum<<<1, 128, 0, s>>>(dZ1, B, HID, grads + OFF_B1);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;

@@ -270,7 +270,128 @@ __global__ void k_wait_selftest(long long cap, int* out, DevStatus* st) {
     }
 }
 
+// ---- training GEMMs on the tensor cores ----
+//
+// C (M x 128, FP32, row-major) = A (M x K) * B (K x 128): A(m, k) = A[m * sam + k * sak],
+// B(k, n) = B[k * sbk + n * sbn], so the same kernel serves X W, H^T dZ and dZ W^T.  Each CTA
+// owns a 128-row tile of C and one K-range (split z, partial written at C + z * M * 128);
+// per chunk of 64 along K, the 128 threads stage A and B rounded to BF16 into the K-major
+// core-matrix layout (rows beyond M and entries beyond the K-range are zero), one thread
+// issues four K = 16 MMAs accumulating in TMEM, and a bounded mbarrier wait ends the chunk.
+// The epilogue reads the accumulator row by row (thread = row).
+constexpr int GT_K = 64;                  // K per staged chunk
+constexpr int GSA = 0;                    // 128 x 64 bf16 = 16 KiB
+constexpr int GSB = GSA + 128 * GT_K * 2; // 128 x 64 bf16 = 16 KiB
+constexpr int GSBAR = GSB + 128 * GT_K * 2;
+// the dynamic shared memory requested is padded to 64 KiB so that at most three CTAs share an
+// SM: 3 x 128 of the 512 TMEM columns, no CTA waits in tcgen05.alloc
+constexpr int SMEM_GT = 64 * 1024;
+static_assert(GSBAR + 16 <= SMEM_GT, "training GEMM shared memory");
+
+__global__ void __launch_bounds__(TC_NT) k_gemm_tc(int M, int K, int kchunk, const float* __restrict__ A,
+                                                   long long sam, long long sak, const float* __restrict__ B,
+                                                   long long sbk, long long sbn, float* __restrict__ C,
+                                                   DevStatus* st) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + GSBAR);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + GSBAR + 8);
+    const uint32_t bar_a = smem_u32(bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int m0 = blockIdx.x * 128;
+    const int kb = blockIdx.y * kchunk, ke = min(K, kb + kchunk);
+    uint32_t parity = 0;
+    bool failed = false, any = false;
+    for (int k0 = kb; k0 < ke && !failed; k0 += GT_K) {
+        // stage: consecutive threads walk the operand's contiguous direction
+        for (int e = tid; e < 128 * GT_K; e += TC_NT) {
+            int m, kk;
+            if (sak == 1) { m = e / GT_K; kk = e % GT_K; } else { kk = e / 128; m = e % 128; }
+            const int k = k0 + kk;
+            const float v = (m0 + m < M && k < ke) ? A[(long long)(m0 + m) * sam + (long long)k * sak] : 0.f;
+            *reinterpret_cast<__nv_bfloat16*>(sm + GSA + core_off(m, kk, GT_K)) = __float2bfloat16_rn(v);
+        }
+        for (int e = tid; e < 128 * GT_K; e += TC_NT) {
+            int n, kk;
+            if (sbk == 1) { n = e / GT_K; kk = e % GT_K; } else { kk = e / 128; n = e % 128; }
+            const int k = k0 + kk;
+            const float v = (k < ke) ? B[(long long)k * sbk + (long long)n * sbn] : 0.f;
+            *reinterpret_cast<__nv_bfloat16*>(sm + GSB + core_off(n, kk, GT_K)) = __float2bfloat16_rn(v);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < GT_K / 16; ++q) {
+                const uint64_t dA = smem_desc(smem_u32(sm + GSA + q * 256), 128, (GT_K / 8) * 128);
+                const uint64_t dB = smem_desc(smem_u32(sm + GSB + q * 256), 128, (GT_K / 8) * 128);
+                mma_f16(tmem, dA, dB, (any || q > 0) ? 1u : 0u);
+            }
+            mma_commit(bar_a);
+        }
+        any = true;
+        if (!bar_wait(bar_a, parity)) failed = true;
+        parity ^= 1u;
+        if (__syncthreads_or(failed)) failed = true;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (!failed) {
+        float* Cz = C + (long long)blockIdx.y * M * 128;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const int m = m0 + tid;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float v[32];
+            if (any) {
+                tmem_ld32(lane_addr + c * 32, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.f;  // an empty K-range
+            }
+            if (m < M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) Cz[(long long)m * 128 + c * 32 + j] = v[j];
+            }
+        }
+    } else if (tid == 0) {
+        record_error(st, SIC_ERR_TIMEOUT, blockIdx.x);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
 }  // namespace
+
+sic_status gemm_tc(sic_handle* h, cudaStream_t s, int M, int K, const float* A, long long sam, long long sak,
+                   const float* B, long long sbk, long long sbn, float* C, int nz) {
+    (void)h;
+    int kchunk = (K + nz - 1) / nz;
+    kchunk = (kchunk + GT_K - 1) / GT_K * GT_K;
+    SIC_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GT));
+    dim3 grid((unsigned)((M + 127) / 128), (unsigned)nz);
+    k_gemm_tc<<<grid, TC_NT, SMEM_GT, s>>>(M, K, kchunk, A, sam, sak, B, sbk, sbn, C, h->d_status);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
 
 extern "C" sic_status sic_selftest_wait_timeout(sic_handle* h, int64_t cap, int32_t* out, void* stream) {
     if (!h || !out || cap < 1) return SIC_ERR_INVALID;

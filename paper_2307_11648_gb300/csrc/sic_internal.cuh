@@ -199,6 +199,11 @@ sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const s
 // fixed-order sum of log v (fill.cu); ws holds sic_build_factor_workspace(n) bytes
 sic_status launch_sum_logv(const double* logv, long long n, double* sum_logv, void* ws, cudaStream_t s);
 
+// tcgen05 BF16 GEMM of the training (mlp_tc.cu): C (M x 128 FP32) [+ z * M * 128 per K-split]
+// = A (M x K, strides sam / sak) * B (K x 128, strides sbk / sbn), operands rounded to BF16
+sic_status gemm_tc(sic_handle* h, cudaStream_t s, int M, int K, const float* A, long long sam, long long sak,
+                   const float* B, long long sbk, long long sbn, float* C, int nz);
+
 // tcgen05 scoring kernel of the proposal network (mlp_tc.cu)
 sic_status sic_proposal_score_tc(sic_handle* h, const float* params, const float* feat, int64_t rows, float* score,
                                  cudaStream_t s);
