@@ -180,3 +180,13 @@ def test_partial_errors_reported(env):
                            sic.SIC_FP64, fb.sel_idx, fb.sel_count)
     fb.run(dp)
     h.sync()
+
+
+def test_partial_no_groups(env):
+    torch, sic, pipeline, h = env
+    kp = sic.kernel(2, 3, 0.1, 1.0, 1e-6)
+    pts = torch.from_numpy(synthetic.points(50, 2, 1)).cuda()
+    gp = torch.zeros(1, dtype=torch.int64, device="cuda")
+    z32 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sic.select_partial(h, pts, kp, gp, gp, gp, z32, 8, 4, 4, sic.SIC_FP32_MIXED, z32, z32)
+    h.sync()

@@ -153,3 +153,15 @@ def test_side_state_errors_reported(env):
         _run_side(env, pts, kp, [np.array([5, 6], np.int32)], [5], 4)
     v1, v2, g = _run_side(env, pts, kp, [np.array([5, 6], np.int32), np.array([], np.int32)], [2, 0], 4)
     assert v1[0, 0] == pytest.approx(1.0 + 1e-8) and np.isfinite(g[0, :2]).all() and v1[1, 0] == -1.0
+
+
+def test_side_state_no_units(env):
+    torch, sic, pipeline, h = env
+    kp = sic.kernel(2, 3, 0.1, 1.0, 1e-8)
+    pts = torch.from_numpy(synthetic.points(50, 2, 1)).cuda()
+    z = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sic.side_state_fp64(h, pts, kp, z, z[:0], 4, gain=out)  # nothing launched
+    h.sync()
+    with pytest.raises(sic.SicError):  # no output requested
+        sic.side_state_fp64(h, pts, kp, z, z[:0], 4)
