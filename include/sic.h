@@ -344,10 +344,12 @@ sic_status sic_build_factor_workspace(int64_t n, size_t* bytes);
  * the group-size classes (groups of <= split members in the 4-worker launch, larger in the
  * 8-worker one; candidates 8 .. 64 capped at max_m), times each with CUDA events on `stream`
  * (synchronising it; not for stream capture), keeps the fastest in the handle for this
- * (k, max_m) -- later sic_build_factor calls with the same k and max_m use it -- and leaves
- * the outputs of that configuration (they do not depend on the split).  *best_split [host]
+ * (k, max_m), then times 8 against 12 worker warps for the large-group launch at that split;
+ * later sic_build_factor calls with the same k and max_m use both choices; it leaves the
+ * outputs of the chosen configuration (they do not depend on either choice).  *best_split [host]
  * receives the choice (may be NULL).  sic_tune_save / sic_tune_load write and read the
- * handle's table as text ("op a b value ms" per line, op 1 = this split, a = k, b = max_m);
+ * handle's table as text ("op a b value ms" per line, op 1 = the split, op 2 = the
+ * large-group launch's worker threads (256 or 384), a = k, b = max_m);
  * a line that does not parse is skipped and reported as SIC_ERR_INVALID.  sic_tune_count /
  * sic_tune_entry list the table.  [device / host] */
 sic_status sic_tune_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,

@@ -458,12 +458,13 @@ extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t
     int split = tune_get(h, TUNE_FILL_SPLIT, k, max_m, FILL_M_SPLIT);
     if (split > max_m) split = max_m;
     if (split < 1) split = 1;
+    const int big_nt = tune_get(h, TUNE_FILL_BIGNT, k, max_m, 256) == 384 ? 384 : 256;
     for (int c = 0; c < 2; ++c) {
         const int lo = c == 0 ? 1 : split + 1, hi = c == 0 ? split : max_m;
         if (lo > hi) break;
         const size_t sm = fill_smem_bytes(k, hi);
-        auto kern = (c == 0) ? k_fill<128> : k_fill<256>;
-        const int block = (c == 0 ? 128 : 256) + 32;
+        auto kern = (c == 0) ? k_fill<128> : (big_nt == 384 ? k_fill<384> : k_fill<256>);
+        const int block = (c == 0 ? 128 : big_nt) + 32;
         SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int grid = persistent_grid(h, kern, block, sm, n_grp);
         kern<<<grid, block, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp, sel_idx,

@@ -22,6 +22,7 @@ struct TuneEntry {
 };
 constexpr int TUNE_MAX = 64;
 constexpr int TUNE_FILL_SPLIT = 1;  // k_fill size classes: groups of <= value members in the first launch
+constexpr int TUNE_FILL_BIGNT = 2;  // worker threads of the large-group k_fill launch (256 or 384)
 
 struct sic_handle {
     int device;

@@ -3,9 +3,10 @@
 // The handle keeps a small table of tuned choices, each keyed by what is tuned and a bucket of
 // the problem's sizes; kernels look their choice up at launch and fall back to a built-in
 // default.  Tuned now: the size-class split of the FP64 fill (groups of at most `split`
-// members run in the 4-worker launch, larger ones in the 8-worker launch, each with its own
-// shared-memory layout and occupancy).  sic_tune_build_factor times every candidate split
-// on the caller's own problem with CUDA events and keeps the fastest; sic_tune_save and
+// members run in the 4-worker launch, larger ones in the large-group launch, each with its
+// own shared-memory layout and occupancy) and the large-group launch's worker warps (8 or
+// 12).  sic_tune_build_factor times every candidate split on the caller's own problem with
+// CUDA events, then the worker count at the best split, and keeps the fastest; sic_tune_save and
 // sic_tune_load keep the table in a text file, one "op a b value ms" line per entry.
 #include <stdio.h>
 
@@ -70,8 +71,31 @@ extern "C" sic_status sic_tune_build_factor(sic_handle* h, const double* pts, in
             best_ms = ms;
         }
     }
+    // then the worker count of the large-group launch at that split
+    int best_nt = 256;
+    if (st == SIC_OK && best < max_m) {
+        tune_put(h, TUNE_FILL_SPLIT, k, max_m, best, best_ms);
+        tune_put(h, TUNE_FILL_BIGNT, k, max_m, 384, 0.f);
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && st == SIC_OK; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) st = SIC_ERR_CUDA;
+            if (st == SIC_OK)
+                st = sic_build_factor(h, pts, n, kp, grp_ptr, n_grp, max_m, sel_idx, sel_count, k, col_ptr, row_idx,
+                                      val, logv, sum_logv, ws, ws_bytes, stream);
+            if (st == SIC_OK && cudaEventRecord(e1, s) != cudaSuccess) st = SIC_ERR_CUDA;
+            if (st == SIC_OK && cudaEventSynchronize(e1) != cudaSuccess) st = SIC_ERR_CUDA;
+            float t = 0.f;
+            if (st == SIC_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = SIC_ERR_CUDA;
+            if (rep == 1 || (rep > 1 && t < ms)) ms = t;
+        }
+        if (st == SIC_OK && ms < best_ms) {
+            best_nt = 384;
+            best_ms = ms;
+        }
+    }
     if (st == SIC_OK) {
         tune_put(h, TUNE_FILL_SPLIT, k, max_m, best, best_ms);
+        tune_put(h, TUNE_FILL_BIGNT, k, max_m, best_nt, best_ms);
         // leave the outputs of the chosen configuration (identical for every split)
         st = sic_build_factor(h, pts, n, kp, grp_ptr, n_grp, max_m, sel_idx, sel_count, k, col_ptr, row_idx, val,
                               logv, sum_logv, ws, ws_bytes, stream);
@@ -118,7 +142,8 @@ extern "C" sic_status sic_tune_load(sic_handle* h, const char* path) {
         if (line[0] == '#' || line[0] == '\n') continue;
         int op, a, b, value;
         double ms;
-        if (sscanf(line, "%d %d %d %d %lf", &op, &a, &b, &value, &ms) != 5 || op != TUNE_FILL_SPLIT || value < 1) {
+        if (sscanf(line, "%d %d %d %d %lf", &op, &a, &b, &value, &ms) != 5 ||
+            (op != TUNE_FILL_SPLIT && op != TUNE_FILL_BIGNT) || value < 1) {
             st = SIC_ERR_INVALID;  // unknown or malformed entry: the rest still loads
             continue;
         }
