@@ -321,6 +321,8 @@ def main():
                          "decreases from the FP64 side state, global allocation")
     ap.add_argument("--case-partial", action="store_true",
                     help="with --case-only: partial selection of nonadjacent groups (256 candidates) and its fill")
+    ap.add_argument("--tune-save", default="", help="with --case-only: autotune the fill first, save the table here")
+    ap.add_argument("--tune-load", default="", help="with --case-only: load a saved autotune table before the run")
     ap.add_argument("--partial-n", type=int, default=1 << 18,
                     help="points of the partial-selection (nonadjacent groups) measurement (0: skip)")
     args = ap.parse_args()
@@ -366,9 +368,16 @@ def main():
             fb = learned.LearnedFactorBuilder(h, hp, learned.Proposal(h, learned.init_params(0), top=4 * cfg["k"]))
         else:
             fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
+        if args.tune_load:
+            sic.tune_load(h, args.tune_load)
+        if args.tune_save:
+            fb.tune(dp)
+            h.sync()
+            sic.tune_save(h, args.tune_save)
         fb.run(dp)
         h.sync()
-        print(json.dumps({"case": args.case_only, "groups": hp.n_units, "sum_logv": float(fb.sum_logv.cpu()[0])}))
+        print(json.dumps({"case": args.case_only, "groups": hp.n_units, "sum_logv": float(fb.sum_logv.cpu()[0]),
+                          "tune": sic.tune_table(h)}))
         return
     t0 = time.perf_counter()
     hp = problem(cfg, cfg["seed"] + rank)
