@@ -190,3 +190,30 @@ def test_partial_no_groups(env):
     z32 = torch.zeros(1, dtype=torch.int32, device="cuda")
     sic.select_partial(h, pts, kp, gp, gp, gp, z32, 8, 4, 4, sic.SIC_FP32_MIXED, z32, z32)
     h.sync()
+
+
+def test_partial_full_size_sampled(env, oracle_lib):
+    """The bench's partial-selection configuration: N = 2^18, groups of 8-64 kept where the
+    ordering puts them, 256 candidates, k = 64, FP32; sampled groups replayed by the oracle
+    (bands of the FP32 parity tests), the fill's sum of log v finite."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    cfg = synthetic.PRESETS["cfg3_aggregated"]
+    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"])
+    hp = pipeline.prepare_partial(synthetic.points(1 << 18, 2, cfg["seed"]), kp, 256, cfg["k"], cfg["m_min"],
+                                  cfg["m_max"])
+    dp = pipeline.DeviceProblem(hp)
+    fb = pipeline.PartialFactorBuilder(h, hp, sic.SIC_FP32_MIXED)
+    fb.run(dp)
+    h.sync()
+    sels = fb.sel_lists()
+    okp = _okernel(oracle, kp)
+    G = hp.n_units
+    rng = np.random.default_rng(3)
+    groups = sorted(set(rng.choice(G, 3, replace=False).tolist()) | {G - 1})
+    stats = ReplayStats()
+    for g in groups:
+        _replay_partial(oracle, okp, hp, g, sels[g], FP32_BAND, stats, FP32_ABS * kp.variance)
+    s = float(fb.sum_logv.cpu()[0])
+    assert np.isfinite(s)
+    print(f"partial full size: groups {G}, replay {stats}, sum log v {s:.1f}")

@@ -165,3 +165,51 @@ def test_side_state_no_units(env):
     h.sync()
     with pytest.raises(sic.SicError):  # no output requested
         sic.side_state_fp64(h, pts, kp, z, z[:0], 4)
+
+
+def test_side_state_full_size_sampled(env, oracle_lib):
+    """The bench's configuration: N = 2^20 supernodes (Matern 3/2, ell = 0.02, nugget 1e-6,
+    8-64 members, k = 64), candidate lists cut to their 256 nearest, FP32 selection with a
+    global budget of 48 picks per column and the decreases from the FP64 side state.
+    Sampled groups: the side state's variances against dense Schur complements of the same
+    picks; the allocation is a valid one (within budget, prefixes, no dropped pick ranked
+    above a kept one)."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    cfg = synthetic.PRESETS["cfg3_aggregated"]
+    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], cfg["length_scale"], cfg["variance"], cfg["nugget"])
+    pts = synthetic.points(cfg["n"], cfg["dim"], cfg["seed"])
+    hp = pipeline.prepare_groups(pts, kp, 256, cfg["k"], cfg["m_min"], cfg["m_max"])
+    sizes = np.diff(hp.grp_ptr)
+    B = int(48 * sizes.sum())
+    dp = pipeline.DeviceProblem(hp)
+    fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED, budget=B, side_fp64=True)
+    fb.run(dp)
+    h.sync()
+    G, k = hp.n_units, hp.k
+    v1 = torch.empty(G * k, dtype=torch.float64, device="cuda")
+    v2 = torch.empty(G * k, dtype=torch.float64, device="cuda")
+    sic.side_state_fp64(h, dp.pts, kp, fb.sel_idx, fb.local_count, k, grp_ptr=dp.grp_ptr, max_m=hp.max_m,
+                        pvar=v1, pvar_p=v2)
+    h.sync()
+    v1, v2 = v1.view(G, k).cpu().numpy(), v2.view(G, k).cpu().numpy()
+    gain = fb.gain.view(G, k).cpu().numpy()
+    sel = fb.sel_idx.view(G, k).cpu().numpy()
+    lcnt, cnt = fb.local_count.cpu().numpy(), fb.sel_count.cpu().numpy()
+    okp = _okernel(oracle, kp)
+    rng = np.random.default_rng(8)
+    groups = sorted(set(rng.choice(G, 10, replace=False).tolist()) | {0, G - 1})
+    for g in groups:
+        P = list(range(int(hp.grp_ptr[g]), int(hp.grp_ptr[g + 1])))
+        c = int(lcnt[g])
+        o1, o2 = oracle.pivot_variances(okp, hp.pts, P, sel[g, :c])
+        assert np.all(np.abs(v1[g, :c] - o1) <= REL * o1 + ABS * kp.variance), g
+        assert np.all(np.abs(v2[g, :c] - o2) <= REL * o2 + ABS * kp.variance), g
+        tol = (2 * REL + ABS * kp.variance / o1 + ABS * kp.variance / o2) / len(P)
+        assert np.all(np.abs(gain[g, :c] - np.log(o1 / o2) / len(P)) <= tol), g
+    assert np.all(cnt >= 0) and np.all(cnt <= lcnt) and int(np.dot(cnt, sizes)) <= B
+    keys = [np.minimum.accumulate(gain[u, :lcnt[u]]) for u in range(G)]
+    kept = min(keys[u][cnt[u] - 1] for u in range(G) if cnt[u] > 0)
+    dropped = max((keys[u][cnt[u]] for u in range(G) if cnt[u] < lcnt[u]), default=-np.inf)
+    assert kept >= dropped
+    print(f"groups {G}: kept {int(np.dot(cnt, sizes))} of {B} nonzeros; sum log v {float(fb.sum_logv.cpu()[0]):.1f}")
