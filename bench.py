@@ -605,6 +605,27 @@ def main():
         raise RuntimeError("end-to-end result differs from the device-timed step")
     del dp2, lb2
 
+    # ---- a10: the factor as a preconditioner, y = L^T x, L x and L L^T x (HBM-bound) on the
+    # step's factor.  Algorithmic bytes per product: the factor once (12 B per nonzero + 8 B per
+    # column pointer), x read once and y written once (8 B x nrhs per point each)
+    hbm_peak = measured_peak("hbm_gbs", 6800.0)
+    nnz_f = int(lb.col_ptr[-1].item())
+    apply_res = {}
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    for nrhs in (1, 8):
+        X = torch.randn(N, nrhs, dtype=torch.float64, device="cuda", generator=gen)
+        Y = torch.empty_like(X)
+        wsa = sic._ws(sic.apply_factor_workspace(N, nrhs, sic.SIC_OP_LLT), "cuda")
+        for name, op, passes in (("LT", sic.SIC_OP_LT, 1), ("L", sic.SIC_OP_L, 1), ("LLT", sic.SIC_OP_LLT, 2)):
+            a_ms, _, _ = timed([lambda: sic.apply_factor(h, lb.col_ptr, lb.fb.row_idx, lb.fb.val, op, X, Y, wsa)],
+                               5, 2)
+            byts = passes * (12.0 * nnz_f + 8.0 * (N + 1) + 2 * 8.0 * nrhs * N)
+            apply_res[f"{name}_nrhs{nrhs}"] = {"ms": a_ms, "gbs": byts / (a_ms * 1e-3) / 1e9,
+                                               "frac": byts / (a_ms * 1e-3) / 1e9 / hbm_peak}
+        del X, Y, wsa
+    apply_res["peak_gbs"] = hbm_peak
+    apply_res["nnz"] = nnz_f
+
     # ---- rooflines (ALU bound; peaks derived from unit counts and the maximum clock)
     rp = lb.rhp
     f32_peak = SMS * FFMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -692,6 +713,7 @@ def main():
             "pcg": pcg,
             "global_allocation": global_alloc,
             "partial_selection": partial,
+            "apply_factor": apply_res,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
