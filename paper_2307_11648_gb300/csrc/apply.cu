@@ -1,39 +1,32 @@
 // y = op(L) x for the CSC factor (its use as a preconditioner, Section 6.4).
-// L^T x is a gather (one warp per column, lanes over the column's entries, a fixed
-// shuffle tree per right-hand side); L x scatters with FP64 atomics (one warp per
-// column).  L L^T x chains the two through the caller's workspace.
+// L^T x is a gather (one warp per column, groups of lanes over the column's entries, a fixed
+// shuffle tree across the groups); L x scatters with FP64 atomics (one warp per column).
+// L L^T x chains the two through the caller's workspace.
 #include "sic_internal.cuh"
 
 namespace {
 
+// NR lanes share one nonzero (NR = 1, 2, 4, 8: the right-hand sides rounded up to a power of
+// two); lane r of such a group handles right-hand side r, so a nonzero's x row (or y row) is
+// one coalesced access, and a warp walks 32 / NR nonzeros of its column at a time.
 template <int NR>
 __global__ void __launch_bounds__(256) k_apply_lt(long long n, const long long* __restrict__ cp,
                                                   const int32_t* __restrict__ ri, const double* __restrict__ v,
                                                   const double* __restrict__ x, double* __restrict__ y, int nrhs) {
     const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, g = lane / NR, r = lane % NR;
     if (c >= n) return;
-    double acc[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+    double acc = 0.0;
     const long long e = cp[c + 1];
-    for (long long p = cp[c] + lane; p < e; p += 32) {
+    for (long long p = cp[c] + g; p < e; p += 32 / NR) {
         const double a = v[p];
         const long long row = ri[p];
-        if (row < 0 || row >= n) continue;  // malformed factor: skip the entry
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-            if (r < nrhs) acc[r] = fma(a, x[row * nrhs + r], acc[r]);
+        if (row < 0 || row >= n || r >= nrhs) continue;  // malformed factor: skip the entry
+        acc = fma(a, x[row * nrhs + r], acc);
     }
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off);
-    }
-    if (lane == 0)
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-            if (r < nrhs) y[c * nrhs + r] = acc[r];
+    for (int off = 16; off >= NR; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane < nrhs) y[c * nrhs + lane] = acc;
 }
 
 template <int NR>
@@ -41,19 +34,15 @@ __global__ void __launch_bounds__(256) k_apply_l(long long n, const long long* _
                                                  const int32_t* __restrict__ ri, const double* __restrict__ v,
                                                  const double* __restrict__ x, double* __restrict__ y, int nrhs) {
     const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (c >= n) return;
-    double xc[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) xc[r] = (r < nrhs) ? x[c * nrhs + r] : 0.0;
+    const int lane = threadIdx.x & 31, g = lane / NR, r = lane % NR;
+    if (c >= n || r >= nrhs) return;
+    const double xc = x[c * nrhs + r];
     const long long e = cp[c + 1];
-    for (long long p = cp[c] + lane; p < e; p += 32) {
+    for (long long p = cp[c] + g; p < e; p += 32 / NR) {
         const double a = v[p];
         const long long row = ri[p];
         if (row < 0 || row >= n) continue;  // malformed factor: skip the entry
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-            if (r < nrhs) atomicAdd(&y[row * nrhs + r], a * xc[r]);
+        atomicAdd(&y[row * nrhs + r], a * xc);
     }
 }
 
