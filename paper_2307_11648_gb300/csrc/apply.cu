@@ -18,15 +18,11 @@ __global__ void __launch_bounds__(256) k_apply_lt(long long n, const long long* 
     if (c >= n) return;
     double acc = 0.0;
     const long long e = cp[c + 1];
-    // branch-free body (a malformed row contributes nothing) so that the unrolled loop issues
-    // several entries' gathers before their FMAs
-#pragma unroll 4
     for (long long p = cp[c] + g; p < e; p += 32 / NR) {
         const double a = v[p];
         const long long row = ri[p];
-        const bool ok = row >= 0 && row < n && r < nrhs;
-        const double xv = ok ? __ldg(x + row * nrhs + r) : 0.0;
-        acc = fma(ok ? a : 0.0, xv, acc);
+        if (row < 0 || row >= n || r >= nrhs) continue;  // malformed factor: skip the entry
+        acc = fma(a, x[row * nrhs + r], acc);
     }
 #pragma unroll
     for (int off = 16; off >= NR; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -42,11 +38,11 @@ __global__ void __launch_bounds__(256) k_apply_l(long long n, const long long* _
     if (c >= n || r >= nrhs) return;
     const double xc = x[c * nrhs + r];
     const long long e = cp[c + 1];
-#pragma unroll 4
     for (long long p = cp[c] + g; p < e; p += 32 / NR) {
         const double a = v[p];
         const long long row = ri[p];
-        if (row >= 0 && row < n) atomicAdd(&y[row * nrhs + r], a * xc);  // a malformed row is skipped
+        if (row < 0 || row >= n) continue;  // malformed factor: skip the entry
+        atomicAdd(&y[row * nrhs + r], a * xc);
     }
 }
 
