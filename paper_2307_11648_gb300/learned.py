@@ -142,6 +142,45 @@ class LearnedFactorBuilder:
         return self.fb.sel_lists()
 
 
+class GuardedBuild:
+    """The learned path judged by the plain greedy, which is also its fallback.
+
+    run(dp) builds the factor with the learned proposal and with plain greedy selection on
+    all candidates, and a reference factor with 2k picks from the same candidates; the KL gap
+    (S_learned - S_plain) / (S_plain - S_ref), S = sum of log v (the same proxy as the
+    benchmark's: logdet Theta cancels in both differences, and S_ref >= logdet Theta makes the
+    denominator a lower bound of 2 KL(plain), so the gap is overstated, never understated).
+    If the gap is at most `max_gap` the learned factor is kept, else the plain one.  `chosen`
+    names the builder whose outputs (col_ptr, row_idx, val, logv, sum_logv) hold the factor.
+    The audit costs a plain and a 2k build; use it once per geometry and kernel, then keep
+    the decision (`use_learned`)."""
+
+    def __init__(self, h: sic.Handle, hp: pipeline.HostProblem, proposal: Proposal, max_gap: float = 0.01,
+                 prec=sic.SIC_FP32_MIXED, device="cuda"):
+        import dataclasses
+        self.max_gap = max_gap
+        self.learned = LearnedFactorBuilder(h, hp, proposal, prec, device)
+        self.plain = pipeline.FactorBuilder(h, hp, prec, device)
+        self.ref = pipeline.FactorBuilder(h, dataclasses.replace(hp, k=2 * hp.k), prec, device)
+        self.h = h
+        self.gap = None
+        self.use_learned = None
+
+    def run(self, dp: pipeline.DeviceProblem, stream=None):
+        for b in (self.learned, self.plain, self.ref):
+            b.run(dp, stream)
+        self.h.sync(stream)
+        s_l, s_p, s_r = (float(b.sum_logv.cpu()[0]) for b in (self.learned, self.plain, self.ref))
+        den = s_p - s_r
+        self.gap = (s_l - s_p) / den if den > 0 else float("inf")
+        self.use_learned = bool(self.gap <= self.max_gap)
+        return self.chosen
+
+    @property
+    def chosen(self):
+        return self.learned.fb if self.use_learned else self.plain
+
+
 # ----------------------------------------------------------------- training --
 
 def training_set(h: sic.Handle, problems, prec=sic.SIC_FP32_MIXED, device="cuda"):

@@ -302,3 +302,24 @@ def test_learned_step_in_cuda_graph(env):
         assert torch.equal(a, b)
     assert torch.equal(ref[3][:nnz], got[3][:nnz])
     assert torch.equal(ref[4], got[4])
+
+
+def test_guarded_build_falls_back_to_plain_greedy(env):
+    """The plain greedy judges the learned path and replaces it when the KL gap exceeds the
+    threshold: an untrained network keeping only 32 of 256 candidates is far off (large
+    gap) and falls back; with a threshold above its measured gap the learned factor is kept.
+    Either way the chosen factor is that builder's own output."""
+    torch, sic, pipeline, learned, h = env
+    kp = sic.kernel(2, 3, 0.05, 1.0, 1e-6)
+    hp = pipeline.prepare_groups(synthetic.points(1 << 14, 2, 5), kp, 256, 16, 8, 32)
+    dp = pipeline.DeviceProblem(hp)
+    prop = learned.Proposal(h, learned.init_params(0), top=2 * hp.k)
+    g = learned.GuardedBuild(h, hp, prop, max_gap=0.01)
+    chosen = g.run(dp)
+    print("untrained proposal KL gap", g.gap)
+    assert g.gap > 0.01 and not g.use_learned and chosen is g.plain
+    g2 = learned.GuardedBuild(h, hp, prop, max_gap=g.gap * 2 + 1.0)
+    chosen2 = g2.run(dp)
+    assert g2.use_learned and chosen2 is g2.learned.fb
+    assert g2.gap == pytest.approx(g.gap, rel=1e-12)
+    assert torch.equal(chosen2.val, g2.learned.fb.val)
