@@ -131,6 +131,16 @@ def select_flops(grp_ptr, cand_ptr, k) -> float:
     return float(2.0 * np.sum(R * m * (m - 1) / 2.0 + C * (k * (k - 1) + k * m + 3.0 * k)))
 
 
+def select_columns_flops(cand_ptr, sel_count) -> float:
+    """Algorithmic FLOPs of the single-target selection (2 per FMA): per step t the
+    left-looking dot over the t earlier picks for the C candidate rows and the target's row,
+    (C + 1) t FMA, then the downdates of var and cov and the score, 3C; kernel evaluations
+    not counted."""
+    C = np.diff(cand_ptr).astype(np.float64)
+    t = sel_count.astype(np.float64)
+    return float(2.0 * np.sum((C + 1.0) * t * (t - 1.0) / 2.0 + 3.0 * C * t))
+
+
 def fill_flops(grp_ptr, sel_count) -> float:
     """Algorithmic FP64 FLOPs of the fill (2 per FMA): Cholesky of the n x n reversed set
     n^3/6 and the m member back substitutions sum_a (n - a)^2 / 2, n = picks + m; the
@@ -209,6 +219,20 @@ def problem(cfg, seed, n=None):
     kp = sic.kernel(cfg["dim"], cfg["nu_x2"], ell, cfg["variance"], cfg["nugget"])
     pts = synthetic.points(n, cfg["dim"], seed)
     return pipeline.prepare_groups(pts, kp, cfg["n_cand"], cfg["k"], cfg["m_min"], cfg["m_max"])
+
+
+def cfg_single_seed(rank):
+    return synthetic.PRESETS["cfg2_single_batched"]["seed"] + rank
+
+
+def single_problem(n, seed):
+    """The single-target workload: n points in the unit cube, Matern 5/2, 512 nearest
+    later-ordered candidates per column, k = 32."""
+    from paper_2307_11648_gb300 import pipeline, sic
+    c = synthetic.PRESETS["cfg2_single_batched"]
+    ell = c["length_scale"] * (c["n"] / n) ** (1.0 / c["dim"])  # same ell / spacing as the full size
+    kp = sic.kernel(c["dim"], c["nu_x2"], ell, c["variance"], c["nugget"])
+    return pipeline.prepare_columns(synthetic.points(n, c["dim"], seed), kp, c["n_cand"], c["k"])
 
 
 def truncated(hp, top):
@@ -323,6 +347,10 @@ def main():
                     help="with --case-only: partial selection of nonadjacent groups (256 candidates) and its fill")
     ap.add_argument("--tune-save", default="", help="with --case-only: autotune the fill first, save the table here")
     ap.add_argument("--tune-load", default="", help="with --case-only: load a saved autotune table before the run")
+    ap.add_argument("--single-n", type=int, default=1 << 16,
+                    help="points of the single-target measurement (3-D, 512 candidates, k = 32; 0: skip)")
+    ap.add_argument("--case-single", action="store_true",
+                    help="with --case-only: one FP32-mixed single-target factor build (3-D, 512 candidates, k = 32)")
     ap.add_argument("--partial-n", type=int, default=1 << 18,
                     help="points of the partial-selection (nonadjacent groups) measurement (0: skip)")
     args = ap.parse_args()
@@ -343,6 +371,22 @@ def main():
     build.build()
     torch.cuda.set_device(local)
     cfg = synthetic.PRESETS[WORKLOAD]
+    if args.case_only and args.case_single:
+        h = sic.Handle(local)
+        shp = single_problem(args.case_only, cfg_single_seed(0))
+        fb = pipeline.FactorBuilder(h, shp, sic.SIC_FP32_MIXED)
+        fb.run(pipeline.DeviceProblem(shp))
+        # then the factor's two products with one right-hand side
+        x = torch.ones(shp.n, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        sums = []
+        for op in (sic.SIC_OP_LT, sic.SIC_OP_L):
+            sic.apply_factor(h, fb.col_ptr, fb.row_idx, fb.val, op, x, y)
+            sums.append(float(y.sum().cpu()))
+        h.sync()
+        print(json.dumps({"case": args.case_only, "columns": shp.n, "sum_logv": float(fb.sum_logv.cpu()[0]),
+                          "apply_sums": sums}))
+        return
     if args.case_only and args.case_partial:
         h = sic.Handle(local)
         php = pipeline.prepare_partial(synthetic.points(args.case_only, 2, cfg["seed"]), sic.kernel(
@@ -539,6 +583,29 @@ def main():
                    "nnz": int(pfb.col_ptr[-1].item())}
         del pfb, pdp, php
         torch.cuda.empty_cache()
+    # ---- single-target selection (one column per unit), 3-D, 512 candidates, k = 32: FP32
+    # mixed and FP64, each with the FP64 fill
+    single = None
+    if args.single_n:
+        shp = single_problem(args.single_n, cfg_single_seed(rank))
+        sdp = pipeline.DeviceProblem(shp)
+        single = {"n": shp.n, "dim": shp.pts.shape[1], "candidates": int(np.diff(shp.cand_ptr).max()), "k": shp.k}
+        unit_peaks = {"fp32": SMS * FFMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6,
+                      "fp64": SMS * DFMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6}
+        for name, prec, unit in [("fp32", sic.SIC_FP32_MIXED, "FP32 FFMA"), ("fp64", sic.SIC_FP64, "FP64 DFMA")]:
+            peak = unit_peaks[name]
+            sfb = pipeline.FactorBuilder(h, shp, prec)
+            s_ms, (ssel_ms, sfill_ms), _ = timed([lambda: sfb.select(sdp), lambda: sfb.fill(sdp)], 3, 1)
+            fl = select_columns_flops(shp.cand_ptr, sfb.sel_count.cpu().numpy())
+            single[name] = {"ms_per_step": s_ms, "select_ms": ssel_ms, "fill_ms": sfill_ms,
+                            "columns_per_s": shp.n / (s_ms * 1e-3), "sum_logv": float(sfb.sum_logv.cpu()[0]),
+                            "nnz": int(sfb.col_ptr[-1].item()),
+                            "select_roofline": {"bound": "alu", "achieved": fl / (ssel_ms * 1e-3) / 1e12,
+                                                "peak": peak / 1e12, "unit": "TFLOP/s",
+                                                "frac": fl / (ssel_ms * 1e-3) / peak, "peak_of": unit}}
+            del sfb
+        del sdp, shp
+        torch.cuda.empty_cache()
     base = S["plain_fp64"] - S["reference_2k"]
     kl_gap = {k: (S[k] - S["plain_fp64"]) / base for k in ["learned_fp32", "plain_fp32", "distance_fp32",
                                                            "learned_global_48", "learned_global_48_side_fp64",
@@ -713,6 +780,7 @@ def main():
             "pcg": pcg,
             "global_allocation": global_alloc,
             "partial_selection": partial,
+            "single_target": single,
             "apply_factor": apply_res,
             "cpu_baseline": cpu,
         }
