@@ -16,7 +16,8 @@
 //   then var_j -= u_j^2 and cov_j -= u_j u_t with u_t = cov_q / sqrt(var_q)
 //   (eq. cond_select; the target's own row of the factor is never stored).
 // FP32 mode works in coordinates relative to the target (formed in FP64) so that
-// candidate-to-candidate differences keep their digits.
+// candidate-to-candidate differences keep their digits; FP64 mode evaluates Theta with the
+// fill's table-driven exp and Newton square root, and 1/sqrt(var_q) by Newton steps.
 // With `gain` non-null, thread 0 also carries the target's variance v_t in FP64
 // (v_{t+1} = v_t - u_t^2, kept at or above the exhaustion floor: the target's own nugget is
 // never explained) and, after the column's last step, the threads write the picks'
@@ -53,9 +54,22 @@ __global__ void __launch_bounds__(NT) k_select_columns(
     __shared__ T wscore[2][NW];
     __shared__ int widx[2][NW];
     __shared__ double gv[KMAX + 1];  // target variance before each pick (gains only)
+    __shared__ double tab[sizeof(T) == 8 ? EXP_TAB : 1];  // s2 2^(j/256): the FP64 Matern's exp
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T NEG = -INFINITY;
+    if constexpr (sizeof(T) == 8) {
+        exp_table_fill(tab, kp.s2);
+        __syncthreads();
+    }
+    // Theta at squared distance d2 (no nugget): in FP64 the table-driven exp and the Newton
+    // square root (few FP64-pipe operations, about 2 ulp)
+    auto theta = [&](T d2) -> T {
+        if constexpr (sizeof(T) == 8)
+            return matern_d2_fast(kp, d2, tab);
+        else
+            return matern<T>(kp, sic_sqrt(d2));
+    };
 
     for (long long c = blockIdx.x; c < n_cols; c += gridDim.x) {
         const long long tgt = targets ? (long long)targets[c] : c;
@@ -107,7 +121,7 @@ __global__ void __launch_bounds__(NT) k_select_columns(
                     }
                 }
                 var[r] = kp.s2 + kp.nugget;
-                cov[r] = matern<T>(kp, sic_sqrt(d2));
+                cov[r] = theta(d2);
             }
         }
         double vt = v0;  // target variance (thread 0, gains only)
@@ -178,8 +192,11 @@ __global__ void __launch_bounds__(NT) k_select_columns(
             }
             if (gi == 0x7fffffff || !(gs > (T)0)) break;
             const Slot<T, KMAX>& P = slot[buf][gw];
-            const T d = sic_sqrt(P.var);
-            const T rs = (T)1 / d;
+            T rs;
+            if constexpr (sizeof(T) == 8)
+                rs = rsqrt_newton(P.var);
+            else
+                rs = (T)1 / sic_sqrt(P.var);
             const T ut = P.cov * rs;
             const T px0 = P.x[0], px1 = P.x[1], px2 = P.x[2];
 #pragma unroll
@@ -187,8 +204,7 @@ __global__ void __launch_bounds__(NT) k_select_columns(
                 if (live[r]) {
                 const int row = tid + r * NT;
                 T d0 = x[r][0] - px0, d1 = x[r][1] - px1, d2v = x[r][2] - px2;
-                T rr = sic_sqrt(d0 * d0 + d1 * d1 + d2v * d2v);
-                T num = matern<T>(kp, rr);
+                T num = theta(fma(d2v, d2v, fma(d1, d1, d0 * d0)));
                 if (row == gi) num += kp.nugget;
 #pragma unroll
                 for (int q0 = 0; q0 < KMAX; q0 += 8) {
@@ -242,8 +258,8 @@ __global__ void __launch_bounds__(NT) k_select_columns(
 // current block from the row's own mirror, and a completed block moves into registers, so no
 // register is indexed by the step and no predicated select touches the whole row.  The
 // pivot's coordinates sit beside the mirror (one float4 per row, written once per column).  The warp argmax is two redux operations on order-preserving
-// score keys (the maximum, then the lowest candidate index among the lanes holding it); the
-// eight warp winners are reduced by every thread as before.  Scores use the fast FP32 divide,
+// score keys (the maximum, then the lowest candidate index among the lanes holding it), and
+// the eight warp winners are reduced the same way by every warp (lane w reads warp w's).  Scores use the fast FP32 divide,
 // the pivot's 1/sqrt(var) and the distances the hardware reciprocal square root (about 2 ulp,
 // far inside the tolerance of FP32 selection).
 template <int KMAX>
@@ -377,22 +393,16 @@ __global__ void __launch_bounds__(NT) k_select_columns_f32(
                     wcov[buf][warp] = bc;
                 }
                 __syncthreads();
-                unsigned gk = wkey[buf][0];
-                int gi = widx[buf][0], gw = 0;
-#pragma unroll
-                for (int w = 1; w < NW; ++w) {
-                    const unsigned kw = wkey[buf][w];
-                    const int iw = widx[buf][w];
-                    if (kw > gk || (kw == gk && iw < gi)) {
-                        gk = kw;
-                        gi = iw;
-                        gw = w;
-                    }
-                }
+                // the eight warp winners, reduced by every warp: lane w < 8 holds warp w's
+                const unsigned kw = (lane < NW) ? wkey[buf][lane] : 0u;
+                const int iw = (lane < NW) ? widx[buf][lane] : 0x7fffffff;
+                const unsigned gk = __reduce_max_sync(FULL, kw);
+                const int gi = (int)__reduce_min_sync(FULL, (kw == gk) ? (unsigned)iw : 0x7fffffffu);
                 if (gk <= 0x80000000u) {  // no candidate left, or the best score is 0
                     go = false;
                     break;
                 }
+                const int gw = __ffs(__ballot_sync(FULL, lane < NW && kw == gk && iw == gi)) - 1;
                 const float rs = rsqrtf(wvar[buf][gw]);
                 const float ut = wcov[buf][gw] * rs;
                 const float4 px = Xm[gi];
