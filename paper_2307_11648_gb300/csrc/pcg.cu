@@ -8,7 +8,8 @@
 // FP32 numbers (hi + lo) and each tile's sum of products is accumulated as a double-FP32
 // pair with the error-free transformations TwoProduct (by fma) and TwoSum (Knuth), then
 // added to an FP64 accumulator -- so the product is accurate to ~1e-14 of sum |K x| and
-// CG can reach small residuals.  With T = double everything is FP64 (reference mode).
+// CG can reach small residuals.  With T = double everything is FP64 (reference mode; the
+// kernel entries by the fill's table-driven exp and Newton square root, about 2 ulp).
 // The diagonal adds the nugget and the shift in FP64.
 // The CG vector updates and dot products are fused kernels with fixed-order reductions
 // (bit-reproducible); the scalars alpha and beta are formed on the device per RHS.
@@ -33,6 +34,8 @@ __global__ void __launch_bounds__(MV_NT) k_matvec(const double* __restrict__ pts
     __shared__ T sx[MV_TILE], sy[MV_TILE], sz[MV_TILE];
     __shared__ T sv[MV_TILE * NR];
     __shared__ float svl[F32 ? MV_TILE * NR : 1];  // low parts of x in FP32 mode
+    __shared__ double tab[F32 ? 1 : EXP_TAB];      // FP64 mode: s2 2^(j/256) for the table-driven exp
+    if constexpr (!F32) exp_table_fill(tab, kp.s2);  // ordered before use by the tile loop's barrier
     const long long i = blockIdx.x * (long long)MV_NT + threadIdx.x;
     const bool live = i < n;
     T xi = 0, yi = 0, zi = 0;
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(MV_NT) k_matvec(const double* __restrict__ pts
             for (int r = 0; r < NR; ++r) part[r] = (T)0;
             for (int t = 0; t < cnt; ++t) {
                 const T dx = xi - sx[t], dy = yi - sy[t], dz = zi - sz[t];
-                const T kv = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
+                const T kv = matern_d2_fast(kp, fma(dz, dz, fma(dy, dy, dx * dx)), tab);
 #pragma unroll
                 for (int r = 0; r < NR; ++r) part[r] = fma(kv, sv[t * NR + r], part[r]);
             }

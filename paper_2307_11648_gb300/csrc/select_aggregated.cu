@@ -139,6 +139,25 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T NEG = -INFINITY;
     const T diag = kp.s2 + kp.nugget;
+    // FP64: Theta by the fill's table-driven exp and Newton square root (about 2 ulp); the
+    // table s2 2^(j/256) follows the pivot rows
+    double* tab = reinterpret_cast<double*>(p2 + (L.mm + k));
+    if constexpr (sizeof(T) == 8) {
+        exp_table_fill(tab, kp.s2);
+        __syncthreads();
+    }
+    auto theta = [&](T d2) -> T {
+        if constexpr (sizeof(T) == 8)
+            return matern_d2_fast(kp, d2, tab);
+        else
+            return matern<T>(kp, sic_sqrt(d2));
+    };
+    auto rsqrt_t = [](T v) -> T {
+        if constexpr (sizeof(T) == 8)
+            return rsqrt_newton(v);
+        else
+            return (T)1 / sic_sqrt(v);
+    };
 
     for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
         const long long g0 = grp_ptr[g];
@@ -195,7 +214,7 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
             for (int i = tid; i < C + m; i += NT) {
                 if (i < C) {
                     T dx = X[i] - ax, dy = X[ldx + i] - ay, dz = X[2 * ldx + i] - az;
-                    T num = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
+                    T num = theta(fma(dz, dz, fma(dy, dy, dx * dx)));
                     num = SMEM ? dot_row(num, F2c + (long long)i * P2, p2, a) : dot_down(num, F2c + i, Cm, p2, a);
                     const T u = num * rs;
                     E2(i, a) = u;
@@ -210,7 +229,7 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                     } else {
                         const long long xt = Cm + ta;
                         T dx = X[xt] - ax, dy = X[ldx + xt] - ay, dz = X[2 * ldx + xt] - az;
-                        T num = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
+                        T num = theta(fma(dz, dz, fma(dy, dy, dx * dx)));
                         num = SMEM ? dot_row(num, F2t + (long long)ta * P2t, p2, a) : dot_down(num, F2t + ta, mm, p2, a);
                         u = num * rs;
                     }
@@ -254,12 +273,12 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                 for (int tau = tid; tau < t; tau += NT) p1[tau] = E1(q, tau);
                 for (int tau = tid; tau < m + t; tau += NT) p2[tau] = E2(q, tau);
                 __syncthreads();
-                const T r1 = (T)1 / sic_sqrt(v1q);
-                const T r2 = (T)1 / sic_sqrt(v2q);
+                const T r1 = rsqrt_t(v1q);
+                const T r2 = rsqrt_t(v2q);
                 for (int r = tid; r < C; r += NT) {
                     if (V2[r] == NEG) continue;
                     T dx = X[r] - qx, dy = X[ldx + r] - qy, dz = X[2 * ldx + r] - qz;
-                    T th = matern<T>(kp, sic_sqrt(dx * dx + dy * dy + dz * dz));
+                    T th = theta(fma(dz, dz, fma(dy, dy, dx * dx)));
                     if (r == q) th += kp.nugget;
                     const T n1 = SMEM ? dot_row(th, F1 + (long long)r * P1, p1, t) : dot_down(th, F1 + r, Cm, p1, t);
                     const T n2 = SMEM ? dot_row(th, F2c + (long long)r * P2, p2, m + t)
@@ -304,7 +323,8 @@ constexpr size_t SMEM_LIMIT = 227 * 1024 - 4096;  // dynamic part; the static ar
 template <typename T>
 size_t agg_smem_bytes(const AggLayout& L, bool in_smem) {
     size_t piv = sizeof(T) * (size_t)((L.k + 3) / 4 * 4 + L.mm + L.k);
-    return in_smem ? sizeof(T) * (size_t)L.size() + piv : piv;
+    const size_t tab = sizeof(T) == 8 ? sizeof(double) * EXP_TAB : 0;  // the FP64 Matern's exp table
+    return (in_smem ? sizeof(T) * (size_t)L.size() + piv : piv) + tab;
 }
 
 // Plan of one launch: where the state lives, threads per CTA, grid, workspace.
