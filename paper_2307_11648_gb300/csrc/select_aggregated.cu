@@ -340,7 +340,8 @@ struct AggPlan {
 template <typename T, int NT, bool SMEM>
 int agg_grid_for(sic_handle* h, size_t smem, long long n_grp) {
     auto kern = k_select_agg<T, NT, SMEM>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // opt in at any size: the static arrays count against the 48 KB default as well
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int g = persistent_grid(h, kern, NT, smem, n_grp);
     if (!SMEM) {
         long long cap = 2LL * h->num_sms;  // bound the workspace (and keep the slabs L2-friendly)

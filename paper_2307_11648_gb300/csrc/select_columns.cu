@@ -487,7 +487,8 @@ sic_status launch_cols_f32(sic_handle* h, const double* pts, long long n, int di
                            int max_cand, int k, int32_t* sel_idx, int32_t* sel_count, double* gain, cudaStream_t s) {
     auto kern = k_select_columns_f32<KMAX, ROWS>;
     constexpr size_t smem = mirror_bytes<KMAX, ROWS>();
-    if (smem > 48 * 1024) SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // opt in at any size: the static arrays count against the 48 KB default as well
+    SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int grid = persistent_grid(h, kern, NT, smem, n_cols);
     kern<<<grid, NT, smem, s>>>(pts, n, dim, make_kp<float>(*kp), (float)sic_floor_of(kp), targets, n_cols,
                                 (const long long*)cand_ptr, cand_idx, max_cand, k, sel_idx, sel_count,

@@ -203,8 +203,8 @@ extern "C" sic_status sic_side_state_fp64(sic_handle* h, const double* pts, int6
     const size_t smem = L.bytes();
     if (smem > 227 * 1024 - 1024) return SIC_ERR_UNSUPPORTED;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
-    if (smem > 48 * 1024)
-        SIC_CUDA_TRY(cudaFuncSetAttribute(k_side, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // opt in at any size: the static arrays count against the 48 KB default as well
+    SIC_CUDA_TRY(cudaFuncSetAttribute(k_side, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = persistent_grid(h, k_side, SIDE_NT, smem, n_units);
     k_side<<<grid, SIDE_NT, smem, (cudaStream_t)stream>>>(pts, n, kp->dim, make_kp<double>(*kp),
                                                           (const long long*)grp_ptr, targets, n_units, sel_idx,

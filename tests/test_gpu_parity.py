@@ -142,6 +142,43 @@ def test_columns_batched_full_size_sampled(env, oracle_lib, prec_name):
     assert np.all(np.isfinite(logv))
 
 
+# every launch shape of the single-target kernel: candidate rows per thread (1, 2, 4 for up to
+# 256, 512, 1024 candidates) x factor entries kept per row (16, 32, 64 for k up to 16, 32, 64)
+SHAPES = [("fp32", 200, 16), ("fp32", 400, 16), ("fp32", 1000, 16), ("fp32", 200, 32), ("fp32", 400, 32),
+          ("fp32", 1000, 32), ("fp32", 200, 64), ("fp32", 400, 64),
+          ("fp64", 200, 16), ("fp64", 400, 16), ("fp64", 1000, 16), ("fp64", 200, 32), ("fp64", 400, 32),
+          ("fp64", 200, 64)]
+
+
+@pytest.mark.parametrize("prec_name,n_cand,k", SHAPES)
+def test_columns_launch_shapes(env, oracle_lib, prec_name, n_cand, k):
+    """N = 1536 in 2-D (Matern 3/2, ell = 0.1, nugget 1e-6): the early columns have the full
+    candidate count, the late ones ragged lists down to none; every 5th column and the last
+    ones replayed by the oracle, their fill checked, the KL sum against the oracle's."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    kp = sic.kernel(2, 3, 0.1, 1.0, 1e-6)
+    hp = pipeline.prepare_columns(synthetic.points(1536, 2, 11), kp, n_cand, k)
+    assert hp.max_cand == n_cand
+    prec = sic.SIC_FP64 if prec_name == "fp64" else sic.SIC_FP32_MIXED
+    fb = _run(env, hp, prec)
+    sels = fb.sel_lists()
+    okp = _okernel(oracle, kp)
+    P = hp.pts
+    cols = sorted(set(range(0, hp.n, 5)) | set(range(hp.n - 40, hp.n)))
+    stats = ReplayStats()
+    band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    ab = 0.0 if prec_name == "fp64" else FP32_ABS * kp.variance
+    for i in cols:
+        cand = hp.cand_idx[hp.cand_ptr[i]:hp.cand_ptr[i + 1]]
+        replay_single(oracle, okp, P, i, cand, hp.k, sels[i], band, stats, abs_band=ab)
+    print(prec_name, n_cand, k, stats)
+    cp, ri, val, logv = fb.csc()
+    _check_fill_columns(oracle, okp, P, cols, sels, cp, ri, val, logv)
+    _, _, _, ologv = oracle.factor_columns(okp, P, sels)
+    assert float(fb.sum_logv.cpu()[0]) == pytest.approx(float(np.sum(ologv)), rel=1e-9)
+
+
 def _check_ordering_sampled(oracle, pts, hp, rng, n_pos=24, n_earlier=64):
     """Reverse-maximin at any size: ell2[p] is the squared distance to the later set and no
     sampled earlier point is farther from that set."""
