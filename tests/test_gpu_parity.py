@@ -237,6 +237,50 @@ def test_aggregated_small_full(env, oracle_lib, prec_name):
     print(f"{prec_name}: worst fill err {worst:.2e}; KL {oracle.kl_from_logv(float(fb.sum_logv.cpu()[0]), ld):.6g}")
 
 
+# launch shapes of the shared-memory / workspace supernodal kernel not met by the other tests:
+# (precision, candidates, k, largest group) -> threads per CTA, state in shared memory or not
+AGG_SHAPES = [("fp32", 200, 80, 16),    # 256 threads, shared memory (k > 64: not the register kernel)
+              ("fp32", 200, 128, 64),   # 256 threads, workspace
+              ("fp32", 400, 16, 16),    # 512 threads, shared memory
+              ("fp64", 200, 64, 64),    # 256 threads, workspace
+              ("fp64", 300, 16, 16)]    # 512 threads, shared memory
+
+
+@pytest.mark.parametrize("prec_name,n_cand,k,mmax", AGG_SHAPES)
+def test_aggregated_launch_shapes(env, oracle_lib, prec_name, n_cand, k, mmax):
+    """N = 2048 in 2-D (Matern 3/2, ell = 0.1, nugget 1e-6), supernodes of 4..mmax members;
+    every third group replayed by the oracle and its members' columns checked."""
+    torch, sic, pipeline, h = env
+    oracle = oracle_lib
+    kp = sic.kernel(2, 3, 0.1, 1.0, 1e-6)
+    hp = pipeline.prepare_groups(synthetic.points(2048, 2, 12), kp, n_cand, k, mmin=4, mmax=mmax)
+    assert hp.max_cand == n_cand
+    prec = sic.SIC_FP64 if prec_name == "fp64" else sic.SIC_FP32_MIXED
+    fb = _run(env, hp, prec)
+    sels = fb.sel_lists()
+    okp = _okernel(oracle, kp)
+    P = hp.pts
+    stats = ReplayStats()
+    band = TIE_BAND if prec_name == "fp64" else FP32_BAND
+    var_abs = 0.0 if prec_name == "fp64" else FP32_ABS * kp.variance
+    gp = hp.grp_ptr
+    G = len(gp) - 1
+    groups = sorted(set(range(0, G, 3)) | {G - 2, G - 1})
+    cp, ri, val, logv = fb.csc()
+    for g in groups:
+        g0, g1 = int(gp[g]), int(gp[g + 1])
+        cand = hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]]
+        replay_multi(oracle, okp, P, g0, g1 - g0, cand, hp.k, sels[g], band, stats, var_abs=var_abs)
+        for a in range(g1 - g0):
+            rows, L, lv = oracle.fill_member(okp, P, g0, g1 - g0, a, sels[g])
+            c = g0 + a
+            assert ri[cp[c]:cp[c + 1]].tolist() == rows.tolist()
+            assert column_errors(val[cp[c]:cp[c + 1]], L) <= L_TOL, f"member {a} of group {g}"
+            assert abs(logv[c] - lv) <= LOGV_TOL
+    print(prec_name, n_cand, k, mmax, stats)
+    assert np.all(np.isfinite(logv))
+
+
 @pytest.mark.parametrize("prec_name", ["fp32", "fp64"])
 def test_aggregated_full_size_sampled(env, oracle_lib, prec_name):
     """Config-3 workload at full size (N=2^20, 2-D, Matern 3/2, ell=0.02, nugget 1e-6,
