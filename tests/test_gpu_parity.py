@@ -420,7 +420,7 @@ def test_select_single_directed(env, oracle_lib, prec_name):
     print(prec_name, stats)
 
 
-@pytest.mark.parametrize("nrhs", [1, 3, 8])
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 8])
 def test_apply_factor(env, oracle_lib, nrhs):
     torch, sic, pipeline, h = env
     oracle = oracle_lib

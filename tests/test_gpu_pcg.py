@@ -29,7 +29,7 @@ def env():
     return torch, sic, pipeline, sic.Handle(0)
 
 
-@pytest.mark.parametrize("nrhs", [1, 3, 8])
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 8])
 def test_matvec_matches_dense(env, oracle_lib, nrhs):
     torch, sic, pipeline, h = env
     n = 3000
