@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts
             for (int a = 0; a < m; ++a) {
                 float dx = x[0] - mx[a * 3], dy = x[1] - mx[a * 3 + 1], dz = x[2] - mx[a * 3 + 2];
                 float d2 = dx * dx + dy * dy + dz * dz;
-                ksum += matern<float>(kp, sqrtf(d2));
+                ksum += matern<float>(kp, d2 > 1e-30f ? d2 * rsqrtf(d2) : 0.f);  // hardware rsqrt, ~2 ulp
                 if (d2 < best) { best = d2; ab = a; }
             }
             const float dmin = sqrtf(best);
