@@ -60,7 +60,10 @@ typedef struct {
     double nugget;        /* >= 0 */
 } sic_kernel;
 
-/* Arithmetic of the selection kernels.  The fill and the KL sum are always FP64. */
+/* Arithmetic of the selection kernels.  The fill and the KL sum are always FP64.
+ * SIC_FP64 evaluates the kernel with a table-driven exp and Newton square roots (about
+ * 2 ulp); SIC_FP32_MIXED uses the hardware's approximate reciprocal, reciprocal square
+ * root and exp (a few ulp of FP32), far below the FP32 state's own resolution. */
 typedef enum {
     SIC_FP64 = 0,        /* scores, partial factor and downdates in FP64 */
     SIC_FP32_MIXED = 1   /* kernel entries, partial factor and downdates in FP32 */
