@@ -18,8 +18,8 @@
 // Theta_{r,P} and solves for F2P by forward substitution (static loops);
 // then k steps, each with a single block barrier: the warp argmax is one redux over
 // order-preserving score keys (ties: lowest lane = lowest candidate index), the warp
-// winners go to double-buffered shared slots with their V1/V2, and every thread reduces
-// the eight slots itself.  Same scores, exhaustion rule and tie-break as k_select_agg.
+// winners go to double-buffered shared slots with their V1/V2, and every warp reduces the
+// eight slots itself with one more redux.  Same scores, exhaustion rule and tie-break as k_select_agg.
 #include <type_traits>
 
 #include "sic_internal.cuh"
@@ -341,19 +341,12 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                     pv2[buf][warp] = V2;
                 }
                 __syncthreads();
-                const uint4 k0 = *reinterpret_cast<const uint4*>(&pkey[buf][0]);
-                const uint4 k1 = *reinterpret_cast<const uint4*>(&pkey[buf][4]);
-                const unsigned kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
-                unsigned bk = kk[0];
-                int bw = 0;
-#pragma unroll
-                for (int w = 1; w < RNT / 32; ++w) {
-                    if (kk[w] > bk) {
-                        bk = kk[w];
-                        bw = w;
-                    }
-                }
+                // the eight warp winners (ascending rows), reduced by every warp: lane w < 8
+                // reads warp w's key; the lowest warp holding the maximum wins
+                const unsigned kw = (lane < RNT / 32) ? pkey[buf][lane] : 0u;
+                const unsigned bk = __reduce_max_sync(FULL, kw);
                 if (bk == 0u) return false;
+                const int bw = __ffs(__ballot_sync(FULL, lane < RNT / 32 && kw == bk)) - 1;
                 const int q = pidx[buf][bw];
                 const float r1 = rsqrtf(pv1[buf][bw]);
                 const float r2 = rsqrtf(pv2[buf][bw]);
