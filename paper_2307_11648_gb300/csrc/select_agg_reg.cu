@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
     __shared__ int pidx[2][RNT / 32];
     __shared__ float pv1[2][RNT / 32], pv2[2][RNT / 32];
     __shared__ float gv1[RK], gv2[RK];  // the picks' two conditional variances (gains only)
+    __shared__ int qs[RK];              // the picks' candidate rows, translated after the steps
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float NEG = -INFINITY;
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                     }
                 }
                 if (tid == 0) {
-                    sel_idx[g * k + t] = cand_idx[b0 + q];
+                    qs[t] = q;  // no global load on the step chain
                     if (gain) {
                         gv1[t] = pv1[buf][bw];
                         gv2[t] = pv2[buf][bw];
@@ -400,10 +401,12 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         if (steps(std::integral_constant<int, 0>{}) && steps(std::integral_constant<int, 1>{}) &&
             steps(std::integral_constant<int, 2>{}))
             steps(std::integral_constant<int, 3>{});
-        if (gain) {
-            // decreases of logdet Theta_{PP|I} per nonzero (Section 5.4.2), off the step chain
-            __syncthreads();
-            for (int q = tid; q < t; q += RNT) gain[g * k + q] = log((double)gv1[q] / (double)gv2[q]) / m;
+        // the picks' global indices and (with gain) the decreases of logdet Theta_{PP|I} per
+        // nonzero (Section 5.4.2), off the step chain
+        __syncthreads();
+        for (int q = tid; q < t; q += RNT) {
+            sel_idx[g * k + q] = cand_idx[b0 + qs[q]];
+            if (gain) gain[g * k + q] = log((double)gv1[q] / (double)gv2[q]) / m;
         }
         if (tid == 0) sel_count[g] = t;
         for (int q = t + tid; q < k; q += RNT) sel_idx[g * k + q] = -1;

@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(NT) k_select_columns_f32(
     __shared__ int widx[2][NW];
     __shared__ float wvar[2][NW], wcov[2][NW];
     __shared__ double gv[KMAX + 1];  // target variance before each pick (gains only)
+    __shared__ int qs[KMAX];         // the picks' candidate rows, translated after the steps
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr unsigned FULL = 0xffffffffu;
 
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(NT) k_select_columns_f32(
                     }
                 }
                 if (tid == 0) {
-                    sel_idx[c * k + t] = cand_idx[b0 + gi];
+                    qs[t] = gi;  // no global load on the step chain
                     if (gain) {
                         gv[t] = vt;
                         vt = fmax(vt - (double)ut * (double)ut, vfloor);
@@ -471,9 +472,10 @@ __global__ void __launch_bounds__(NT) k_select_columns_f32(
             }
         };
         static_for<0, KMAX / 8>(block);
-        if (gain) {
-            __syncthreads();
-            for (int q = tid; q < t; q += NT) gain[c * k + q] = log(gv[q] / gv[q + 1]);
+        __syncthreads();
+        for (int q = tid; q < t; q += NT) {
+            sel_idx[c * k + q] = cand_idx[b0 + qs[q]];
+            if (gain) gain[c * k + q] = log(gv[q] / gv[q + 1]);
         }
         if (tid == 0) sel_count[c] = t;
         for (int q = t + tid; q < k; q += NT) sel_idx[c * k + q] = -1;
