@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
     __shared__ int wix[NW];
     __shared__ int s_fail;
     __shared__ double gv1[128], gv2[128];  // the picks' two conditional variances (gains only)
+    __shared__ int qs[128];                // the picks' candidate rows, translated after the steps
 
     const long long Cm = L.Cm, mm = L.mm, ldx = L.Cm + L.mm;
     const long long P1 = L.p1(), P2 = L.p2(), P2t = L.p2t();
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                     }
                 }
                 if (tid == 0) {
-                    sel_idx[g * k + t] = cand_idx[b0 + q];
+                    qs[t] = q;  // no global load on the step chain
                     if (gain) {
                         gv1[t] = (double)v1q;
                         gv2[t] = (double)v2q;
@@ -303,10 +304,12 @@ __global__ void __launch_bounds__(NT, 1) k_select_agg(
                 }
             }
         }
-        if (gain) {
-            // decreases of logdet Theta_{PP|I} per nonzero (Section 5.4.2), off the step chain
-            __syncthreads();
-            for (int q = tid; q < t; q += NT) gain[g * k + q] = log(gv1[q] / gv2[q]) / m;
+        // the picks' global indices and (with gain) the decreases of logdet Theta_{PP|I} per
+        // nonzero (Section 5.4.2), off the step chain
+        __syncthreads();
+        for (int q = tid; q < t; q += NT) {
+            sel_idx[g * k + q] = cand_idx[b0 + qs[q]];
+            if (gain) gain[g * k + q] = log(gv1[q] / gv2[q]) / m;
         }
         if (tid == 0) sel_count[g] = t;
         for (int q = t + tid; q < k; q += NT) sel_idx[g * k + q] = -1;

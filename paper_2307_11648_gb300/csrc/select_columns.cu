@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(NT) k_select_columns(
     __shared__ T wscore[2][NW];
     __shared__ int widx[2][NW];
     __shared__ double gv[KMAX + 1];  // target variance before each pick (gains only)
+    __shared__ int qs[KMAX];         // the picks' candidate rows, translated after the steps
     __shared__ double tab[sizeof(T) == 8 ? EXP_TAB : 1];  // s2 2^(j/256): the FP64 Matern's exp
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(NT) k_select_columns(
                 }
             }
             if (tid == 0) {
-                sel_idx[c * k + t] = cand_idx[b0 + gi];
+                qs[t] = gi;  // no global load on the step chain
                 if (gain) {
                     gv[t] = vt;
                     vt = fmax(vt - (double)ut * (double)ut, vfloor);
@@ -236,9 +237,10 @@ __global__ void __launch_bounds__(NT) k_select_columns(
                 }
             }
         }
-        if (gain) {
-            __syncthreads();
-            for (int q = tid; q < t; q += NT) gain[c * k + q] = log(gv[q] / gv[q + 1]);
+        __syncthreads();
+        for (int q = tid; q < t; q += NT) {
+            sel_idx[c * k + q] = cand_idx[b0 + qs[q]];
+            if (gain) gain[c * k + q] = log(gv[q] / gv[q + 1]);
         }
         if (tid == 0) sel_count[c] = t;
         for (int q = t + tid; q < k; q += NT) sel_idx[c * k + q] = -1;
