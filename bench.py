@@ -703,7 +703,7 @@ def main():
     bf16_peak = measured_peak("bf16_tflops", 1900.0)
     fill_tf = fill_flops(hp.grp_ptr, sel_count_learned) / (fill_ms * 1e-3) / 1e12
     kernels = {
-        "k_select_agg<float> (256 candidates)": {"ms": sel_ms, "achieved_tflops": sel_tf, "peak_tflops": f32_peak,
+        "k_select_agg_reg (FP32, 256 candidates)": {"ms": sel_ms, "achieved_tflops": sel_tf, "peak_tflops": f32_peak,
                                                  "frac": sel_tf / f32_peak, "unit_peak": "FP32 FFMA"},
         "k_fill (FP64)": {"ms": fill_ms, "achieved_tflops": fill_tf, "peak_tflops": f64_peak,
                           "frac": fill_tf / f64_peak, "unit_peak": "FP64 DFMA"},
