@@ -15,9 +15,11 @@
 //   u_j = (Theta_{jq} - F_j . F_q) / sqrt(var_q) (left-looking, Appendix B.1),
 //   then var_j -= u_j^2 and cov_j -= u_j u_t with u_t = cov_q / sqrt(var_q)
 //   (eq. cond_select; the target's own row of the factor is never stored).
-// FP32 mode works in coordinates relative to the target (formed in FP64) so that
-// candidate-to-candidate differences keep their digits; FP64 mode evaluates Theta with the
-// fill's table-driven exp and Newton square root, and 1/sqrt(var_q) by Newton steps.
+// k_select_columns serves FP64 (it evaluates Theta with the fill's table-driven exp and
+// Newton square root, and 1/sqrt(var_q) by Newton steps); FP32 runs k_select_columns_f32
+// below, which works in coordinates relative to the target (formed in FP64) so that
+// candidate-to-candidate differences keep their digits, and reads the pivot's row from a
+// shared-memory mirror instead of a published slot.
 // With `gain` non-null, thread 0 also carries the target's variance v_t in FP64
 // (v_{t+1} = v_t - u_t^2, kept at or above the exhaustion floor: the target's own nugget is
 // never explained) and, after the column's last step, the threads write the picks'
