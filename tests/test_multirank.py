@@ -57,3 +57,19 @@ def test_flop_accounting_small_case():
     sc = np.array([4, 1])
     # group 1: n=6: 36 + (36 + 25)/2 = 66.5; group 2: n=4: 64/6 + (16 + 9 + 4)/2
     assert bench.fill_flops(gp, sc) == pytest.approx(2.0 * (216 / 6 + 30.5 + 64 / 6 + 14.5))
+
+
+def test_single_target_flop_accounting_by_steps():
+    """select_columns_flops against a step-by-step count of the same definition: at step t the
+    left-looking dot over t earlier picks for the C candidate rows and the target's row, then 3C
+    for the two downdates and the score (2 FLOPs per FMA)."""
+    import numpy as np
+
+    import bench
+    cp = np.array([0, 7, 7, 19, 20], np.int64)  # 7, 0, 12 and 1 candidates
+    sc = np.array([5, 0, 12, 1], np.int32)
+    want = 0.0
+    for C, picks in zip(np.diff(cp), sc):
+        for t in range(picks):
+            want += 2.0 * ((C + 1) * t + 3 * C)
+    assert bench.select_columns_flops(cp, sc) == pytest.approx(want)
