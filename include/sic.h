@@ -171,7 +171,9 @@ sic_status sic_select_single(sic_handle* h, const double* x_train, int64_t n, co
  * padding); sel_count[n_cols] [device] the number of picks.  All columns run in one
  * persistent launch.  Limits: 1 <= k <= 64, every candidate count <= max_cand <= 1024
  * (max_cand is the caller's bound on cand_ptr[c+1]-cand_ptr[c]; a column above it is
- * reported as SIC_ERR_INVALID by sic_sync).  No workspace. */
+ * reported as SIC_ERR_INVALID by sic_sync); k > 32 needs max_cand <= 512 in FP32 and
+ * max_cand <= 256 in FP64, k in 17..32 with max_cand > 512 needs FP32 (SIC_ERR_UNSUPPORTED
+ * otherwise).  No workspace. */
 sic_status sic_select_columns(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
                               const int32_t* targets, int64_t n_cols, const int64_t* cand_ptr,
                               const int32_t* cand_idx, int32_t max_cand, int32_t k, sic_precision prec,
