@@ -153,38 +153,65 @@ def fill_flops(grp_ptr, sel_count) -> float:
 
 # ------------------------------------------------------------- oracle ----
 
-def oracle_sample(hp, seconds: float, threads: int):
-    """Time the CPU oracle (FP64 two-factor greedy + per-member dense fill) on random
-    supernodes until `seconds` have elapsed.  Returns (columns/s, columns, groups, s)."""
+def _oracle_unit(okp, P, gp, cand_ptr, cand_idx, k, g):
+    """One supernode through the oracle: FP64 two-factor greedy, then the dense fill of
+    every member column.  Returns the member count."""
+    import oracle
+    g0, g1 = int(gp[g]), int(gp[g + 1])
+    cand = cand_idx[cand_ptr[g]:cand_ptr[g + 1]]
+    sel = oracle.select_multi(okp, P, g0, g1 - g0, cand, k)["sel"]
+    for a in range(g1 - g0):
+        oracle.fill_member(okp, P, g0, g1 - g0, a, sel)
+    return g1 - g0
+
+
+def oracle_batch(prob, groups, threads: int):
+    """Run the CPU oracle on the given supernodes over `threads` host threads.
+    Returns (columns, seconds)."""
     from concurrent.futures import ThreadPoolExecutor
 
     import oracle
     oracle.build()
-    kp = hp.kp
-    okp = oracle.kernel(kp.dim, kp.nu_x2, kp.length_scale, kp.variance, kp.nugget)
-    gp, P = hp.grp_ptr, hp.pts
-    G = len(gp) - 1
-    order = np.random.default_rng(0).permutation(G)
-
-    def one(g):
-        g0, g1 = int(gp[g]), int(gp[g + 1])
-        cand = hp.cand_idx[hp.cand_ptr[g]:hp.cand_ptr[g + 1]]
-        sel = oracle.select_multi(okp, P, g0, g1 - g0, cand, hp.k)["sel"]
-        for a in range(g1 - g0):
-            oracle.fill_member(okp, P, g0, g1 - g0, a, sel)
-        return g1 - g0
-
-    cols = groups = 0
+    kd = prob["kernel"]
+    okp = oracle.kernel(kd["dim"], kd["nu_x2"], kd["length_scale"], kd["variance"], kd["nugget"])
+    P, gp, cp, ci, k = prob["pts"], prob["grp_ptr"], prob["cand_ptr"], prob["cand_idx"], int(prob["k"])
     t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
-        i = 0
-        while time.perf_counter() - t0 < seconds and i < G:
-            batch = order[i:i + 4 * threads]
-            i += len(batch)
-            cols += sum(ex.map(one, batch))
-            groups += len(batch)
-    el = time.perf_counter() - t0
-    return cols / el, cols, groups, el
+        cols = sum(ex.map(lambda g: _oracle_unit(okp, P, gp, cp, ci, k, g), groups, chunksize=4))
+    return cols, time.perf_counter() - t0
+
+
+def oracle_sample(prob, seconds: float, threads: int, seed: int = 0):
+    """Time the CPU oracle on random supernodes of the problem for about `seconds`: a short
+    calibration batch, then one batch sized to fill the rest.  Returns
+    (columns/s, columns, groups, s) of the whole sample."""
+    G = len(prob["grp_ptr"]) - 1
+    order = np.random.default_rng(seed).permutation(G)
+    first = order[:2 * threads]
+    c0, t0 = oracle_batch(prob, first, threads)
+    rest = int(max(0.0, seconds - t0) * len(first) / max(t0, 1e-9))
+    second = order[len(first):len(first) + rest]
+    c1, t1 = oracle_batch(prob, second, threads) if len(second) else (0, 0.0)
+    return (c0 + c1) / (t0 + t1), c0 + c1, len(first) + len(second), t0 + t1
+
+
+def host_problem_dict(hp):
+    """The prepared inputs as plain arrays (what the oracle needs; no library objects)."""
+    kp = hp.kp
+    return {"pts": hp.pts, "grp_ptr": hp.grp_ptr, "cand_ptr": hp.cand_ptr, "cand_idx": hp.cand_idx, "k": hp.k,
+            "kernel": {"dim": kp.dim, "nu_x2": kp.nu_x2, "length_scale": kp.length_scale,
+                       "variance": kp.variance, "nugget": kp.nugget}}
+
+
+def prepared_by_child(path: str):
+    """The config-3 problem prepared (ordering, grouping, candidates: libsic host code) in a
+    child process and handed over as an .npz, so that the process timing the oracle never
+    loads libsic."""
+    subprocess.check_call([sys.executable, os.path.join(ROOT, "bench.py"), "--prep-only", path])
+    z = np.load(path)
+    kd = {key: z["kernel_" + key].item() for key in ("dim", "nu_x2", "length_scale", "variance", "nugget")}
+    return {"pts": z["pts"], "grp_ptr": z["grp_ptr"], "cand_ptr": z["cand_ptr"], "cand_idx": z["cand_idx"],
+            "k": int(z["k"]), "kernel": kd}
 
 
 # ---------------------------------------------------------------- main ---
@@ -296,27 +323,43 @@ def pcg_comparison(h, cfg, params, n, nrhs=8, shift=1e-4, tol=1e-8):
 
 
 def run_reference(args, ws, rank):
+    """The oracle arm: every step times the FP64 CPU oracle on a bounded random sample of the
+    config-3 supernodes (about --ref-seconds of work on all host cores); ms_per_step is that
+    sample's own wall time and value the sample's columns per second."""
     if rank != 0:
         return
-    cfg = synthetic.PRESETS[WORKLOAD]
-    hp = problem(cfg, cfg["seed"])
+    import tempfile
+    with tempfile.TemporaryDirectory() as td:
+        prob = prepared_by_child(os.path.join(td, "problem.npz"))
     threads = os.cpu_count() or 1
-    vals, cols_tot = [], 0
+    G = len(prob["grp_ptr"]) - 1
+    order = np.random.default_rng(0).permutation(G)
+    # calibration (untimed): groups per second on this host, to size the steps
+    c, t = oracle_batch(prob, order[:4 * threads], threads)
+    per_step = max(threads, int(args.ref_seconds * 4 * threads / max(t, 1e-9)))
+    pos = 4 * threads
     for _ in range(args.warmup):
-        oracle_sample(hp, 1.0, threads)
+        oracle_batch(prob, order[pos:pos + threads], threads)
+        pos += threads
+    step_s, cols_tot = [], 0
     for _ in range(args.steps):
-        v, cols, groups, el = oracle_sample(hp, args.ref_seconds, threads)
-        vals.append(v)
+        batch = np.take(order, np.arange(pos, pos + per_step), mode="wrap")
+        pos += per_step
+        cols, el = oracle_batch(prob, batch, threads)
+        step_s.append(el)
         cols_tot += cols
-    v = statistics.median(vals)
+    el_tot = sum(step_s)
+    v = cols_tot / el_tot
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "columns/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * hp.n / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "N=2^20 uniform [0,1]^2, Matern 3/2, ell=0.02, nugget 1e-6, supernodes 8..64, "
-                                   "C=1024, k=64 (plain greedy, FP64 CPU oracle)", "groups": hp.n_units},
+                                   "C=1024, k=64 (plain greedy, FP64 CPU oracle)", "groups": G,
+                       "step": f"{per_step} random supernodes per step (a bounded sample of the {G})"},
             "cpu_baseline": {"value": v, "unit": "columns/s", "cores": threads, "kind": "oracle",
-                             "sample": f"random supernodes, {args.ref_seconds:.0f} s per step of FP64 two-factor "
-                                       f"greedy + dense fill ({cols_tot} columns over {args.steps} steps)"},
+                             "sample": f"{per_step} random supernodes per step, FP64 two-factor greedy + dense fill "
+                                       f"on all 1024 candidates ({cols_tot} columns over {args.steps} steps, "
+                                       f"{el_tot:.1f} s); inputs prepared in a child process"},
             "e2e": {"value": v, "unit": "columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -328,7 +371,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sic", choices=["sic", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=5.0,
+                    help="oracle seconds per step of the reference arm (and of the cpu_baseline sample x 2)")
+    ap.add_argument("--prep-only", default="", help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-n", type=int, default=1 << 18, help="points per training problem")
     ap.add_argument("--epochs", type=int, default=3)
@@ -354,6 +399,12 @@ def main():
     ap.add_argument("--partial-n", type=int, default=1 << 18,
                     help="points of the partial-selection (nonadjacent groups) measurement (0: skip)")
     args = ap.parse_args()
+    if args.prep_only:
+        cfg = synthetic.PRESETS[WORKLOAD]
+        d = host_problem_dict(problem(cfg, cfg["seed"]))
+        kd = d.pop("kernel")
+        np.savez(args.prep_only, **d, **{"kernel_" + key: v for key, v in kd.items()})
+        return
     ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
@@ -734,7 +785,7 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        v, cols, groups, el = oracle_sample(hp, args.ref_seconds, threads)
+        v, cols, groups, el = oracle_sample(host_problem_dict(hp), 2 * args.ref_seconds, threads)
         cpu = {"value": v, "unit": "columns/s", "cores": threads, "kind": "oracle",
                "sample": f"{groups} random supernodes ({cols} columns), FP64 two-factor greedy + dense fill on all "
                          f"1024 candidates, {el:.1f} s"}

@@ -325,9 +325,11 @@ sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, 
  * Its scratch is a fixed static device array inside libsic (512 KiB, held by every GPU
  * that loads the library until the process exits), so n + 1 may not exceed
  * 67,108,864 (= 2^26); larger n returns SIC_ERR_UNSUPPORTED.  The call allocates
- * nothing: no cudaMalloc, cudaFree or allocating library routine.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and caches it; make
- * that first call before any stream capture.  All calls share the one array and it
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.  Outside stream
+ * capture every call looks up the array's device address (cudaGetSymbolAddress) on the
+ * current device, so a device reset between calls is harmless; a call made while `stream`
+ * is being captured reuses the address of the last uncaptured call on that device, so make
+ * one call on the device before any capture (else SIC_ERR_CUDA).  All calls share the one array and it
  * keeps the last call's contents (nothing in it needs to start at zero): calls that
  * may overlap on the GPU -- on different streams without an ordering between them, or
  * from several threads -- race on it and must be serialised by the caller. */

@@ -493,14 +493,21 @@ std::mutex g_noalloc_mutex;
 long long* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 
 // Device address of g_nnz_scratch on `device` (the current device).  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once per
-// device and cached.
-cudaError_t noalloc_scratch(int device, long long** out) {
+// array's name is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress.  Outside stream capture it is looked up on every call (a reset of
+// the device or a new primary context may load the module at another address); during a
+// capture the address of the last lookup on this device is used, so one call must have
+// been made on the device before the capture began.
+cudaError_t noalloc_scratch(int device, cudaStream_t s, long long** out) {
     if (device < 0 || device >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[device]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_noalloc_addr[device]) {
+        if (cap != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
         void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_nnz_scratch);
+        e = cudaGetSymbolAddress(&ptr, g_nnz_scratch);
         if (e != cudaSuccess) return e;
         g_noalloc_addr[device] = (long long*)ptr;
     }
@@ -517,9 +524,9 @@ extern "C" sic_status sic_factor_nnz_noalloc(sic_handle* h, const int64_t* grp_p
     const long long nb = (len + SCAN_TILE - 1) / SCAN_TILE;
     if (nb > NOALLOC_MAX_TILES) return SIC_ERR_UNSUPPORTED;  // beyond the static scratch
     SIC_CUDA_TRY(cudaSetDevice(h->device));
-    long long* partial = nullptr;
-    SIC_CUDA_TRY(noalloc_scratch(h->device, &partial));
     cudaStream_t s = (cudaStream_t)stream;
+    long long* partial = nullptr;
+    SIC_CUDA_TRY(noalloc_scratch(h->device, s, &partial));
     long long* v = (long long*)col_ptr;
     // the tile totals are written before they are read, so the scratch needs no clearing;
     // only the output's last entry must start at zero (as in sic_factor_nnz)
