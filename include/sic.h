@@ -142,6 +142,20 @@ sic_status sic_prep_candidates_partial(const double* pts, int64_t n, int32_t dim
                                        const int64_t* grp_ptr, int64_t n_grp, int32_t n_cand, int64_t* cand_ptr,
                                        int32_t* cand_idx, int32_t n_threads);
 
+/* Slices of one factor for several GPUs (Section 4: units are independent; see "one factor
+ * built in slices" below): contiguous unit ranges, part r = units bounds[r] .. bounds[r+1]-1
+ * (bounds[n_parts + 1], bounds[0] = 0, bounds[n_parts] = n_units), cut where the running
+ * estimated cost crosses r / n_parts of the total, so every part's cost is within one
+ * unit's cost of the even share.  Cost of unit u with C_u = min(cand_ptr[u+1] - cand_ptr[u],
+ * max_cand) candidates and m_u targets (grp_ptr[u+1] - grp_ptr[u]; 1 when grp_ptr is NULL),
+ * n_u = k + m_u:  C_u (k^2 + k m_u + m_u^2 / 2) + 13 (n_u^3 / 6 + m_u n_u^2 / 2)  -- the
+ * selection's FP32 multiply-adds (two partial factors, k picks) plus the fill's FP64
+ * multiply-adds, weighted by 13, the measured ratio of the fill's time per FP64
+ * multiply-add to the selection's time per FP32 multiply-add on GB300.  max_cand: the
+ * candidates the selection will see (e.g. the proposal's top count), <= 0 for all.  [host] */
+sic_status sic_prep_partition(const int64_t* cand_ptr, const int64_t* grp_ptr, int64_t n_units, int32_t k,
+                              int32_t max_cand, int32_t n_parts, int64_t* bounds);
+
 /* Candidates for directed GP regression (Section 3): pts holds the n_targets target
  * points first, then the training points.  For each target i < n_targets, the n_cand
  * training positions (>= n_targets) nearest to it, sorted by (distance, position), go
@@ -374,6 +388,44 @@ sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t n, const s
                             const int32_t* sel_count, int32_t k, const int64_t* col_ptr, int32_t* row_idx,
                             double* val, double* logv, double* sum_logv, void* ws, size_t ws_bytes,
                             void* stream);
+
+/* ------------------------------------------ one factor built in slices [device] -- */
+/*
+ * Section 4: the columns (or supernodes) of the factor are independent of one another, so
+ * one factor can be built in slices -- contiguous ranges of units, e.g. one per GPU, every
+ * slice holding all the points -- and the slices' CSC pieces concatenated.  A slice is the
+ * units u0 .. u1-1 of the whole problem: grp_ptr + u0 (n_grp = u1 - u0 groups, positions
+ * unchanged) or, without groups, the single columns u0 .. u1-1 (selected with
+ * sic_select_columns' `targets` = u0 .. u1-1); its columns are col0 .. col0 + n_cols - 1
+ * (col0 = grp_ptr[u0] or u0).
+ *
+ * sic_factor_nnz_range: col_ptr[0 .. n_cols] [device] for the slice's columns, starting at
+ * `base` (col_ptr[c - col0] is the offset of column c; base = 0 for a slice's own arrays, or
+ * the entries of all earlier slices for the whole factor's col_ptr).  Units outside the
+ * column range are reported by sic_sync as SIC_ERR_INVALID.  ws: sic_factor_nnz_workspace(
+ * n_cols) bytes.  sic_factor_nnz is the case col0 = 0, n_cols = n, base = 0.
+ *
+ * sic_build_factor_range: the fill of the slice (pts, n: all points).  Column c's entries go
+ * to row_idx / val at col_ptr[c - col0] - base, so row_idx / val hold just the slice's
+ * col_ptr[n_cols] - base entries; logv[n_cols] receives log v of the slice's columns and
+ * *sum_logv their fixed-order sum.  ws: sic_build_factor_workspace(n_cols) bytes.
+ * sic_build_factor is the case col0 = 0, n_cols = n, base = 0; the entries of a column do
+ * not depend on the slicing (each unit's arithmetic is the same).
+ *
+ * sic_sum_fixed: *sum [device] = the sum of x[0 .. n) [device] in the fixed order of
+ * sic_build_factor's sum_logv (tiles of 2048, then the tile sums), so that the log v of a
+ * factor gathered from slices sums to the bit-identical value of one whole build.  ws:
+ * sic_build_factor_workspace(n) bytes. */
+sic_status sic_factor_nnz_range(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, const int32_t* sel_count,
+                                int64_t col0, int64_t n_cols, int64_t base, int64_t* col_ptr, void* ws,
+                                size_t ws_bytes, void* stream);
+sic_status sic_build_factor_range(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                  const int64_t* grp_ptr, int64_t n_grp, int32_t max_m, const int32_t* sel_idx,
+                                  const int32_t* sel_count, int32_t k, int64_t col0, int64_t n_cols,
+                                  const int64_t* col_ptr, int64_t base, int32_t* row_idx, double* val, double* logv,
+                                  double* sum_logv, void* ws, size_t ws_bytes, void* stream);
+sic_status sic_sum_fixed(sic_handle* h, const double* x, int64_t n, double* sum, void* ws, size_t ws_bytes,
+                         void* stream);
 
 /* y = op(L) x for the CSC factor; x, y are n x nrhs row-major FP64 (x[r * nrhs + c]),
  * 1 <= nrhs <= 8, all [device].  SIC_OP_L: y = L x; SIC_OP_LT: y = L^T x;

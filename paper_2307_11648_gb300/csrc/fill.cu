@@ -28,8 +28,10 @@ constexpr int SUM_TILE = 2048;   // elements per partial-sum block
 
 // ---------------------------------------------------------------- nnz + scan --
 
+// Entry counts of the columns col0 .. col0 + n_cols - 1 (out[c - col0]); without groups unit u
+// is column col0 + u.
 __global__ void k_nnz_count(const long long* __restrict__ grp_ptr, long long n_grp, const int32_t* __restrict__ cnt,
-                            long long n, long long* __restrict__ out, DevStatus* st) {
+                            long long col0, long long n_cols, long long* __restrict__ out, DevStatus* st) {
     long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (u >= n_grp) return;
     if (!grp_ptr) {
@@ -37,12 +39,12 @@ __global__ void k_nnz_count(const long long* __restrict__ grp_ptr, long long n_g
         return;
     }
     long long g0 = grp_ptr[u], g1 = grp_ptr[u + 1];
-    if (g0 < 0 || g1 > n || g1 <= g0) {
+    if (g0 < col0 || g1 > col0 + n_cols || g1 <= g0) {
         record_error(st, SIC_ERR_INVALID, u);
         return;
     }
     int m = (int)(g1 - g0);
-    for (int a = 0; a < m; ++a) out[g0 + a] = (long long)(m - a) + cnt[u];
+    for (int a = 0; a < m; ++a) out[g0 - col0 + a] = (long long)(m - a) + cnt[u];
 }
 
 // Block-local exclusive scan of a tile; the tile total goes to partial[blockIdx].
@@ -98,9 +100,10 @@ __global__ void __launch_bounds__(256) k_scan_partials(long long* __restrict__ p
     if (threadIdx.x == 0) *total = carry;
 }
 
-__global__ void k_scan_add(long long* __restrict__ v, long long n, const long long* __restrict__ partial) {
+__global__ void k_scan_add(long long* __restrict__ v, long long n, const long long* __restrict__ partial,
+                           long long base) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) v[i] += partial[i / SCAN_TILE];
+    if (i < n) v[i] += partial[i / SCAN_TILE] + base;
 }
 
 // ------------------------------------------------------------------- the fill --
@@ -153,10 +156,11 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
                                                   const long long* __restrict__ grp_ptr, long long n_units,
                                                   const int32_t* __restrict__ sel_idx,
                                                   const int32_t* __restrict__ sel_count, int k, int max_m,
-                                                  int m_lo, int m_hi,
-                                                  long long n, const long long* __restrict__ col_ptr,
-                                                  int32_t* __restrict__ row_idx, double* __restrict__ val,
-                                                  double* __restrict__ logv, DevStatus* st) {
+                                                  int m_lo, int m_hi, long long n, long long col0,
+                                                  long long n_cols, const long long* __restrict__ col_ptr,
+                                                  long long base, int32_t* __restrict__ row_idx,
+                                                  double* __restrict__ val, double* __restrict__ logv,
+                                                  DevStatus* st) {
     extern __shared__ double smem_d[];
     const int nmax = k + m_hi;  // shared memory is laid out for this launch's size class
     double* G = smem_d;                                     // packed lower, nmax(nmax+1)/2
@@ -173,10 +177,11 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
     exp_table_fill(tab, kp.s2);
 
     for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const long long g0 = grp_ptr ? grp_ptr[u] : u;
+        const long long g0 = grp_ptr ? grp_ptr[u] : col0 + u;
         const int m = grp_ptr ? (int)(grp_ptr[u + 1] - g0) : 1;
         const int cnt = sel_count[u];
-        if (m < 1 || m > max_m || cnt < 0 || cnt > k || g0 < 0 || g0 + m > n) {
+        const long long c0 = g0 - col0;  // the unit's first column within the slice
+        if (m < 1 || m > max_m || cnt < 0 || cnt > k || g0 < 0 || g0 + m > n || c0 < 0 || c0 + m > n_cols) {
             if (tid == 0 && m_lo == 1) record_error(st, SIC_ERR_INVALID, u);  // reported by the first class
             continue;
         }
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
             else srt[rank] = v;
         }
         for (int a = worker ? tid : m; a < m; a += FILL_NT)
-            if (col_ptr[g0 + a + 1] - col_ptr[g0 + a] != (long long)(m - a + cnt)) bad = true;
+            if (col_ptr[c0 + a + 1] - col_ptr[c0 + a] != (long long)(m - a + cnt)) bad = true;
         if (__syncthreads_or(bad)) {
             if (tid == 0) record_error(st, SIC_ERR_INVALID, u);
             continue;
@@ -300,21 +305,21 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
                 }
             }
             if (has) {
-                const long long c0 = col_ptr[g0 + a];
+                const long long e0 = col_ptr[c0 + a] - base;
                 const double sc = rsqrt_newton(G[pk(jb, jb)]);
 #pragma unroll
                 for (int q = 0; q < FILL_HSLOTS; ++q) {
                     const int i = hl + 16 * q;
                     if (i <= jb) {
-                        row_idx[c0 + jb - i] = pos[i];
-                        val[c0 + jb - i] = bv[q] * sc;
+                        row_idx[e0 + jb - i] = pos[i];
+                        val[e0 + jb - i] = bv[q] * sc;
                     }
                 }
             }
         }
         // log v of every member, one member per thread (the FP64 log once per lane instead of
         // once per warp)
-        for (int a = worker ? tid : m; a < m; a += FILL_NT) logv[g0 + a] = log(G[pk(nn - 1 - a, nn - 1 - a)]);
+        for (int a = worker ? tid : m; a < m; a += FILL_NT) logv[c0 + a] = log(G[pk(nn - 1 - a, nn - 1 - a)]);
         __syncthreads();
     }
 }
@@ -396,26 +401,40 @@ extern "C" sic_status sic_factor_nnz_workspace(int64_t n, size_t* bytes) {
     return SIC_OK;
 }
 
-extern "C" sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, const int32_t* sel_count,
-                                     int64_t n, int64_t* col_ptr, void* ws, size_t ws_bytes, void* stream) {
-    if (!h || !sel_count || !col_ptr || n < 1 || n_grp < 1 || (!grp_ptr && n_grp != n)) return SIC_ERR_INVALID;
-    size_t need = 0;
-    sic_factor_nnz_workspace(n, &need);
-    if (!ws || ws_bytes < need) return SIC_ERR_INVALID;
-    SIC_CUDA_TRY(cudaSetDevice(h->device));
-    cudaStream_t s = (cudaStream_t)stream;
-    long long* v = (long long*)col_ptr;
-    long long* partial = (long long*)ws;
-    long long len = n + 1;
-    long long nb = (len + SCAN_TILE - 1) / SCAN_TILE;
-    SIC_CUDA_TRY(cudaMemsetAsync(v + n, 0, sizeof(long long), s));
-    k_nnz_count<<<(unsigned)((n_grp + 255) / 256), 256, 0, s>>>((const long long*)grp_ptr, n_grp, sel_count, n, v,
-                                                                  h->d_status);
+// count + exclusive scan of the columns col0 .. col0 + n_cols - 1 into col_ptr[0 .. n_cols],
+// offsets starting at `base`; `partial` holds the tile totals (nb + 1 entries)
+static sic_status launch_nnz(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, const int32_t* sel_count,
+                             long long col0, long long n_cols, long long base, long long* v, long long* partial,
+                             cudaStream_t s) {
+    const long long len = n_cols + 1;
+    const long long nb = (len + SCAN_TILE - 1) / SCAN_TILE;
+    SIC_CUDA_TRY(cudaMemsetAsync(v + n_cols, 0, sizeof(long long), s));
+    k_nnz_count<<<(unsigned)((n_grp + 255) / 256), 256, 0, s>>>((const long long*)grp_ptr, n_grp, sel_count, col0,
+                                                                  n_cols, v, h->d_status);
     k_scan_tile<<<(unsigned)nb, 256, 0, s>>>(v, len, partial);
     k_scan_partials<<<1, 256, 0, s>>>(partial, nb, partial + nb);
-    k_scan_add<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(v, len, partial);
+    k_scan_add<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(v, len, partial, base);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
+}
+
+extern "C" sic_status sic_factor_nnz_range(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp,
+                                           const int32_t* sel_count, int64_t col0, int64_t n_cols, int64_t base,
+                                           int64_t* col_ptr, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || !sel_count || !col_ptr || col0 < 0 || n_cols < 1 || n_grp < 1 || base < 0 ||
+        (!grp_ptr && n_grp != n_cols))
+        return SIC_ERR_INVALID;
+    size_t need = 0;
+    sic_factor_nnz_workspace(n_cols, &need);
+    if (!ws || ws_bytes < need) return SIC_ERR_INVALID;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    return launch_nnz(h, grp_ptr, n_grp, sel_count, col0, n_cols, base, (long long*)col_ptr, (long long*)ws,
+                      (cudaStream_t)stream);
+}
+
+extern "C" sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int64_t n_grp, const int32_t* sel_count,
+                                     int64_t n, int64_t* col_ptr, void* ws, size_t ws_bytes, void* stream) {
+    return sic_factor_nnz_range(h, grp_ptr, n_grp, sel_count, 0, n, 0, col_ptr, ws, ws_bytes, stream);
 }
 
 // sum of log v in a fixed order (two launches), shared with the partial-pattern fill
@@ -434,19 +453,21 @@ extern "C" sic_status sic_build_factor_workspace(int64_t n, size_t* bytes) {
     return SIC_OK;
 }
 
-extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
-                                       const int64_t* grp_ptr, int64_t n_grp, int32_t max_m, const int32_t* sel_idx,
-                                       const int32_t* sel_count, int32_t k, const int64_t* col_ptr,
-                                       int32_t* row_idx, double* val, double* logv, double* sum_logv, void* ws,
-                                       size_t ws_bytes, void* stream) {
+extern "C" sic_status sic_build_factor_range(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                             const int64_t* grp_ptr, int64_t n_grp, int32_t max_m,
+                                             const int32_t* sel_idx, const int32_t* sel_count, int32_t k,
+                                             int64_t col0, int64_t n_cols, const int64_t* col_ptr, int64_t base,
+                                             int32_t* row_idx, double* val, double* logv, double* sum_logv, void* ws,
+                                             size_t ws_bytes, void* stream) {
     if (!h || !pts || !sic_valid_kernel(kp) || n < 1 || n_grp < 1 || !sel_count || !col_ptr || !row_idx || !val ||
-        !logv || !sum_logv || k < 0 || (k > 0 && !sel_idx))
+        !logv || !sum_logv || k < 0 || (k > 0 && !sel_idx) || col0 < 0 || n_cols < 1 || col0 + n_cols > n ||
+        base < 0)
         return SIC_ERR_INVALID;
-    if (!grp_ptr && (n_grp != n || max_m != 1)) return SIC_ERR_INVALID;
+    if (!grp_ptr && (n_grp != n_cols || max_m != 1)) return SIC_ERR_INVALID;
     if (max_m < 1) return SIC_ERR_INVALID;
     if (max_m > 64 || k > 128) return SIC_ERR_UNSUPPORTED;
     size_t need = 0;
-    sic_build_factor_workspace(n, &need);
+    sic_build_factor_workspace(n_cols, &need);
     if (!ws || ws_bytes < need) return SIC_ERR_INVALID;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -468,14 +489,33 @@ extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t
         SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int grid = persistent_grid(h, kern, block, sm, n_grp);
         kern<<<grid, block, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp, sel_idx,
-                                     sel_count, k, max_m, lo, hi, n, (const long long*)col_ptr, row_idx, val, logv,
-                                     h->d_status);
+                                     sel_count, k, max_m, lo, hi, n, col0, n_cols, (const long long*)col_ptr, base,
+                                     row_idx, val, logv, h->d_status);
     }
-    long long nb = (n + SUM_TILE - 1) / SUM_TILE;
-    k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n, (double*)ws);
+    long long nb = (n_cols + SUM_TILE - 1) / SUM_TILE;
+    k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n_cols, (double*)ws);
     k_sum_final<<<1, 256, 0, s>>>((const double*)ws, nb, sum_logv);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
+}
+
+extern "C" sic_status sic_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                       const int64_t* grp_ptr, int64_t n_grp, int32_t max_m, const int32_t* sel_idx,
+                                       const int32_t* sel_count, int32_t k, const int64_t* col_ptr,
+                                       int32_t* row_idx, double* val, double* logv, double* sum_logv, void* ws,
+                                       size_t ws_bytes, void* stream) {
+    return sic_build_factor_range(h, pts, n, kp, grp_ptr, n_grp, max_m, sel_idx, sel_count, k, 0, n, col_ptr, 0,
+                                  row_idx, val, logv, sum_logv, ws, ws_bytes, stream);
+}
+
+extern "C" sic_status sic_sum_fixed(sic_handle* h, const double* x, int64_t n, double* sum, void* ws, size_t ws_bytes,
+                                    void* stream) {
+    if (!h || !x || !sum || n < 1) return SIC_ERR_INVALID;
+    size_t need = 0;
+    sic_build_factor_workspace(n, &need);
+    if (!ws || ws_bytes < need) return SIC_ERR_INVALID;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    return launch_sum_logv(x, n, sum, ws, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------ allocation-free nnz scan --
@@ -530,12 +570,5 @@ extern "C" sic_status sic_factor_nnz_noalloc(sic_handle* h, const int64_t* grp_p
     long long* v = (long long*)col_ptr;
     // the tile totals are written before they are read, so the scratch needs no clearing;
     // only the output's last entry must start at zero (as in sic_factor_nnz)
-    SIC_CUDA_TRY(cudaMemsetAsync(v + n, 0, sizeof(long long), s));
-    k_nnz_count<<<(unsigned)((n_grp + 255) / 256), 256, 0, s>>>((const long long*)grp_ptr, n_grp, sel_count, n, v,
-                                                                  h->d_status);
-    k_scan_tile<<<(unsigned)nb, 256, 0, s>>>(v, len, partial);
-    k_scan_partials<<<1, 256, 0, s>>>(partial, nb, partial + nb);
-    k_scan_add<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(v, len, partial);
-    SIC_CUDA_TRY(cudaGetLastError());
-    return SIC_OK;
+    return launch_nnz(h, grp_ptr, n_grp, sel_count, 0, n, 0, v, partial, s);
 }

@@ -453,3 +453,35 @@ extern "C" sic_status sic_prep_candidates_partial(const double* pts, int64_t n, 
     }
     return SIC_OK;
 }
+
+// Contiguous unit ranges of near-equal estimated cost for building one factor in slices.
+extern "C" sic_status sic_prep_partition(const int64_t* cand_ptr, const int64_t* grp_ptr, int64_t n_units, int32_t k,
+                                         int32_t max_cand, int32_t n_parts, int64_t* bounds) {
+    if (!cand_ptr || !bounds || n_units < 0 || k < 0 || n_parts < 1) return SIC_ERR_INVALID;
+    // running cost W[u] of units 0 .. u-1
+    std::vector<double> W((size_t)n_units + 1, 0.0);
+    const double kk = (double)k;
+    for (int64_t u = 0; u < n_units; ++u) {
+        int64_t c = cand_ptr[u + 1] - cand_ptr[u];
+        if (c < 0) return SIC_ERR_INVALID;
+        if (max_cand > 0 && c > max_cand) c = max_cand;
+        const int64_t mi = grp_ptr ? grp_ptr[u + 1] - grp_ptr[u] : 1;
+        if (mi < 1) return SIC_ERR_INVALID;
+        const double m = (double)mi, C = (double)c, nn = kk + m;
+        const double select = C * (kk * kk + kk * m + 0.5 * m * m);
+        const double fill = nn * nn * nn / 6.0 + 0.5 * m * nn * nn;
+        W[(size_t)u + 1] = W[(size_t)u] + select + 13.0 * fill;
+    }
+    const double total = W[(size_t)n_units];
+    bounds[0] = 0;
+    for (int32_t r = 1; r < n_parts; ++r) {
+        // first u with W[u] >= r / n_parts of the total (the cut falls between units)
+        const double target = total * (double)r / (double)n_parts;
+        int64_t u = (int64_t)(std::lower_bound(W.begin(), W.end(), target) - W.begin());
+        if (u > n_units) u = n_units;
+        if (u < bounds[r - 1]) u = bounds[r - 1];
+        bounds[r] = u;
+    }
+    bounds[n_parts] = n_units;
+    return SIC_OK;
+}

@@ -80,8 +80,8 @@ def reduced_problem(hp: pipeline.HostProblem, top: int) -> pipeline.HostProblem:
     cnt = np.minimum(np.diff(hp.cand_ptr), top)
     ptr = np.zeros(len(cnt) + 1, np.int64)
     ptr[1:] = np.cumsum(cnt)
-    return pipeline.HostProblem(hp.pts, hp.kp, hp.k, ptr, np.zeros(max(int(ptr[-1]), 1), np.int32), hp.grp_ptr,
-                                hp.order, hp.ell2)
+    bounds = None if hp.bounds is None else (min(hp.bounds[0], top), hp.bounds[1])
+    return dataclasses.replace(hp, cand_ptr=ptr, cand_idx=np.zeros(max(int(ptr[-1]), 1), np.int32), bounds=bounds)
 
 
 class LearnedFactorBuilder:
@@ -102,7 +102,7 @@ class LearnedFactorBuilder:
             class _R:
                 pass
             r = _R()
-            r.hp, r.pts, r.grp_ptr = self.rhp, dp.pts, dp.grp_ptr
+            r.hp, r.pts, r.grp_ptr, r.targets = self.rhp, dp.pts, dp.grp_ptr, getattr(dp, "targets", None)
             r.cand_ptr, r.cand_idx = self.buf["out_ptr"], self.buf["out_idx"]
             self.rdp = r
         return self.rdp

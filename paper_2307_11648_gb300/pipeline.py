@@ -13,6 +13,7 @@ be replayed (and captured in a CUDA graph) without allocation.
 """
 from __future__ import annotations
 
+import dataclasses
 from dataclasses import dataclass
 
 import numpy as np
@@ -31,21 +32,39 @@ class HostProblem:
     order: np.ndarray | None = None    # old point index per position (for reference)
     ell2: np.ndarray | None = None
     members: np.ndarray | None = None  # nonadjacent groups: member positions (grp_ptr indexes it)
+    col0: int = 0                      # a slice of a larger factor: its first column ...
+    n_cols: int | None = None          # ... and its column count (None: all n columns)
+    targets: np.ndarray | None = None  # single columns of a slice: their positions (int32)
+    bounds: tuple | None = None        # (max_cand, max_m) of the whole problem, kept by a slice so
+                                       # that its launches take the whole build's shapes
 
     @property
     def n(self):
         return self.pts.shape[0]
 
     @property
+    def ncols(self):
+        """Columns of the factor this problem builds (all n, or a slice's)."""
+        return self.n if self.n_cols is None else self.n_cols
+
+    @property
+    def sliced(self):
+        return self.col0 != 0 or self.ncols != self.n
+
+    @property
     def n_units(self):
-        return self.n if self.grp_ptr is None else len(self.grp_ptr) - 1
+        return len(self.cand_ptr) - 1
 
     @property
     def max_cand(self):
+        if self.bounds is not None:
+            return self.bounds[0]
         return int(np.max(np.diff(self.cand_ptr))) if self.n_units else 0
 
     @property
     def max_m(self):
+        if self.bounds is not None:
+            return self.bounds[1]
         return 1 if self.grp_ptr is None else int(np.max(np.diff(self.grp_ptr)))
 
     @property
@@ -92,6 +111,22 @@ def prepare_partial(points: np.ndarray, kp: sic.Kernel, n_cand: int, k: int, mmi
     return HostProblem(P, kp, k, ptr, idx, gp, order, ell2, members)
 
 
+def slice_problem(hp: HostProblem, u0: int, u1: int) -> HostProblem:
+    """Units u0 .. u1-1 of hp as a problem of their own (a slice of hp's factor, Section 4:
+    units are independent): the same points, the units' candidate lists (offsets from 0) and
+    their columns col0 .. col0 + n_cols - 1 (for single columns, targets u0 .. u1-1)."""
+    cp = hp.cand_ptr[u0:u1 + 1]
+    ptr = np.ascontiguousarray(cp - cp[0])
+    idx = np.ascontiguousarray(hp.cand_idx[int(cp[0]):int(cp[-1])])
+    bounds = (hp.max_cand, hp.max_m)
+    if hp.grp_ptr is None:
+        return dataclasses.replace(hp, cand_ptr=ptr, cand_idx=idx, col0=int(u0), n_cols=int(u1 - u0),
+                                   targets=np.arange(u0, u1, dtype=np.int32), bounds=bounds)
+    gp = np.ascontiguousarray(hp.grp_ptr[u0:u1 + 1])
+    return dataclasses.replace(hp, cand_ptr=ptr, cand_idx=idx, grp_ptr=gp, col0=int(gp[0]),
+                               n_cols=int(gp[-1] - gp[0]), bounds=bounds)
+
+
 class DeviceProblem:
     def __init__(self, hp: HostProblem, device="cuda"):
         import torch
@@ -103,6 +138,7 @@ class DeviceProblem:
         self.cand_idx = torch.from_numpy(idx).to(device)
         self.grp_ptr = torch.from_numpy(hp.grp_ptr).to(device) if hp.grp_ptr is not None else None
         self.members = torch.from_numpy(hp.members).to(device) if hp.members is not None else None
+        self.targets = torch.from_numpy(hp.targets).to(device) if hp.targets is not None else None
 
 
 class FactorBuilder:
@@ -129,25 +165,26 @@ class FactorBuilder:
             self.local_count = torch.empty(U, dtype=torch.int32, device=dev)
             self.gain = torch.empty(U * k, dtype=torch.float64, device=dev)
             self.ws_alloc = sic._ws(sic.allocate_global_workspace(U, k), dev)
-        self.col_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        nc = hp.ncols
+        self.col_ptr = torch.empty(nc + 1, dtype=torch.int64, device=dev)
         # capacity: every column holds at most (its group's later members) + k + 1 entries
         if nnz_cap is None:
             if hp.grp_ptr is None:
-                nnz_cap = n * (k + 1)
+                nnz_cap = nc * (k + 1)
             else:
                 m = np.diff(hp.grp_ptr)
                 nnz_cap = int(np.sum(m * (m + 1) // 2 + m * k))
         self.nnz_cap = nnz_cap
         self.row_idx = torch.empty(nnz_cap, dtype=torch.int32, device=dev)
         self.val = torch.empty(nnz_cap, dtype=torch.float64, device=dev)
-        self.logv = torch.empty(n, dtype=torch.float64, device=dev)
+        self.logv = torch.empty(nc, dtype=torch.float64, device=dev)
         self.sum_logv = torch.zeros(1, dtype=torch.float64, device=dev)
         if hp.grp_ptr is None:
             self.ws_sel = None
         else:
             self.ws_sel = sic._ws(sic.select_aggregated_workspace(h, U, hp.max_cand, hp.max_m, k, prec), dev)
-        self.ws_nnz = sic._ws(sic.factor_nnz_workspace(n), dev)
-        self.ws_fill = sic._ws(sic.build_factor_workspace(n), dev)
+        self.ws_nnz = sic._ws(sic.factor_nnz_workspace(nc), dev)
+        self.ws_fill = sic._ws(sic.build_factor_workspace(nc), dev)
 
     def select(self, dp: DeviceProblem, stream=None):
         self.select_local(dp, stream)
@@ -160,7 +197,8 @@ class FactorBuilder:
         own = None if self.side_fp64 else self.gain
         if hp.grp_ptr is None:
             sic.select_columns(self.h, dp.pts, hp.kp, dp.cand_ptr, dp.cand_idx, hp.max_cand, hp.k, self.prec,
-                               self.sel_idx, self.local_count, stream=stream, gain=own)
+                               self.sel_idx, self.local_count, targets=getattr(dp, "targets", None), stream=stream,
+                               gain=own)
         else:
             sic.select_aggregated(self.h, dp.pts, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, hp.max_cand, hp.max_m,
                                   hp.k, self.prec, self.sel_idx, self.local_count, self.ws_sel, stream=stream,
@@ -181,9 +219,23 @@ class FactorBuilder:
 
     def fill(self, dp: DeviceProblem, stream=None):
         hp = self.hp
+        if hp.sliced:
+            sic.factor_nnz_range(self.h, dp.grp_ptr, self.sel_count, hp.col0, hp.ncols, 0, self.col_ptr,
+                                 self.ws_nnz, stream=stream)
+            sic.build_factor_range(self.h, dp.pts, hp.kp, dp.grp_ptr, hp.max_m, self.sel_idx, self.sel_count, hp.k,
+                                   hp.col0, hp.ncols, self.col_ptr, 0, self.row_idx, self.val, self.logv,
+                                   self.sum_logv, self.ws_fill, stream=stream)
+            return
         sic.factor_nnz(self.h, dp.grp_ptr, self.sel_count, hp.n, self.col_ptr, self.ws_nnz, stream=stream)
         sic.build_factor(self.h, dp.pts, hp.kp, dp.grp_ptr, hp.max_m, self.sel_idx, self.sel_count, hp.k,
                          self.col_ptr, self.row_idx, self.val, self.logv, self.sum_logv, self.ws_fill, stream=stream)
+
+    def col_ptr_from(self, dp: DeviceProblem, base: int, out, stream=None):
+        """out[0 .. ncols] = this build's column pointers with offsets starting at `base` (the
+        entries of the slices before it): the slice's part of the whole factor's col_ptr."""
+        hp = self.hp
+        sic.factor_nnz_range(self.h, dp.grp_ptr, self.sel_count, hp.col0, hp.ncols, base, out, self.ws_nnz,
+                             stream=stream)
 
     def run(self, dp: DeviceProblem, stream=None):
         self.select(dp, stream)
@@ -233,8 +285,8 @@ class PartialFactorBuilder:
         self.val = torch.empty(self.nnz_cap, dtype=torch.float64, device=dev)
         self.logv = torch.empty(n, dtype=torch.float64, device=dev)
         self.sum_logv = torch.zeros(1, dtype=torch.float64, device=dev)
-        self.ws_nnz = sic._ws(sic.factor_nnz_workspace(n), dev)
-        self.ws_fill = sic._ws(sic.build_factor_workspace(n), dev)
+        self.ws_nnz = sic._ws(sic.factor_nnz_workspace(nc), dev)
+        self.ws_fill = sic._ws(sic.build_factor_workspace(nc), dev)
 
     def select(self, dp: DeviceProblem, stream=None):
         hp = self.hp

@@ -32,7 +32,7 @@ EXPORTS = [
     "sic_build_factor_partial", "sic_tune_build_factor", "sic_tune_save", "sic_tune_load", "sic_tune_count",
     "sic_tune_entry",
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
-    "sic_build_factor",
+    "sic_build_factor", "sic_prep_partition", "sic_factor_nnz_range", "sic_build_factor_range", "sic_sum_fixed",
     "sic_apply_factor_workspace", "sic_apply_factor",
     "sic_matern_matvec", "sic_pcg_workspace", "sic_pcg_solve", "sic_selftest_wait_timeout",
     "sic_selftest_fp64_math",
@@ -83,6 +83,11 @@ def lib():
             "sic_prep_candidates_targets": (st, [vp, i64, i32, i64, i32, vp, vp, i32]),
             "sic_gp_predict": (st, [vp, vp, i64, pk, vp, i64, vp, vp, i32, vp, vp, vp, vp]),
             "sic_prep_groups": (st, [vp, vp, i64, i32, i32, d, i32, i32, vp, vp, vp, i32]),
+            "sic_prep_partition": (st, [vp, vp, i64, i32, i32, i32, vp]),
+            "sic_factor_nnz_range": (st, [vp, vp, i64, vp, i64, i64, i64, vp, vp, sz, vp]),
+            "sic_build_factor_range": (st, [vp, vp, i64, pk, vp, i64, i32, vp, vp, i32, i64, i64, vp, i64, vp, vp,
+                                            vp, vp, vp, sz, vp]),
+            "sic_sum_fixed": (st, [vp, vp, i64, vp, vp, sz, vp]),
             "sic_prep_candidates_groups": (st, [vp, i64, i32, vp, i64, i32, vp, vp, i32]),
             "sic_select_single_workspace": (st, [i64, i32, st, C.POINTER(sz)]),
             "sic_select_single": (st, [vp, vp, i64, vp, pk, i32, st, vp, vp, vp, vp, sz, vp]),
@@ -257,6 +262,17 @@ def prep_groups(pts: np.ndarray, ell2: np.ndarray, K: int, lam: float = 1.5, mmi
                                  _hptr(members, np.int64), _hptr(gp, np.int64), _hptr(ng, np.int64), n_threads),
            "sic_prep_groups")
     return members, gp[:ng[0] + 1].copy()
+
+
+def prep_partition(cand_ptr: np.ndarray, grp_ptr, k: int, n_parts: int, max_cand: int = 0) -> np.ndarray:
+    """sic_prep_partition: unit bounds of n_parts contiguous slices of near-equal cost."""
+    cand_ptr = np.ascontiguousarray(cand_ptr, dtype=np.int64)
+    gp = np.ascontiguousarray(grp_ptr, dtype=np.int64) if grp_ptr is not None else None
+    bounds = np.empty(n_parts + 1, np.int64)
+    _check(lib().sic_prep_partition(_hptr(cand_ptr, np.int64), _hptr(gp, np.int64) if gp is not None else None,
+                                    len(cand_ptr) - 1, k, max_cand, n_parts, _hptr(bounds, np.int64)),
+           "sic_prep_partition")
+    return bounds
 
 
 def prep_candidates_groups(pts: np.ndarray, grp_ptr: np.ndarray, n_cand: int, n_threads: int = 0):
@@ -482,6 +498,39 @@ def factor_nnz_noalloc(h: Handle, grp_ptr, sel_count, n: int, col_ptr, stream=No
                                         _dptr(sel_count, torch.int32, "sel_count"), n,
                                         _dptr(col_ptr, torch.int64, "col_ptr"), _stream(stream)),
            "sic_factor_nnz_noalloc", h)
+
+
+def factor_nnz_range(h: Handle, grp_ptr, sel_count, col0: int, n_cols: int, base: int, col_ptr, ws, stream=None):
+    """sic_factor_nnz_range: col_ptr[0 .. n_cols] of the slice's columns, starting at base."""
+    import torch
+    n_grp = grp_ptr.numel() - 1 if grp_ptr is not None else n_cols
+    _check(lib().sic_factor_nnz_range(h.ptr, _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp,
+                                      _dptr(sel_count, torch.int32, "sel_count"), col0, n_cols, base,
+                                      _dptr(col_ptr, torch.int64, "col_ptr"), _dptr(ws), ws.numel(), _stream(stream)),
+           "sic_factor_nnz_range", h)
+
+
+def build_factor_range(h: Handle, pts, kp: Kernel, grp_ptr, max_m: int, sel_idx, sel_count, k: int, col0: int,
+                       n_cols: int, col_ptr, base: int, row_idx, val, logv, sum_logv, ws, stream=None):
+    """sic_build_factor_range: the fill of the slice of columns col0 .. col0 + n_cols - 1."""
+    import torch
+    n = pts.shape[0]
+    n_grp = grp_ptr.numel() - 1 if grp_ptr is not None else n_cols
+    _check(lib().sic_build_factor_range(h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp),
+                                        _dptr(grp_ptr, torch.int64, "grp_ptr"), n_grp, max_m,
+                                        _dptr(sel_idx, torch.int32, "sel_idx"),
+                                        _dptr(sel_count, torch.int32, "sel_count"), k, col0, n_cols,
+                                        _dptr(col_ptr, torch.int64, "col_ptr"), base,
+                                        _dptr(row_idx, torch.int32, "row_idx"), _dptr(val, torch.float64, "val"),
+                                        _dptr(logv, torch.float64, "logv"), _dptr(sum_logv, torch.float64, "sum_logv"),
+                                        _dptr(ws), ws.numel(), _stream(stream)), "sic_build_factor_range", h)
+
+
+def sum_fixed(h: Handle, x, out, ws, stream=None):
+    """sic_sum_fixed: out[0] = sum of x in the fill's fixed order."""
+    import torch
+    _check(lib().sic_sum_fixed(h.ptr, _dptr(x, torch.float64, "x"), x.numel(), _dptr(out, torch.float64, "out"),
+                               _dptr(ws), ws.numel(), _stream(stream)), "sic_sum_fixed", h)
 
 
 def build_factor_workspace(n: int) -> int:

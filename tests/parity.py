@@ -1,30 +1,86 @@
 """Parity helpers: compare the CUDA path's selections and factor with the oracle.
 
 Selections are compared by *oracle replay*: run the oracle; at the first step where the
-GPU picked differently, the oracle's own score of the GPU's pick must be within the
-stated relative band of the oracle's best score at that step (a near-tie); the oracle
-then continues from the GPU's pick.  Counts must match under the replayed prefix.
-Returns the number of steps that needed the band, so tests can report it.
+GPU picked differently, the oracle scores the GPU's pick in the same state (the same
+earlier picks); if the pick is acceptable the oracle continues from it.  Counts must
+match under the replayed prefix.
+
+What is compared is each pick's decrease of the unit's objective, in nats of 2 KL
+(eq. obj_chol: 2 KL = sum_i log v_i - logdet Theta), computed by the oracle in FP64:
+  * single target (Section 3.1): D = log(v_t / v_{t+1}) = -log(1 - cov_j^2 / (var_j v_t)),
+    v_t the target's conditional variance before the step;
+  * supernode (Section 5.2, eq. greedy_mult): D = log(var_j|I / var_j|I,P), the decrease of
+    logdet Theta_{PP|I}.
+The gap of a differing pick is g = D(oracle best) - D(GPU pick) >= 0.
+
+FP64 selections: a differing pick is a near-tie when the two scores agree to TIE_BAND
+relative (1e-10); nothing else is accepted.
+
+FP32 selections (the benchmark spec precision split: state in FP32): a differing pick is accepted
+when g <= REL32 * D(best) + delta, where REL32 = 1e-3 is the stated relative band and
+delta is what FP32 arithmetic cannot resolve in this state.  Derivation of delta: after
+t picks every FP32 conditional (co)variance carries an absolute error of at most
+E = E32 * (t + 1) * sigma^2 with E32 = 8 eps32 = 4.8e-7: the kernel entry of a step is
+accurate to about 2 ulp of sigma^2 (hardware exp), its dot product with the earlier
+columns adds a rounding of that size, and the column is scaled by a hardware reciprocal
+square root (2 ulp) before its square is subtracted, so one downdate moves a variance by
+up to ~8 ulp of sigma^2; successive downdates' errors add up (worst case: linearly in t).
+Then
+  * single target: the score s = cov^2 / var of a candidate is known to
+    E (2a + a^2) with a = |cov| / var, so two scores closer than E (2a_b + a_b^2 + 2a_c + a_c^2)
+    cannot be ordered in FP32; in decrease units delta = log(1 + that / v_{t+1,b});
+  * supernode: log var|I and log var|I,P are known to E1 / var|I and E2 / var|I,P, with
+    E2 counting the m target columns of the second factor as downdates too
+    (E1 = E32 (t + 1) sigma^2, E2 = E32 (m + t + 1) sigma^2), so
+    delta = log((v1_c + E1)(v2_b + E2) / ((v2_c - E2)(v1_b - E1))) - log(v1_c v2_b / (v2_c v1_b))
+    (the two decreases' intervals overlap), any pick being accepted once v2_c <= E2.
+(a, v1, v2 from dense FP64 solves.)  delta is tiny while the candidates' conditional
+variances are large and grows as they approach E -- on the finest supernodes the targets
+nearly determine every candidate (var|I,P ~ 2 nugget), where FP32 cannot rank candidates
+at all; the aggregate bound on sum log v (the survey's FP32 tolerance,
+sum log v_FP32 <= sum log v_FP64 + 1e-3 KL_plain) is the check of what that costs.
+
+Every test asserts the fraction of steps that needed acceptance and the worst gap
+(ReplayStats.check), with caps stated in the test.
 """
+import math
+
 import numpy as np
+
+TIE_BAND = 1e-10
+E32 = 8 * 2.0 ** -24
+REL32 = 1e-3
+UNRESOLVED = 1e-3  # a step whose delta exceeds this many nats is not resolvable in FP32
 
 
 class ReplayStats:
     def __init__(self):
         self.steps = 0
         self.banded = 0
-        self.worst = 0.0
+        self.worst = 0.0        # largest gap g (nats)
+        self.unresolved = 0     # accepted steps whose FP32 resolution delta > UNRESOLVED
         self.units = 0
+        self.records = []       # (g, delta) of every differing step
+
+    @property
+    def frac(self):
+        return self.banded / max(1, self.steps)
 
     def __repr__(self):
-        return (f"units={self.units} steps={self.steps} banded={self.banded} "
-                f"({self.banded / max(1, self.steps):.2e}) worst_rel_gap={self.worst:.3e}")
+        return (f"units={self.units} steps={self.steps} banded={self.banded} ({self.frac:.2e}) "
+                f"worst_gap={self.worst:.3e} nats unresolved={self.unresolved}")
+
+    def check(self, max_frac, max_gap):
+        """The stated caps of a test: fraction of steps that differ from the oracle's pick
+        and the largest decrease gap among them."""
+        assert self.frac <= max_frac, f"{self}: banded fraction above {max_frac}"
+        assert self.worst <= max_gap, f"{self}: worst gap above {max_gap} nats"
 
 
-def _replay(run, gpu_sel, cand, band, stats, what, abs_band=0.0, resolves=None):
-    """run(forced) -> oracle dict with sel/best/chosen; forced lists indices into cand.
-    A differing pick is accepted when best - chosen <= band * |best| + abs_band, or when
-    resolves(prefix, oracle_pick, gpu_pick) says the two are not resolved apart."""
+def _replay(run, gpu_sel, cand, stats, what, accept):
+    """run(forced) -> oracle dict with sel/best/chosen(/vtar); forced lists indices into cand.
+    accept(j, r2, best_pick, gpu_pick, prefix) -> (ok, gap, delta) for a differing step j
+    (r2: the oracle run forced through the GPU's pick j)."""
     pos2idx = {int(p): i for i, p in enumerate(cand)}
     gpu_sel = [int(x) for x in gpu_sel]
     forced = []
@@ -45,19 +101,59 @@ def _replay(run, gpu_sel, cand, band, stats, what, abs_band=0.0, resolves=None):
             raise AssertionError(f"{what}: gpu pick {gpu_sel[j]} at step {j} is not a candidate")
         forced = [pos2idx[p] for p in gpu_sel[:j + 1]]
         r2 = run(forced)
-        best, chosen = float(r2["best"][j]), float(r2["chosen"][j])
-        gap = (best - chosen) / abs(best) if best != 0 else abs(best - chosen)
+        ok, gap, delta = accept(j, r2, o[j], gpu_sel[j], gpu_sel[:j])
         stats.banded += 1
         stats.worst = max(stats.worst, gap)
-        if best - chosen > band * abs(best) + abs_band and not (resolves and resolves(gpu_sel[:j], o[j], gpu_sel[j])):
-            raise AssertionError(f"{what}: step {j} gpu picked {gpu_sel[j]} with oracle score {chosen!r}, "
-                                 f"oracle best {best!r} (relative gap {gap:.3e} > {band:.1e})")
+        stats.records.append((gap, delta))
+        if delta > UNRESOLVED:
+            stats.unresolved += 1
+        if not ok:
+            raise AssertionError(f"{what}: step {j} gpu picked {gpu_sel[j]} (oracle best {o[j]}): decrease gap "
+                                 f"{gap:.3e} nats above the accepted {delta:.3e} (+{REL32:g} relative)")
 
 
-def replay_single(oracle, kp, P, target, cand, k, gpu_sel, band, stats, floor=None, abs_band=0.0):
+def _tie(best, chosen):
+    return best - chosen <= TIE_BAND * abs(best)
+
+
+def cond_single(oracle, kp, P, t, S, j):
+    """(v_t, cov, var): the target's variance, its covariance with j and j's variance, all
+    conditioned on the positions S, by dense FP64 solves."""
+    S = [int(x) for x in S]
+    K = oracle.theta_matrix(kp, P, S + [int(t), int(j)])
+    s = len(S)
+    if s:
+        X = np.linalg.solve(K[:s, :s], K[:s, s:])
+        A = K[s:, s:] - K[:s, s:].T @ X
+    else:
+        A = K[s:, s:]
+    return float(A[0, 0]), float(A[0, 1]), float(A[1, 1])
+
+
+def replay_single(oracle, kp, P, target, cand, k, gpu_sel, stats, fp32=False, floor=None):
+    """Single-target replay; the oracle's scores are cov^2 / var and vtar[t] the target's
+    variance before step t."""
+
     def run(forced):
         return oracle.select_single(kp, P, target, cand, k, floor=floor, forced=forced if forced else None)
-    _replay(run, gpu_sel, cand, band, stats, f"column {target}", abs_band)
+
+    def accept(j, r2, b, c, prefix):
+        best, chosen, vt = float(r2["best"][j]), float(r2["chosen"][j]), float(r2["vtar"][j])
+        vb, vc = max(vt - best, 1e-300), max(vt - chosen, 1e-300)
+        gap = max(0.0, math.log(vc / vb))
+        if not fp32:
+            return _tie(best, chosen), gap, 0.0
+        E = E32 * (j + 1) * kp.variance
+        res = 0.0
+        for q in (b, c):
+            _, cov, var = cond_single(oracle, kp, P, target, prefix, q)
+            a = abs(cov) / max(var, 1e-300)
+            res += E * (2 * a + a * a)
+        delta = math.log1p(res / vb)
+        dbest = math.log(vt / vb)
+        return gap <= REL32 * dbest + delta, gap, delta
+
+    _replay(run, gpu_sel, cand, stats, f"column {target}", accept)
 
 
 def conditional_variances(oracle, kp, P, g0, m, S, j):
@@ -76,20 +172,28 @@ def conditional_variances(oracle, kp, P, g0, m, S, j):
     return float(v1), float(v2)
 
 
-def replay_multi(oracle, kp, P, g0, m, cand, k, gpu_sel, band, stats, floor=None, abs_band=0.0, var_abs=0.0):
-    """var_abs > 0: a differing pick is also accepted when the ratio scores var1 / var2 of
-    the two picks cannot be told apart with every conditional variance known only to
-    +-var_abs: (v1_c + E) / (v2_c - E) >= (v1_b - E) / (v2_b + E)."""
+def replay_multi(oracle, kp, P, g0, m, cand, k, gpu_sel, stats, fp32=False, floor=None):
+    """Supernode replay; the oracle's scores are var|I / var|I,P, the decrease their log."""
+
     def run(forced):
         return oracle.select_multi(kp, P, g0, m, cand, k, floor=floor, forced=forced if forced else None)
 
-    def resolves(prefix, best_pick, gpu_pick):
-        E = var_abs
-        v1b, v2b = conditional_variances(oracle, kp, P, g0, m, prefix, best_pick)
-        v1c, v2c = conditional_variances(oracle, kp, P, g0, m, prefix, gpu_pick)
-        return v2c <= E or (v1c + E) / (v2c - E) >= (v1b - E) / (v2b + E)
+    def accept(j, r2, b, c, prefix):
+        best, chosen = float(r2["best"][j]), float(r2["chosen"][j])
+        gap = max(0.0, math.log(best / chosen))
+        if not fp32:
+            return _tie(best, chosen), gap, 0.0
+        E1 = E32 * (j + 1) * kp.variance          # var|I: j downdates
+        E2 = E32 * (m + j + 1) * kp.variance      # var|I,P: m target columns, then j downdates
+        v1b, v2b = conditional_variances(oracle, kp, P, g0, m, prefix, b)
+        v1c, v2c = conditional_variances(oracle, kp, P, g0, m, prefix, c)
+        if v2c <= E2 or v1b <= E1:
+            return True, gap, math.inf
+        delta = (math.log((v1c + E1) * (v2b + E2) / ((v2c - E2) * (v1b - E1)))
+                 - math.log(v1c * v2b / (v2c * v1b)))
+        return gap <= REL32 * math.log(best) + delta, gap, delta
 
-    _replay(run, gpu_sel, cand, band, stats, f"group at {g0}", abs_band, resolves if var_abs > 0 else None)
+    _replay(run, gpu_sel, cand, stats, f"group at {g0}", accept)
 
 
 def column_errors(L_gpu, L_ref):

@@ -210,7 +210,7 @@ def test_columns_global_fp64_matches_oracle(env, oracle_lib):
     same = 0
     for i in range(hp.n):
         picks = sel[i, :lcnt[i]]
-        replay_single(oracle, okp, P, i, cl[i], k, picks, TIE_BAND, stats)
+        replay_single(oracle, okp, P, i, cl[i], k, picks, stats)
         if np.array_equal(picks, osel[i]):
             same += 1
             np.testing.assert_allclose(gain[i, :lcnt[i]], ogain[i], rtol=GAIN_REL, atol=GAIN_ABS, err_msg=str(i))
@@ -260,7 +260,7 @@ def test_groups_global_fp64_matches_oracle(env, oracle_lib):
     same = 0
     for g in range(G):
         picks = sel[g, :lcnt[g]]
-        replay_multi(oracle, okp, P, int(hp.grp_ptr[g]), int(sizes[g]), cl[g], k, picks, TIE_BAND, stats)
+        replay_multi(oracle, okp, P, int(hp.grp_ptr[g]), int(sizes[g]), cl[g], k, picks, stats)
         if np.array_equal(picks, osel[g]):
             same += 1
             np.testing.assert_allclose(gain[g, :lcnt[g]], ogain[g], rtol=GAIN_REL, atol=GAIN_ABS, err_msg=str(g))

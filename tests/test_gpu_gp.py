@@ -53,7 +53,7 @@ def test_gp_predict_matches_oracle(env, oracle_lib, prec_name):
         assert np.all(cand >= 300)
         picks = sel[t, :cnt[t]]
         if prec_name == "fp64":
-            replay_single(oracle, okp, pts, t, cand, 24, picks, 1e-10, stats)
+            replay_single(oracle, okp, pts, t, cand, 24, picks, stats)
         m_ref, v_ref = OG.predict(okp, pts, t, picks, y)
         assert mean[t] == pytest.approx(m_ref, rel=1e-9, abs=1e-12), t
         assert abs(var[t] - v_ref) <= 1e-9 * kp.variance, t

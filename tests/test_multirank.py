@@ -1,6 +1,6 @@
-"""The multi-process path of bench.py on CPU: two gloo ranks on 127.0.0.1 agree on the
-max-over-ranks step time and pass the barrier; each rank's problem seed differs (weak
-scaling over independent problems, no data-path collective)."""
+"""The multi-process timing of bench.py on CPU: two gloo ranks on 127.0.0.1 agree on the
+max-over-ranks step time and pass the barrier (the sliced build's own collectives are
+tested in test_shard.py); and the FLOP accounting of the bench's roofline lines."""
 import os
 import socket
 
