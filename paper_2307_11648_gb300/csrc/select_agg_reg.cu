@@ -26,12 +26,11 @@
 
 namespace {
 
-constexpr int RNT = 256;       // threads = max candidates
+constexpr int RNT = 256;       // largest thread count = max candidates
 constexpr int RK = 64;         // max picks
 constexpr int RM = 64;         // max targets
 constexpr int RP = RK + 4;     // mirror pitch of F1 and F2S rows (floats)
 constexpr int RPM = RM + 4;    // mirror pitch of F2P rows and of the target factor
-constexpr int LDX = RNT + RM;  // staged coordinates: candidates then targets
 constexpr unsigned FULL = 0xffffffffu;
 // workspace slot of one group: chol(Theta_PP) packed by rows (RM (RM + 1) / 2), its reciprocal
 // diagonal (RM) and a failure flag
@@ -174,21 +173,27 @@ __global__ void __launch_bounds__(32 * LP_WARPS) k_agg_target_chol(const double*
     }
 }
 
-__global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
+// NT threads (candidate rows) per group: 256, one CTA per SM; or 128 for lists of at most 128
+// candidates, two CTAs (groups) per SM with the same per-thread state
+template <int NT>
+__global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
     const double* __restrict__ pts, long long n, int dim, KP<float> kp, float floor_,
     const long long* __restrict__ grp_ptr, long long n_grp, const long long* __restrict__ cand_ptr,
     const int32_t* __restrict__ cand_idx, int k, int max_m, int32_t* __restrict__ sel_idx,
     int32_t* __restrict__ sel_count, const float* __restrict__ lp_ws, double* __restrict__ gain, DevStatus* st) {
+    constexpr int LDX = NT + RM;      // staged coordinates: candidates then targets
+    constexpr int NW = NT / 32;       // warps
+    static_assert(NT * RP >= RM * RPM + RM, "the target factor overlays the F1 mirror");
     extern __shared__ __align__(16) float smf[];
-    float* F1m = smf;                 // [RNT][RP]
-    float* F2Sm = F1m + RNT * RP;     // [RNT][RP]
-    float* F2Pm = F2Sm + RNT * RP;    // [RNT][RPM]
-    float* X = F2Pm + RNT * RPM;      // [3][LDX]
+    float* F1m = smf;                 // [NT][RP]
+    float* F2Sm = F1m + NT * RP;      // [NT][RP]
+    float* F2Pm = F2Sm + NT * RP;     // [NT][RPM]
+    float* X = F2Pm + NT * RPM;       // [3][LDX]
     float* Lp = F1m;                  // [RM][RPM] chol(Theta_PP), overlays F1m before the steps
     float* rLp = F1m + RM * RPM;      // [RM] reciprocal diagonal of Lp
-    __shared__ __align__(16) unsigned pkey[2][RNT / 32];
-    __shared__ int pidx[2][RNT / 32];
-    __shared__ float pv1[2][RNT / 32], pv2[2][RNT / 32];
+    __shared__ __align__(16) unsigned pkey[2][NW];
+    __shared__ int pidx[2][NW];
+    __shared__ float pv1[2][NW], pv2[2][NW];
     __shared__ float gv1[RK], gv2[RK];  // the picks' two conditional variances (gains only)
     __shared__ int qs[RK];              // the picks' candidate rows, translated after the steps
     __shared__ int s_fail;
@@ -201,12 +206,12 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         const int m = (int)(grp_ptr[g + 1] - g0);
         const long long b0 = cand_ptr[g];
         const int C = (int)(cand_ptr[g + 1] - b0);
-        if (m < 1 || m > RM || m > max_m || C < 0 || C > RNT || g0 < 0 || g0 + m > n) {
+        if (m < 1 || m > RM || m > max_m || C < 0 || C > NT || g0 < 0 || g0 + m > n) {
             if (tid == 0) {
                 record_error(st, SIC_ERR_INVALID, g);
                 sel_count[g] = 0;
             }
-            for (int q = tid; q < k; q += RNT) sel_idx[g * k + q] = -1;
+            for (int q = tid; q < k; q += NT) sel_idx[g * k + q] = -1;
             continue;
         }
         // ---- stage coordinates relative to the first member (differences formed in FP64)
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         if (tid < m) {
 #pragma unroll
             for (int d = 0; d < 3; ++d)
-                X[d * LDX + RNT + tid] = (d < dim) ? (float)(pts[(g0 + tid) * dim + d] - org[d]) : 0.f;
+                X[d * LDX + NT + tid] = (d < dim) ? (float)(pts[(g0 + tid) * dim + d] - org[d]) : 0.f;
         }
         // zero this thread's pick mirrors except F1m (which holds Lp until the steps)
 #pragma unroll
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         for (int a = 0; a < RM; ++a) {
             F2P[a] = 0.f;
             if (live && a < m) {
-                const float dx = xr - X[RNT + a], dy = yr - X[LDX + RNT + a], dz = zr - X[2 * LDX + RNT + a];
+                const float dx = xr - X[NT + a], dy = yr - X[LDX + NT + a], dz = zr - X[2 * LDX + NT + a];
                 F2P[a] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
             }
         }
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         {
             const float* src = lp_ws + g * (long long)LP_SLOT;
             const int tri = m * (m + 1) / 2;
-            for (int e = tid; e < tri; e += RNT) {
+            for (int e = tid; e < tri; e += NT) {
                 int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
                 while (i * (i + 1) / 2 > e) --i;
                 while ((i + 1) * (i + 2) / 2 <= e) ++i;
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         __syncthreads();
         if (s_fail) {
             if (tid == 0) sel_count[g] = 0;
-            for (int q = tid; q < k; q += RNT) sel_idx[g * k + q] = -1;
+            for (int q = tid; q < k; q += NT) sel_idx[g * k + q] = -1;
             __syncthreads();
             continue;
         }
@@ -308,9 +313,7 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         for (int c = 0; c < RM / 4; ++c)
             *reinterpret_cast<float4*>(F2Pm + tid * RPM + 4 * c) =
                 make_float4(F2P[4 * c], F2P[4 * c + 1], F2P[4 * c + 2], F2P[4 * c + 3]);
-        if (tid < RNT) {  // the tail of the pitch
-            *reinterpret_cast<float4*>(F2Pm + tid * RPM + RM) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        *reinterpret_cast<float4*>(F2Pm + tid * RPM + RM) = make_float4(0.f, 0.f, 0.f, 0.f);  // pitch tail
         __syncthreads();  // Lp is no longer read: F1m becomes the F1 mirror
 #pragma unroll
         for (int c = 0; c < RP / 4; ++c)
@@ -342,12 +345,12 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
                     pv2[buf][warp] = V2;
                 }
                 __syncthreads();
-                // the eight warp winners (ascending rows), reduced by every warp: lane w < 8
+                // the warp winners (ascending rows), reduced by every warp: lane w < NW
                 // reads warp w's key; the lowest warp holding the maximum wins
-                const unsigned kw = (lane < RNT / 32) ? pkey[buf][lane] : 0u;
+                const unsigned kw = (lane < NW) ? pkey[buf][lane] : 0u;
                 const unsigned bk = __reduce_max_sync(FULL, kw);
                 if (bk == 0u) return false;
-                const int bw = __ffs(__ballot_sync(FULL, lane < RNT / 32 && kw == bk)) - 1;
+                const int bw = __ffs(__ballot_sync(FULL, lane < NW && kw == bk)) - 1;
                 const int q = pidx[buf][bw];
                 const float r1 = rsqrtf(pv1[buf][bw]);
                 const float r2 = rsqrtf(pv2[buf][bw]);
@@ -404,12 +407,12 @@ __global__ void __launch_bounds__(RNT, 1) k_select_agg_reg(
         // the picks' global indices and (with gain) the decreases of logdet Theta_{PP|I} per
         // nonzero (Section 5.4.2), off the step chain
         __syncthreads();
-        for (int q = tid; q < t; q += RNT) {
+        for (int q = tid; q < t; q += NT) {
             sel_idx[g * k + q] = cand_idx[b0 + qs[q]];
             if (gain) gain[g * k + q] = log((double)gv1[q] / (double)gv2[q]) / m;
         }
         if (tid == 0) sel_count[g] = t;
-        for (int q = t + tid; q < k; q += RNT) sel_idx[g * k + q] = -1;
+        for (int q = t + tid; q < k; q += NT) sel_idx[g * k + q] = -1;
         __syncthreads();
     }
 }
@@ -424,19 +427,22 @@ size_t agg_reg_workspace(long long n_grp) { return sizeof(float) * (size_t)LP_SL
 
 sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
                           const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx,
-                          int max_m, int k, int32_t* sel_idx, int32_t* sel_count, double* gain, void* ws,
+                          int max_cand, int max_m, int k, int32_t* sel_idx, int32_t* sel_count, double* gain, void* ws,
                           size_t ws_bytes, cudaStream_t s) {
     if (!ws || ws_bytes < agg_reg_workspace(n_grp)) return SIC_ERR_INVALID;
     const KP<float> kpf = make_kp<float>(*kp);
     const int lgrid = persistent_grid(h, k_agg_target_chol, 32 * LP_WARPS, 0, (n_grp + LP_WARPS - 1) / LP_WARPS);
     k_agg_target_chol<<<lgrid, 32 * LP_WARPS, 0, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp,
                                                        (float*)ws);
-    const size_t smem = sizeof(float) * ((size_t)RNT * RP * 2 + (size_t)RNT * RPM + 3 * (size_t)LDX);
-    SIC_CUDA_TRY(cudaFuncSetAttribute(k_select_agg_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = persistent_grid(h, k_select_agg_reg, RNT, smem, n_grp > 0 ? n_grp : 1);
-    k_select_agg_reg<<<grid, RNT, smem, s>>>(pts, n, kp->dim, kpf, (float)sic_floor_of(kp),
-                                             (const long long*)grp_ptr, n_grp, (const long long*)cand_ptr, cand_idx,
-                                             k, max_m, sel_idx, sel_count, (const float*)ws, gain, h->d_status);
+    // 128 threads (two groups per SM) when every list has at most 128 candidates
+    const int nt = max_cand <= 128 ? 128 : RNT;
+    auto kern = nt == 128 ? k_select_agg_reg<128> : k_select_agg_reg<RNT>;
+    const size_t smem = sizeof(float) * ((size_t)nt * RP * 2 + (size_t)nt * RPM + 3 * (size_t)(nt + RM));
+    SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = persistent_grid(h, kern, nt, smem, n_grp > 0 ? n_grp : 1);
+    kern<<<grid, nt, smem, s>>>(pts, n, kp->dim, kpf, (float)sic_floor_of(kp), (const long long*)grp_ptr, n_grp,
+                                (const long long*)cand_ptr, cand_idx, k, max_m, sel_idx, sel_count, (const float*)ws,
+                                gain, h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }

@@ -433,8 +433,8 @@ extern "C" sic_status sic_select_aggregated_gain(sic_handle* h, const double* pt
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (agg_reg_applies(prec, max_cand, max_m, k))
-        return launch_agg_reg(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_m, k, sel_idx, sel_count, gain,
-                              ws, ws_bytes, s);
+        return launch_agg_reg(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, sel_idx,
+                              sel_count, gain, ws, ws_bytes, s);
     if (prec == SIC_FP64)
         return launch_agg<double>(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, sel_idx,
                                   sel_count, gain, ws, ws_bytes, s);

@@ -194,8 +194,8 @@ bool agg_reg_applies(sic_precision prec, int max_cand, int max_m, int k);
 size_t agg_reg_workspace(long long n_grp);
 sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
                           const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx,
-                          int max_m, int k, int32_t* sel_idx, int32_t* sel_count, double* gain, void* ws,
-                          size_t ws_bytes, cudaStream_t s);
+                          int max_cand, int max_m, int k, int32_t* sel_idx, int32_t* sel_count, double* gain,
+                          void* ws, size_t ws_bytes, cudaStream_t s);
 
 // fixed-order sum of log v (fill.cu); ws holds sic_build_factor_workspace(n) bytes
 sic_status launch_sum_logv(const double* logv, long long n, double* sum_logv, void* ws, cudaStream_t s);

@@ -9,6 +9,7 @@ only allocates buffers, batches rows and loops.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 import time
 

@@ -285,8 +285,8 @@ class PartialFactorBuilder:
         self.val = torch.empty(self.nnz_cap, dtype=torch.float64, device=dev)
         self.logv = torch.empty(n, dtype=torch.float64, device=dev)
         self.sum_logv = torch.zeros(1, dtype=torch.float64, device=dev)
-        self.ws_nnz = sic._ws(sic.factor_nnz_workspace(nc), dev)
-        self.ws_fill = sic._ws(sic.build_factor_workspace(nc), dev)
+        self.ws_nnz = sic._ws(sic.factor_nnz_workspace(n), dev)
+        self.ws_fill = sic._ws(sic.build_factor_workspace(n), dev)
 
     def select(self, dp: DeviceProblem, stream=None):
         hp = self.hp

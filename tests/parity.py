@@ -18,27 +18,27 @@ relative (1e-10); nothing else is accepted.
 
 FP32 selections (the benchmark spec precision split: state in FP32): a differing pick is accepted
 when g <= REL32 * D(best) + delta, where REL32 = 1e-3 is the stated relative band and
-delta is what FP32 arithmetic cannot resolve in this state.  Derivation of delta: after
-t picks every FP32 conditional (co)variance carries an absolute error of at most
-E = E32 * (t + 1) * sigma^2 with E32 = 8 eps32 = 4.8e-7: the kernel entry of a step is
-accurate to about 2 ulp of sigma^2 (hardware exp), its dot product with the earlier
-columns adds a rounding of that size, and the column is scaled by a hardware reciprocal
-square root (2 ulp) before its square is subtracted, so one downdate moves a variance by
-up to ~8 ulp of sigma^2; successive downdates' errors add up (worst case: linearly in t).
-Then
+delta is what FP32 arithmetic cannot resolve in this state.  Derivation of delta (first
+order): a new column u = n / sqrt(v) of a partial factor is formed from a numerator n known
+to about 4 ulp of sigma^2 (the kernel entry's hardware exp, the dot product's roundings)
+divided by the square root of its pivot's conditional variance v, so u's error is
+amplified by sigma / sqrt(v); the downdate var -= u^2 then moves a variance by up to
+2 |u| du <= 2 sigma du.  Summed over the columns (errors add, worst case):
+    E = E32 sigma^2 (1 + sum over the factor's columns of sqrt(sigma^2 / v)),  E32 = 8 eps32,
+the pivots v being the FP64 conditional variances of the earlier picks (and, for the
+second factor of a supernode, of the targets first: its m target columns).  Then
   * single target: the score s = cov^2 / var of a candidate is known to
     E (2a + a^2) with a = |cov| / var, so two scores closer than E (2a_b + a_b^2 + 2a_c + a_c^2)
     cannot be ordered in FP32; in decrease units delta = log(1 + that / v_{t+1,b});
-  * supernode: log var|I and log var|I,P are known to E1 / var|I and E2 / var|I,P, with
-    E2 counting the m target columns of the second factor as downdates too
-    (E1 = E32 (t + 1) sigma^2, E2 = E32 (m + t + 1) sigma^2), so
+  * supernode: log var|I and log var|I,P are known to E1 / var|I and E2 / var|I,P (E1 over
+    the picks' columns, E2 over the targets' and the picks' columns of the second factor), so
     delta = log((v1_c + E1)(v2_b + E2) / ((v2_c - E2)(v1_b - E1))) - log(v1_c v2_b / (v2_c v1_b))
     (the two decreases' intervals overlap), any pick being accepted once v2_c <= E2.
-(a, v1, v2 from dense FP64 solves.)  delta is tiny while the candidates' conditional
-variances are large and grows as they approach E -- on the finest supernodes the targets
-nearly determine every candidate (var|I,P ~ 2 nugget), where FP32 cannot rank candidates
-at all; the aggregate bound on sum log v (the survey's FP32 tolerance,
-sum log v_FP32 <= sum log v_FP64 + 1e-3 KL_plain) is the check of what that costs.
+(a, v1, v2 and the pivots from dense FP64 solves.)  delta is tiny while the variances in
+play are large and unbounded once a candidate's var|I,P approaches E2: on the finest
+supernodes the targets nearly determine every candidate (var|I,P ~ 2 nugget), where FP32
+cannot rank candidates at all; the aggregate bound on sum log v (the survey's FP32
+tolerance, sum log v_FP32 <= sum log v_FP64 + 1e-3 KL_plain) is the check of what that costs.
 
 Every test asserts the fraction of steps that needed acceptance and the worst gap
 (ReplayStats.check), with caps stated in the test.
@@ -143,7 +143,8 @@ def replay_single(oracle, kp, P, target, cand, k, gpu_sel, stats, fp32=False, fl
         gap = max(0.0, math.log(vc / vb))
         if not fp32:
             return _tie(best, chosen), gap, 0.0
-        E = E32 * (j + 1) * kp.variance
+        piv, _ = oracle.pivot_variances(kp, P, [], prefix)
+        E = E32 * kp.variance * (1.0 + float(np.sum(np.sqrt(kp.variance / np.maximum(piv, 1e-300)))))
         res = 0.0
         for q in (b, c):
             _, cov, var = cond_single(oracle, kp, P, target, prefix, q)
@@ -183,8 +184,13 @@ def replay_multi(oracle, kp, P, g0, m, cand, k, gpu_sel, stats, fp32=False, floo
         gap = max(0.0, math.log(best / chosen))
         if not fp32:
             return _tie(best, chosen), gap, 0.0
-        E1 = E32 * (j + 1) * kp.variance          # var|I: j downdates
-        E2 = E32 * (m + j + 1) * kp.variance      # var|I,P: m target columns, then j downdates
+        # pivots of the two factors: the picks given the earlier picks (first factor); the
+        # targets given the earlier targets, then the picks given the targets and earlier picks
+        piv1, piv2 = oracle.pivot_variances(kp, P, list(range(g0, g0 + m)), prefix)
+        tdiag = np.diag(np.linalg.cholesky(oracle.theta_matrix(kp, P, list(range(g0, g0 + m))))) ** 2
+        amp = lambda v: float(np.sum(np.sqrt(kp.variance / np.maximum(v, 1e-300))))  # noqa: E731
+        E1 = E32 * kp.variance * (1.0 + amp(piv1))
+        E2 = E32 * kp.variance * (1.0 + amp(tdiag) + amp(piv2))
         v1b, v2b = conditional_variances(oracle, kp, P, g0, m, prefix, b)
         v1c, v2c = conditional_variances(oracle, kp, P, g0, m, prefix, c)
         if v2c <= E2 or v1b <= E1:

@@ -3,7 +3,8 @@
 Tolerances follow the parity tests (tests/parity.py): FP64 picks identical except at
 near-ties of the oracle's decreases within 1e-10 relative (oracle replay); an FP32 pick
 within 1e-3 relative of the oracle's best decrease plus the FP32 resolution of the two
-picks' decreases, 2 E m (1/v_b + 1/v_c) with E = 8 eps32 (t + 1) sigma^2 after t picks and v the pick's variance
+picks' decreases, 2 E m (1/v_b + 1/v_c) with E as in tests/parity.py over the members' and the earlier
+picks' pivot variances and v the pick's variance
 given the members and earlier picks (each of the up to m member terms of the decrease is
 a log-ratio of FP32 variances no smaller than v); the decreases of agreeing FP64 picks to
 1e-9 relative plus 1e-12; the fill of the resulting pattern as in the parity tests (rows
@@ -64,7 +65,8 @@ def _replay_partial(oracle, okp, hp, g, gpu_sel, stats, fp32):
         gap = max(0.0, best - chosen)
         if not fp32:
             return best - chosen <= TIE_BAND * abs(best), gap, 0.0
-        E = E32 * (j + 1) * okp.variance
+        piv = oracle.pivot_variances(okp, hp.pts, [], list(mem) + list(prefix))[0]
+        E = E32 * okp.variance * (1.0 + float(np.sum(np.sqrt(okp.variance / np.maximum(piv, 1e-300)))))
         vb = _var_given(oracle, okp, hp.pts, list(mem) + list(prefix), b)
         vc = _var_given(oracle, okp, hp.pts, list(mem) + list(prefix), c)
         delta = 2 * E * len(mem) * (1 / max(vb, 1e-300) + 1 / max(vc, 1e-300))

@@ -153,3 +153,27 @@ def test_two_gloo_ranks_assemble_the_oracle_factor(sic):
         assert np.array_equal(r[4], logv)
         assert r[5] == res[0][6] + res[1][6]       # the all-reduce adds the slices' sums
     assert res[0][5] == pytest.approx(float(np.sum(logv)), rel=1e-14)
+
+
+def test_slice_problem_host_side(sic):
+    """pipeline.slice_problem and the proposal's reduced problem on the host: the slice keeps the
+    whole problem's points and launch bounds, rebased candidate lists and its column range."""
+    from paper_2307_11648_gb300 import learned, pipeline
+    hp = _problem()
+    U = hp.n_units
+    b = sic.prep_partition(hp.cand_ptr, hp.grp_ptr, hp.k, 3)
+    cols = 0
+    for r in range(3):
+        sl = pipeline.slice_problem(hp, int(b[r]), int(b[r + 1]))
+        assert sl.pts is hp.pts and sl.n_units == b[r + 1] - b[r]
+        assert sl.col0 == hp.grp_ptr[b[r]] and sl.ncols == hp.grp_ptr[b[r + 1]] - hp.grp_ptr[b[r]]
+        assert sl.sliced and (sl.max_cand, sl.max_m) == (hp.max_cand, hp.max_m)
+        assert sl.cand_ptr[0] == 0
+        assert np.array_equal(sl.cand_idx, hp.cand_idx[hp.cand_ptr[b[r]]:hp.cand_ptr[b[r + 1]]])
+        red = learned.reduced_problem(sl, 16)
+        assert red.max_cand == min(hp.max_cand, 16) and red.col0 == sl.col0 and red.ncols == sl.ncols
+        cols += sl.ncols
+    assert cols == hp.n and not pipeline.slice_problem(hp, 0, U).sliced
+    cp = pipeline.prepare_columns(synthetic.points(300, 2, 4), hp.kp, 16, 4)
+    sl = pipeline.slice_problem(cp, 100, 200)
+    assert sl.targets.tolist() == list(range(100, 200)) and sl.col0 == 100 and sl.ncols == 100
