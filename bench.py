@@ -196,6 +196,110 @@ def oracle_sample(prob, seconds: float, threads: int, seed: int = 0):
     return (c0 + c1) / (t0 + t1), c0 + c1, len(first) + len(second), t0 + t1
 
 
+def proposal_gain_clustered(h, cfg, n, epochs):
+    """Where the proposal network earns its place: a clustered cloud (half of the points in a
+    square of side 0.05), the config-3 kernel with ell scaled to n points, a network trained on
+    two clustered clouds of other seeds; KL gap (S_A - S_plain64) / (S_plain64 - S_ref) of the
+    learned proposal and of distance truncation at top = 128 and 256."""
+    import torch
+
+    from paper_2307_11648_gb300 import learned, pipeline, sic
+    ell = cfg["length_scale"] * math.sqrt(cfg["n"] / n)
+    kp = sic.kernel(cfg["dim"], cfg["nu_x2"], ell, cfg["variance"], cfg["nugget"])
+
+    def prob(seed, k=cfg["k"]):
+        return pipeline.prepare_groups(synthetic.clustered_points(n, cfg["dim"], seed), kp, cfg["n_cand"], k,
+                                       cfg["m_min"], cfg["m_max"])
+
+    feat, label, _ = learned.training_set(h, [prob(1001), prob(1002)])
+    params, _ = learned.train(h, feat, label, epochs=epochs, batch=65536, lr=2e-3, seed=0)
+    del feat, label
+    hp = prob(cfg["seed"])
+    dp = pipeline.DeviceProblem(hp)
+    S = {}
+
+    def run(name, b, d=dp):
+        b.run(d)
+        h.sync()
+        S[name] = float(b.sum_logv.cpu()[0])
+
+    run("plain64", pipeline.FactorBuilder(h, hp, sic.SIC_FP64))
+    run("plain32", pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED))
+    run("ref", pipeline.FactorBuilder(h, dataclasses.replace(hp, k=2 * hp.k), sic.SIC_FP32_MIXED))
+    out = {"n": n, "geometry": "clustered_points: half of the points in the centred square of side 0.05"}
+    for top in (128, 256):
+        run(f"learned{top}", learned.LearnedFactorBuilder(h, hp, learned.Proposal(h, params, top=top)))
+        dhp = truncated(hp, top)
+        run(f"distance{top}", pipeline.FactorBuilder(h, dhp, sic.SIC_FP32_MIXED), pipeline.DeviceProblem(dhp))
+        base = S["plain64"] - S["ref"]
+        out[f"top{top}"] = {"learned_kl_gap": (S[f"learned{top}"] - S["plain64"]) / base,
+                            "distance_kl_gap": (S[f"distance{top}"] - S["plain64"]) / base}
+    out["plain_fp32_kl_gap"] = (S["plain32"] - S["plain64"]) / (S["plain64"] - S["ref"])
+    del dp
+    torch.cuda.empty_cache()
+    return out
+
+
+def config1(h, timed, stream, oracle_s=3.0, naive_cols=4):
+    """Config 1: N = 4096 points in the unit square (seed 0), Matern 3/2, ell = 0.1, nugget 1e-8,
+    k = 16 of the 256 nearest later points per column, FP64.  The GPU build (selection + fill +
+    sum of log v) as a CUDA graph; the oracle on all host cores and on one, on columns taken
+    in order until about `oracle_s` seconds have passed (Cholesky-form greedy + dense fill);
+    and the naive greedy (a fresh dense factorisation per candidate and step, O(C k^4)) on
+    `naive_cols` columns."""
+    import torch
+
+    import oracle
+    from paper_2307_11648_gb300 import pipeline, sic
+    oracle.build()
+    c = synthetic.PRESETS["cfg1_single_fp64"]
+    kp = sic.kernel(c["dim"], c["nu_x2"], c["length_scale"], c["variance"], c["nugget"])
+    hp = pipeline.prepare_columns(synthetic.points(c["n"], c["dim"], c["seed"]), kp, c["n_cand"], c["k"])
+    dp = pipeline.DeviceProblem(hp)
+    fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP64)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        fb.run(dp)
+    stream.wait_stream(side)
+    with torch.cuda.graph(g):
+        fb.run(dp)
+    g_ms, _, _ = timed([g.replay], 10, 3)
+    okp = oracle.kernel(kp.dim, kp.nu_x2, kp.length_scale, kp.variance, kp.nugget)
+
+    def col(i):
+        sel = oracle.select_single(okp, hp.pts, i, hp.cand_idx[hp.cand_ptr[i]:hp.cand_ptr[i + 1]], hp.k)["sel"]
+        oracle.fill_column(okp, hp.pts, i, sel)
+
+    def rate(threads):
+        from concurrent.futures import ThreadPoolExecutor
+        done, t0 = 0, time.perf_counter()
+        with ThreadPoolExecutor(threads) as ex:
+            while time.perf_counter() - t0 < oracle_s and done < hp.n:
+                batch = range(done, min(hp.n, done + 8 * threads))
+                list(ex.map(col, batch))
+                done = batch[-1] + 1
+        return done / (time.perf_counter() - t0), done
+
+    threads = os.cpu_count() or 1
+    all_rate, all_cols = rate(threads)
+    one_rate, one_cols = rate(1)
+    t0 = time.perf_counter()
+    for i in range(naive_cols):
+        oracle.select_single_naive(okp, hp.pts, i, hp.cand_idx[hp.cand_ptr[i]:hp.cand_ptr[i + 1]], hp.k)
+    naive_rate = naive_cols / (time.perf_counter() - t0)
+    out = {"workload": "N=4096 uniform [0,1]^2 (seed 0), Matern 3/2, ell=0.1, nugget 1e-8, C=256, k=16, FP64",
+           "gpu_graph_ms": g_ms, "gpu_columns_per_s": hp.n / (g_ms * 1e-3),
+           "sum_logv": float(fb.sum_logv.cpu()[0]),
+           "oracle_all_cores": {"columns_per_s": all_rate, "cores": threads, "sample_columns": all_cols},
+           "oracle_one_core": {"columns_per_s": one_rate, "sample_columns": one_cols},
+           "oracle_naive_one_core": {"columns_per_s": naive_rate, "sample_columns": naive_cols,
+                                     "form": "O(C k^4): dense re-factorisation per candidate and step"}}
+    del g, fb, dp
+    return out
+
+
 def host_problem_dict(hp):
     """The prepared inputs as plain arrays (what the oracle needs; no library objects)."""
     kp = hp.kp
@@ -512,6 +616,9 @@ def main():
                     help="points of the single-target measurement (3-D, 512 candidates, k = 32; 0: skip)")
     ap.add_argument("--case-single", action="store_true",
                     help="with --case-only: one FP32-mixed single-target factor build (3-D, 512 candidates, k = 32)")
+    ap.add_argument("--clustered-n", type=int, default=1 << 18,
+                    help="points of the clustered-cloud comparison of the proposal against distance order (0: skip)")
+    ap.add_argument("--cfg1", type=int, default=1, help="the config-1 line (FP64 path, oracle timings; 0: skip)")
     ap.add_argument("--sharded", action="store_true",
                     help="the multi-GPU path (one factor in slices, gathered) even on one GPU")
     ap.add_argument("--partial-n", type=int, default=1 << 18,
@@ -636,8 +743,8 @@ def main():
     if ws > 1 or args.sharded:
         run_sharded(args, ws, rank, local, h, hp, proposal, timed, prep_s, train_s)
         h.close()
-        if ws > 1:
-            import torch.distributed as dist
+        import torch.distributed as dist
+        if dist.is_initialized():
             dist.destroy_process_group()
         return
 
@@ -701,6 +808,14 @@ def main():
     S["distance_fp32"] = float(fd.sum_logv.cpu()[0])
     del fd, ddp
     torch.cuda.empty_cache()
+    # ---- the same network keeping only 2k = 128 candidates (the 128-thread selection kernel,
+    # two supernodes per SM): not the configured 4k, reported beside it
+    l128 = learned.LearnedFactorBuilder(h, hp, learned.Proposal(h, params, top=2 * cfg["k"]), sic.SIC_FP32_MIXED)
+    l128_ms, _, _ = timed([lambda: l128.run(dp)], args.steps, 1)
+    S["learned_top128_fp32"] = float(l128.sum_logv.cpu()[0])
+    del l128
+    torch.cuda.empty_cache()
+    clustered = proposal_gain_clustered(h, cfg, args.clustered_n, args.epochs) if args.clustered_n else None
     # ---- global greedy allocation of nonzeros (Section 5.4): the learned step with the
     # nonzeros of 48 picks per supernode shared out by the global greedy (at most 64 per
     # supernode), against 48 picks everywhere
@@ -774,7 +889,20 @@ def main():
             sfb = pipeline.FactorBuilder(h, shp, prec)
             s_ms, (ssel_ms, sfill_ms), _ = timed([lambda: sfb.select(sdp), lambda: sfb.fill(sdp)], 3, 1)
             fl = select_columns_flops(shp.cand_ptr, sfb.sel_count.cpu().numpy())
-            single[name] = {"ms_per_step": s_ms, "select_ms": ssel_ms, "fill_ms": sfill_ms,
+            # the whole build (one persistent selection launch, the nnz scan, the fill) captured
+            # once in a CUDA graph and replayed
+            sg = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                sfb.run(sdp)
+            stream.wait_stream(side)
+            with torch.cuda.graph(sg):
+                sfb.run(sdp)
+            g_ms, _, _ = timed([sg.replay], 3, 1)
+            del sg
+            single[name] = {"ms_per_step": s_ms, "graph_ms_per_step": g_ms,
+                            "graph_columns_per_s": shp.n / (g_ms * 1e-3), "select_ms": ssel_ms, "fill_ms": sfill_ms,
                             "columns_per_s": shp.n / (s_ms * 1e-3), "sum_logv": float(sfb.sum_logv.cpu()[0]),
                             "nnz": int(sfb.col_ptr[-1].item()),
                             "select_roofline": {"bound": "alu", "achieved": fl / (ssel_ms * 1e-3) / 1e12,
@@ -783,8 +911,10 @@ def main():
             del sfb
         del sdp, shp
         torch.cuda.empty_cache()
+    cfg1 = config1(h, timed, stream) if args.cfg1 and rank == 0 else None
     base = S["plain_fp64"] - S["reference_2k"]
     kl_gap = {k: (S[k] - S["plain_fp64"]) / base for k in ["learned_fp32", "plain_fp32", "distance_fp32",
+                                                           "learned_top128_fp32",
                                                            "learned_global_48", "learned_global_48_side_fp64",
                                                            "learned_even_48"]}
 
@@ -937,6 +1067,9 @@ def main():
             "fp32_plain": {"value": ws * N / (p32_ms * 1e-3), "unit": "columns/s", "ms_per_step": p32_ms,
                            "select_ms": p32_sel, "fill_ms": p32_fill},
             "distance_top256_fp32": {"value": ws * N / (d_ms * 1e-3), "unit": "columns/s", "ms_per_step": d_ms},
+            "learned_top128_fp32": {"value": ws * N / (l128_ms * 1e-3), "unit": "columns/s", "ms_per_step": l128_ms,
+                                    "note": "top 2k = 128 instead of the configured 4k (not the headline)"},
+            "proposal_gain_clustered": clustered,
             "speedup_vs_fp64_plain": p64_ms / t_step,
             "timing": "CUDA graph of the whole step, replayed; phases_ms from the same launches issued "
                       "eagerly with events between phases",
@@ -958,6 +1091,7 @@ def main():
             "global_allocation": global_alloc,
             "partial_selection": partial,
             "single_target": single,
+            "config1": cfg1,
             "apply_factor": apply_res,
             "cpu_baseline": cpu,
         }
