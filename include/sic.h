@@ -370,7 +370,8 @@ sic_status sic_build_factor_workspace(int64_t n, size_t* bytes);
  * outputs of the chosen configuration (they do not depend on either choice).  *best_split [host]
  * receives the choice (may be NULL).  sic_tune_save / sic_tune_load write and read the
  * handle's table as text ("op a b value ms" per line, op 1 = the split, op 2 = the
- * large-group launch's worker threads (256 or 384), a = k, b = max_m);
+ * large-group launch's worker threads (256 or 384), a = k, b = max_m; op 3 = the supernodal
+ * selection's plan of sic_tune_select_aggregated, a = k + 256 prec, b = 128 max_cand + max_m);
  * a line that does not parse is skipped and reported as SIC_ERR_INVALID.  sic_tune_count /
  * sic_tune_entry list the table.  [device / host] */
 sic_status sic_tune_build_factor(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
@@ -378,6 +379,23 @@ sic_status sic_tune_build_factor(sic_handle* h, const double* pts, int64_t n, co
                                  const int32_t* sel_count, int32_t k, const int64_t* col_ptr, int32_t* row_idx,
                                  double* val, double* logv, double* sum_logv, void* ws, size_t ws_bytes,
                                  void* stream, int32_t* best_split);
+/* Autotuned launch plan of the supernodal selection (this library's launch tuning; the paper
+ * has no counterpart): the same arguments and results as sic_select_aggregated, but it runs
+ * the selection once per launch plan that gives the same picks -- threads per CTA (128 or 256
+ * for the register-resident FP32 kernel with at most 128 candidates; 256 or 512 for the
+ * generic kernel) and the generic kernel's state in shared memory (when it fits) or in the
+ * workspace (when `ws` holds it) --, each three times with CUDA events on `stream`
+ * (synchronising it; not for stream capture), keeps the fastest in the handle for (k, prec,
+ * max_cand, max_m) (op 3 of the table: value = 2 * threads + 1 if in shared memory, or the
+ * register kernel's threads), and leaves the picks of a final run with it.  Later
+ * sic_select_aggregated calls in that bucket use it (the default plan when the given
+ * workspace is too small for it).  *choice [host] receives the value (may be NULL).
+ * SIC_ERR_INVALID when no plan fits the given workspace.  [device / host] */
+sic_status sic_tune_select_aggregated(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                      const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr,
+                                      const int32_t* cand_idx, int32_t max_cand, int32_t max_m, int32_t k,
+                                      sic_precision prec, int32_t* sel_idx, int32_t* sel_count, void* ws,
+                                      size_t ws_bytes, void* stream, int32_t* choice);
 sic_status sic_tune_save(const sic_handle* h, const char* path);
 sic_status sic_tune_load(sic_handle* h, const char* path);
 int32_t sic_tune_count(const sic_handle* h);

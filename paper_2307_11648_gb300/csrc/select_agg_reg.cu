@@ -249,16 +249,19 @@ __global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
         __syncthreads();
         const float xr = live ? X[tid] : 0.f, yr = live ? X[LDX + tid] : 0.f, zr = live ? X[2 * LDX + tid] : 0.f;
 
-        // ---- Theta_{r,P} of the own row (kept in F2P until the forward substitution)
-        float F2P[RM];
-#pragma unroll
-        for (int a = 0; a < RM; ++a) {
-            F2P[a] = 0.f;
-            if (live && a < m) {
+        // ---- Theta_{r,P} of the own row, into the own row of the F2P mirror (loops over a, not
+        // unrolled: the setup runs once per group, and straight-line code of this size would
+        // be fetched from L2 every time)
+        float* own2 = F2Pm + tid * RPM;
+        for (int a = 0; a < m; ++a) {
+            float v = 0.f;
+            if (live) {
                 const float dx = xr - X[NT + a], dy = yr - X[LDX + NT + a], dz = zr - X[2 * LDX + NT + a];
-                F2P[a] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                v = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
             }
+            own2[a] = v;
         }
+        for (int a = m; a < RPM; ++a) own2[a] = 0.f;  // entries past m are zero (read by the steps' dots)
         // ---- Lp = chol(Theta_PP) and its reciprocal diagonal from the targets' Cholesky launch
         {
             const float* src = lp_ws + g * (long long)LP_SLOT;
@@ -285,35 +288,37 @@ __global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
             __syncthreads();
             continue;
         }
-        // ---- F2P = Lp^-1 Theta_{P,r} (forward substitution, in place) and V2 = Theta_rr|P
+        // ---- F2P = Lp^-1 Theta_{P,r} (forward substitution in place on the own mirror row) and
+        // V2 = Theta_rr|P; then the row moves into registers
         float V1 = live ? diag : NEG, V2 = live ? diag : NEG;
         if (live) {
-#pragma unroll
-            for (int a = 0; a < RM; ++a) {
-                if (a < m) {
-                    const float* la = Lp + a * RPM;
-                    float s0 = F2P[a], s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-                    for (int c = 0; c + 4 <= a; c += 4) {
-                        const float4 l4 = *reinterpret_cast<const float4*>(la + c);
-                        s0 = fmaf(-F2P[c], l4.x, s0);
-                        s1 = fmaf(-F2P[c + 1], l4.y, s1);
-                        s2 = fmaf(-F2P[c + 2], l4.z, s2);
-                        s3 = fmaf(-F2P[c + 3], l4.w, s3);
-                    }
-#pragma unroll
-                    for (int c = a & ~3; c < a; ++c) s0 = fmaf(-F2P[c], la[c], s0);
-                    const float u = ((s0 + s1) + (s2 + s3)) * rLp[a];
-                    F2P[a] = u;
-                    V2 = fmaf(-u, u, V2);
+            for (int a = 0; a < m; ++a) {
+                const float* la = Lp + a * RPM;
+                float s0 = own2[a], s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                int c = 0;
+                for (; c + 4 <= a; c += 4) {
+                    const float4 x4 = *reinterpret_cast<const float4*>(own2 + c);
+                    const float4 l4 = *reinterpret_cast<const float4*>(la + c);
+                    s0 = fmaf(-x4.x, l4.x, s0);
+                    s1 = fmaf(-x4.y, l4.y, s1);
+                    s2 = fmaf(-x4.z, l4.z, s2);
+                    s3 = fmaf(-x4.w, l4.w, s3);
                 }
+                for (; c < a; ++c) s0 = fmaf(-own2[c], la[c], s0);
+                const float u = ((s0 + s1) + (s2 + s3)) * rLp[a];
+                own2[a] = u;
+                V2 = fmaf(-u, u, V2);
             }
         }
+        float F2P[RM];
 #pragma unroll
-        for (int c = 0; c < RM / 4; ++c)
-            *reinterpret_cast<float4*>(F2Pm + tid * RPM + 4 * c) =
-                make_float4(F2P[4 * c], F2P[4 * c + 1], F2P[4 * c + 2], F2P[4 * c + 3]);
-        *reinterpret_cast<float4*>(F2Pm + tid * RPM + RM) = make_float4(0.f, 0.f, 0.f, 0.f);  // pitch tail
+        for (int c = 0; c < RM / 4; ++c) {
+            const float4 x4 = *reinterpret_cast<const float4*>(own2 + 4 * c);
+            F2P[4 * c] = x4.x;
+            F2P[4 * c + 1] = x4.y;
+            F2P[4 * c + 2] = x4.z;
+            F2P[4 * c + 3] = x4.w;
+        }
         __syncthreads();  // Lp is no longer read: F1m becomes the F1 mirror
 #pragma unroll
         for (int c = 0; c < RP / 4; ++c)
@@ -434,8 +439,13 @@ sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const s
     const int lgrid = persistent_grid(h, k_agg_target_chol, 32 * LP_WARPS, 0, (n_grp + LP_WARPS - 1) / LP_WARPS);
     k_agg_target_chol<<<lgrid, 32 * LP_WARPS, 0, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp,
                                                        (float*)ws);
-    // 128 threads (two groups per SM) when every list has at most 128 candidates
-    const int nt = max_cand <= 128 ? 128 : RNT;
+    // 128 threads (two groups per SM) when every list has at most 128 candidates, unless the
+    // autotuner chose 256 for this bucket (each row's arithmetic is the same either way)
+    int nt = max_cand <= 128 ? 128 : RNT;
+    if (max_cand <= 128 &&
+        tune_get(h, TUNE_SELECT_AGG, tune_select_key_a(k, SIC_FP32_MIXED), tune_select_key_b(max_cand, max_m), 0) ==
+            RNT)
+        nt = RNT;
     auto kern = nt == 128 ? k_select_agg_reg<128> : k_select_agg_reg<RNT>;
     const size_t smem = sizeof(float) * ((size_t)nt * RP * 2 + (size_t)nt * RPM + 3 * (size_t)(nt + RM));
     SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -353,13 +353,23 @@ int agg_grid_for(sic_handle* h, size_t smem, long long n_grp) {
     return g;
 }
 
+// The launch plan: state in shared memory when it fits, 256 threads up to 256 candidates and 512
+// beyond -- or, with `variant` (2 * threads + 1 if in shared memory, as the autotuner stores
+// it), that plan when it is possible.  Every plan gives the same picks: each candidate row's
+// arithmetic and the argmax's tie-break do not depend on the thread count, and the shared-
+// memory and workspace dot products sum in the same order.
 template <typename T>
-AggPlan agg_plan(sic_handle* h, long long n_grp, int max_cand, int max_m, int k) {
+AggPlan agg_plan(sic_handle* h, long long n_grp, int max_cand, int max_m, int k, int variant = 0) {
     AggPlan P;
     P.L = agg_layout(max_cand, max_m, k, true);
     P.smem = agg_smem_bytes<T>(P.L, true) <= SMEM_LIMIT;
-    if (!P.smem) P.L = agg_layout(max_cand, max_m, k, false);
     P.nt = (max_cand <= 256) ? 256 : 512;
+    if (variant) {
+        const int vnt = variant / 2;
+        if (vnt == 256 || vnt == 512) P.nt = vnt;
+        if (!(variant & 1)) P.smem = false;
+    }
+    if (!P.smem) P.L = agg_layout(max_cand, max_m, k, false);
     P.smem_bytes = agg_smem_bytes<T>(P.L, P.smem);
     long long work = n_grp > 0 ? n_grp : 1;
     if (P.nt == 256)
@@ -397,7 +407,11 @@ sic_status launch_agg(sic_handle* h, const double* pts, long long n, const sic_k
                       int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx, int max_cand, int max_m, int k,
                       int32_t* sel_idx, int32_t* sel_count, double* gain, void* ws, size_t ws_bytes,
                       cudaStream_t s) {
-    AggPlan P = agg_plan<T>(h, n_grp, max_cand, max_m, k);
+    const int prec = sizeof(T) == 8 ? SIC_FP64 : SIC_FP32_MIXED;
+    const int variant = tune_get(h, TUNE_SELECT_AGG, tune_select_key_a(k, prec), tune_select_key_b(max_cand, max_m), 0);
+    AggPlan P = agg_plan<T>(h, n_grp, max_cand, max_m, k, variant);
+    if (variant && P.ws_bytes > 0 && (!ws || ws_bytes < P.ws_bytes))
+        P = agg_plan<T>(h, n_grp, max_cand, max_m, k);  // the tuned plan needs more workspace than given
     if (P.ws_bytes > 0 && (!ws || ws_bytes < P.ws_bytes)) return SIC_ERR_INVALID;
     KP<T> kpt = make_kp<T>(*kp);
     T fl = (T)sic_floor_of(kp);
@@ -451,4 +465,87 @@ extern "C" sic_status sic_select_aggregated(sic_handle* h, const double* pts, in
                                             size_t ws_bytes, void* stream) {
     return sic_select_aggregated_gain(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, prec,
                                       sel_idx, sel_count, nullptr, ws, ws_bytes, stream);
+}
+
+// ------------------------------------------------------------------ autotuning --
+//
+// sic_tune_select_aggregated: every launch plan of this problem's kind that gives the same
+// picks (threads per CTA; the generic kernel's state in shared memory or in the workspace,
+// where the given workspace holds it) is run three times on the caller's stream and problem,
+// the first run warming up; the fastest is kept in the handle for (k, precision, max_cand,
+// max_m), later sic_select_aggregated calls launch it, and the outputs of a final run with it
+// are left in sel_idx / sel_count.
+namespace {
+template <typename T>
+int agg_variants(sic_handle* h, long long n_grp, int max_cand, int max_m, int k, size_t ws_bytes, int* out) {
+    int nv = 0;
+    for (int nt : {256, 512})
+        for (int sm = 1; sm >= 0; --sm) {
+            const int v = 2 * nt + sm;
+            AggPlan P = agg_plan<T>(h, n_grp, max_cand, max_m, k, v);
+            if (P.nt != nt || (int)P.smem != sm || P.ws_bytes > ws_bytes) continue;  // not possible here
+            out[nv++] = v;
+        }
+    return nv;
+}
+}  // namespace
+
+extern "C" sic_status sic_tune_select_aggregated(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
+                                                 const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr,
+                                                 const int32_t* cand_idx, int32_t max_cand, int32_t max_m, int32_t k,
+                                                 sic_precision prec, int32_t* sel_idx, int32_t* sel_count, void* ws,
+                                                 size_t ws_bytes, void* stream, int32_t* choice) {
+    if (!h || (prec != SIC_FP64 && prec != SIC_FP32_MIXED) || max_cand < 0 || max_m < 1 || k < 1)
+        return SIC_ERR_INVALID;
+    if (max_m > 64 || max_cand > 4096 || k > 128) return SIC_ERR_UNSUPPORTED;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    const int a = tune_select_key_a(k, prec), b = tune_select_key_b(max_cand, max_m);
+    int vars[4], nv = 0;
+    if (agg_reg_applies(prec, max_cand, max_m, k)) {
+        vars[nv++] = 256;
+        if (max_cand <= 128) vars[nv++] = 128;
+    } else if (prec == SIC_FP64) {
+        nv = agg_variants<double>(h, n_grp, max_cand, max_m, k, ws ? ws_bytes : 0, vars);
+    } else {
+        nv = agg_variants<float>(h, n_grp, max_cand, max_m, k, ws ? ws_bytes : 0, vars);
+    }
+    if (nv == 0) return SIC_ERR_INVALID;  // no plan fits the given workspace
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    SIC_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SIC_ERR_CUDA;
+    }
+    sic_status st = SIC_OK;
+    int best = -1;
+    float best_ms = 0.f;
+    for (int vi = 0; vi < nv && st == SIC_OK; ++vi) {
+        tune_put(h, TUNE_SELECT_AGG, a, b, vars[vi], 0.f);
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && st == SIC_OK; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) st = SIC_ERR_CUDA;
+            if (st == SIC_OK)
+                st = sic_select_aggregated(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, prec,
+                                           sel_idx, sel_count, ws, ws_bytes, stream);
+            if (st == SIC_OK && cudaEventRecord(e1, s) != cudaSuccess) st = SIC_ERR_CUDA;
+            if (st == SIC_OK && cudaEventSynchronize(e1) != cudaSuccess) st = SIC_ERR_CUDA;
+            float t = 0.f;
+            if (st == SIC_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = SIC_ERR_CUDA;
+            if (rep == 1 || (rep > 1 && t < ms)) ms = t;
+        }
+        if (st == SIC_OK && (best < 0 || ms < best_ms)) {
+            best = vars[vi];
+            best_ms = ms;
+        }
+    }
+    if (st == SIC_OK) {
+        tune_put(h, TUNE_SELECT_AGG, a, b, best, best_ms);
+        st = sic_select_aggregated(h, pts, n, kp, grp_ptr, n_grp, cand_ptr, cand_idx, max_cand, max_m, k, prec, sel_idx,
+                                   sel_count, ws, ws_bytes, stream);
+        if (choice) *choice = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }

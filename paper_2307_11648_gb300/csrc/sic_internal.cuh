@@ -23,6 +23,12 @@ struct TuneEntry {
 constexpr int TUNE_MAX = 64;
 constexpr int TUNE_FILL_SPLIT = 1;  // k_fill size classes: groups of <= value members in the first launch
 constexpr int TUNE_FILL_BIGNT = 2;  // worker threads of the large-group k_fill launch (256 or 384)
+// supernodal selection launch, keyed a = k + 256 * precision, b = 128 * max_cand + max_m:
+// value = 2 * threads per CTA + 1 if the state lives in shared memory (generic kernel), or the
+// threads per CTA of the register-resident kernel (128 or 256)
+constexpr int TUNE_SELECT_AGG = 3;
+inline int tune_select_key_a(int k, int prec) { return k + 256 * prec; }
+inline int tune_select_key_b(int max_cand, int max_m) { return 128 * max_cand + max_m; }
 
 struct sic_handle {
     int device;

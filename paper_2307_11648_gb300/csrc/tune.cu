@@ -5,7 +5,8 @@
 // default.  Tuned now: the size-class split of the FP64 fill (groups of at most `split`
 // members run in the 4-worker launch, larger ones in the large-group launch, each with its
 // own shared-memory layout and occupancy) and the large-group launch's worker warps (8 or
-// 12).  sic_tune_build_factor times every candidate split on the caller's own problem with
+// 12); and the supernodal selection's launch plan (sic_tune_select_aggregated in
+// select_aggregated.cu: threads per CTA, state in shared memory or in the workspace).  sic_tune_build_factor times every candidate split on the caller's own problem with
 // CUDA events, then the worker count at the best split, and keeps the fastest; sic_tune_save and
 // sic_tune_load keep the table in a text file, one "op a b value ms" line per entry.
 #include <stdio.h>
@@ -143,7 +144,7 @@ extern "C" sic_status sic_tune_load(sic_handle* h, const char* path) {
         int op, a, b, value;
         double ms;
         if (sscanf(line, "%d %d %d %d %lf", &op, &a, &b, &value, &ms) != 5 ||
-            (op != TUNE_FILL_SPLIT && op != TUNE_FILL_BIGNT) || value < 1) {
+            (op != TUNE_FILL_SPLIT && op != TUNE_FILL_BIGNT && op != TUNE_SELECT_AGG) || value < 1) {
             st = SIC_ERR_INVALID;  // unknown or malformed entry: the rest still loads
             continue;
         }

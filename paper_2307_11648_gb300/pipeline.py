@@ -155,6 +155,7 @@ class FactorBuilder:
                  budget: int | None = None, side_fp64: bool = False):
         import torch
         self.h, self.hp, self.prec, self.budget, self.side_fp64 = h, hp, prec, budget, side_fp64
+        self.select_plan = None
         n, U, k = hp.n, hp.n_units, hp.k
         dev = device
         self.sel_idx = torch.empty(U * k, dtype=torch.int32, device=dev)
@@ -242,9 +243,14 @@ class FactorBuilder:
         self.fill(dp, stream)
 
     def tune(self, dp: DeviceProblem, stream=None) -> int:
-        """Select, then tune the fill's launch split on this problem (kept in the handle for
-        later fills with the same k and group bound); returns the chosen split."""
+        """Tune the supernodal selection's launch plan (groups only), select, then tune the
+        fill's launch split on this problem (both kept in the handle for later calls with the
+        same sizes); returns the chosen split (the selection's plan: `select_plan`)."""
         hp = self.hp
+        if hp.grp_ptr is not None:
+            self.select_plan = sic.tune_select_aggregated(self.h, dp.pts, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx,
+                                                          hp.max_cand, hp.max_m, hp.k, self.prec, self.sel_idx,
+                                                          self.local_count, self.ws_sel, stream=stream)
         self.select(dp, stream)
         sic.factor_nnz(self.h, dp.grp_ptr, self.sel_count, hp.n, self.col_ptr, self.ws_nnz, stream=stream)
         return sic.tune_build_factor(self.h, dp.pts, hp.kp, dp.grp_ptr, hp.max_m, self.sel_idx, self.sel_count, hp.k,

@@ -29,7 +29,7 @@ EXPORTS = [
     "sic_select_aggregated_workspace", "sic_select_aggregated",
     "sic_select_columns_gain", "sic_select_aggregated_gain", "sic_allocate_global_workspace", "sic_allocate_global",
     "sic_side_state_fp64", "sic_prep_candidates_partial", "sic_select_partial", "sic_partial_columns",
-    "sic_build_factor_partial", "sic_tune_build_factor", "sic_tune_save", "sic_tune_load", "sic_tune_count",
+    "sic_build_factor_partial", "sic_tune_build_factor", "sic_tune_select_aggregated", "sic_tune_save", "sic_tune_load", "sic_tune_count",
     "sic_tune_entry",
     "sic_factor_nnz_workspace", "sic_factor_nnz", "sic_factor_nnz_noalloc", "sic_build_factor_workspace",
     "sic_build_factor", "sic_prep_partition", "sic_factor_nnz_range", "sic_build_factor_range", "sic_sum_fixed",
@@ -112,6 +112,8 @@ def lib():
             "sic_build_factor_workspace": (st, [i64, C.POINTER(sz)]),
             "sic_tune_build_factor": (st, [vp, vp, i64, pk, vp, i64, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, sz,
                                            vp, C.POINTER(i32)]),
+            "sic_tune_select_aggregated": (st, [vp, vp, i64, pk, vp, i64, vp, vp, i32, i32, i32, st, vp, vp, vp, sz,
+                                                vp, C.POINTER(i32)]),
             "sic_tune_save": (st, [vp, C.c_char_p]),
             "sic_tune_load": (st, [vp, C.c_char_p]),
             "sic_tune_count": (i32, [vp]),
@@ -389,6 +391,22 @@ def partial_columns(h: Handle, n: int, grp_ptr, members, sel_idx, sel_count, k: 
                                      k, kc, _dptr(col_sel, torch.int32, "col_sel"),
                                      _dptr(col_count, torch.int32, "col_count"), _stream(stream)),
            "sic_partial_columns", h)
+
+
+def tune_select_aggregated(h: Handle, pts, kp: Kernel, grp_ptr, cand_ptr, cand_idx, max_cand: int, max_m: int,
+                           k: int, prec: int, sel_idx, sel_count, ws, stream=None) -> int:
+    """sic_tune_select_aggregated: the selection with its launch plan tuned (kept in the handle)."""
+    import torch
+    n = pts.shape[0]
+    choice = C.c_int32(0)
+    _check(lib().sic_tune_select_aggregated(h.ptr, _dptr(pts, torch.float64, "pts"), n, C.byref(kp),
+                                            _dptr(grp_ptr, torch.int64, "grp_ptr"), grp_ptr.numel() - 1,
+                                            _dptr(cand_ptr, torch.int64, "cand_ptr"),
+                                            _dptr(cand_idx, torch.int32, "cand_idx"), max_cand, max_m, k, prec,
+                                            _dptr(sel_idx, torch.int32, "sel_idx"),
+                                            _dptr(sel_count, torch.int32, "sel_count"), _dptr(ws), ws.numel(),
+                                            _stream(stream), C.byref(choice)), "sic_tune_select_aggregated", h)
+    return choice.value
 
 
 def tune_build_factor(h: Handle, pts, kp: Kernel, grp_ptr, max_m: int, sel_idx, sel_count, k: int, col_ptr,
