@@ -15,7 +15,8 @@
 //
 // Per group: the targets' factor chol(Theta_PP) comes from a separate launch over all
 // groups (FP32, one warp per group) through the workspace; every thread evaluates its
-// Theta_{r,P} and solves for F2P by forward substitution (static loops);
+// Theta_{r,P} and solves for F2P by forward substitution, in loops over its own row of
+// the F2P mirror (compact code: the setup runs once per group), then loads the row into registers;
 // then k steps, each with a single block barrier: the warp argmax is one redux over
 // order-preserving score keys (ties: lowest lane = lowest candidate index), the warp
 // winners go to double-buffered shared slots with their V1/V2, and every warp reduces the
@@ -43,11 +44,12 @@ __device__ __forceinline__ unsigned score_key(float s) {
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // monotone in s; 0 is below every key
 }
 
-// acc - r . piv over the 16-element blocks that start below len (r is zero from len on,
-// piv is finite everywhere)
+// Sums of a step's products of the own factor rows with the pivot's rows, a[0..3] += four
+// independent partial sums.  They do not depend on the kernel entry Theta_{r,q}, so they start
+// as soon as the pivot is known and run beside its evaluation; the new column's numerator is
+// Theta_{r,q} - (a0 + a1) - (a2 + a3).
 template <int N>
-__device__ __forceinline__ float reg_dot(float acc, const float (&r)[N], const float* __restrict__ piv, int len) {
-    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+__device__ __forceinline__ void acc_reg(float (&a)[4], const float (&r)[N], const float* __restrict__ piv, int len) {
 #pragma unroll
     for (int b = 0; b < N / 16; ++b) {
         if (16 * b < len) {
@@ -55,44 +57,42 @@ __device__ __forceinline__ float reg_dot(float acc, const float (&r)[N], const f
             for (int c = 0; c < 4; ++c) {
                 const int e = 16 * b + 4 * c;
                 const float4 p = *reinterpret_cast<const float4*>(piv + e);
-                acc = fmaf(-r[e], p.x, acc);
-                a1 = fmaf(-r[e + 1], p.y, a1);
-                a2 = fmaf(-r[e + 2], p.z, a2);
-                a3 = fmaf(-r[e + 3], p.w, a3);
+                a[0] = fmaf(r[e], p.x, a[0]);
+                a[1] = fmaf(r[e + 1], p.y, a[1]);
+                a[2] = fmaf(r[e + 2], p.z, a[2]);
+                a[3] = fmaf(r[e + 3], p.w, a[3]);
             }
         }
     }
-    return (acc + a1) + (a2 + a3);
 }
 
-// acc - r . piv over the first NB 16-element blocks (static)
 template <int NB, int N>
-__device__ __forceinline__ float dot_blocks(float acc, const float (&r)[N], const float* __restrict__ piv) {
-    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+__device__ __forceinline__ void acc_blocks(float (&a)[4], const float (&r)[N], const float* __restrict__ piv) {
 #pragma unroll
     for (int e = 0; e < 16 * NB; e += 4) {
         const float4 p = *reinterpret_cast<const float4*>(piv + e);
-        acc = fmaf(-r[e], p.x, acc);
-        a1 = fmaf(-r[e + 1], p.y, a1);
-        a2 = fmaf(-r[e + 2], p.z, a2);
-        a3 = fmaf(-r[e + 3], p.w, a3);
+        a[0] = fmaf(r[e], p.x, a[0]);
+        a[1] = fmaf(r[e + 1], p.y, a[1]);
+        a[2] = fmaf(r[e + 2], p.z, a[2]);
+        a[3] = fmaf(r[e + 3], p.w, a[3]);
     }
-    return (acc + a1) + (a2 + a3);
 }
 
-// acc - own . piv over one 16-element block, both read from shared memory
-__device__ __forceinline__ float dot_mirror(float acc, const float* __restrict__ own, const float* __restrict__ piv) {
-    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+// the current block: entries below `len` (< 16) of the own row and the pivot's, from shared
+// memory, four at a time (entries from len on are zero on both sides)
+__device__ __forceinline__ void acc_mirror(float (&a)[4], const float* __restrict__ own, const float* __restrict__ piv,
+                                           int len) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const float4 r = *reinterpret_cast<const float4*>(own + 4 * c);
-        const float4 p = *reinterpret_cast<const float4*>(piv + 4 * c);
-        acc = fmaf(-r.x, p.x, acc);
-        a1 = fmaf(-r.y, p.y, a1);
-        a2 = fmaf(-r.z, p.z, a2);
-        a3 = fmaf(-r.w, p.w, a3);
+        if (4 * c < len) {
+            const float4 r = *reinterpret_cast<const float4*>(own + 4 * c);
+            const float4 p = *reinterpret_cast<const float4*>(piv + 4 * c);
+            a[0] = fmaf(r.x, p.x, a[0]);
+            a[1] = fmaf(r.y, p.y, a[1]);
+            a[2] = fmaf(r.z, p.z, a[2]);
+            a[3] = fmaf(r.w, p.w, a[3]);
+        }
     }
-    return (acc + a1) + (a2 + a3);
 }
 
 // The targets' Cholesky factor Lp = chol(Theta_PP) of every group, FP32, one warp per
@@ -360,17 +360,20 @@ __global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
                 const float r1 = rsqrtf(pv1[buf][bw]);
                 const float r2 = rsqrtf(pv2[buf][bw]);
                 if (V2 != NEG) {
+                    // the own rows' products with the pivot's rows: blocks 0..TB-1 from registers,
+                    // the current block TB (tt entries so far) from the own row's mirror
+                    float s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
+                    acc_blocks<TB>(s1, F1, F1m + q * RP);
+                    acc_mirror(s1, F1m + tid * RP + 16 * TB, F1m + q * RP + 16 * TB, tt);
+                    acc_reg(s2, F2P, F2Pm + q * RPM, m);
+                    acc_blocks<TB>(s2, F2S, F2Sm + q * RP);
+                    acc_mirror(s2, F2Sm + tid * RP + 16 * TB, F2Sm + q * RP + 16 * TB, tt);
                     const float dx = xr - X[q], dy = yr - X[LDX + q], dz = zr - X[2 * LDX + q];
                     const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     float th = matern<float>(kp, d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
                     if (tid == q) th += kp.nugget;
-                    // blocks 0..TB-1 from registers, the current block TB from the own row's
-                    // mirror (its entries from tt on are still zero)
-                    float n1 = dot_blocks<TB>(th, F1, F1m + q * RP);
-                    n1 = dot_mirror(n1, F1m + tid * RP + 16 * TB, F1m + q * RP + 16 * TB);
-                    float n2 = reg_dot(th, F2P, F2Pm + q * RPM, m);
-                    n2 = dot_blocks<TB>(n2, F2S, F2Sm + q * RP);
-                    n2 = dot_mirror(n2, F2Sm + tid * RP + 16 * TB, F2Sm + q * RP + 16 * TB);
+                    const float n1 = th - ((s1[0] + s1[1]) + (s1[2] + s1[3]));
+                    const float n2 = th - ((s2[0] + s2[1]) + (s2[2] + s2[3]));
                     const float u1 = n1 * r1, u2 = n2 * r2;
                     F1m[tid * RP + t] = u1;
                     F2Sm[tid * RP + t] = u2;
