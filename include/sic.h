@@ -577,6 +577,15 @@ sic_status sic_selftest_fp64_math(sic_handle* h, const sic_kernel* kp, const dou
                                   double* out_sqrt, double* out_rsqrt, double* out_exp, double* out_kernel,
                                   void* stream);
 
+/* Evaluates the double-float Matern of the fill (not part of the paper): out[i] = the kernel
+ * of *kp (no nugget) between points pa[i] and pb[i] (n x dim each, [device]), computed as the
+ * fill computes its entries -- coordinates relative to an origin (here pa[i]) split into
+ * double-floats, distance, square root and table-driven exponential in double-float
+ * arithmetic on the FP32 pipe, one FP64 addition at the end.  out [device, n doubles].  Tests
+ * compare it with the FP64 oracle (absolute error a few 1e-15 of the variance). */
+sic_status sic_selftest_matern_df(sic_handle* h, const sic_kernel* kp, const double* pa, const double* pb, int64_t n,
+                                  double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,14 +11,16 @@
 // since U = J G J (J the reversal), member a's column is J G^{-T} e_j = d_j^{-1/2} J L^{-T} e_j
 // with j = n-1-a: one back substitution per member, one member per half-warp, the
 // right-hand side in registers.  v_a = G_jj^2 = d_j, so logv = log d_j (eq. inverse_cond).  Rows are written diagonal first, then
-// ascending, to the caller's CSC arrays.  Theta entries use the FP64 Matern of
-// matern_d2_fast (table-driven exp, Newton sqrt): this GPU issues two FP64 FMAs per
-// clock per SM, so FP64 instructions are spent on the factorisation.
+// ascending, to the caller's CSC arrays.  Theta entries use the double-float Matern of
+// dfloat.cuh on the FP32 pipe (one FP64 addition per entry): this GPU retires about one FP64
+// warp instruction per 80 clocks per SM sub-partition, so FP64 instructions are spent on the
+// factorisation.
 //
 // Also here: the nnz count + exclusive scan that builds col_ptr, and the fixed-order
 // two-pass sum of logv (bit-reproducible).
 #include <mutex>
 
+#include "dfloat.cuh"
 #include "sic_internal.cuh"
 
 namespace {
@@ -167,14 +169,19 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
     double* rG = G + (long long)nmax * (nmax + 1) / 2;      // 1 / G_jj
     double* cj = rG + nmax;                                 // the current column of L
     double* cu = cj + nmax;                                 // the same column before scaling by 1/d_j
-    double* xyz = cu + nmax;                                // 3 x nmax
-    double* tab = xyz + 3 * nmax;                           // 2^(j/256) (exp_neg_table)
-    int* pos = reinterpret_cast<int*>(tab + EXP_TAB);       // nmax
+    // coordinates relative to the unit's first member as double-floats: high parts [3][nmax],
+    // then low parts [3][nmax] (the space of 3 x nmax doubles)
+    float* xh = reinterpret_cast<float*>(cu + nmax);
+    float* xl = xh + 3 * nmax;
+    float* tab_hi = xl + 3 * nmax;                          // s2 2^(j/256) as double-floats
+    float* tab_lo = tab_hi + DF_EXP_TAB;                    // (the space of EXP_TAB doubles)
+    int* pos = reinterpret_cast<int*>(tab_lo + DF_EXP_TAB); // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool worker = tid < FILL_NT;  // the pivot warp joins only the barriers and the pivots
-    exp_table_fill(tab, kp.s2);
+    const DfMatern dfk = df_matern_params(kp);
+    df_exp_table_fill(tab_hi, tab_lo, kp.s2);
 
     for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         const long long g0 = grp_ptr ? grp_ptr[u] : col0 + u;
@@ -207,26 +214,26 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
             if (tid == 0) record_error(st, SIC_ERR_INVALID, u);
             continue;
         }
-        // R order: picks descending, then members descending
+        // R order: picks descending, then members descending; coordinates relative to the first
+        // member (differences in FP64, then split into double-floats: per point, not per entry)
         for (int i = worker ? tid : nn; i < nn; i += FILL_NT) {
             const int p = (i < cnt) ? srt[cnt - 1 - i] : (int)(g0 + m - 1 - (i - cnt));
             pos[i] = p;
-            for (int d = 0; d < 3; ++d) xyz[d * nmax + i] = (d < dim) ? pts[(long long)p * dim + d] : 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const dfl c = df_from_double((d < dim) ? pts[(long long)p * dim + d] - pts[g0 * dim + d] : 0.0);
+                xh[d * nmax + i] = c.hi;
+                xl[d * nmax + i] = c.lo;
+            }
         }
         if (tid == 0) s_bad = 0;
         __syncthreads();
-        // Theta_RR, packed lower, one flat entry per thread
+        // Theta_RR, packed lower, one flat entry per thread, by the double-float Matern on the
+        // FP32 pipe (one FP64 addition per entry; the FP64 pipe is left to the factorisation)
         const int tri = nn * (nn + 1) / 2;
         for (int e = worker ? tid : tri; e < tri; e += FILL_NT) {
             const int i = pk_row(e);
             const int j = e - i * (i + 1) / 2;
-            const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j];
-            double d2 = fma(dy, dy, dx * dx);
-            if (dim == 3) {
-                const double dz = xyz[2 * nmax + i] - xyz[2 * nmax + j];
-                d2 = fma(dz, dz, d2);
-            }
-            double v = matern_d2_fast(kp, d2, tab);
+            double v = matern_df(dfk, xh, xl, i, j, nmax, dim, tab_hi, tab_lo);
             if (i == j) v += kp.nugget;
             G[e] = v;
         }
@@ -375,9 +382,44 @@ __global__ void k_fp64_math(KP<double> kp, const double* __restrict__ x, long lo
     }
 }
 
+// out[i] = the double-float Matern between points pa[i] and pb[i] (n x dim each), with pa[i]
+// as the origin of the coordinates, as the fill evaluates its entries
+__global__ void k_matern_df(KP<double> kp, int dim, const double* __restrict__ pa, const double* __restrict__ pb,
+                            long long n, double* __restrict__ out) {
+    __shared__ float tab_hi[DF_EXP_TAB], tab_lo[DF_EXP_TAB];
+    __shared__ float xh[3 * 2 * 256], xl[3 * 2 * 256];
+    df_exp_table_fill(tab_hi, tab_lo, kp.s2);
+    __syncthreads();
+    const DfMatern dfk = df_matern_params(kp);
+    const int t = threadIdx.x;
+    for (long long i0 = blockIdx.x * 256LL; i0 < n; i0 += 256LL * gridDim.x) {
+        const long long i = i0 + t;
+        for (int d = 0; d < 3; ++d) {
+            const dfl c = df_from_double((i < n && d < dim) ? pb[i * dim + d] - pa[i * dim + d] : 0.0);
+            xh[d * 512 + t] = 0.f;
+            xl[d * 512 + t] = 0.f;
+            xh[d * 512 + 256 + t] = c.hi;
+            xl[d * 512 + 256 + t] = c.lo;
+        }
+        if (i < n) out[i] = matern_df(dfk, xh, xl, t, 256 + t, 512, dim, tab_hi, tab_lo);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- entry points --
+
+extern "C" sic_status sic_selftest_matern_df(sic_handle* h, const sic_kernel* kp, const double* pa, const double* pb,
+                                             int64_t n, double* out, void* stream) {
+    if (!h || !sic_valid_kernel(kp) || n < 0 || (n > 0 && (!pa || !pb || !out))) return SIC_ERR_INVALID;
+    if (n == 0) return SIC_OK;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4LL * h->num_sms) blocks = 4LL * h->num_sms;
+    k_matern_df<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(make_kp<double>(*kp), kp->dim, pa, pb, n, out);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
 
 extern "C" sic_status sic_selftest_fp64_math(sic_handle* h, const sic_kernel* kp, const double* x, int64_t n,
                                              double* out_sqrt, double* out_rsqrt, double* out_exp,

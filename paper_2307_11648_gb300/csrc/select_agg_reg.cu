@@ -44,12 +44,11 @@ __device__ __forceinline__ unsigned score_key(float s) {
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // monotone in s; 0 is below every key
 }
 
-// Sums of a step's products of the own factor rows with the pivot's rows, a[0..3] += four
-// independent partial sums.  They do not depend on the kernel entry Theta_{r,q}, so they start
-// as soon as the pivot is known and run beside its evaluation; the new column's numerator is
-// Theta_{r,q} - (a0 + a1) - (a2 + a3).
+// acc - r . piv over the 16-element blocks that start below len (r is zero from len on,
+// piv is finite everywhere)
 template <int N>
-__device__ __forceinline__ void acc_reg(float (&a)[4], const float (&r)[N], const float* __restrict__ piv, int len) {
+__device__ __forceinline__ float reg_dot(float acc, const float (&r)[N], const float* __restrict__ piv, int len) {
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
     for (int b = 0; b < N / 16; ++b) {
         if (16 * b < len) {
@@ -57,19 +56,55 @@ __device__ __forceinline__ void acc_reg(float (&a)[4], const float (&r)[N], cons
             for (int c = 0; c < 4; ++c) {
                 const int e = 16 * b + 4 * c;
                 const float4 p = *reinterpret_cast<const float4*>(piv + e);
-                a[0] = fmaf(r[e], p.x, a[0]);
-                a[1] = fmaf(r[e + 1], p.y, a[1]);
-                a[2] = fmaf(r[e + 2], p.z, a[2]);
-                a[3] = fmaf(r[e + 3], p.w, a[3]);
+                acc = fmaf(-r[e], p.x, acc);
+                a1 = fmaf(-r[e + 1], p.y, a1);
+                a2 = fmaf(-r[e + 2], p.z, a2);
+                a3 = fmaf(-r[e + 3], p.w, a3);
             }
         }
     }
+    return (acc + a1) + (a2 + a3);
 }
 
+// acc - r . piv over the first NB 16-element blocks (static)
 template <int NB, int N>
-__device__ __forceinline__ void acc_blocks(float (&a)[4], const float (&r)[N], const float* __restrict__ piv) {
+__device__ __forceinline__ float dot_blocks(float acc, const float (&r)[N], const float* __restrict__ piv) {
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
     for (int e = 0; e < 16 * NB; e += 4) {
+        const float4 p = *reinterpret_cast<const float4*>(piv + e);
+        acc = fmaf(-r[e], p.x, acc);
+        a1 = fmaf(-r[e + 1], p.y, a1);
+        a2 = fmaf(-r[e + 2], p.z, a2);
+        a3 = fmaf(-r[e + 3], p.w, a3);
+    }
+    return (acc + a1) + (a2 + a3);
+}
+
+// acc - own . piv over one 16-element block, both read from shared memory
+__device__ __forceinline__ float dot_mirror(float acc, const float* __restrict__ own, const float* __restrict__ piv) {
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float4 r = *reinterpret_cast<const float4*>(own + 4 * c);
+        const float4 p = *reinterpret_cast<const float4*>(piv + 4 * c);
+        acc = fmaf(-r.x, p.x, acc);
+        a1 = fmaf(-r.y, p.y, a1);
+        a2 = fmaf(-r.z, p.z, a2);
+        a3 = fmaf(-r.w, p.w, a3);
+    }
+    return (acc + a1) + (a2 + a3);
+}
+
+// Sums of a step's products of the own factor rows with the pivot's rows, a[0..3] += four
+// independent partial sums.  They do not depend on the kernel entry Theta_{r,q}, so they start
+// as soon as the pivot is known and run beside its evaluation; the new column's numerator is
+// Theta_{r,q} - (a0 + a1) - (a2 + a3).
+// over the 16-element blocks B0 .. NB-1 (static)
+template <int B0, int NB, int N>
+__device__ __forceinline__ void acc_blocks(float (&a)[4], const float (&r)[N], const float* __restrict__ piv) {
+#pragma unroll
+    for (int e = 16 * B0; e < 16 * NB; e += 4) {
         const float4 p = *reinterpret_cast<const float4*>(piv + e);
         a[0] = fmaf(r[e], p.x, a[0]);
         a[1] = fmaf(r[e + 1], p.y, a[1]);
@@ -362,18 +397,26 @@ __global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
                 if (V2 != NEG) {
                     // the own rows' products with the pivot's rows: blocks 0..TB-1 from registers,
                     // the current block TB (tt entries so far) from the own row's mirror
+                    // (the first segment of each sum -- F1's first block, F2's target columns, which
+                    // usually carry most of the correlation -- is subtracted from the kernel entry
+                    // term by term, as fused operations, so that its cancellation loses nothing;
+                    // the other segments are summed first, while the entry is evaluated)
                     float s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
-                    acc_blocks<TB>(s1, F1, F1m + q * RP);
-                    acc_mirror(s1, F1m + tid * RP + 16 * TB, F1m + q * RP + 16 * TB, tt);
-                    acc_reg(s2, F2P, F2Pm + q * RPM, m);
-                    acc_blocks<TB>(s2, F2S, F2Sm + q * RP);
+                    if constexpr (TB >= 1) {
+                        acc_blocks<1, TB>(s1, F1, F1m + q * RP);
+                        acc_mirror(s1, F1m + tid * RP + 16 * TB, F1m + q * RP + 16 * TB, tt);
+                    }
+                    acc_blocks<0, TB>(s2, F2S, F2Sm + q * RP);
                     acc_mirror(s2, F2Sm + tid * RP + 16 * TB, F2Sm + q * RP + 16 * TB, tt);
                     const float dx = xr - X[q], dy = yr - X[LDX + q], dz = zr - X[2 * LDX + q];
                     const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     float th = matern<float>(kp, d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
                     if (tid == q) th += kp.nugget;
-                    const float n1 = th - ((s1[0] + s1[1]) + (s1[2] + s1[3]));
-                    const float n2 = th - ((s2[0] + s2[1]) + (s2[2] + s2[3]));
+                    float n1;
+                    if constexpr (TB >= 1) n1 = dot_blocks<1>(th, F1, F1m + q * RP);
+                    else n1 = dot_mirror(th, F1m + tid * RP, F1m + q * RP);
+                    n1 -= (s1[0] + s1[1]) + (s1[2] + s1[3]);
+                    const float n2 = reg_dot(th, F2P, F2Pm + q * RPM, m) - ((s2[0] + s2[1]) + (s2[2] + s2[3]));
                     const float u1 = n1 * r1, u2 = n2 * r2;
                     F1m[tid * RP + t] = u1;
                     F2Sm[tid * RP + t] = u2;

@@ -35,7 +35,7 @@ EXPORTS = [
     "sic_build_factor", "sic_prep_partition", "sic_factor_nnz_range", "sic_build_factor_range", "sic_sum_fixed",
     "sic_apply_factor_workspace", "sic_apply_factor",
     "sic_matern_matvec", "sic_pcg_workspace", "sic_pcg_solve", "sic_selftest_wait_timeout",
-    "sic_selftest_fp64_math",
+    "sic_selftest_fp64_math", "sic_selftest_matern_df",
     "sic_mlp_param_count", "sic_proposal_features", "sic_proposal_score",
     "sic_proposal_topk", "sic_proposal_labels", "sic_mlp_train_workspace", "sic_mlp_grads", "sic_adamw_step",
 ]
@@ -125,6 +125,7 @@ def lib():
             "sic_matern_matvec": (st, [vp, vp, i64, pk, d, st, vp, vp, i32, vp]),
             "sic_selftest_wait_timeout": (st, [vp, i64, vp, vp]),
             "sic_selftest_fp64_math": (st, [vp, pk, vp, i64, vp, vp, vp, vp, vp]),
+            "sic_selftest_matern_df": (st, [vp, pk, vp, vp, i64, vp, vp]),
             "sic_pcg_workspace": (st, [i64, i32, C.POINTER(sz)]),
             "sic_pcg_solve": (st, [vp, vp, i64, pk, d, st, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp, sz, vp]),
             "sic_mlp_param_count": (i32, []),
@@ -699,6 +700,18 @@ def selftest_fp64_math(h: Handle, kp: Kernel, x, stream=None):
                                         *[_dptr(o, torch.float64, "out") for o in outs], _stream(stream)),
            "sic_selftest_fp64_math", h)
     return outs
+
+
+def selftest_matern_df(h: Handle, kp: Kernel, pa, pb, stream=None):
+    """The fill's double-float Matern between the rows of pa and pb (CUDA float64, n x dim)."""
+    import torch
+    pa, pb = pa.contiguous(), pb.contiguous()
+    out = torch.empty(pa.shape[0], dtype=torch.float64, device=pa.device)
+    _check(lib().sic_selftest_matern_df(h.ptr, C.byref(kp), _dptr(pa, torch.float64, "pa"),
+                                        _dptr(pb, torch.float64, "pb"), pa.shape[0],
+                                        _dptr(out, torch.float64, "out"), _stream(stream)),
+           "sic_selftest_matern_df", h)
+    return out
 
 
 def gp_predict(h: Handle, pts, kp: Kernel, targets, sel_idx, sel_count, k: int, y, mean, var, stream=None):

@@ -89,3 +89,33 @@ def test_matern_against_oracle(env, oracle_lib, nu_x2):
     err = np.abs(kv - ref) / (ref * (6 + 3 * t) * ULP)
     print(f"nu={nu_x2}/2 Matern max err / ((6 + 3t) ulp)", err.max())
     assert err.max() <= 1.0
+
+
+@pytest.mark.parametrize("dim,nu_x2,ell,variance", [(2, 3, 0.02, 1.0), (3, 5, 0.05, 1.0), (2, 1, 0.1, 2.5),
+                                                    (2, 3, 0.1, 1.0)])
+def test_double_float_matern_against_the_oracle(env, oracle_lib, dim, nu_x2, ell, variance):
+    """The fill's double-float Matern (dfloat.cuh: coordinates relative to an origin as
+    double-floats, distance, square root and table-driven exponential in double-float on
+    the FP32 pipe) against the oracle's FP64 Matern (C, libm exp) on point pairs at
+    distances from 1e-7 ell to 40 ell, coordinates in the unit cube: the absolute error
+    must stay below 8e-15 of the variance (about 2^-48 (1 + t) of the entry, t up to ~30,
+    plus the double-float coordinates' 2^-48 of their distance to the origin) -- what the
+    FP64 fill needs: its entries' errors enter the factorisation as a perturbation of
+    Theta of that absolute size."""
+    torch, sic, h = env
+    kp = sic.kernel(dim, nu_x2, ell, variance, 0.0)
+    n = 200000
+    pa = synthetic.uniform(81, 0, n * dim).reshape(n, dim)
+    direc = synthetic.normal(82, n * dim).reshape(n, dim)
+    direc /= np.linalg.norm(direc, axis=1, keepdims=True)
+    u = synthetic.uniform(83, 0, n)
+    r = ell * np.exp(np.log(1e-7) + u * (np.log(40.0) - np.log(1e-7)))
+    pb = pa + direc * r[:, None]
+    got = sic.selftest_matern_df(h, kp, torch.from_numpy(pa).cuda(), torch.from_numpy(pb).cuda()).cpu().numpy()
+    h.sync()
+    okp = oracle_lib.kernel(dim, nu_x2, ell, variance, 0.0)
+    ref = np.array([oracle_lib.matern(okp, float(np.linalg.norm(b - a))) for a, b in zip(pa, pb)])
+    err = np.abs(got - ref)
+    print(f"dim {dim} nu {nu_x2}/2 ell {ell}: max abs err {err.max() / variance:.3e} of the variance, "
+          f"max rel err where the entry > 1e-3: {np.max(err[ref > 1e-3 * variance] / ref[ref > 1e-3 * variance]):.3e}")
+    assert err.max() <= 8e-15 * variance
