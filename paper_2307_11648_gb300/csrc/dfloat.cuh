@@ -99,26 +99,27 @@ __device__ __forceinline__ void df_exp_table_fill(float* tab_hi, float* tab_lo, 
     }
 }
 
-// scale * exp(-t), t >= 0 double-float.  For t <= 20: Tang's table-driven reduction (ACM TOMS
+// scale * exp(-t), t >= 0 double-float.  For t <= 36: Tang's table-driven reduction (ACM TOMS
 // 15(2), 1989) carried out in double-float.  k = round(256 t / ln 2), r = k ln2/256 - t with
 // |r| <= ln2/512 (about); ln2/256 is split into L_HI (9 significant bits, so k L_HI is exact
-// for k < 2^15), L_MID and L_LO3, the product k L_MID taken exactly, so r is exact up to the
+// for k < 2^15; here k <= 13296), L_MID and L_LO3, the product k L_MID taken exactly, so r is exact up to the
 // rounding of terms below 1e-9.  e^r - 1 = r + r^2/2 + r^2 (r/6 + r^2/24) (the r^5 term is below
 // 4e-17), r and r^2 in double-float; with -k = 256 q + j (0 <= j < 256) the result is
 // 2^q (T_j + T_j (e^r - 1)), T_j = scale 2^(j/256) from the table, the power of two exact.
-// Absolute error about 2^-48 (1 + t) scale exp(-t), below 4e-15 scale for every t.  For t > 20
-// the value is below 2.1e-9 scale and the FP32 exponential (a few ulp) keeps the absolute
-// error below 1e-15 scale; t above 80 returns 0.
+// Absolute error about 2^-48 (1 + t) scale exp(-t), below 4e-15 scale for every t.  For t > 36
+// the value is below 2.4e-16 scale and the FP32 exponential (relative error about 1e-6, the
+// rounding of its argument included) keeps the absolute error below 1e-18 scale even after the
+// Matern polynomial (below 470 there); t above 80 returns 0.
 __device__ __forceinline__ dfl df_exp_neg(dfl t, float scale, const float* __restrict__ tab_hi,
                                           const float* __restrict__ tab_lo) {
-    if (t.hi > 20.f) return {t.hi > 80.f ? 0.f : __fmul_rn(scale, __expf(-t.hi)), 0.f};
+    if (t.hi > 36.f) return {t.hi > 80.f ? 0.f : __fmul_rn(scale, __expf(-t.hi)), 0.f};
     constexpr float INV_L = 369.329925537109375f;             // 256 / ln 2 (any rounding works)
     constexpr float L_HI = 0.00270843505859375f;              // ln2/256 to 9 bits
     constexpr float L_MID = -8.288845378956466e-07f;          // ln2/256 - L_HI, FP32
     constexpr float L_LO3 = 6.432011600578363e-15f;           // the rest (below 5e-23 remains)
     constexpr float MAGIC = 12582912.f;                       // 1.5 * 2^23: rounds to an integer
     const float kf = __fsub_rn(__fadd_rn(__fmul_rn(t.hi, INV_L), MAGIC), MAGIC);
-    const int k = (int)kf;  // exact: 0 <= kf <= 7387
+    const int k = (int)kf;  // exact: 0 <= kf <= 13296
     const float a0 = __fsub_rn(__fmul_rn(kf, L_HI), t.hi);   // exact: k L_HI exact, Sterbenz
     const dfl m = df_two_prod(kf, L_MID);
     const float rest = __fadd_rn(__fsub_rn(m.lo, t.lo), __fmul_rn(kf, L_LO3));
@@ -127,13 +128,12 @@ __device__ __forceinline__ dfl df_exp_neg(dfl t, float scale, const float* __res
     // e^r - 1
     const dfl r2 = df_two_prod(r.hi, r.hi);
     const float w = __fmul_rn(r.hi, __fmaf_rn(r.hi, 1.f / 24.f, 1.f / 6.f));
-    const float tail = __fadd_rn(__fadd_rn(__fmul_rn(0.5f, r2.lo), __fmul_rn(__fadd_rn(r.hi, r.hi), r.lo)),
-                                 __fmul_rn(r2.hi, w));
+    const float tail = __fadd_rn(__fadd_rn(__fmul_rn(0.5f, r2.lo), __fmul_rn(r.hi, r.lo)), __fmul_rn(r2.hi, w));
     dfl p = df_two_sum(r.hi, __fmul_rn(0.5f, r2.hi));
     p = df_fast_two_sum(p.hi, __fadd_rn(p.lo, __fadd_rn(r.lo, tail)));
     // exp(-t) = 2^(-k/256) e^r, -k = 256 q + j
     const int mk = -k;
-    const int q = mk >> 8;  // floor(-k / 256), in [-29, 0]
+    const int q = mk >> 8;  // floor(-k / 256), in [-52, 0]
     const int j = mk & (DF_EXP_TAB - 1);
     const dfl T = {tab_hi[j], tab_lo[j]};
     const dfl e = df_add(T, df_mul(T, p));

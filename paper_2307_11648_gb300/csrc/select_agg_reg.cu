@@ -208,6 +208,97 @@ __global__ void __launch_bounds__(32 * LP_WARPS) k_agg_target_chol(const double*
     }
 }
 
+// The targets' columns F2P = Theta_{r,P} chol(Theta_PP)^-T of every candidate row r of every
+// group, FP32, for k_select_agg_reg: one thread per row, TC_ROWS rows per CTA and several CTAs
+// per SM, so that the per-row chains (m kernel entries, then a forward substitution of m steps)
+// of many groups are in flight together -- inside the selection kernel, with one group per SM,
+// they left the SM waiting.  Same arithmetic, in the same order, as the selection kernel's own
+// staging would do.  Output: group g's entry (a, r) at f2p[(g0 - G0 + a) * NT + r], g0 =
+// grp_ptr[g], G0 = grp_ptr[0] (the groups are consecutive positions).  Rows of candidates that
+// are not valid, and groups whose targets' factor failed, are skipped (the selection kernel
+// reports them).
+constexpr int TC_ROWS = 128;
+constexpr size_t TC_SMEM = sizeof(float) * ((size_t)RM * RPM + RM + 3 * RM + (size_t)TC_ROWS * RPM);
+
+template <int NT>
+__global__ void __launch_bounds__(TC_ROWS) k_agg_target_cols(const double* __restrict__ pts, long long n, int dim,
+                                                              KP<float> kp, const long long* __restrict__ grp_ptr,
+                                                              long long n_grp, const long long* __restrict__ cand_ptr,
+                                                              const int32_t* __restrict__ cand_idx,
+                                                              const float* __restrict__ lp_ws, float* __restrict__ f2p,
+                                                              int max_m) {
+    extern __shared__ __align__(16) float smc[];
+    float* Lp = smc;                  // [RM][RPM]
+    float* rLp = Lp + RM * RPM;       // [RM]
+    float* XP = rLp + RM;             // [3][RM] the targets' coordinates
+    float* rows = XP + 3 * RM;        // [TC_ROWS][RPM] the threads' rows
+    constexpr int CH = NT / TC_ROWS;  // row chunks per group
+    const int tid = threadIdx.x;
+    const long long G0 = grp_ptr[0];
+    for (long long it = blockIdx.x; it < n_grp * CH; it += gridDim.x) {
+        const long long g = it / CH;
+        const int ch = (int)(it % CH);
+        const long long g0 = grp_ptr[g];
+        const int m = (int)(grp_ptr[g + 1] - g0);
+        const long long b0 = cand_ptr[g];
+        const int C = (int)(cand_ptr[g + 1] - b0);
+        const float* src = lp_ws + g * (long long)LP_SLOT;
+        if (m < 1 || m > max_m || C < 0 || C > NT || g0 < 0 || g0 + m > n || src[LP_PACKED + RM] != 0.f ||
+            ch * TC_ROWS >= C || g0 - G0 + m > n_grp * (long long)max_m)
+            continue;  // uniform over the CTA; the selection kernel reports what is invalid
+        double org[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) org[d] = pts[g0 * dim + d];
+        const int tri = m * (m + 1) / 2;
+        for (int e = tid; e < tri; e += TC_ROWS) {
+            int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+            while (i * (i + 1) / 2 > e) --i;
+            while ((i + 1) * (i + 2) / 2 <= e) ++i;
+            Lp[i * RPM + (e - i * (i + 1) / 2)] = src[e];
+        }
+        if (tid < m) {
+            rLp[tid] = src[LP_PACKED + tid];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) XP[d * RM + tid] = (d < dim) ? (float)(pts[(g0 + tid) * dim + d] - org[d]) : 0.f;
+        }
+        __syncthreads();
+        const int r = ch * TC_ROWS + tid;
+        if (r < C) {
+            const long long p = cand_idx[b0 + r];
+            if (p >= g0 + m && p < n) {
+                const float xr = (float)(pts[p * dim] - org[0]);
+                const float yr = dim > 1 ? (float)(pts[p * dim + 1] - org[1]) : 0.f;
+                const float zr = dim > 2 ? (float)(pts[p * dim + 2] - org[2]) : 0.f;
+                float* own = rows + tid * RPM;
+                for (int a = 0; a < m; ++a) {
+                    const float dx = xr - XP[a], dy = yr - XP[RM + a], dz = zr - XP[2 * RM + a];
+                    own[a] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                }
+                float* out = f2p + (g0 - G0) * NT + r;
+                for (int a = 0; a < m; ++a) {
+                    const float* la = Lp + a * RPM;
+                    float s0 = own[a], s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                    int c = 0;
+                    for (; c + 4 <= a; c += 4) {
+                        const float4 x4 = *reinterpret_cast<const float4*>(own + c);
+                        const float4 l4 = *reinterpret_cast<const float4*>(la + c);
+                        s0 = fmaf(-x4.x, l4.x, s0);
+                        s1 = fmaf(-x4.y, l4.y, s1);
+                        s2 = fmaf(-x4.z, l4.z, s2);
+                        s3 = fmaf(-x4.w, l4.w, s3);
+                    }
+                    for (; c < a; ++c) s0 = fmaf(-own[c], la[c], s0);
+                    const float u = ((s0 + s1) + (s2 + s3)) * rLp[a];
+                    own[a] = u;
+                    out[(long long)a * NT] = u;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // NT threads (candidate rows) per group: 256, one CTA per SM; or 128 for lists of at most 128
 // candidates, two CTAs (groups) per SM with the same per-thread state
 template <int NT>
@@ -215,17 +306,15 @@ __global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
     const double* __restrict__ pts, long long n, int dim, KP<float> kp, float floor_,
     const long long* __restrict__ grp_ptr, long long n_grp, const long long* __restrict__ cand_ptr,
     const int32_t* __restrict__ cand_idx, int k, int max_m, int32_t* __restrict__ sel_idx,
-    int32_t* __restrict__ sel_count, const float* __restrict__ lp_ws, double* __restrict__ gain, DevStatus* st) {
+    int32_t* __restrict__ sel_count, const float* __restrict__ lp_ws, const float* __restrict__ f2p,
+    double* __restrict__ gain, DevStatus* st) {
     constexpr int LDX = NT + RM;      // staged coordinates: candidates then targets
     constexpr int NW = NT / 32;       // warps
-    static_assert(NT * RP >= RM * RPM + RM, "the target factor overlays the F1 mirror");
     extern __shared__ __align__(16) float smf[];
     float* F1m = smf;                 // [NT][RP]
     float* F2Sm = F1m + NT * RP;      // [NT][RP]
     float* F2Pm = F2Sm + NT * RP;     // [NT][RPM]
     float* X = F2Pm + NT * RPM;       // [3][LDX]
-    float* Lp = F1m;                  // [RM][RPM] chol(Theta_PP), overlays F1m before the steps
-    float* rLp = F1m + RM * RPM;      // [RM] reciprocal diagonal of Lp
     __shared__ __align__(16) unsigned pkey[2][NW];
     __shared__ int pidx[2][NW];
     __shared__ float pv1[2][NW], pv2[2][NW];
@@ -241,7 +330,8 @@ __global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
         const int m = (int)(grp_ptr[g + 1] - g0);
         const long long b0 = cand_ptr[g];
         const int C = (int)(cand_ptr[g + 1] - b0);
-        if (m < 1 || m > RM || m > max_m || C < 0 || C > NT || g0 < 0 || g0 + m > n) {
+        if (m < 1 || m > RM || m > max_m || C < 0 || C > NT || g0 < 0 || g0 + m > n ||
+            g0 - grp_ptr[0] + m > n_grp * (long long)max_m) {  // (the last: its targets' columns lie beyond the workspace)
             if (tid == 0) {
                 record_error(st, SIC_ERR_INVALID, g);
                 sel_count[g] = 0;
@@ -266,98 +356,49 @@ __global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
 #pragma unroll
             for (int d = 0; d < 3; ++d) X[d * LDX + tid] = (d < dim) ? (float)(pts[p * dim + d] - org[d]) : 0.f;
         }
-        if (tid < m) {
+        // zero this thread's rows of the pick mirrors
 #pragma unroll
-            for (int d = 0; d < 3; ++d)
-                X[d * LDX + NT + tid] = (d < dim) ? (float)(pts[(g0 + tid) * dim + d] - org[d]) : 0.f;
-        }
-        // zero this thread's pick mirrors except F1m (which holds Lp until the steps)
-#pragma unroll
-        for (int c = 0; c < RP / 4; ++c)
+        for (int c = 0; c < RP / 4; ++c) {
+            *reinterpret_cast<float4*>(F1m + tid * RP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
             *reinterpret_cast<float4*>(F2Sm + tid * RP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (tid < RM) {
-#pragma unroll
-            for (int c = 0; c < RPM / 4; ++c)
-                *reinterpret_cast<float4*>(Lp + tid * RPM + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (tid == 0) s_fail = 0;
+        // the targets' factor failed? (reported here; k_agg_target_cols skipped the group)
+        if (tid == 0) {
+            const float f = lp_ws[g * (long long)LP_SLOT + LP_PACKED + RM];
+            s_fail = 0;
+            if (f != 0.f) {
+                record_error(st, f == 2.f ? SIC_ERR_NOT_PD : SIC_ERR_INVALID, g);
+                s_fail = 1;
+            }
+        }
         __syncthreads();
         const float xr = live ? X[tid] : 0.f, yr = live ? X[LDX + tid] : 0.f, zr = live ? X[2 * LDX + tid] : 0.f;
-
-        // ---- Theta_{r,P} of the own row, into the own row of the F2P mirror (loops over a, not
-        // unrolled: the setup runs once per group, and straight-line code of this size would
-        // be fetched from L2 every time)
-        float* own2 = F2Pm + tid * RPM;
-        for (int a = 0; a < m; ++a) {
-            float v = 0.f;
-            if (live) {
-                const float dx = xr - X[NT + a], dy = yr - X[LDX + NT + a], dz = zr - X[2 * LDX + NT + a];
-                v = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
-            }
-            own2[a] = v;
-        }
-        for (int a = m; a < RPM; ++a) own2[a] = 0.f;  // entries past m are zero (read by the steps' dots)
-        // ---- Lp = chol(Theta_PP) and its reciprocal diagonal from the targets' Cholesky launch
-        {
-            const float* src = lp_ws + g * (long long)LP_SLOT;
-            const int tri = m * (m + 1) / 2;
-            for (int e = tid; e < tri; e += NT) {
-                int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-                while (i * (i + 1) / 2 > e) --i;
-                while ((i + 1) * (i + 2) / 2 <= e) ++i;
-                Lp[i * RPM + (e - i * (i + 1) / 2)] = src[e];
-            }
-            if (tid < m) rLp[tid] = src[LP_PACKED + tid];
-            if (tid == 0) {
-                const float f = src[LP_PACKED + RM];
-                if (f != 0.f) {
-                    record_error(st, f == 2.f ? SIC_ERR_NOT_PD : SIC_ERR_INVALID, g);
-                    s_fail = 1;
-                }
-            }
-        }
-        __syncthreads();
         if (s_fail) {
             if (tid == 0) sel_count[g] = 0;
             for (int q = tid; q < k; q += NT) sel_idx[g * k + q] = -1;
             __syncthreads();
             continue;
         }
-        // ---- F2P = Lp^-1 Theta_{P,r} (forward substitution in place on the own mirror row) and
-        // V2 = Theta_rr|P; then the row moves into registers
-        float V1 = live ? diag : NEG, V2 = live ? diag : NEG;
-        if (live) {
-            for (int a = 0; a < m; ++a) {
-                const float* la = Lp + a * RPM;
-                float s0 = own2[a], s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                int c = 0;
-                for (; c + 4 <= a; c += 4) {
-                    const float4 x4 = *reinterpret_cast<const float4*>(own2 + c);
-                    const float4 l4 = *reinterpret_cast<const float4*>(la + c);
-                    s0 = fmaf(-x4.x, l4.x, s0);
-                    s1 = fmaf(-x4.y, l4.y, s1);
-                    s2 = fmaf(-x4.z, l4.z, s2);
-                    s3 = fmaf(-x4.w, l4.w, s3);
-                }
-                for (; c < a; ++c) s0 = fmaf(-own2[c], la[c], s0);
-                const float u = ((s0 + s1) + (s2 + s3)) * rLp[a];
-                own2[a] = u;
-                V2 = fmaf(-u, u, V2);
-            }
-        }
+        // ---- the own row of F2P (k_agg_target_cols) into registers and the mirror, and
+        // V2 = Theta_rr|P = Theta_rr - |F2P row|^2 (downdated in the same order as the solve)
         float F2P[RM];
+        float V1 = live ? diag : NEG, V2 = live ? diag : NEG;
+        {
+            const float* src = f2p + (g0 - grp_ptr[0]) * NT + tid;
 #pragma unroll
-        for (int c = 0; c < RM / 4; ++c) {
-            const float4 x4 = *reinterpret_cast<const float4*>(own2 + 4 * c);
-            F2P[4 * c] = x4.x;
-            F2P[4 * c + 1] = x4.y;
-            F2P[4 * c + 2] = x4.z;
-            F2P[4 * c + 3] = x4.w;
+            for (int a = 0; a < RM; ++a) {
+                F2P[a] = 0.f;
+                if (live && a < m) F2P[a] = src[(long long)a * NT];
+            }
+#pragma unroll
+            for (int a = 0; a < RM; ++a)
+                if (live && a < m) V2 = fmaf(-F2P[a], F2P[a], V2);
+#pragma unroll
+            for (int c = 0; c < RM / 4; ++c)
+                *reinterpret_cast<float4*>(F2Pm + tid * RPM + 4 * c) =
+                    make_float4(F2P[4 * c], F2P[4 * c + 1], F2P[4 * c + 2], F2P[4 * c + 3]);
+            *reinterpret_cast<float4*>(F2Pm + tid * RPM + RM) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        __syncthreads();  // Lp is no longer read: F1m becomes the F1 mirror
-#pragma unroll
-        for (int c = 0; c < RP / 4; ++c)
-            *reinterpret_cast<float4*>(F1m + tid * RP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
         float F1[RK], F2S[RK];
 #pragma unroll
         for (int c = 0; c < RK; ++c) {
@@ -474,17 +515,23 @@ bool agg_reg_applies(sic_precision prec, int max_cand, int max_m, int k) {
     return prec == SIC_FP32_MIXED && max_cand <= RNT && max_m <= RM && k <= RK;
 }
 
-size_t agg_reg_workspace(long long n_grp) { return sizeof(float) * (size_t)LP_SLOT * (size_t)(n_grp > 0 ? n_grp : 1); }
+// the targets' factors (LP_SLOT floats per group), then the targets' columns of every
+// candidate row (at most n_grp * max_m positions of RNT rows)
+size_t agg_reg_workspace(long long n_grp, int max_m) {
+    const long long g = n_grp > 0 ? n_grp : 1;
+    return sizeof(float) * ((size_t)LP_SLOT * (size_t)g + (size_t)g * (size_t)max_m * RNT);
+}
 
 sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
                           const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx,
                           int max_cand, int max_m, int k, int32_t* sel_idx, int32_t* sel_count, double* gain, void* ws,
                           size_t ws_bytes, cudaStream_t s) {
-    if (!ws || ws_bytes < agg_reg_workspace(n_grp)) return SIC_ERR_INVALID;
+    if (!ws || ws_bytes < agg_reg_workspace(n_grp, max_m)) return SIC_ERR_INVALID;
     const KP<float> kpf = make_kp<float>(*kp);
+    float* lp = (float*)ws;
+    float* f2p = lp + (size_t)LP_SLOT * (size_t)(n_grp > 0 ? n_grp : 1);
     const int lgrid = persistent_grid(h, k_agg_target_chol, 32 * LP_WARPS, 0, (n_grp + LP_WARPS - 1) / LP_WARPS);
-    k_agg_target_chol<<<lgrid, 32 * LP_WARPS, 0, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp,
-                                                       (float*)ws);
+    k_agg_target_chol<<<lgrid, 32 * LP_WARPS, 0, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp, lp);
     // 128 threads (two groups per SM) when every list has at most 128 candidates, unless the
     // autotuner chose 256 for this bucket (each row's arithmetic is the same either way)
     int nt = max_cand <= 128 ? 128 : RNT;
@@ -492,13 +539,18 @@ sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const s
         tune_get(h, TUNE_SELECT_AGG, tune_select_key_a(k, SIC_FP32_MIXED), tune_select_key_b(max_cand, max_m), 0) ==
             RNT)
         nt = RNT;
+    auto cols = nt == 128 ? k_agg_target_cols<128> : k_agg_target_cols<RNT>;
+    SIC_CUDA_TRY(cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    const int cgrid = persistent_grid(h, cols, TC_ROWS, TC_SMEM, n_grp * (nt / TC_ROWS));
+    cols<<<cgrid, TC_ROWS, TC_SMEM, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp,
+                                          (const long long*)cand_ptr, cand_idx, lp, f2p, max_m);
     auto kern = nt == 128 ? k_select_agg_reg<128> : k_select_agg_reg<RNT>;
     const size_t smem = sizeof(float) * ((size_t)nt * RP * 2 + (size_t)nt * RPM + 3 * (size_t)(nt + RM));
     SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = persistent_grid(h, kern, nt, smem, n_grp > 0 ? n_grp : 1);
     kern<<<grid, nt, smem, s>>>(pts, n, kp->dim, kpf, (float)sic_floor_of(kp), (const long long*)grp_ptr, n_grp,
-                                (const long long*)cand_ptr, cand_idx, k, max_m, sel_idx, sel_count, (const float*)ws,
-                                gain, h->d_status);
+                                (const long long*)cand_ptr, cand_idx, k, max_m, sel_idx, sel_count, lp, f2p, gain,
+                                h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }

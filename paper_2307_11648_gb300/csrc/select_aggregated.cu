@@ -391,7 +391,7 @@ extern "C" sic_status sic_select_aggregated_workspace(sic_handle* h, int64_t n_g
     if (max_m > 64 || max_cand > 4096 || k > 128) return SIC_ERR_UNSUPPORTED;
     if (cudaSetDevice(h->device) != cudaSuccess) return SIC_ERR_CUDA;
     if (agg_reg_applies(prec, max_cand, max_m, k))
-        *bytes = agg_reg_workspace(n_grp);
+        *bytes = agg_reg_workspace(n_grp, max_m);
     else if (prec == SIC_FP64)
         *bytes = agg_plan<double>(h, n_grp, max_cand, max_m, k).ws_bytes;
     else if (prec == SIC_FP32_MIXED)

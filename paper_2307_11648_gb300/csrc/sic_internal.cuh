@@ -197,7 +197,7 @@ static inline int persistent_grid(const sic_handle* h, K kernel, int threads, si
 // register-resident FP32 supernodal selection (select_agg_reg.cu): used by
 // sic_select_aggregated when agg_reg_applies; its workspace holds the targets' factors
 bool agg_reg_applies(sic_precision prec, int max_cand, int max_m, int k);
-size_t agg_reg_workspace(long long n_grp);
+size_t agg_reg_workspace(long long n_grp, int max_m);
 sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
                           const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr, const int32_t* cand_idx,
                           int max_cand, int max_m, int k, int32_t* sel_idx, int32_t* sel_count, double* gain,
