@@ -209,15 +209,15 @@ __global__ void __launch_bounds__(32 * LP_WARPS) k_agg_target_chol(const double*
 }
 
 // The targets' columns F2P = Theta_{r,P} chol(Theta_PP)^-T of every candidate row r of every
-// group, FP32, for k_select_agg_reg: one thread per row, TC_ROWS rows per CTA and several CTAs
-// per SM, so that the per-row chains (m kernel entries, then a forward substitution of m steps)
-// of many groups are in flight together -- inside the selection kernel, with one group per SM,
+// group, FP32, for k_select_agg_reg: one thread per row, one group per CTA and two CTAs per
+// SM, so that the per-row chains (m kernel entries, then a forward substitution of m steps)
+// of several groups are in flight together -- inside the selection kernel, with one group per SM,
 // they left the SM waiting.  Same arithmetic, in the same order, as the selection kernel's own
 // staging would do.  Output: group g's entry (a, r) at f2p[(g0 - G0 + a) * NT + r], g0 =
 // grp_ptr[g], G0 = grp_ptr[0] (the groups are consecutive positions).  Rows of candidates that
 // are not valid, and groups whose targets' factor failed, are skipped (the selection kernel
 // reports them).
-constexpr int TC_ROWS = 128;
+constexpr int TC_ROWS = RNT;  // one CTA per group: the targets' factor is staged once
 constexpr size_t TC_SMEM = sizeof(float) * ((size_t)RM * RPM + RM + 3 * RM + (size_t)TC_ROWS * RPM);
 
 template <int NT>
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_agg_target_cols(const double* __res
     float* rLp = Lp + RM * RPM;       // [RM]
     float* XP = rLp + RM;             // [3][RM] the targets' coordinates
     float* rows = XP + 3 * RM;        // [TC_ROWS][RPM] the threads' rows
-    constexpr int CH = NT / TC_ROWS;  // row chunks per group
+    constexpr int CH = NT >= TC_ROWS ? NT / TC_ROWS : 1;  // row chunks per group
     const int tid = threadIdx.x;
     const long long G0 = grp_ptr[0];
     for (long long it = blockIdx.x; it < n_grp * CH; it += gridDim.x) {
@@ -271,9 +271,17 @@ __global__ void __launch_bounds__(TC_ROWS) k_agg_target_cols(const double* __res
                 const float yr = dim > 1 ? (float)(pts[p * dim + 1] - org[1]) : 0.f;
                 const float zr = dim > 2 ? (float)(pts[p * dim + 2] - org[2]) : 0.f;
                 float* own = rows + tid * RPM;
-                for (int a = 0; a < m; ++a) {
-                    const float dx = xr - XP[a], dy = yr - XP[RM + a], dz = zr - XP[2 * RM + a];
-                    own[a] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                for (int a0 = 0; a0 < m; a0 += 4) {  // four independent entries in flight
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int a = min(a0 + u, m - 1);
+                        const float dx = xr - XP[a], dy = yr - XP[RM + a], dz = zr - XP[2 * RM + a];
+                        v[u] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (a0 + u < m) own[a0 + u] = v[u];
                 }
                 float* out = f2p + (g0 - G0) * NT + r;
                 for (int a = 0; a < m; ++a) {
@@ -541,7 +549,7 @@ sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const s
         nt = RNT;
     auto cols = nt == 128 ? k_agg_target_cols<128> : k_agg_target_cols<RNT>;
     SIC_CUDA_TRY(cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    const int cgrid = persistent_grid(h, cols, TC_ROWS, TC_SMEM, n_grp * (nt / TC_ROWS));
+    const int cgrid = persistent_grid(h, cols, TC_ROWS, TC_SMEM, n_grp * (nt >= TC_ROWS ? nt / TC_ROWS : 1));
     cols<<<cgrid, TC_ROWS, TC_SMEM, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp,
                                           (const long long*)cand_ptr, cand_idx, lp, f2p, max_m);
     auto kern = nt == 128 ? k_select_agg_reg<128> : k_select_agg_reg<RNT>;
