@@ -11,10 +11,9 @@
 // since U = J G J (J the reversal), member a's column is J G^{-T} e_j = d_j^{-1/2} J L^{-T} e_j
 // with j = n-1-a: one back substitution per member, one member per half-warp, the
 // right-hand side in registers.  v_a = G_jj^2 = d_j, so logv = log d_j (eq. inverse_cond).  Rows are written diagonal first, then
-// ascending, to the caller's CSC arrays.  Theta entries use the double-float Matern of
-// dfloat.cuh on the FP32 pipe (one FP64 addition per entry): this GPU retires about one FP64
-// warp instruction per 80 clocks per SM sub-partition, so FP64 instructions are spent on the
-// factorisation.
+// ascending, to the caller's CSC arrays.  Theta entries use the FP64 Matern of
+// matern_d2_fast (table-driven exp, Newton sqrt): this GPU issues two FP64 FMAs per
+// clock per SM, so FP64 instructions are spent sparingly.
 //
 // Also here: the nnz count + exclusive scan that builds col_ptr, and the fixed-order
 // two-pass sum of logv (bit-reproducible).
@@ -169,19 +168,14 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
     double* rG = G + (long long)nmax * (nmax + 1) / 2;      // 1 / G_jj
     double* cj = rG + nmax;                                 // the current column of L
     double* cu = cj + nmax;                                 // the same column before scaling by 1/d_j
-    // coordinates relative to the unit's first member as double-floats: high parts [3][nmax],
-    // then low parts [3][nmax] (the space of 3 x nmax doubles)
-    float* xh = reinterpret_cast<float*>(cu + nmax);
-    float* xl = xh + 3 * nmax;
-    float* tab_hi = xl + 3 * nmax;                          // s2 2^(j/256) as double-floats
-    float* tab_lo = tab_hi + DF_EXP_TAB;                    // (the space of EXP_TAB doubles)
-    int* pos = reinterpret_cast<int*>(tab_lo + DF_EXP_TAB); // nmax
+    double* xyz = cu + nmax;                                // 3 x nmax
+    double* tab = xyz + 3 * nmax;                           // 2^(j/256) (exp_neg_table)
+    int* pos = reinterpret_cast<int*>(tab + EXP_TAB);       // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool worker = tid < FILL_NT;  // the pivot warp joins only the barriers and the pivots
-    const DfMatern dfk = df_matern_params(kp);
-    df_exp_table_fill(tab_hi, tab_lo, kp.s2);
+    exp_table_fill(tab, kp.s2);
 
     for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         const long long g0 = grp_ptr ? grp_ptr[u] : col0 + u;
@@ -214,26 +208,29 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
             if (tid == 0) record_error(st, SIC_ERR_INVALID, u);
             continue;
         }
-        // R order: picks descending, then members descending; coordinates relative to the first
-        // member (differences in FP64, then split into double-floats: per point, not per entry)
+        // R order: picks descending, then members descending
         for (int i = worker ? tid : nn; i < nn; i += FILL_NT) {
             const int p = (i < cnt) ? srt[cnt - 1 - i] : (int)(g0 + m - 1 - (i - cnt));
             pos[i] = p;
-            for (int d = 0; d < 3; ++d) {
-                const dfl c = df_from_double((d < dim) ? pts[(long long)p * dim + d] - pts[g0 * dim + d] : 0.0);
-                xh[d * nmax + i] = c.hi;
-                xl[d * nmax + i] = c.lo;
-            }
+            for (int d = 0; d < 3; ++d) xyz[d * nmax + i] = (d < dim) ? pts[(long long)p * dim + d] : 0.0;
         }
         if (tid == 0) s_bad = 0;
         __syncthreads();
-        // Theta_RR, packed lower, one flat entry per thread, by the double-float Matern on the
-        // FP32 pipe (one FP64 addition per entry; the FP64 pipe is left to the factorisation)
+        // Theta_RR, packed lower, one flat entry per thread, in FP64 (the double-float Matern of
+        // dfloat.cuh would leave the FP64 pipe to the factorisation, but its ~1e-14 of the
+        // variance per entry is amplified by 1/v in the Schur complements, v ~ 2 nugget on the
+        // finest groups: factor columns then miss the oracle's by more than 1e-8)
         const int tri = nn * (nn + 1) / 2;
         for (int e = worker ? tid : tri; e < tri; e += FILL_NT) {
             const int i = pk_row(e);
             const int j = e - i * (i + 1) / 2;
-            double v = matern_df(dfk, xh, xl, i, j, nmax, dim, tab_hi, tab_lo);
+            const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j];
+            double d2 = fma(dy, dy, dx * dx);
+            if (dim == 3) {
+                const double dz = xyz[2 * nmax + i] - xyz[2 * nmax + j];
+                d2 = fma(dz, dz, d2);
+            }
+            double v = matern_d2_fast(kp, d2, tab);
             if (i == j) v += kp.nugget;
             G[e] = v;
         }
