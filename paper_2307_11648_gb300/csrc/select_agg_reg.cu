@@ -209,28 +209,29 @@ __global__ void __launch_bounds__(32 * LP_WARPS) k_agg_target_chol(const double*
 }
 
 // The targets' columns F2P = Theta_{r,P} chol(Theta_PP)^-T of every candidate row r of every
-// group, FP32, for k_select_agg_reg: one thread per row (the row in registers), one group per
-// CTA and two CTAs per SM, so that the per-row chains (m kernel entries, then a forward
-// substitution of m steps) of several groups are in flight together -- inside the selection
-// kernel, with one group per SM, they left the SM waiting.  The same arithmetic in the same
-// order as a forward substitution inside the selection kernel.  Output: group g's entry (a, r) at f2p[(g0 - G0 + a) * NT + r], g0 =
+// group, FP32, for k_select_agg_reg: one thread per row, one group per CTA and two CTAs per
+// SM, so that the per-row chains (m kernel entries, then a forward substitution of m steps)
+// of several groups are in flight together -- inside the selection kernel, with one group per SM,
+// they left the SM waiting.  Same arithmetic, in the same order, as the selection kernel's own
+// staging would do.  Output: group g's entry (a, r) at f2p[(g0 - G0 + a) * NT + r], g0 =
 // grp_ptr[g], G0 = grp_ptr[0] (the groups are consecutive positions).  Rows of candidates that
 // are not valid, and groups whose targets' factor failed, are skipped (the selection kernel
 // reports them).
 constexpr int TC_ROWS = RNT;  // one CTA per group: the targets' factor is staged once
-constexpr size_t TC_SMEM = sizeof(float) * ((size_t)RM * RPM + RM + 3 * RM);
+constexpr size_t TC_SMEM = sizeof(float) * ((size_t)RM * RPM + RM + 3 * RM + (size_t)TC_ROWS * RPM);
 
 template <int NT>
-__global__ void __launch_bounds__(TC_ROWS, 2) k_agg_target_cols(const double* __restrict__ pts, long long n, int dim,
-                                                                 KP<float> kp, const long long* __restrict__ grp_ptr,
-                                                                 long long n_grp, const long long* __restrict__ cand_ptr,
-                                                                 const int32_t* __restrict__ cand_idx,
-                                                                 const float* __restrict__ lp_ws, float* __restrict__ f2p,
-                                                                 int max_m) {
+__global__ void __launch_bounds__(TC_ROWS) k_agg_target_cols(const double* __restrict__ pts, long long n, int dim,
+                                                              KP<float> kp, const long long* __restrict__ grp_ptr,
+                                                              long long n_grp, const long long* __restrict__ cand_ptr,
+                                                              const int32_t* __restrict__ cand_idx,
+                                                              const float* __restrict__ lp_ws, float* __restrict__ f2p,
+                                                              int max_m) {
     extern __shared__ __align__(16) float smc[];
     float* Lp = smc;                  // [RM][RPM]
     float* rLp = Lp + RM * RPM;       // [RM]
     float* XP = rLp + RM;             // [3][RM] the targets' coordinates
+    float* rows = XP + 3 * RM;        // [TC_ROWS][RPM] the threads' rows
     constexpr int CH = NT >= TC_ROWS ? NT / TC_ROWS : 1;  // row chunks per group
     const int tid = threadIdx.x;
     const long long G0 = grp_ptr[0];
@@ -269,35 +270,36 @@ __global__ void __launch_bounds__(TC_ROWS, 2) k_agg_target_cols(const double* __
                 const float xr = (float)(pts[p * dim] - org[0]);
                 const float yr = dim > 1 ? (float)(pts[p * dim + 1] - org[1]) : 0.f;
                 const float zr = dim > 2 ? (float)(pts[p * dim + 2] - org[2]) : 0.f;
-                // the row in registers (static indices; entries from m on stay zero)
-                float x[RM];
+                float* own = rows + tid * RPM;
+                for (int a0 = 0; a0 < m; a0 += 4) {  // four independent entries in flight
+                    float v[4];
 #pragma unroll
-                for (int a = 0; a < RM; ++a) {
-                    x[a] = 0.f;
-                    if (a < m) {
+                    for (int u = 0; u < 4; ++u) {
+                        const int a = min(a0 + u, m - 1);
                         const float dx = xr - XP[a], dy = yr - XP[RM + a], dz = zr - XP[2 * RM + a];
-                        x[a] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                        v[u] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
                     }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (a0 + u < m) own[a0 + u] = v[u];
                 }
                 float* out = f2p + (g0 - G0) * NT + r;
-#pragma unroll
-                for (int a = 0; a < RM; ++a) {
-                    if (a < m) {
-                        const float* la = Lp + a * RPM;
-                        float s0 = x[a], s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-                        for (int c = 0; c + 4 <= a; c += 4) {
-                            const float4 l4 = *reinterpret_cast<const float4*>(la + c);
-                            s0 = fmaf(-x[c], l4.x, s0);
-                            s1 = fmaf(-x[c + 1], l4.y, s1);
-                            s2 = fmaf(-x[c + 2], l4.z, s2);
-                            s3 = fmaf(-x[c + 3], l4.w, s3);
-                        }
-#pragma unroll
-                        for (int c = a & ~3; c < a; ++c) s0 = fmaf(-x[c], la[c], s0);
-                        x[a] = ((s0 + s1) + (s2 + s3)) * rLp[a];
-                        out[(long long)a * NT] = x[a];
+                for (int a = 0; a < m; ++a) {
+                    const float* la = Lp + a * RPM;
+                    float s0 = own[a], s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                    int c = 0;
+                    for (; c + 4 <= a; c += 4) {
+                        const float4 x4 = *reinterpret_cast<const float4*>(own + c);
+                        const float4 l4 = *reinterpret_cast<const float4*>(la + c);
+                        s0 = fmaf(-x4.x, l4.x, s0);
+                        s1 = fmaf(-x4.y, l4.y, s1);
+                        s2 = fmaf(-x4.z, l4.z, s2);
+                        s3 = fmaf(-x4.w, l4.w, s3);
                     }
+                    for (; c < a; ++c) s0 = fmaf(-own[c], la[c], s0);
+                    const float u = ((s0 + s1) + (s2 + s3)) * rLp[a];
+                    own[a] = u;
+                    out[(long long)a * NT] = u;
                 }
             }
         }
