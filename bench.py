@@ -377,10 +377,11 @@ def truncated(hp, top):
     return pipeline.HostProblem(hp.pts, hp.kp, hp.k, ptr, idx, hp.grp_ptr, hp.order, hp.ell2)
 
 
-def pcg_comparison(h, cfg, params, n, nrhs=8, shift=1e-4, tol=1e-8):
+def pcg_comparison(h, cfg, params, n, nrhs=8, shift=1e-4, tol=1e-8, caps=None):
     """Config-5 style comparison: CG on (Theta + shift I) x = b, b ~ N(0, 1), with the factors of
     that matrix from the learned proposal, plain greedy and k nearest neighbours (first k
-    candidates) as preconditioners, and without; FP32-entry matvec with compensated sums."""
+    candidates) as preconditioners, and without; FP32-entry matvec with compensated sums.
+    caps: iteration cap per preconditioner ("learned", "conditional", "knn", "none"); 0 skips it."""
     import torch
 
     from paper_2307_11648_gb300 import learned, pipeline, sic
@@ -404,13 +405,17 @@ def pcg_comparison(h, cfg, params, n, nrhs=8, shift=1e-4, tol=1e-8):
         nnz = int(fb.col_ptr[-1].item())
         return (fb.col_ptr, fb.row_idx[:nnz].contiguous(), fb.val[:nnz].contiguous())
 
-    lb = learned.LearnedFactorBuilder(h, hp, learned.Proposal(h, params, top=4 * cfg["k"]), sic.SIC_FP32_MIXED)
-    lb.run(dp)
-    out["learned"] = solve(csc(lb.fb), 1000)
-    del lb
+    caps = dict({"learned": 1000, "conditional": 1000, "knn": 1000, "none": 300}, **(caps or {}))
+    out["caps"] = caps
+    if caps["learned"]:
+        lb = learned.LearnedFactorBuilder(h, hp, learned.Proposal(h, params, top=4 * cfg["k"]), sic.SIC_FP32_MIXED)
+        lb.run(dp)
+        out["learned"] = solve(csc(lb.fb), caps["learned"])
+        del lb
     fb = pipeline.FactorBuilder(h, hp, sic.SIC_FP32_MIXED)
     fb.run(dp)
-    out["conditional"] = solve(csc(fb), 1000)
+    if caps["conditional"]:
+        out["conditional"] = solve(csc(fb), caps["conditional"])
     U, k = hp.n_units, hp.k
     sel = np.full((U, k), -1, np.int32)
     cnt = np.zeros(U, np.int32)
@@ -421,9 +426,11 @@ def pcg_comparison(h, cfg, params, n, nrhs=8, shift=1e-4, tol=1e-8):
     fb.sel_idx.copy_(torch.from_numpy(sel.ravel()))
     fb.sel_count.copy_(torch.from_numpy(cnt))
     fb.fill(dp)
-    out["knn"] = solve(csc(fb), 1000)
-    out["none"] = solve(None, 300)
-    out["legend"] = "[iterations per right-hand side, max final relative residual, wall ms]; 'none' capped at 300"
+    if caps["knn"]:
+        out["knn"] = solve(csc(fb), caps["knn"])
+    if caps["none"]:
+        out["none"] = solve(None, caps["none"])
+    out["legend"] = "[iterations per right-hand side, max final relative residual, wall ms]; capped at 'caps'"
     return out
 
 
@@ -605,6 +612,13 @@ def main():
     ap.add_argument("--case-mlp", action="store_true",
                     help="with --case-only: run the proposal (untrained network) and select on its top 256")
     ap.add_argument("--pcg-n", type=int, default=1 << 16, help="points of the preconditioning comparison (0: skip)")
+    ap.add_argument("--pcg-only", type=int, default=0, metavar="N",
+                    help="only the preconditioning comparison at N points (trained proposal), one JSON line")
+    ap.add_argument("--pcg-caps", default="",
+                    help="iteration caps, e.g. learned=1000,conditional=1000,knn=60,none=0 (0 skips)")
+    ap.add_argument("--pcg-nrhs", type=int, default=8)
+    ap.add_argument("--pcg-untrained", action="store_true",
+                    help="with --pcg-only: the untrained network (a profiling case)")
     ap.add_argument("--case-global", action="store_true",
                     help="with --case-only: the learned step with a budget of 48 picks per supernode on average, "
                          "decreases from the FP64 side state, global allocation")
@@ -662,6 +676,23 @@ def main():
         h.sync()
         print(json.dumps({"case": args.case_only, "columns": shp.n, "sum_logv": float(fb.sum_logv.cpu()[0]),
                           "apply_sums": sums}))
+        return
+    if args.pcg_only:
+        h = sic.Handle(local)
+        if args.pcg_untrained:
+            params = learned.init_params(0)
+        else:
+            train_probs = [problem(cfg, 1000 + i, args.train_n) for i in (1, 2)]
+            feat, label, _ = learned.training_set(h, train_probs)
+            params, _ = learned.train(h, feat, label, epochs=args.epochs, batch=65536, lr=2e-3, seed=0)
+            del feat, label, train_probs
+            torch.cuda.empty_cache()
+        caps = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.pcg_caps.split(",") if kv}
+        p5 = synthetic.PRESETS["cfg5_pcg"]
+        res = pcg_comparison(h, cfg, params, args.pcg_only, nrhs=args.pcg_nrhs, shift=p5["shift"], tol=p5["tol"],
+                             caps=caps)
+        res["trained"] = not args.pcg_untrained
+        print(json.dumps({"pcg": res}))
         return
     if args.case_only and args.case_partial:
         h = sic.Handle(local)
