@@ -54,15 +54,6 @@ __device__ __forceinline__ dfl df_from_double(double x) {
     return {hi, __double2float_rn(x - (double)hi)};
 }
 
-// A float as the FP64 number of the same value, by its bit pattern (integer operations only;
-// zero for zero and subnormal inputs, below 1.2e-38)
-__device__ __forceinline__ double f32_as_f64(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-    return e ? __hiloint2double((int)hi, (int)(u << 29)) : 0.0;
-}
-
 // hi + lo in FP64: exact (the two parts' 48 bits fit in 53), one FP64 addition
 __device__ __forceinline__ double df_to_double(dfl x) { return f32_as_f64(x.hi) + f32_as_f64(x.lo); }
 

@@ -6,14 +6,17 @@
 // s = (P_0..P_{m-1}, S sorted), the factor block is L = U^{-T} where U U^T =
 // Theta_{s,s}, U upper triangular.  The CTA forms Theta on the reversed order
 // R = reverse(s) in packed lower storage in shared memory (one entry per thread), factors
-// it Theta_{RR} = L D L^T = G G^T with G = L D^{1/2} (right-looking, the trailing update
-// flat over the threads; one thread takes each pivot's reciprocal; no square roots), and
-// since U = J G J (J the reversal), member a's column is J G^{-T} e_j = d_j^{-1/2} J L^{-T} e_j
-// with j = n-1-a: one back substitution per member, one member per half-warp, the
-// right-hand side in registers.  v_a = G_jj^2 = d_j, so logv = log d_j (eq. inverse_cond).  Rows are written diagonal first, then
-// ascending, to the caller's CSC arrays.  Theta entries use the FP64 Matern of
-// matern_d2_fast (table-driven exp, Newton sqrt): this GPU issues two FP64 FMAs per
-// clock per SM, so FP64 instructions are spent sparingly.
+// it Theta_{RR} = L D L^T = G G^T with G = L D^{1/2} (blocked right-looking: panels of
+// FILL_B columns in FP64, each panel's update of the trailing matrix as exact integer dot
+// products of fixed-point G rows, one FP64 rounding per entry and panel; one thread takes
+// each pivot's reciprocal square root), and since U = J G J (J the reversal), member a's
+// column is J G^{-T} e_j = d_j^{-1/2} J L^{-T} e_j with j = n-1-a: one back substitution per
+// member, one member per half-warp, the right-hand side in registers.  v_a = G_jj^2 = d_j,
+// so logv = log d_j (eq. inverse_cond).  Rows are written diagonal first, then ascending, to
+// the caller's CSC arrays.  Theta entries use the FP64 Matern of matern_d2_fast
+// (table-driven exp and Newton square root, each with its non-critical steps in
+// double-float on the FP32 pipe): this GPU issues two FP64 FMAs per clock per SM, so FP64
+// instructions are spent sparingly.
 //
 // Also here: the nnz count + exclusive scan that builds col_ptr, and the fixed-order
 // two-pass sum of logv (bit-reproducible).
@@ -113,6 +116,13 @@ __global__ void k_scan_add(long long* __restrict__ v, long long n, const long lo
 // warps in flight where fewer CTAs fit per SM); lane 0 of one more warp takes the pivots
 constexpr int FILL_HSLOTS = 12;  // right-hand-side entries per half-warp lane: nn <= 192 = 16 * FILL_HSLOTS
 constexpr int FILL_M_SPLIT = 32;  // groups of at most this size run in their own launch
+constexpr int FILL_B = 4;         // panel width of the blocked LDL^T (integer trailing update)
+
+// doubles of the scratch region: the points' coordinates while Theta is formed, then the
+// panel's rows in fixed point ((2 FILL_B + 1) ints per row)
+__host__ __device__ constexpr int fill_scratch_doubles(int nmax) {
+    return 3 * nmax > ((2 * FILL_B + 1) * nmax + 1) / 2 ? 3 * nmax : ((2 * FILL_B + 1) * nmax + 1) / 2;
+}
 
 // Packed lower-triangle index (nn <= 192, so every index fits in 32 bits; 32-bit integer
 // arithmetic and int-to-float conversions stay off the FP64 pipe).
@@ -127,33 +137,116 @@ __device__ __forceinline__ int pk_row(int e) {
 }
 
 // Pivot of column c of the LDL^T factorisation from its final Schur complement v: D_cc = v
-// (kept on the diagonal) and 1 / v (an FP32 reciprocal seed refined by two Newton steps:
-// relative error 2^-23 -> 2^-46 -> ~2^-92, four FP64 operations); a non-positive pivot
-// raises *bad.  The range test reads the bits (no FP64 compare).
-__device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* rG, int* bad) {
+// (kept on the diagonal), d^(-1/2) by rsqrt_newton and 1/d as its square (six FP64 operations
+// with the diagonal's update), into the two-column ring piv = {1/d, 1/d, d^-1/2, d^-1/2}
+// (slot c & 1).  A non-positive pivot raises *bad.  The range test reads the bits (no FP64
+// compare).
+__device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* piv, int* bad) {
     const long long vb = __double_as_longlong(v);
     if (vb <= 0 || vb >= 0x7ff0000000000000LL) {  // not in (+0, +inf): non-positive, infinite or NaN
         *bad = 1;
         return;
     }
-    double r;
-    const unsigned hi = (unsigned)__double2hiint(v);
-    if (hi < 0x38700000u || hi >= 0x47700000u) {
-        r = 1.0 / v;
-    } else {
-        float y;
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__uint_as_float((hi << 3) - (896u << 23))));
-        const unsigned yb = __float_as_uint(y);
-        r = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
-        r = fma(r, fma(-v, r, 1.0), r);
-        r = fma(r, fma(-v, r, 1.0), r);
-    }
+    const double rs = rsqrt_newton(v);
     G[pk(c, c)] = v;
-    rG[c] = r;
+    piv[c & 1] = rs * rs;
+    piv[2 + (c & 1)] = rs;
 }
 
+// ---- the exact integer update of a panel ----
+//
+// A row of a panel, its FILL_B values g_j (entries of G = L D^(1/2)), is held in fixed point:
+// g_j = M_j 2^(E - 1075) with E the largest biased exponent among them and M_j the 53-bit
+// significands shifted to E and truncated (signed; zero and subnormal values count as 0), split
+// as M_j = Mh_j 2^26 + Ml_j (Mh signed, 0 <= Ml < 2^26).  Layout (ints, leading dimension ld):
+// Mh_j at fx[j ld + row], Ml_j at fx[(B + j) ld + row], E at fx[2 B ld + row].
+// The dot product of two rows, sum_j M_ij M_lj = 2^52 sum Mh Mh + 2^26 sum (Mh Ml + Ml Mh)
+// + sum Ml Ml, is exact in three 64-bit sums of 32 x 32-bit products (|terms| < 2^54, B <= 8),
+// combined in 128 bits and rounded once to FP64.  Truncating to the row's exponent costs each
+// value at most 2^-52 of the row's largest: with G's rows (|G_ij| <= sqrt(A_ii)) the error of an
+// entry's update stays within B 2^-52 sqrt(A_ii A_ll), the order of the FP64 Cholesky's own
+// backward error bound.
+template <int B>
+__device__ __forceinline__ void fx_row_store(const double (&g)[B], int* __restrict__ fx, int ld, int row) {
+    int e[B];
+    int E = 0;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        e[j] = (__double2hiint(g[j]) >> 20) & 0x7ff;
+        E = max(E, e[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        const long long u = __double_as_longlong(g[j]);
+        long long m = e[j] ? ((u & 0xfffffffffffffLL) | 0x10000000000000LL) : 0LL;
+        const int sh = E - e[j];
+        m = sh < 63 ? (m >> sh) : 0LL;
+        if (u < 0) m = -m;
+        fx[j * ld + row] = (int)(m >> 26);
+        fx[(B + j) * ld + row] = (int)(m & 0x3ffffffLL);
+    }
+    fx[2 * B * ld + row] = E;
+}
+
+// S = a2 2^52 + a1 2^26 + a0 (a0 >= 0), times 2^(ex - 2150), rounded once to FP64 (to nearest,
+// ties away from zero); 0 below FP64's normal range.  Integer operations only.
+__device__ __forceinline__ double fx_to_double(long long a2, long long a1, long long a0, int ex) {
+    unsigned long long lo = (unsigned long long)a2 << 52;
+    long long hi = a2 >> 12;
+    const unsigned long long t1 = (unsigned long long)a1 << 26;
+    lo += t1;
+    hi += (a1 >> 38) + (lo < t1 ? 1 : 0);
+    const unsigned long long t0 = (unsigned long long)a0;
+    lo += t0;
+    hi += lo < t0 ? 1 : 0;
+    const bool neg = hi < 0;
+    if (neg) {
+        lo = ~lo + 1ULL;
+        hi = ~hi + (lo == 0ULL ? 1 : 0);
+    }
+    const unsigned long long uh = (unsigned long long)hi;
+    if ((uh | lo) == 0ULL) return 0.0;
+    int p;                   // position of the leading bit of |S|
+    unsigned long long mt;   // its leading 54 bits
+    if (uh) {
+        p = 127 - __clzll((long long)uh);
+        const int sft = p - 53;  // >= 11
+        mt = sft >= 64 ? (uh >> (sft - 64)) : ((uh << (64 - sft)) | (lo >> sft));
+    } else {
+        p = 63 - __clzll((long long)lo);
+        mt = p >= 53 ? (lo >> (p - 53)) : (lo << (53 - p));
+    }
+    mt = (mt + 1ULL) >> 1;  // 53 bits, rounded
+    if (mt >> 53) {
+        mt >>= 1;
+        ++p;
+    }
+    const int be = ex + p - 1127;  // |S| 2^(ex - 2150) = (mt 2^-52) 2^(p + ex - 2150)
+    if (be <= 0) return 0.0;
+    return __longlong_as_double((long long)(((neg ? 1ULL : 0ULL) << 63) | ((unsigned long long)be << 52) |
+                                            (mt & 0xfffffffffffffULL)));
+}
+
+template <int B>
+__device__ __forceinline__ double fx_dot(const int* __restrict__ fx, int ld, int i, int l) {
+    long long a2 = 0, a1 = 0, a0 = 0;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        const int hi_ = fx[j * ld + i], li = fx[(B + j) * ld + i];
+        const int hl = fx[j * ld + l], ll = fx[(B + j) * ld + l];
+        a2 += (long long)hi_ * hl;
+        a1 += (long long)hi_ * ll + (long long)li * hl;
+        a0 += (long long)li * ll;
+    }
+    return fx_to_double(a2, a1, a0, fx[2 * B * ld + i] + fx[2 * B * ld + l]);
+}
+
+// CTAs per SM the register budget is set for (shared memory allows about this many at the
+// largest group of each launch)
+constexpr int fill_min_ctas(int nt) { return nt == 128 ? 5 : (nt == 256 ? 3 : 2); }
+
 template <int FILL_NT>
-__global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
+__global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(const double* __restrict__ pts, int dim, KP<double> kp,
                                                   const long long* __restrict__ grp_ptr, long long n_units,
                                                   const int32_t* __restrict__ sel_idx,
                                                   const int32_t* __restrict__ sel_count, int k, int max_m,
@@ -165,12 +258,13 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
     extern __shared__ double smem_d[];
     const int nmax = k + m_hi;  // shared memory is laid out for this launch's size class
     double* G = smem_d;                                     // packed lower, nmax(nmax+1)/2
-    double* rG = G + (long long)nmax * (nmax + 1) / 2;      // 1 / G_jj
-    double* cj = rG + nmax;                                 // the current column of L
-    double* cu = cj + nmax;                                 // the same column before scaling by 1/d_j
-    double* xyz = cu + nmax;                                // 3 x nmax
-    double* tab = xyz + 3 * nmax;                           // 2^(j/256) (exp_neg_table)
-    int* pos = reinterpret_cast<int*>(tab + EXP_TAB);       // nmax
+    double* piv = G + (long long)nmax * (nmax + 1) / 2;     // 1/d and d^(-1/2) of two columns (ring)
+    double* cj = piv + 4;                                   // the current column of L
+    double* cu = cj + nmax;                                 // the panel's columns of U at the current column
+    double* tab = cu + FILL_B;                              // 2^(j/256) (exp_neg_table)
+    double* xyz = tab + EXP_TAB;                            // 3 x nmax, while Theta is formed; then
+    int* fx = reinterpret_cast<int*>(xyz);                  // the panel's rows in fixed point, (2 FILL_B + 1) x nmax
+    int* pos = reinterpret_cast<int*>(xyz + fill_scratch_doubles(nmax));  // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -188,6 +282,10 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
         }
         if (m < m_lo || m > m_hi) continue;  // another launch's size class
         const int nn = cnt + m;
+        if (nn > FILL_NT) {  // excluded by the launcher (FILL_NT >= k + m_hi)
+            if (tid == 0) record_error(st, SIC_ERR_UNSUPPORTED, u);
+            continue;
+        }
         // picks sorted ascending by rank; they must be distinct positions after the unit,
         // and col_ptr must match the pattern
         bool bad = false;
@@ -235,42 +333,88 @@ __global__ void __launch_bounds__(FILL_NT + 32) k_fill(const double* __restrict_
             G[e] = v;
         }
         __syncthreads();
-        // right-looking LDL^T factorisation Theta_RR = L D L^T in place on the packed lower
-        // triangle (no square roots: G = L D^{1/2} is never formed): for column j, d_j = A_jj,
-        // L_ij = A_ij / d_j, then A_il -= L_ij A_lj over the trailing triangle j < l <= i with
-        // one flat entry per worker thread.  The FP64 units are per SM sub-partition and charge
-        // a warp instruction whatever its active lanes, so the flat update keeps the worker
-        // warps equally loaded with full warps.  The next pivot (its diagonal update and
-        // reciprocal, a chain of dependent FP64 operations) is taken by the pivot warp while
-        // the workers update the rest.
-        if (tid == FILL_NT) fill_pivot(G[0], 0, G, rG, &s_bad);
+        // blocked right-looking LDL^T factorisation Theta_RR = L D L^T in place on the packed
+        // lower triangle, in panels of FILL_B columns.  Within a panel, column by column in FP64:
+        // d_j = A_jj, L_ij = A_ij / d_j, and the panel's later columns are updated
+        // (A_il -= L_ij A_lj, flat over the worker threads).  The rows below the panel keep
+        // G_ij = A_ij d_j^(-1/2) (G = L D^(1/2)) in registers and, once the panel is complete, in
+        // fixed point; the trailing matrix then takes the panel's whole rank-FILL_B update as one
+        // exact integer dot product of two G rows per entry, rounded once and subtracted in FP64
+        // (fx_dot): FILL_B FP64 FMAs become one FP64 addition, the products going to the integer
+        // multiply-add units.  The FP64 units are per SM sub-partition and charge a warp
+        // instruction whatever its active lanes, so the flat loops keep full warps.  The next
+        // pivot (its diagonal update, reciprocal and reciprocal square root, a chain of
+        // dependent FP64 operations) is taken by the pivot warp while the workers update the
+        // rest.
+        constexpr int SLOTS = 1;  // rows per worker thread: nn <= FILL_NT (the launcher's choice)
+        double gv[SLOTS][FILL_B];  // G_ij of the thread's rows below the panel (row tid + sl FILL_NT)
+        if (tid == FILL_NT) fill_pivot(G[0], 0, G, piv, &s_bad);
         __syncthreads();
-        for (int j = 0; j < nn; ++j) {
-            if (s_bad) break;
-            const double rd = rG[j];
-            for (int i = worker ? j + 1 + tid : nn; i < nn; i += FILL_NT) {
-                const int a = pk(i, j);
-                const double uv = G[a];
-                const double l = uv * rd;
-                G[a] = l;
-                cj[i] = l;
-                cu[i] = uv;
-            }
-            __syncthreads();
-            const int nt = nn - 1 - j;
-            const int T = nt * (nt + 1) / 2;
-            if (worker) {
-                for (int e = tid + 1; e < T; e += FILL_NT) {  // entry 0, A_{j+1,j+1}, is the pivot warp's
-                    const int ii = pk_row(e);
-                    const int i = ii + j + 1, l = e - ii * (ii + 1) / 2 + j + 1;
-                    const int a = pk(i, l);
-                    G[a] = fma(-cj[i], cu[l], G[a]);
+        for (int J = 0; J < nn && !s_bad; J += FILL_B) {
+            const int je = min(J + FILL_B, nn);
+#pragma unroll
+            for (int jj = 0; jj < FILL_B; ++jj) {
+                const int j = J + jj;
+                if (j >= je || s_bad) break;  // uniform: s_bad is read after a barrier
+                const double rd = piv[j & 1], rsd = piv[2 + (j & 1)];
+                if (worker) {
+#pragma unroll
+                    for (int sl = 0; sl < SLOTS; ++sl) {
+                        const int i = tid + sl * FILL_NT;
+                        if (i > j && i < nn) {
+                            const int a = pk(i, j);
+                            const double uv = G[a];
+                            const double l = uv * rd;
+                            G[a] = l;
+                            cj[i] = l;
+                            if (i < je) cu[i - J] = uv;
+                            else gv[sl][jj] = uv * rsd;
+                        }
+                    }
+                    if (j == je - 1) {  // the panel is complete: its rows below go to fixed point
+#pragma unroll
+                        for (int sl = 0; sl < SLOTS; ++sl) {
+                            const int i = tid + sl * FILL_NT;
+                            if (i >= je && i < nn) fx_row_store<FILL_B>(gv[sl], fx, nmax, i);
+                        }
+                    }
                 }
-            } else if (tid == FILL_NT && nt > 0) {
-                const int a = pk(j + 1, j + 1);
-                fill_pivot(fma(-cj[j + 1], cu[j + 1], G[a]), j + 1, G, rG, &s_bad);
+                __syncthreads();
+                if (j < je - 1) {
+                    // the panel's later columns lc: rows i >= lc (entry (j+1, j+1) is the pivot warp's)
+                    if (worker) {
+                        for (int lc = j + 1; lc < je; ++lc) {
+                            const double ul = cu[lc - J];
+                            for (int i = lc + (lc == j + 1) + tid; i < nn; i += FILL_NT) {
+                                const int a = pk(i, lc);
+                                G[a] = fma(-cj[i], ul, G[a]);
+                            }
+                        }
+                    } else if (tid == FILL_NT) {
+                        const int a = pk(j + 1, j + 1);
+                        fill_pivot(fma(-cj[j + 1], cu[j + 1 - J], G[a]), j + 1, G, piv, &s_bad);
+                    }
+                    __syncthreads();
+                }
             }
-            __syncthreads();
+            // the trailing matrix, entries (i, l) with je <= l <= i < nn, takes the panel's update;
+            // entry (je, je) and the next pivot are the pivot warp's.  je < nn implies a full panel.
+            if (je < nn && !s_bad) {
+                const int nt = nn - je;
+                const int T = nt * (nt + 1) / 2;
+                if (worker) {
+                    for (int e = tid + 1; e < T; e += FILL_NT) {
+                        const int ii = pk_row(e);
+                        const int i = je + ii, l = je + e - ii * (ii + 1) / 2;
+                        const int a = pk(i, l);
+                        G[a] -= fx_dot<FILL_B>(fx, nmax, i, l);
+                    }
+                } else if (tid == FILL_NT) {
+                    const int a = pk(je, je);
+                    fill_pivot(G[a] - fx_dot<FILL_B>(fx, nmax, je, je), je, G, piv, &s_bad);
+                }
+                __syncthreads();
+            }
         }
         __syncthreads();
         if (s_bad) {
@@ -360,8 +504,9 @@ __global__ void __launch_bounds__(256) k_sum_final(const double* __restrict__ pa
 }
 
 size_t fill_smem_bytes(int k, int max_m) {
-    size_t nmax = (size_t)k + (size_t)max_m;
-    return sizeof(double) * (nmax * (nmax + 1) / 2 + 3 * nmax + 3 * nmax + EXP_TAB) + sizeof(int) * (nmax + (size_t)k);
+    const int nmax = k + max_m;
+    return sizeof(double) * ((size_t)nmax * (nmax + 1) / 2 + 4 + nmax + FILL_B + EXP_TAB + fill_scratch_doubles(nmax)) +
+           sizeof(int) * ((size_t)nmax + (size_t)k);
 }
 
 __global__ void k_fp64_math(KP<double> kp, const double* __restrict__ x, long long n, double* __restrict__ os,
@@ -523,8 +668,10 @@ extern "C" sic_status sic_build_factor_range(sic_handle* h, const double* pts, i
         const int lo = c == 0 ? 1 : split + 1, hi = c == 0 ? split : max_m;
         if (lo > hi) break;
         const size_t sm = fill_smem_bytes(k, hi);
-        auto kern = (c == 0) ? k_fill<128> : (big_nt == 384 ? k_fill<384> : k_fill<256>);
-        const int block = (c == 0 ? 128 : big_nt) + 32;
+        // worker threads: at least one per row of the largest unit (k + hi)
+        const int nt = (c == 0 && k + hi <= 128) ? 128 : (c == 0 || big_nt != 384 ? 256 : 384);
+        auto kern = nt == 128 ? k_fill<128> : (nt == 384 ? k_fill<384> : k_fill<256>);
+        const int block = nt + 32;
         SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int grid = persistent_grid(h, kern, block, sm, n_grp);
         kern<<<grid, block, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp, sel_idx,

@@ -84,15 +84,46 @@ __device__ __forceinline__ T matern(const KP<T>& k, T r) {
 
 // ---- FP64 Matern with few FP64-pipe instructions (GB300 issues 2 DFMA / clk / SM) ----
 //
-// exp(x), x <= 0: table-driven reduction after Tang (ACM TOMS 15(2), 1989).  With
-// k = round(256 x / ln 2) = 256 q + j, x = k ln2/256 + r, |r| <= ln2/512, and
-// exp(x) = 2^q * 2^(j/256) * e^r.  ln2/256 is split into its double rounding and the tail,
-// so r carries ~1e-19 absolute error for |k| < 2^18; e^r - 1 = r + r^2 (1/2 + r/6 + r^2/24),
-// truncation below 4e-17.  The result is formed as T_j + T_j p in one fused operation and
-// scaled by adding q to the exponent field.  Error: the table's rounding plus one final
-// rounding (about 1.5 ulp).  9 FP64 operations.  Arguments below -700 return 0
-// (exp(-700) ~ 1e-304).  `tab` holds scale * 2^(j/256), j = 0..255 (exp_table_fill), so the
-// routine returns scale * exp(x) (the Matern fill folds the variance in this way).
+// The routines below keep FP64 operations for the steps that need 53 bits (an exact
+// reduction, one Newton step, the final fused rounding) and do the rest on the FP32 pipe in
+// double-float arithmetic: a value hi + lo of two FP32 numbers, built from the error-free
+// transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and the exact product a b = p + e,
+// e = fma(a, b, -p); the explicit-rounding intrinsics keep the compiler from contracting
+// or reassociating them.
+
+// A float as the FP64 number of the same value, by its bit pattern (integer operations only;
+// zero for zero and subnormal inputs, below 1.2e-38)
+__device__ __forceinline__ double f32_as_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return e ? __hiloint2double((int)hi, (int)(u << 29)) : 0.0;
+}
+
+// x split by its bits into hi + lo (integer operations and one integer-to-float conversion):
+// hi = x with the significand truncated to 24 bits, lo = the remaining 29 bits rounded to 24,
+// so |x - hi - lo| <= 2^-48 |x|.  Valid for 2^-74 <= |x| < 2^128 and for x = 0; below 2^-74
+// lo is 0 (|x - hi| < 2^-23 |x|) and below 2^-126 hi is 0 as well.
+__device__ __forceinline__ void f64_split(double x, float& hi, float& lo) {
+    const unsigned H = (unsigned)__double2hiint(x), L = (unsigned)__double2loint(x);
+    const unsigned e = (H >> 20) & 0x7ffu, sg = H & 0x80000000u;
+    hi = e > 896u ? __uint_as_float(sg | ((e - 896u) << 23) | ((H & 0xfffffu) << 3) | (L >> 29)) : 0.f;
+    const float m = __uint2float_rn(L & 0x1fffffffu);  // the low 29 bits, times 2^(e - 1075)
+    lo = e >= 949u ? __fmul_rn(m, __uint_as_float(sg | ((e - 948u) << 23))) : 0.f;
+}
+
+// exp(x), -700 <= x <= 700: table-driven reduction after Tang (ACM TOMS 15(2), 1989).  With
+// k = round(256 x / ln 2) = 256 q + j (from an FP32 product: off by at most one from the
+// nearest integer, which only widens |r| to ~1.6e-3), x = k ln2/256 + r and
+// exp(x) = 2^q * 2^(j/256) * e^r.  ln2/256 = L1 + L2 with L1 rounded to 35 significant bits,
+// so k L1 is exact for |k| < 2^18 and r1 = x - k L1 is an exact FP64 operation; r = r1 - k L2
+// (|k L2| < 1.4e-8) and s = e^r - 1 = r + r^2/2 + r^3/6 + r^4/24 + r^5/120 (truncation below
+// 3e-20) are formed in double-float (relative error about 2^-47 of s, |s| < 2e-3), s goes to
+// FP64 in one addition, and the result is T_j + T_j s in one fused operation, scaled by adding
+// q to the exponent field.  Error: the table's rounding plus one final rounding.  3 FP64
+// operations.  Arguments below -700 return 0 (exp(-700) ~ 1e-304).  `tab` holds
+// scale * 2^(j/256), j = 0..255 (exp_table_fill), so the routine returns scale * exp(x) (the
+// Matern fill folds the variance in this way).
 constexpr int EXP_TAB = 256;
 
 __device__ __forceinline__ void exp_table_fill(double* tab, double scale = 1.0) {
@@ -100,58 +131,109 @@ __device__ __forceinline__ void exp_table_fill(double* tab, double scale = 1.0) 
 }
 
 __device__ __forceinline__ double exp_neg_table(double x, const double* __restrict__ tab) {
-    constexpr double SHIFT = 6755399441055744.0;                // 1.5 * 2^52
-    constexpr double INV_L = 369.32993046757463228;             // 256 / ln 2
-    constexpr double L1 = 0.6931471805599453094172321 / 256.0;  // ln2/256, rounded
-    constexpr double L2 = 2.3190468138462996e-17 / 256.0;       // ln2/256 - L1
+    constexpr float INV_L = 369.329925537109375f;              // 256 / ln 2 (any rounding works)
+    constexpr double L1 = 0.0027076061741126978;               // ln2/256 to 35 bits (0x1.62e42fefcp-9)
+    constexpr float L2_HI = -5.0411406413196705e-14f;          // ln2/256 - L1, as a double-float
+    constexpr float L2_LO = -8.917921829536205e-22f;
+    constexpr float THIRD_HI = 0.3333333432674408f, THIRD_LO = -9.934107758624577e-09f;  // 1/3
+    const unsigned xh = (unsigned)__double2hiint(x);
     // x < -700 <=> (x negative) high word above that of -700.0 (integer compare, no FP64 op)
-    if ((unsigned)__double2hiint(x) > 0xC085E000u) return 0.0;
-    double kd = fma(x, INV_L, SHIFT);  // k in the low word, two's complement
-    const int k = __double2loint(kd);
-    kd -= SHIFT;
-    double r = fma(-kd, L1, x);
-    r = fma(-kd, L2, r);
-    double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
-    q = fma(q, r, 0.5);
-    const double p = fma(r * r, q, r);  // e^r - 1
+    if (xh > 0xC085E000u) return 0.0;
+    const unsigned ex = (xh >> 20) & 0x7ffu;
+    const float xf = ex > 896u ? __uint_as_float((xh & 0x80000000u) | ((ex - 896u) << 23) | ((xh & 0xfffffu) << 3))
+                               : 0.f;  // x to ~2^-20 (a float of the high word)
+    const float kf = rintf(__fmul_rn(xf, INV_L));
+    const int k = (int)kf;
+    const double r1 = fma(-f32_as_f64(kf), L1, x);  // exact
+    float ah, al;
+    f64_split(r1, ah, al);
+    // r = (ah + al) - k L2, k L2 = kl + kle
+    const float kl = __fmul_rn(kf, L2_HI);
+    const float kle = __fmaf_rn(kf, L2_LO, __fmaf_rn(kf, L2_HI, -kl));
+    float rh = __fadd_rn(ah, -kl);
+    float rl = __fadd_rn(__fsub_rn(ah, __fsub_rn(rh, __fsub_rn(rh, ah))), __fsub_rn(-kl, __fsub_rn(rh, ah)));  // TwoSum
+    rl = __fadd_rn(rl, __fsub_rn(al, kle));
+    {  // renormalise (Fast2Sum: |rh| >= |rl|)
+        const float t = __fadd_rn(rh, rl);
+        rl = __fsub_rn(rl, __fsub_rn(t, rh));
+        rh = t;
+    }
+    // r^2 = p + pl (pl: the product's error and the cross term 2 rh rl)
+    const float p = __fmul_rn(rh, rh);
+    const float pl = __fmaf_rn(2.f * rh, rl, __fmaf_rn(rh, rh, -p));
+    // r^3/6 = (r^2/2)(r/3): r/3 = t3 + t3l, then (p/2) t3 exactly as c3 + c3l
+    const float t3 = __fmul_rn(rh, THIRD_HI);
+    const float t3l = __fmaf_rn(rl, THIRD_HI, __fmaf_rn(rh, THIRD_LO, __fmaf_rn(rh, THIRD_HI, -t3)));
+    const float ph = 0.5f * p;
+    const float c3 = __fmul_rn(ph, t3);
+    const float c3l = __fmaf_rn(0.5f * pl, t3, __fmaf_rn(ph, t3l, __fmaf_rn(ph, t3, -c3)));
+    // r^4/24 + r^5/120 in FP32 (below 3e-13)
+    const float c4 = __fmul_rn(__fmul_rn(p, p), __fmaf_rn(rh, 1.f / 120.f, 1.f / 24.f));
+    // q = ph + c3 (TwoSum) + the small terms; s = rh + q.hi (TwoSum) + the rest
+    const float qh = __fadd_rn(ph, c3);
+    const float qb = __fsub_rn(qh, ph);
+    const float ql = __fadd_rn(__fadd_rn(__fsub_rn(ph, __fsub_rn(qh, qb)), __fsub_rn(c3, qb)),
+                               __fadd_rn(__fadd_rn(0.5f * pl, c3l), c4));
+    const float sh = __fadd_rn(rh, qh);
+    const float sb = __fsub_rn(sh, rh);
+    const float sl = __fadd_rn(__fadd_rn(__fsub_rn(rh, __fsub_rn(sh, sb)), __fsub_rn(qh, sb)), __fadd_rn(rl, ql));
+    const double s = f32_as_f64(sh) + f32_as_f64(sl);
     const double tj = tab[k & (EXP_TAB - 1)];
-    const double e = fma(tj, p, tj);
+    const double e = fma(tj, s, tj);
     return __hiloint2double(__double2hiint(e) + ((k >> 8) << 20), __double2loint(e));
 }
 
-// sqrt(d2), d2 >= 0: an FP32 reciprocal-square-root seed (from the high word, ~2^-20)
-// refined by two Newton steps on the residual d2 - r^2 with the fixed half-reciprocal h:
-// the relative error goes 2^-20 -> 1.5 * 2^-40 -> ~2^-59, under one rounding of the last
-// fused step.  5 FP64 operations; the range tests are integer compares on the high word.
-// d2 < 2^-120 returns 0 (the square root is below 1e-18); d2 > 2^120 uses sqrt().
+// sqrt(d2), d2 >= 0.  For 2^-74 <= d2 < 2^120: an FP32 root r0 = dh rsqrt(dh) of the high part
+// (~2^-22), one Newton step on the exact residual dh + dl - r0^2 in double-float
+// (r1 = r0 + c to ~2^-43), then one FP64 Newton step r = r1 + (d2 - r1^2) / (2 r0): under one
+// rounding of the last fused operation.  3 FP64 operations.  Below 2^-74: the FP32 seed of the
+// high word refined by two FP64 Newton steps (5 operations); below 2^-120 the result is 0 (the
+// square root is below 1e-18); from 2^120 on, sqrt().
 __device__ __forceinline__ double sqrt_newton(double d2) {
     const unsigned hi = (unsigned)__double2hiint(d2);
-    if (hi < 0x38700000u) return 0.0;  // 2^-120 (and +0)
     if (hi >= 0x47700000u) return sqrt(d2);  // 2^120
-    const float f = __uint_as_float((hi << 3) - (896u << 23));  // exponent rebased 1023 -> 127
-    const unsigned yb = __float_as_uint(rsqrtf(f));
-    const unsigned yhi = (yb >> 3) + (896u << 20), ylo = yb << 29;
-    const double y = __hiloint2double((int)yhi, (int)ylo);
-    const double h = __hiloint2double((int)(yhi - (1u << 20)), (int)ylo);  // y / 2
-    double r = d2 * y;
-    r = fma(h, fma(-r, r, d2), r);
-    r = fma(h, fma(-r, r, d2), r);
-    return r;
+    if (hi < 0x3B500000u) {                  // 2^-74
+        if (hi < 0x38700000u) return 0.0;    // 2^-120 (and +0)
+        const float f = __uint_as_float((hi << 3) - (896u << 23));  // exponent rebased 1023 -> 127
+        const unsigned yb = __float_as_uint(rsqrtf(f));
+        const unsigned yhi = (yb >> 3) + (896u << 20), ylo = yb << 29;
+        const double y = __hiloint2double((int)yhi, (int)ylo);
+        const double h = __hiloint2double((int)(yhi - (1u << 20)), (int)ylo);  // y / 2
+        double r = d2 * y;
+        r = fma(h, fma(-r, r, d2), r);
+        return fma(h, fma(-r, r, d2), r);
+    }
+    float dh, dl;
+    f64_split(d2, dh, dl);
+    const float y = rsqrtf(dh);
+    const float r0 = __fmul_rn(dh, y);
+    const float h0 = 0.5f * y;  // 1 / (2 r0), ~2^-22
+    const float p = __fmul_rn(r0, r0);
+    const float pe = __fmaf_rn(r0, r0, -p);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(dh, p), pe), dl);  // dh - p exact (Sterbenz)
+    const double r1 = f32_as_f64(r0) + f32_as_f64(__fmul_rn(res, h0));
+    return fma(f32_as_f64(h0), fma(-r1, r1, d2), r1);
 }
 
-// 1/sqrt(x), x > 0, in FP64: the FP32 seed of sqrt_newton refined by two Newton steps
-// y <- y (3/2 - (x/2) y^2) (relative error 2^-20 -> ~2^-39 -> ~2^-77, then rounding:
-// about 2 ulp).  7 FP64 operations; x outside [2^-120, 2^120) uses 1 / sqrt(x).
+// 1/sqrt(x), x > 0, in FP64.  For 2^-74 <= x < 2^100: an FP32 reciprocal square root y of the
+// high part (~2^-22), one Newton step on the residual 1 - (xh + xl) y^2 in double-float
+// (y1 = y + c to ~2^-43), then one FP64 Newton step y1 + (y/2)(1 - (x y1) y1) (~2^-86 before
+// two roundings: about 1 ulp).  4 FP64 operations.  Outside that range, 1 / sqrt(x).
 __device__ __forceinline__ double rsqrt_newton(double x) {
     const unsigned hi = (unsigned)__double2hiint(x);
-    if (hi < 0x38700000u || hi >= 0x47700000u) return 1.0 / sqrt(x);
-    const float f = __uint_as_float((hi << 3) - (896u << 23));
-    const unsigned yb = __float_as_uint(rsqrtf(f));
-    double y = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
-    const double hx = 0.5 * x;
-    y = y * fma(-hx * y, y, 1.5);
-    y = y * fma(-hx * y, y, 1.5);
-    return y;
+    if (hi < 0x3B500000u || hi >= 0x46300000u) return 1.0 / sqrt(x);
+    float xh, xl;
+    f64_split(x, xh, xl);
+    const float y = rsqrtf(xh);
+    const float y2 = __fmul_rn(y, y);
+    const float y2e = __fmaf_rn(y, y, -y2);  // y^2 = y2 + y2e exactly
+    const float p = __fmul_rn(xh, y2);
+    const float pe = __fmaf_rn(xh, y2, -p);  // xh y2 = p + pe exactly
+    // e0 = 1 - x y^2 = ((1 - p) - pe) - xh y2e - xl y2 (1 - p exact: p is within 2^-20 of 1)
+    const float e0 = __fmaf_rn(-xl, y2, __fmaf_rn(-xh, y2e, __fsub_rn(__fsub_rn(1.f, p), pe)));
+    const float h = 0.5f * y;
+    const double y1 = f32_as_f64(y) + f32_as_f64(__fmul_rn(h, e0));
+    return fma(f32_as_f64(h), fma(-(x * y1), y1, 1.0), y1);
 }
 
 // FP64 Matern from a squared distance with the two routines above (same parameterisation
