@@ -47,13 +47,13 @@ SM_MAX_MHZ = 2070.0
 FFMA_PER_SM_CLK = 128   # FP32 FMA lanes per SM per clock
 DFMA_PER_SM_CLK = 2     # FP64 FMA per SM per clock on GB300 (1.26 TFLOP/s nominal at 2070 MHz)
 # kernels of one learned step: k_features, k_mlp_tc, k_topk_counts + k_scan_one_block +
-# k_topk_compact, k_agg_target_chol + k_select_agg_reg, k_nnz_count + k_scan_tile +
-# k_scan_partials + k_scan_add, k_fill x 2 (two group-size classes) + k_sum_tiles +
-# k_sum_final (plus one memset node)
-LAUNCHES_PER_STEP = 15
+# k_topk_compact, k_agg_target_chol + k_agg_target_cols + k_select_agg_reg, k_nnz_count +
+# k_scan_tile + k_scan_partials + k_scan_add, k_fill x 2 (two group-size classes) +
+# k_sum_tiles + k_sum_final (plus one memset node)
+LAUNCHES_PER_STEP = 16
 # DRAM read + write bytes of the two k_fill launches of one learned step at N = 2^19
 # (22,423 supernodes), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
-FILL_DRAM_BYTES_N2E19 = 17.650944e6 + 259.233280e6 + 9.646848e6 + 124.519680e6
+FILL_DRAM_BYTES_N2E19 = None  # to be measured again for the current kernel
 FILL_GROUPS_N2E19 = 22423
 
 
@@ -1054,12 +1054,15 @@ def main():
         # DRAM bytes of the two k_fill launches measured at N = 2^19, scaled by the supernode
         # count; the algorithmic bytes are the factor written (row index + value per nonzero),
         # col_ptr and log v, the points and the picks read
-        traffic = FILL_DRAM_BYTES_N2E19 * hp.n_units / FILL_GROUPS_N2E19
+        traffic = FILL_DRAM_BYTES_N2E19 * hp.n_units / FILL_GROUPS_N2E19 if FILL_DRAM_BYTES_N2E19 else None
         roof = {"bound": "alu", "kernel": "k_fill (FP64 fill, both launches)", "achieved": fill_tf,
                 "peak": f64_peak, "unit": "TFLOP/s", "frac": fill_tf / f64_peak, "traffic": traffic,
                 "traffic_algorithmic": nnz * 12.0 + N * (8.0 + 8.0 + 8.0 * hp.pts.shape[1]) + hp.n_units * hp.k * 4.0,
                 "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (derived from unit counts; a DFMA "
-                               "throughput kernel saturates at 1.6 FMA/clk/SM = 1.0 TFLOP/s)"}
+                               "throughput kernel saturates at 1.6 FMA/clk/SM = 1.0 TFLOP/s)",
+                "achieved_of": "the LDL^T's and the back substitutions' multiply-adds (2 FLOPs each) per second, "
+                               "FP64-equivalent: each panel's trailing update runs as exact integer products "
+                               "with one FP64 addition per entry"}
     else:
         roof = {"bound": "alu", "kernel": "k_select_agg<float>", "achieved": sel_tf, "peak": f32_peak,
                 "unit": "TFLOP/s", "frac": sel_tf / f32_peak, "traffic": None,
