@@ -119,9 +119,10 @@ constexpr int FILL_M_SPLIT = 32;  // groups of at most this size run in their ow
 constexpr int FILL_B = 4;         // panel width of the blocked LDL^T (integer trailing update)
 
 // doubles of the scratch region: the points' coordinates while Theta is formed, then the
-// panel's rows in fixed point ((2 FILL_B + 1) ints per row)
+// panel's rows in fixed point ((2 FILL_B + 1) ints per row); even, so what follows stays
+// 16-byte aligned
 __host__ __device__ constexpr int fill_scratch_doubles(int nmax) {
-    return 3 * nmax > ((2 * FILL_B + 1) * nmax + 1) / 2 ? 3 * nmax : ((2 * FILL_B + 1) * nmax + 1) / 2;
+    return ((3 * nmax > ((2 * FILL_B + 1) * nmax + 1) / 2 ? 3 * nmax : ((2 * FILL_B + 1) * nmax + 1) / 2) + 1) & ~1;
 }
 
 // Packed lower-triangle index (nn <= 192, so every index fits in 32 bits; 32-bit integer
@@ -158,8 +159,9 @@ __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* p
 // A row of a panel, its FILL_B values g_j (entries of G = L D^(1/2)), is held in fixed point:
 // g_j = M_j 2^(E - 1075) with E the largest biased exponent among them and M_j the 53-bit
 // significands shifted to E and truncated (signed; zero and subnormal values count as 0), split
-// as M_j = Mh_j 2^26 + Ml_j (Mh signed, 0 <= Ml < 2^26).  Layout (ints, leading dimension ld):
-// Mh_j at fx[j ld + row], Ml_j at fx[(B + j) ld + row], E at fx[2 B ld + row].
+// as M_j = Mh_j 2^26 + Ml_j (Mh signed, 0 <= Ml < 2^26).  Layout (B = 4, ld rows, fx 16-byte
+// aligned): the Mh of a row as one int4 at fx[4 row], its Ml at fx[4 (ld + row)], E at
+// fx[8 ld + row] (a warp reading consecutive rows reads consecutive 16-byte words).
 // The dot product of two rows, sum_j M_ij M_lj = 2^52 sum Mh Mh + 2^26 sum (Mh Ml + Ml Mh)
 // + sum Ml Ml, is exact in three 64-bit sums of 32 x 32-bit products (|terms| < 2^54, B <= 8),
 // combined in 128 bits and rounded once to FP64.  Truncating to the row's exponent costs each
@@ -168,6 +170,7 @@ __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* p
 // backward error bound.
 template <int B>
 __device__ __forceinline__ void fx_row_store(const double (&g)[B], int* __restrict__ fx, int ld, int row) {
+    static_assert(B == 4, "the fixed-point rows are stored as int4");
     int e[B];
     int E = 0;
 #pragma unroll
@@ -175,6 +178,7 @@ __device__ __forceinline__ void fx_row_store(const double (&g)[B], int* __restri
         e[j] = (__double2hiint(g[j]) >> 20) & 0x7ff;
         E = max(E, e[j]);
     }
+    int mh[B], ml[B];
 #pragma unroll
     for (int j = 0; j < B; ++j) {
         const long long u = __double_as_longlong(g[j]);
@@ -182,10 +186,12 @@ __device__ __forceinline__ void fx_row_store(const double (&g)[B], int* __restri
         const int sh = E - e[j];
         m = sh < 63 ? (m >> sh) : 0LL;
         if (u < 0) m = -m;
-        fx[j * ld + row] = (int)(m >> 26);
-        fx[(B + j) * ld + row] = (int)(m & 0x3ffffffLL);
+        mh[j] = (int)(m >> 26);
+        ml[j] = (int)(m & 0x3ffffffLL);
     }
-    fx[2 * B * ld + row] = E;
+    reinterpret_cast<int4*>(fx)[row] = make_int4(mh[0], mh[1], mh[2], mh[3]);
+    reinterpret_cast<int4*>(fx)[ld + row] = make_int4(ml[0], ml[1], ml[2], ml[3]);
+    fx[8 * ld + row] = E;
 }
 
 // S = a2 2^52 + a1 2^26 + a0 (a0 >= 0), times 2^(ex - 2150), rounded once to FP64 (to nearest,
@@ -229,16 +235,19 @@ __device__ __forceinline__ double fx_to_double(long long a2, long long a1, long 
 
 template <int B>
 __device__ __forceinline__ double fx_dot(const int* __restrict__ fx, int ld, int i, int l) {
+    static_assert(B == 4, "the fixed-point rows are stored as int4");
+    const int4 hi4 = reinterpret_cast<const int4*>(fx)[i], li4 = reinterpret_cast<const int4*>(fx)[ld + i];
+    const int4 hl4 = reinterpret_cast<const int4*>(fx)[l], ll4 = reinterpret_cast<const int4*>(fx)[ld + l];
+    const int hi_[4] = {hi4.x, hi4.y, hi4.z, hi4.w}, li[4] = {li4.x, li4.y, li4.z, li4.w};
+    const int hl[4] = {hl4.x, hl4.y, hl4.z, hl4.w}, ll[4] = {ll4.x, ll4.y, ll4.z, ll4.w};
     long long a2 = 0, a1 = 0, a0 = 0;
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-        const int hi_ = fx[j * ld + i], li = fx[(B + j) * ld + i];
-        const int hl = fx[j * ld + l], ll = fx[(B + j) * ld + l];
-        a2 += (long long)hi_ * hl;
-        a1 += (long long)hi_ * ll + (long long)li * hl;
-        a0 += (long long)li * ll;
+    for (int j = 0; j < 4; ++j) {
+        a2 += (long long)hi_[j] * hl[j];
+        a1 += (long long)hi_[j] * ll[j] + (long long)li[j] * hl[j];
+        a0 += (long long)li[j] * ll[j];
     }
-    return fx_to_double(a2, a1, a0, fx[2 * B * ld + i] + fx[2 * B * ld + l]);
+    return fx_to_double(a2, a1, a0, fx[8 * ld + i] + fx[8 * ld + l]);
 }
 
 // CTAs per SM the register budget is set for (shared memory allows about this many at the
@@ -257,14 +266,14 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                                                   DevStatus* st) {
     extern __shared__ double smem_d[];
     const int nmax = k + m_hi;  // shared memory is laid out for this launch's size class
-    double* G = smem_d;                                     // packed lower, nmax(nmax+1)/2
+    double* tab = smem_d;                                   // 2^(j/256) (exp_neg_table)
+    double* xyz = tab + EXP_TAB;                            // 3 x nmax, while Theta is formed; then
+    int* fx = reinterpret_cast<int*>(xyz);                  // the panel's rows in fixed point (16-byte aligned)
+    double* G = xyz + fill_scratch_doubles(nmax);           // packed lower, nmax(nmax+1)/2
     double* piv = G + (long long)nmax * (nmax + 1) / 2;     // 1/d and d^(-1/2) of two columns (ring)
     double* cj = piv + 4;                                   // the current column of L
     double* cu = cj + nmax;                                 // the panel's columns of U at the current column
-    double* tab = cu + FILL_B;                              // 2^(j/256) (exp_neg_table)
-    double* xyz = tab + EXP_TAB;                            // 3 x nmax, while Theta is formed; then
-    int* fx = reinterpret_cast<int*>(xyz);                  // the panel's rows in fixed point, (2 FILL_B + 1) x nmax
-    int* pos = reinterpret_cast<int*>(xyz + fill_scratch_doubles(nmax));  // nmax
+    int* pos = reinterpret_cast<int*>(cu + FILL_B);         // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -318,10 +327,9 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
         // dfloat.cuh would leave the FP64 pipe to the factorisation, but its ~1e-14 of the
         // variance per entry is amplified by 1/v in the Schur complements, v ~ 2 nugget on the
         // finest groups: factor columns then miss the oracle's by more than 1e-8)
-        const int tri = nn * (nn + 1) / 2;
-        for (int e = worker ? tid : tri; e < tri; e += FILL_NT) {
-            const int i = pk_row(e);
-            const int j = e - i * (i + 1) / 2;
+        // entry e = i (i + 1) / 2 + j, stepped by FILL_NT
+        int i = worker ? pk_row(tid) : nn, j = worker ? tid - i * (i + 1) / 2 : 0;
+        while (i < nn) {
             const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j];
             double d2 = fma(dy, dy, dx * dx);
             if (dim == 3) {
@@ -330,7 +338,12 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
             }
             double v = matern_d2_fast(kp, d2, tab);
             if (i == j) v += kp.nugget;
-            G[e] = v;
+            G[pk(i, j)] = v;
+            j += FILL_NT;
+            while (j > i) {
+                j -= i + 1;
+                ++i;
+            }
         }
         __syncthreads();
         // blocked right-looking LDL^T factorisation Theta_RR = L D L^T in place on the packed
@@ -401,13 +414,17 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
             // entry (je, je) and the next pivot are the pivot warp's.  je < nn implies a full panel.
             if (je < nn && !s_bad) {
                 const int nt = nn - je;
-                const int T = nt * (nt + 1) / 2;
                 if (worker) {
-                    for (int e = tid + 1; e < T; e += FILL_NT) {
-                        const int ii = pk_row(e);
-                        const int i = je + ii, l = je + e - ii * (ii + 1) / 2;
-                        const int a = pk(i, l);
-                        G[a] -= fx_dot<FILL_B>(fx, nmax, i, l);
+                    // entry e = ii (ii + 1) / 2 + ll of the trailing triangle, stepped by FILL_NT
+                    int ii = pk_row(tid + 1), ll = tid + 1 - ii * (ii + 1) / 2;
+                    while (ii < nt) {
+                        const int i = je + ii, l = je + ll;
+                        G[pk(i, l)] -= fx_dot<FILL_B>(fx, nmax, i, l);
+                        ll += FILL_NT;
+                        while (ll > ii) {
+                            ll -= ii + 1;
+                            ++ii;
+                        }
                     }
                 } else if (tid == FILL_NT) {
                     const int a = pk(je, je);
