@@ -233,22 +233,25 @@ __device__ __forceinline__ double fx_to_double(long long a2, long long a1, long 
                                             (mt & 0xfffffffffffffULL)));
 }
 
+// the exact dot product of rows i and l: S = a2 2^52 + a1 2^26 + a0 at scale 2^(ex - 2150)
 template <int B>
-__device__ __forceinline__ double fx_dot(const int* __restrict__ fx, int ld, int i, int l) {
+__device__ __forceinline__ void fx_dot(const int* __restrict__ fx, int ld, int i, int l, long long& a2, long long& a1,
+                                       long long& a0, int& ex) {
     static_assert(B == 4, "the fixed-point rows are stored as int4");
     const int4 hi4 = reinterpret_cast<const int4*>(fx)[i], li4 = reinterpret_cast<const int4*>(fx)[ld + i];
     const int4 hl4 = reinterpret_cast<const int4*>(fx)[l], ll4 = reinterpret_cast<const int4*>(fx)[ld + l];
     const int hi_[4] = {hi4.x, hi4.y, hi4.z, hi4.w}, li[4] = {li4.x, li4.y, li4.z, li4.w};
     const int hl[4] = {hl4.x, hl4.y, hl4.z, hl4.w}, ll[4] = {ll4.x, ll4.y, ll4.z, ll4.w};
-    long long a2 = 0, a1 = 0, a0 = 0;
+    a2 = a1 = a0 = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         a2 += (long long)hi_[j] * hl[j];
         a1 += (long long)hi_[j] * ll[j] + (long long)li[j] * hl[j];
         a0 += (long long)li[j] * ll[j];
     }
-    return fx_to_double(a2, a1, a0, fx[8 * ld + i] + fx[8 * ld + l]);
+    ex = fx[8 * ld + i] + fx[8 * ld + l];
 }
+
 
 // CTAs per SM the register budget is set for (shared memory allows about this many at the
 // largest group of each launch)
@@ -271,9 +274,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
     int* fx = reinterpret_cast<int*>(xyz);                  // the panel's rows in fixed point (16-byte aligned)
     double* G = xyz + fill_scratch_doubles(nmax);           // packed lower, nmax(nmax+1)/2
     double* piv = G + (long long)nmax * (nmax + 1) / 2;     // 1/d and d^(-1/2) of two columns (ring)
-    double* cj = piv + 4;                                   // the current column of L
-    double* cu = cj + nmax;                                 // the panel's columns of U at the current column
-    int* pos = reinterpret_cast<int*>(cu + FILL_B);         // nmax
+    int* pos = reinterpret_cast<int*>(piv + 4);             // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -328,8 +329,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
         // variance per entry is amplified by 1/v in the Schur complements, v ~ 2 nugget on the
         // finest groups: factor columns then miss the oracle's by more than 1e-8)
         // entry e = i (i + 1) / 2 + j, stepped by FILL_NT
-        int i = worker ? pk_row(tid) : nn, j = worker ? tid - i * (i + 1) / 2 : 0;
-        while (i < nn) {
+        for (int i = worker ? pk_row(tid) : nn, j = worker ? tid - i * (i + 1) / 2 : 0; i < nn;) {
             const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j];
             double d2 = fma(dy, dy, dx * dx);
             if (dim == 3) {
@@ -359,8 +359,16 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
         // pivot (its diagonal update, reciprocal and reciprocal square root, a chain of
         // dependent FP64 operations) is taken by the pivot warp while the workers update the
         // rest.
-        constexpr int SLOTS = 1;  // rows per worker thread: nn <= FILL_NT (the launcher's choice)
-        double gv[SLOTS][FILL_B];  // G_ij of the thread's rows below the panel (row tid + sl FILL_NT)
+        // Worker thread i owns row i (nn <= FILL_NT, the launcher's choice).  Within a panel the
+        // triangle keeps the panel's entries unscaled (U_lj = A_lj), so that every row owner can
+        // apply column j to its own row's later panel columns without waiting for the others
+        // (A_il -= L_ij U_lj reads row l's entry (l, j), which nobody writes during the panel);
+        // the owner of row j+1 takes the next pivot from its own updated diagonal, so a column
+        // costs one barrier.  The panel's L entries are written back after its last column.
+        const int i = tid;
+        const int rowi = pk(i, 0);
+        double gv[FILL_B];  // G_ij = U_ij d_j^(-1/2) of the thread's row, when below the panel
+        double lv[FILL_B];  // L_ij = U_ij / d_j of the thread's row
         if (tid == FILL_NT) fill_pivot(G[0], 0, G, piv, &s_bad);
         __syncthreads();
         for (int J = 0; J < nn && !s_bad; J += FILL_B) {
@@ -370,45 +378,27 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                 const int j = J + jj;
                 if (j >= je || s_bad) break;  // uniform: s_bad is read after a barrier
                 const double rd = piv[j & 1], rsd = piv[2 + (j & 1)];
-                if (worker) {
+                if (worker && i > j && i < nn) {
+                    const double uv = G[rowi + j];  // final
+                    const double l = uv * rd;
+                    lv[jj] = l;
+                    gv[jj] = uv * rsd;
 #pragma unroll
-                    for (int sl = 0; sl < SLOTS; ++sl) {
-                        const int i = tid + sl * FILL_NT;
-                        if (i > j && i < nn) {
-                            const int a = pk(i, j);
-                            const double uv = G[a];
-                            const double l = uv * rd;
-                            G[a] = l;
-                            cj[i] = l;
-                            if (i < je) cu[i - J] = uv;
-                            else gv[sl][jj] = uv * rsd;
-                        }
+                    for (int c2 = jj + 1; c2 < FILL_B; ++c2) {
+                        const int lc = J + c2;
+                        if (lc < je && lc <= i) G[rowi + lc] = fma(-l, G[pk(lc, j)], G[rowi + lc]);
                     }
-                    if (j == je - 1) {  // the panel is complete: its rows below go to fixed point
-#pragma unroll
-                        for (int sl = 0; sl < SLOTS; ++sl) {
-                            const int i = tid + sl * FILL_NT;
-                            if (i >= je && i < nn) fx_row_store<FILL_B>(gv[sl], fx, nmax, i);
-                        }
-                    }
+                    if (i == j + 1 && i < je) fill_pivot(G[rowi + i], i, G, piv, &s_bad);
+                    if (j == je - 1 && i >= je) fx_row_store<FILL_B>(gv, fx, nmax, i);  // rows below: fixed point
                 }
                 __syncthreads();
-                if (j < je - 1) {
-                    // the panel's later columns lc: rows i >= lc (entry (j+1, j+1) is the pivot warp's)
-                    if (worker) {
-                        for (int lc = j + 1; lc < je; ++lc) {
-                            const double ul = cu[lc - J];
-                            for (int i = lc + (lc == j + 1) + tid; i < nn; i += FILL_NT) {
-                                const int a = pk(i, lc);
-                                G[a] = fma(-cj[i], ul, G[a]);
-                            }
-                        }
-                    } else if (tid == FILL_NT) {
-                        const int a = pk(j + 1, j + 1);
-                        fill_pivot(fma(-cj[j + 1], cu[j + 1 - J], G[a]), j + 1, G, piv, &s_bad);
-                    }
-                    __syncthreads();
-                }
+            }
+            // the panel's L entries of row i (read by nobody until the next panel; the trailing
+            // update below touches only columns >= je)
+            if (worker && i > J && i < nn) {
+#pragma unroll
+                for (int c2 = 0; c2 < FILL_B; ++c2)
+                    if (J + c2 < je && J + c2 < i) G[rowi + J + c2] = lv[c2];
             }
             // the trailing matrix, entries (i, l) with je <= l <= i < nn, takes the panel's update;
             // entry (je, je) and the next pivot are the pivot warp's.  je < nn implies a full panel.
@@ -419,7 +409,10 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                     int ii = pk_row(tid + 1), ll = tid + 1 - ii * (ii + 1) / 2;
                     while (ii < nt) {
                         const int i = je + ii, l = je + ll;
-                        G[pk(i, l)] -= fx_dot<FILL_B>(fx, nmax, i, l);
+                        long long a2, a1, a0;
+                        int ex;
+                        fx_dot<FILL_B>(fx, nmax, i, l, a2, a1, a0, ex);
+                        G[pk(i, l)] -= fx_to_double(a2, a1, a0, ex);
                         ll += FILL_NT;
                         while (ll > ii) {
                             ll -= ii + 1;
@@ -428,7 +421,10 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                     }
                 } else if (tid == FILL_NT) {
                     const int a = pk(je, je);
-                    fill_pivot(G[a] - fx_dot<FILL_B>(fx, nmax, je, je), je, G, piv, &s_bad);
+                    long long a2, a1, a0;
+                    int ex;
+                    fx_dot<FILL_B>(fx, nmax, je, je, a2, a1, a0, ex);
+                    fill_pivot(G[a] - fx_to_double(a2, a1, a0, ex), je, G, piv, &s_bad);
                 }
                 __syncthreads();
             }
@@ -522,7 +518,7 @@ __global__ void __launch_bounds__(256) k_sum_final(const double* __restrict__ pa
 
 size_t fill_smem_bytes(int k, int max_m) {
     const int nmax = k + max_m;
-    return sizeof(double) * ((size_t)nmax * (nmax + 1) / 2 + 4 + nmax + FILL_B + EXP_TAB + fill_scratch_doubles(nmax)) +
+    return sizeof(double) * ((size_t)nmax * (nmax + 1) / 2 + 4 + EXP_TAB + fill_scratch_doubles(nmax)) +
            sizeof(int) * ((size_t)nmax + (size_t)k);
 }
 
