@@ -7,8 +7,8 @@
 // Theta_{s,s}, U upper triangular.  The CTA forms Theta on the reversed order
 // R = reverse(s) in packed lower storage in shared memory (one entry per thread), factors
 // it Theta_{RR} = L D L^T = G G^T with G = L D^{1/2} (blocked right-looking: panels of
-// FILL_B columns in FP64, each panel's update of the trailing matrix as exact integer dot
-// products of fixed-point G rows, one FP64 rounding per entry and panel; one thread takes
+// FILL_B columns in FP64, each panel's update of the trailing matrix as integer dot products
+// (exact 32 x 32-bit products) of fixed-point G rows, one FP64 subtraction per entry and panel; one thread takes
 // each pivot's reciprocal square root), and since U = J G J (J the reversal), member a's
 // column is J G^{-T} e_j = d_j^{-1/2} J L^{-T} e_j with j = n-1-a: one back substitution per
 // member, one member per half-warp, the right-hand side in registers.  v_a = G_jj^2 = d_j,
@@ -154,7 +154,7 @@ __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* p
     piv[2 + (c & 1)] = rs;
 }
 
-// ---- the exact integer update of a panel ----
+// ---- the integer update of a panel ----
 //
 // A row of a panel, its FILL_B values g_j (entries of G = L D^(1/2)), is held in fixed point:
 // g_j = M_j 2^(E - 1075) with E the largest biased exponent among them and M_j the 53-bit
@@ -162,12 +162,11 @@ __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* p
 // as M_j = Mh_j 2^26 + Ml_j (Mh signed, 0 <= Ml < 2^26).  Layout (B = 4, ld rows, fx 16-byte
 // aligned): the Mh of a row as one int4 at fx[4 row], its Ml at fx[4 (ld + row)], E at
 // fx[8 ld + row] (a warp reading consecutive rows reads consecutive 16-byte words).
-// The dot product of two rows, sum_j M_ij M_lj = 2^52 sum Mh Mh + 2^26 sum (Mh Ml + Ml Mh)
-// + sum Ml Ml, is exact in three 64-bit sums of 32 x 32-bit products (|terms| < 2^54, B <= 8),
-// combined in 128 bits and rounded once to FP64.  Truncating to the row's exponent costs each
-// value at most 2^-52 of the row's largest: with G's rows (|G_ij| <= sqrt(A_ii)) the error of an
-// entry's update stays within B 2^-52 sqrt(A_ii A_ll), the order of the FP64 Cholesky's own
-// backward error bound.
+// The dot product of two rows is formed from exact 32 x 32-bit products (fx_dot).  Truncating
+// to the row's exponent costs each value at most 2^-52 of the row's largest, and fx_dot's own
+// truncations stay below 2^-51 of the largest product: with G's rows (|G_ij| <= sqrt(A_ii)) the
+// error of an entry's update stays within a few B 2^-52 sqrt(A_ii A_ll), the order of the FP64
+// Cholesky's own backward error bound.
 template <int B>
 __device__ __forceinline__ void fx_row_store(const double (&g)[B], int* __restrict__ fx, int ld, int row) {
     static_assert(B == 4, "the fixed-point rows are stored as int4");
@@ -194,62 +193,35 @@ __device__ __forceinline__ void fx_row_store(const double (&g)[B], int* __restri
     fx[8 * ld + row] = E;
 }
 
-// S = a2 2^52 + a1 2^26 + a0 (a0 >= 0), times 2^(ex - 2150), rounded once to FP64 (to nearest,
-// ties away from zero); 0 below FP64's normal range.  Integer operations only.
-__device__ __forceinline__ double fx_to_double(long long a2, long long a1, long long a0, int ex) {
-    unsigned long long lo = (unsigned long long)a2 << 52;
-    long long hi = a2 >> 12;
-    const unsigned long long t1 = (unsigned long long)a1 << 26;
-    lo += t1;
-    hi += (a1 >> 38) + (lo < t1 ? 1 : 0);
-    const unsigned long long t0 = (unsigned long long)a0;
-    lo += t0;
-    hi += lo < t0 ? 1 : 0;
-    const bool neg = hi < 0;
-    if (neg) {
-        lo = ~lo + 1ULL;
-        hi = ~hi + (lo == 0ULL ? 1 : 0);
-    }
-    const unsigned long long uh = (unsigned long long)hi;
-    if ((uh | lo) == 0ULL) return 0.0;
-    int p;                   // position of the leading bit of |S|
-    unsigned long long mt;   // its leading 54 bits
-    if (uh) {
-        p = 127 - __clzll((long long)uh);
-        const int sft = p - 53;  // >= 11
-        mt = sft >= 64 ? (uh >> (sft - 64)) : ((uh << (64 - sft)) | (lo >> sft));
-    } else {
-        p = 63 - __clzll((long long)lo);
-        mt = p >= 53 ? (lo >> (p - 53)) : (lo << (53 - p));
-    }
-    mt = (mt + 1ULL) >> 1;  // 53 bits, rounded
-    if (mt >> 53) {
-        mt >>= 1;
-        ++p;
-    }
-    const int be = ex + p - 1127;  // |S| 2^(ex - 2150) = (mt 2^-52) 2^(p + ex - 2150)
+// s 2^e2 as FP64 by integer operations, the significand truncated (relative error < 2^-52);
+// 0 for s = 0 and below FP64's normal range
+__device__ __forceinline__ double i64_scaled(long long s, int e2) {
+    if (s == 0) return 0.0;
+    const unsigned long long sg = (unsigned long long)s & (1ULL << 63);
+    const unsigned long long mag = s < 0 ? 0ULL - (unsigned long long)s : (unsigned long long)s;
+    const int z = __clzll((long long)mag);
+    const int be = e2 + 63 - z + 1023;
     if (be <= 0) return 0.0;
-    return __longlong_as_double((long long)(((neg ? 1ULL : 0ULL) << 63) | ((unsigned long long)be << 52) |
-                                            (mt & 0xfffffffffffffULL)));
+    return __longlong_as_double((long long)(sg | ((unsigned long long)be << 52) | (((mag << z) >> 11) & 0xfffffffffffffULL)));
 }
 
-// the exact dot product of rows i and l: S = a2 2^52 + a1 2^26 + a0 at scale 2^(ex - 2150)
+// sum_j g_ij g_lj of rows i and l: 2^52 sum Mh Mh + 2^26 sum (Mh Ml + Ml Mh) exactly in two 64-bit
+// sums of 32 x 32-bit products, scaled down by 2^52 into one 64-bit integer (the dropped fraction
+// and the omitted sum Ml Ml are below 5 units of 2^(Ei + El - 2098)), converted to FP64
 template <int B>
-__device__ __forceinline__ void fx_dot(const int* __restrict__ fx, int ld, int i, int l, long long& a2, long long& a1,
-                                       long long& a0, int& ex) {
+__device__ __forceinline__ double fx_dot(const int* __restrict__ fx, int ld, int i, int l) {
     static_assert(B == 4, "the fixed-point rows are stored as int4");
     const int4 hi4 = reinterpret_cast<const int4*>(fx)[i], li4 = reinterpret_cast<const int4*>(fx)[ld + i];
     const int4 hl4 = reinterpret_cast<const int4*>(fx)[l], ll4 = reinterpret_cast<const int4*>(fx)[ld + l];
     const int hi_[4] = {hi4.x, hi4.y, hi4.z, hi4.w}, li[4] = {li4.x, li4.y, li4.z, li4.w};
     const int hl[4] = {hl4.x, hl4.y, hl4.z, hl4.w}, ll[4] = {ll4.x, ll4.y, ll4.z, ll4.w};
-    a2 = a1 = a0 = 0;
+    long long a2 = 0, a1 = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         a2 += (long long)hi_[j] * hl[j];
         a1 += (long long)hi_[j] * ll[j] + (long long)li[j] * hl[j];
-        a0 += (long long)li[j] * ll[j];
     }
-    ex = fx[8 * ld + i] + fx[8 * ld + l];
+    return i64_scaled(a2 + (a1 >> 26), fx[8 * ld + i] + fx[8 * ld + l] - 2098);
 }
 
 
@@ -352,7 +324,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
         // (A_il -= L_ij A_lj, flat over the worker threads).  The rows below the panel keep
         // G_ij = A_ij d_j^(-1/2) (G = L D^(1/2)) in registers and, once the panel is complete, in
         // fixed point; the trailing matrix then takes the panel's whole rank-FILL_B update as one
-        // exact integer dot product of two G rows per entry, rounded once and subtracted in FP64
+        // integer dot product of two G rows per entry (exact products), subtracted in FP64
         // (fx_dot): FILL_B FP64 FMAs become one FP64 addition, the products going to the integer
         // multiply-add units.  The FP64 units are per SM sub-partition and charge a warp
         // instruction whatever its active lanes, so the flat loops keep full warps.  The next
@@ -409,10 +381,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                     int ii = pk_row(tid + 1), ll = tid + 1 - ii * (ii + 1) / 2;
                     while (ii < nt) {
                         const int i = je + ii, l = je + ll;
-                        long long a2, a1, a0;
-                        int ex;
-                        fx_dot<FILL_B>(fx, nmax, i, l, a2, a1, a0, ex);
-                        G[pk(i, l)] -= fx_to_double(a2, a1, a0, ex);
+                        G[pk(i, l)] -= fx_dot<FILL_B>(fx, nmax, i, l);
                         ll += FILL_NT;
                         while (ll > ii) {
                             ll -= ii + 1;
@@ -421,10 +390,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                     }
                 } else if (tid == FILL_NT) {
                     const int a = pk(je, je);
-                    long long a2, a1, a0;
-                    int ex;
-                    fx_dot<FILL_B>(fx, nmax, je, je, a2, a1, a0, ex);
-                    fill_pivot(G[a] - fx_to_double(a2, a1, a0, ex), je, G, piv, &s_bad);
+                    fill_pivot(G[a] - fx_dot<FILL_B>(fx, nmax, je, je), je, G, piv, &s_bad);
                 }
                 __syncthreads();
             }
