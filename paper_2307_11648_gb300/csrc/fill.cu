@@ -225,6 +225,79 @@ __device__ __forceinline__ double fx_dot(const int* __restrict__ fx, int ld, int
 }
 
 
+// A coordinate x in fixed point at the largest biased exponent E of its dimension in the unit:
+// x 2^(1084 - E), so that |x_fix| < 2^62; exact for every x whose exponent is within 9 of E (a
+// unit's points are near one another: their coordinates share the exponent unless they are
+// within a few length scales of zero, where the truncation below 2^(E - 1085) is far below an
+// ulp of the kernel entries).  Integer operations only.
+__device__ __forceinline__ long long fx_coord(double x, int E) {
+    const long long u = __double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7ff);
+    if (!e) return 0LL;
+    const long long mant = (u & 0xfffffffffffffLL) | 0x10000000000000LL;
+    const int sh = E - e;  // >= 0
+    const long long f = sh <= 9 ? (mant << (9 - sh)) : (sh - 9 < 63 ? (mant >> (sh - 9)) : 0LL);
+    return u < 0 ? -f : f;
+}
+
+// dx^2 of one dimension, exact in 128 bits (h:l), for a difference |dx| < 2^63
+__device__ __forceinline__ void sq128(long long dx, unsigned long long& h, unsigned long long& l) {
+    const unsigned long long a = dx < 0 ? 0ULL - (unsigned long long)dx : (unsigned long long)dx;
+    const unsigned ah = (unsigned)(a >> 32), al = (unsigned)a;
+    const unsigned long long q0 = (unsigned long long)al * al;
+    const unsigned long long q1 = ((unsigned long long)ah * al) << 1;  // ah < 2^31
+    l = q0 + (q1 << 32);
+    h = (unsigned long long)ah * ah + (q1 >> 32) + (l < q0 ? 1ULL : 0ULL);
+}
+
+// The squared distance between points i and j from their fixed-point coordinates (xf[d ld + i],
+// scale 2^(1084 - E_d) in dimension d): each dimension's square exact in 128 bits, aligned to the
+// largest scale (a right shift, dropping bits below 2^-125 of the largest term), summed and
+// rounded once to FP64 (to nearest, ties away from zero).  Integer operations only.
+__device__ __forceinline__ double fx_dist2(const long long* __restrict__ xf, int ld, int dim, int i, int j, int E0,
+                                           int E1, int E2) {
+    const int Em = max(E0, max(dim > 1 ? E1 : 0, dim > 2 ? E2 : 0));
+    unsigned long long h = 0ULL, l = 0ULL;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= dim) break;
+        unsigned long long sh, sl;
+        sq128(xf[d * ld + i] - xf[d * ld + j], sh, sl);
+        const int s = 2 * (Em - (d == 0 ? E0 : (d == 1 ? E1 : E2)));
+        if (s >= 128) {
+            sh = sl = 0ULL;
+        } else if (s >= 64) {
+            sl = sh >> (s - 64);
+            sh = 0ULL;
+        } else if (s > 0) {
+            sl = (sl >> s) | (sh << (64 - s));
+            sh >>= s;
+        }
+        l += sl;
+        h += sh + (l < sl ? 1ULL : 0ULL);
+    }
+    if ((h | l) == 0ULL) return 0.0;
+    int p;
+    unsigned long long t;  // the leading 64 bits, leading bit at 63
+    if (h) {
+        const int z = __clzll((long long)h);
+        p = 127 - z;
+        t = z ? ((h << z) | (l >> (64 - z))) : h;
+    } else {
+        const int z = __clzll((long long)l);
+        p = 63 - z;
+        t = l << z;
+    }
+    unsigned long long mt = ((t >> 10) + 1ULL) >> 1;  // 53 bits, rounded
+    if (mt >> 53) {
+        mt >>= 1;
+        ++p;
+    }
+    const int be = p + 2 * Em - 1145;  // |X| 2^(2 Em - 2168) = (mt 2^-52) 2^(p + 2 Em - 2168)
+    if (be <= 0) return 0.0;
+    return __longlong_as_double((long long)(((unsigned long long)be << 52) | (mt & 0xfffffffffffffULL)));
+}
+
 // CTAs per SM the register budget is set for (shared memory allows about this many at the
 // largest group of each launch)
 constexpr int fill_min_ctas(int nt) { return nt == 128 ? 5 : (nt == 256 ? 3 : 2); }
@@ -249,6 +322,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
     int* pos = reinterpret_cast<int*>(piv + 4);             // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
+    __shared__ unsigned s_emax[3];  // the largest biased exponent of the unit's coordinates, per dimension
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool worker = tid < FILL_NT;  // the pivot warp joins only the barriers and the pivots
     exp_table_fill(tab, kp.s2);
@@ -284,31 +358,47 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
         }
         for (int a = worker ? tid : m; a < m; a += FILL_NT)
             if (col_ptr[c0 + a + 1] - col_ptr[c0 + a] != (long long)(m - a + cnt)) bad = true;
+        if (tid < 3) s_emax[tid] = 0u;
         if (__syncthreads_or(bad)) {
             if (tid == 0) record_error(st, SIC_ERR_INVALID, u);
             continue;
         }
-        // R order: picks descending, then members descending
-        for (int i = worker ? tid : nn; i < nn; i += FILL_NT) {
-            const int p = (i < cnt) ? srt[cnt - 1 - i] : (int)(g0 + m - 1 - (i - cnt));
-            pos[i] = p;
-            for (int d = 0; d < 3; ++d) xyz[d * nmax + i] = (d < dim) ? pts[(long long)p * dim + d] : 0.0;
+        // R order: picks descending, then members descending; the coordinates go to fixed point
+        // at the unit's largest exponent in each dimension (fx_coord), so that differences and
+        // squared distances are exact integer arithmetic (fx_dist2)
+        {
+            unsigned em[3] = {0u, 0u, 0u};
+            for (int i = worker ? tid : nn; i < nn; i += FILL_NT) {
+                const int p = (i < cnt) ? srt[cnt - 1 - i] : (int)(g0 + m - 1 - (i - cnt));
+                pos[i] = p;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const double x = (d < dim) ? pts[(long long)p * dim + d] : 0.0;
+                    xyz[d * nmax + i] = x;
+                    em[d] = max(em[d], ((unsigned)__double2hiint(x) >> 20) & 0x7ffu);
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                em[d] = __reduce_max_sync(0xffffffffu, em[d]);
+                if (lane == 0 && em[d]) atomicMax(&s_emax[d], em[d]);
+            }
         }
         if (tid == 0) s_bad = 0;
         __syncthreads();
-        // Theta_RR, packed lower, one flat entry per thread, in FP64 (the double-float Matern of
-        // dfloat.cuh would leave the FP64 pipe to the factorisation, but its ~1e-14 of the
+        const int E0 = (int)s_emax[0], E1 = (int)s_emax[1], E2 = (int)s_emax[2];
+        long long* xf = reinterpret_cast<long long*>(xyz);
+        for (int i = worker ? tid : nn; i < nn; i += FILL_NT)
+            for (int d = 0; d < dim; ++d) xf[d * nmax + i] = fx_coord(xyz[d * nmax + i], d == 0 ? E0 : (d == 1 ? E1 : E2));
+        __syncthreads();
+        // Theta_RR, packed lower, one flat entry per thread: the squared distance exact from the
+        // fixed-point coordinates, the Matern in FP64 (matern_d2_fast; the all-double-float
+        // Matern of dfloat.cuh would spare the FP64 pipe entirely, but its ~1e-14 of the
         // variance per entry is amplified by 1/v in the Schur complements, v ~ 2 nugget on the
         // finest groups: factor columns then miss the oracle's by more than 1e-8)
         // entry e = i (i + 1) / 2 + j, stepped by FILL_NT
         for (int i = worker ? pk_row(tid) : nn, j = worker ? tid - i * (i + 1) / 2 : 0; i < nn;) {
-            const double dx = xyz[i] - xyz[j], dy = xyz[nmax + i] - xyz[nmax + j];
-            double d2 = fma(dy, dy, dx * dx);
-            if (dim == 3) {
-                const double dz = xyz[2 * nmax + i] - xyz[2 * nmax + j];
-                d2 = fma(dz, dz, d2);
-            }
-            double v = matern_d2_fast(kp, d2, tab);
+            double v = matern_d2_fast(kp, fx_dist2(xf, nmax, dim, i, j, E0, E1, E2), tab);
             if (i == j) v += kp.nugget;
             G[pk(i, j)] = v;
             j += FILL_NT;
