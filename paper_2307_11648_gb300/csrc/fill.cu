@@ -138,20 +138,18 @@ __device__ __forceinline__ int pk_row(int e) {
 }
 
 // Pivot of column c of the LDL^T factorisation from its final Schur complement v: D_cc = v
-// (kept on the diagonal), d^(-1/2) by rsqrt_newton and 1/d as its square (six FP64 operations
-// with the diagonal's update), into the two-column ring piv = {1/d, 1/d, d^-1/2, d^-1/2}
-// (slot c & 1).  A non-positive pivot raises *bad.  The range test reads the bits (no FP64
-// compare).
+// (kept on the diagonal) and d^(-1/2) by rsqrt_newton (five FP64 operations with the
+// diagonal's update) into the two-column ring piv (slot c & 1); the column is then scaled as
+// G_ic = U_ic d^(-1/2) and L_ic = G_ic d^(-1/2).  A non-positive pivot raises *bad.  The range
+// test reads the bits (no FP64 compare).
 __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* piv, int* bad) {
     const long long vb = __double_as_longlong(v);
     if (vb <= 0 || vb >= 0x7ff0000000000000LL) {  // not in (+0, +inf): non-positive, infinite or NaN
         *bad = 1;
         return;
     }
-    const double rs = rsqrt_newton(v);
     G[pk(c, c)] = v;
-    piv[c & 1] = rs * rs;
-    piv[2 + (c & 1)] = rs;
+    piv[c & 1] = rsqrt_newton(v);
 }
 
 // ---- the integer update of a panel ----
@@ -318,7 +316,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
     double* xyz = tab + EXP_TAB;                            // 3 x nmax, while Theta is formed; then
     int* fx = reinterpret_cast<int*>(xyz);                  // the panel's rows in fixed point (16-byte aligned)
     double* G = xyz + fill_scratch_doubles(nmax);           // packed lower, nmax(nmax+1)/2
-    double* piv = G + (long long)nmax * (nmax + 1) / 2;     // 1/d and d^(-1/2) of two columns (ring)
+    double* piv = G + (long long)nmax * (nmax + 1) / 2;     // d^(-1/2) of two columns (ring; 4 slots kept)
     int* pos = reinterpret_cast<int*>(piv + 4);             // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
@@ -439,12 +437,13 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
             for (int jj = 0; jj < FILL_B; ++jj) {
                 const int j = J + jj;
                 if (j >= je || s_bad) break;  // uniform: s_bad is read after a barrier
-                const double rd = piv[j & 1], rsd = piv[2 + (j & 1)];
+                const double rsd = piv[j & 1];
                 if (worker && i > j && i < nn) {
                     const double uv = G[rowi + j];  // final
-                    const double l = uv * rd;
+                    const double g = uv * rsd;
+                    const double l = g * rsd;       // L_ij = U_ij / d_j
                     lv[jj] = l;
-                    gv[jj] = uv * rsd;
+                    gv[jj] = g;
 #pragma unroll
                     for (int c2 = jj + 1; c2 < FILL_B; ++c2) {
                         const int lc = J + c2;
