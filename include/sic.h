@@ -501,7 +501,8 @@ sic_status sic_pcg_solve(sic_handle* h, const double* pts, int64_t n, const sic_
  */
 int32_t sic_mlp_param_count(void);
 
-/* feat must hold cand_ptr[n_grp] * 8 floats [device]. */
+/* feat must hold cand_ptr[n_grp] * 8 floats [device], 16-byte aligned (each candidate's row is
+ * written as two 16-byte words); a misaligned feat returns SIC_ERR_INVALID. */
 sic_status sic_proposal_features(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
                                  const int64_t* grp_ptr, int64_t n_grp, const int64_t* cand_ptr,
                                  const int32_t* cand_idx, float* feat, void* stream);

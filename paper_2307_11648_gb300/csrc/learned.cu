@@ -106,14 +106,11 @@ __global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts
             }
             const float dmin = sqrtf(best);
             float cx = x[0] - cen[0], cy = x[1] - cen[1], cz = x[2] - cen[2];
-            f[0] = (x[0] - mx[ab * 3]) * ri;
-            f[1] = (x[1] - mx[ab * 3 + 1]) * ri;
-            f[2] = dmin * ri;
-            f[3] = sqrtf(cx * cx + cy * cy + cz * cz) * ri;
-            f[4] = (float)r / (float)C;
-            f[5] = matern<float>(kp, dmin) * inv_s2;
-            f[6] = (float)m * (1.f / 64.f);
-            f[7] = ksum * inv_m * inv_s2;
+            // two 16-byte stores per candidate (the row of 8 features is 32-byte aligned)
+            reinterpret_cast<float4*>(f)[0] = make_float4((x[0] - mx[ab * 3]) * ri, (x[1] - mx[ab * 3 + 1]) * ri, dmin * ri,
+                                                          sqrtf(cx * cx + cy * cy + cz * cz) * ri);
+            reinterpret_cast<float4*>(f)[1] = make_float4((float)r / (float)C, matern<float>(kp, dmin) * inv_s2,
+                                                          (float)m * (1.f / 64.f), ksum * inv_m * inv_s2);
         }
         __syncthreads();
     }
@@ -508,7 +505,7 @@ extern "C" sic_status sic_proposal_features(sic_handle* h, const double* pts, in
                                             const int64_t* cand_ptr, const int32_t* cand_idx, float* feat,
                                             void* stream) {
     if (!h || !pts || n < 1 || !sic_valid_kernel(kp) || !grp_ptr || n_grp < 1 || !cand_ptr || !cand_idx ||
-        !feat)
+        !feat || ((uintptr_t)feat & 15u))
         return SIC_ERR_INVALID;
     SIC_CUDA_TRY(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;

@@ -63,6 +63,10 @@ def test_features_match_oracle(env, oracle_lib):
         err = np.abs(F[a:b] - ref)
         err[amb, :2] = 0
         assert np.all(err <= 2e-5 * np.maximum(1.0, np.abs(ref))), g
+    # the rows are written as 16-byte words: a buffer off that alignment is refused before any launch
+    off = torch.empty(rows * 8 + 1, dtype=torch.float32, device="cuda")[1:].view(rows, 8)
+    with pytest.raises(sic.SicError):
+        sic.proposal_features(h, dp.pts, hp.kp, dp.grp_ptr, dp.cand_ptr, dp.cand_idx, off)
 
 
 @pytest.mark.parametrize("bf16", [False, True])
