@@ -357,7 +357,8 @@ sic_status sic_factor_nnz_noalloc(sic_handle* h, const int64_t* grp_ptr, int64_t
  * device, summed in a fixed order so that repeated runs agree bit for bit).  The KL
  * divergence of the factor is (sum_logv - logdet Theta) / 2 (eq. obj_chol).
  * grp_ptr NULL means single columns (n_grp = n).  max_m bounds the group size (1
- * without groups, <= 64).  Needs sic_build_factor_workspace bytes of ws. */
+ * without groups, <= 64).  Needs sic_build_factor_workspace bytes of ws (the fixed-order sum's
+ * partials and the launches' work counters, which the call zeroes on the stream itself). */
 
 sic_status sic_build_factor_workspace(int64_t n, size_t* bytes);
 /* Autotuned variant (this library's launch tuning; the paper has no counterpart): the same

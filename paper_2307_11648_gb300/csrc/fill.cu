@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                                                   long long n_cols, const long long* __restrict__ col_ptr,
                                                   long long base, int32_t* __restrict__ row_idx,
                                                   double* __restrict__ val, double* __restrict__ logv,
-                                                  DevStatus* st) {
+                                                  unsigned long long* __restrict__ ctr, DevStatus* st) {
     extern __shared__ double smem_d[];
     const int nmax = k + m_hi;  // shared memory is laid out for this launch's size class
     double* tab = smem_d;                                   // 2^(j/256) (exp_neg_table)
@@ -324,8 +324,17 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool worker = tid < FILL_NT;  // the pivot warp joins only the barriers and the pivots
     exp_table_fill(tab, kp.s2);
-
-    for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+    // units are taken from a work counter (*ctr, zeroed before the launch), so that the CTAs finish
+    // together whatever the units' sizes; s_next is double-buffered, one barrier per fetch
+    __shared__ long long s_next[2];
+    int nb_ = 0;
+    auto fetch = [&]() -> long long {
+        nb_ ^= 1;
+        if (tid == 0) s_next[nb_] = (long long)atomicAdd(ctr, 1ULL);
+        __syncthreads();
+        return s_next[nb_];
+    };
+    for (long long u = fetch(); u < n_units; u = fetch()) {
         const long long g0 = grp_ptr ? grp_ptr[u] : col0 + u;
         const int m = grp_ptr ? (int)(grp_ptr[u + 1] - g0) : 1;
         const int cnt = sel_count[u];
@@ -690,6 +699,12 @@ extern "C" sic_status sic_factor_nnz(sic_handle* h, const int64_t* grp_ptr, int6
 }
 
 // sum of log v in a fixed order (two launches), shared with the partial-pattern fill
+// bytes of the fixed-order sum's tile partials at the front of the fill's workspace
+static size_t fill_partials_bytes(long long n) {
+    const long long nb = (n + SUM_TILE - 1) / SUM_TILE;
+    return sizeof(double) * (size_t)(nb > 0 ? nb : 1);
+}
+
 sic_status launch_sum_logv(const double* logv, long long n, double* sum_logv, void* ws, cudaStream_t s) {
     long long nb = (n + SUM_TILE - 1) / SUM_TILE;
     k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n, (double*)ws);
@@ -700,8 +715,7 @@ sic_status launch_sum_logv(const double* logv, long long n, double* sum_logv, vo
 
 extern "C" sic_status sic_build_factor_workspace(int64_t n, size_t* bytes) {
     if (!bytes || n < 0) return SIC_ERR_INVALID;
-    long long nb = (n + SUM_TILE - 1) / SUM_TILE;
-    *bytes = sizeof(double) * (size_t)(nb > 0 ? nb : 1);
+    *bytes = fill_partials_bytes(n) + 2 * sizeof(unsigned long long);  // partial sums, then two work counters
     return SIC_OK;
 }
 
@@ -732,6 +746,10 @@ extern "C" sic_status sic_build_factor_range(sic_handle* h, const double* pts, i
     if (split > max_m) split = max_m;
     if (split < 1) split = 1;
     const int big_nt = tune_get(h, TUNE_FILL_BIGNT, k, max_m, 256) == 384 ? 384 : 256;
+    // the two launches' work counters, after the partial sums in the workspace
+    unsigned long long* ctr = reinterpret_cast<unsigned long long*>(
+        reinterpret_cast<char*>(ws) + fill_partials_bytes(n_cols));
+    SIC_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s));
     for (int c = 0; c < 2; ++c) {
         const int lo = c == 0 ? 1 : split + 1, hi = c == 0 ? split : max_m;
         if (lo > hi) break;
@@ -744,7 +762,7 @@ extern "C" sic_status sic_build_factor_range(sic_handle* h, const double* pts, i
         const int grid = persistent_grid(h, kern, block, sm, n_grp);
         kern<<<grid, block, sm, s>>>(pts, kp->dim, make_kp<double>(*kp), (const long long*)grp_ptr, n_grp, sel_idx,
                                      sel_count, k, max_m, lo, hi, n, col0, n_cols, (const long long*)col_ptr, base,
-                                     row_idx, val, logv, h->d_status);
+                                     row_idx, val, logv, ctr + c, h->d_status);
     }
     long long nb = (n_cols + SUM_TILE - 1) / SUM_TILE;
     k_sum_tiles<<<(unsigned)nb, 256, 0, s>>>(logv, n_cols, (double*)ws);
