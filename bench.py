@@ -53,7 +53,7 @@ DFMA_PER_SM_CLK = 2     # FP64 FMA per SM per clock on GB300 (1.26 TFLOP/s nomin
 LAUNCHES_PER_STEP = 16
 # DRAM read + write bytes of the two k_fill launches of one learned step at N = 2^19
 # (22,423 supernodes), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
-FILL_DRAM_BYTES_N2E19 = 17165568 + 260083456 + 9680384 + 119601408
+FILL_DRAM_BYTES_N2E19 = 16787200 + 259102720 + 10191616 + 116883456
 FILL_GROUPS_N2E19 = 22423
 
 

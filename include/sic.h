@@ -579,6 +579,16 @@ sic_status sic_selftest_fp64_math(sic_handle* h, const sic_kernel* kp, const dou
                                   double* out_sqrt, double* out_rsqrt, double* out_exp, double* out_kernel,
                                   void* stream);
 
+/* The fill's integer arithmetic on independent inputs (not part of the paper), for tests:
+ * d2[i] = the squared distance between points pa[i] and pb[i] (n x dim, dim 1..3) from their
+ * fixed-point coordinates (each dimension at the larger of the two points' exponents; exact
+ * differences and squares, one rounding), dot[i] = sum_j ga[i][j] gb[i][j] of two 4-vectors
+ * (n x 4) in the panels' fixed-point form (53-bit significands at each vector's largest
+ * exponent, exact 32 x 32-bit products, the sum truncated below 2^-51 of the largest product).
+ * All pointers [device]; d2, dot: n doubles each. */
+sic_status sic_selftest_fixed_point(sic_handle* h, const double* pa, const double* pb, int64_t n, int32_t dim,
+                                    double* d2, const double* ga, const double* gb, double* dot, void* stream);
+
 /* Evaluates the double-float Matern of the fill (not part of the paper): out[i] = the kernel
  * of *kp (no nugget) between points pa[i] and pb[i] (n x dim each, [device]), computed as the
  * fill computes its entries -- coordinates relative to an origin (here pa[i]) split into

@@ -624,9 +624,57 @@ __global__ void k_matern_df(KP<double> kp, int dim, const double* __restrict__ p
     }
 }
 
+// the fill's integer routines on independent inputs: d2[i] = fx_dist2 of points pa[i], pb[i]
+// (each dimension's fixed-point exponent the larger of the two points'), dot[i] = fx_dot of the
+// 4-vectors ga[i], gb[i] (each stored by fx_row_store); one thread per i
+__global__ void k_fixed_point(const double* __restrict__ pa, const double* __restrict__ pb, long long n, int dim,
+                              double* __restrict__ d2, const double* __restrict__ ga, const double* __restrict__ gb,
+                              double* __restrict__ dot) {
+    __shared__ __align__(16) int fx[9 * 2 * 256];  // two rows per thread, ld = 512
+    __shared__ long long xf[3 * 512];
+    const int t = threadIdx.x;
+    for (long long i = blockIdx.x * 256LL + t; i - t < n; i += 256LL * gridDim.x) {
+        const bool live = i < n;
+        int E[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            const double a = live ? pa[i * dim + d] : 0.0, b = live ? pb[i * dim + d] : 0.0;
+            E[d] = max((int)(((unsigned)__double2hiint(a) >> 20) & 0x7ffu), (int)(((unsigned)__double2hiint(b) >> 20) & 0x7ffu));
+            xf[d * 512 + 2 * t] = fx_coord(a, E[d]);
+            xf[d * 512 + 2 * t + 1] = fx_coord(b, E[d]);
+        }
+        double g1[4], g2[4];
+        for (int j = 0; j < 4; ++j) {
+            g1[j] = live ? ga[i * 4 + j] : 0.0;
+            g2[j] = live ? gb[i * 4 + j] : 0.0;
+        }
+        fx_row_store<4>(g1, fx, 512, 2 * t);
+        fx_row_store<4>(g2, fx, 512, 2 * t + 1);
+        __syncthreads();
+        if (live) {
+            d2[i] = fx_dist2(xf, 512, dim, 2 * t, 2 * t + 1, E[0], E[1], E[2]);
+            dot[i] = fx_dot<4>(fx, 512, 2 * t, 2 * t + 1);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- entry points --
+
+extern "C" sic_status sic_selftest_fixed_point(sic_handle* h, const double* pa, const double* pb, int64_t n,
+                                               int32_t dim, double* d2, const double* ga, const double* gb,
+                                               double* dot, void* stream) {
+    if (!h || n < 0 || dim < 1 || dim > 3 || (n > 0 && (!pa || !pb || !d2 || !ga || !gb || !dot)))
+        return SIC_ERR_INVALID;
+    if (n == 0) return SIC_OK;
+    SIC_CUDA_TRY(cudaSetDevice(h->device));
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4LL * h->num_sms) blocks = 4LL * h->num_sms;
+    k_fixed_point<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(pa, pb, n, dim, d2, ga, gb, dot);
+    SIC_CUDA_TRY(cudaGetLastError());
+    return SIC_OK;
+}
 
 extern "C" sic_status sic_selftest_matern_df(sic_handle* h, const sic_kernel* kp, const double* pa, const double* pb,
                                              int64_t n, double* out, void* stream) {

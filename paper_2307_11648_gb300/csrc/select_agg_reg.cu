@@ -137,12 +137,20 @@ __device__ __forceinline__ void acc_mirror(float (&a)[4], const float* __restric
 __global__ void __launch_bounds__(32 * LP_WARPS) k_agg_target_chol(const double* __restrict__ pts, long long n,
                                                                     int dim, KP<float> kp,
                                                                     const long long* __restrict__ grp_ptr,
-                                                                    long long n_grp, float* __restrict__ ws) {
+                                                                    long long n_grp, float* __restrict__ ws,
+                                                                    unsigned long long* __restrict__ ctr) {
     __shared__ __align__(16) float lsm[LP_WARPS][RM * RPM + 3 * RM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float* Lp = lsm[w];
     float* XP = Lp + RM * RPM;
-    for (long long g = (long long)blockIdx.x * LP_WARPS + w; g < n_grp; g += (long long)gridDim.x * LP_WARPS) {
+    // each warp takes its next group from a work counter zeroed before the launch (the
+    // groups' m^3 / 6 costs differ by a factor of up to 512)
+    auto fetch = [&]() -> long long {
+        unsigned long long v = 0ULL;
+        if (lane == 0) v = atomicAdd(ctr, 1ULL);
+        return (long long)__shfl_sync(0xffffffffu, v, 0);
+    };
+    for (long long g = fetch(); g < n_grp; g = fetch()) {
         const long long g0 = grp_ptr[g];
         const int m = (int)(grp_ptr[g + 1] - g0);
         float* out = ws + g * (long long)LP_SLOT;
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_agg_target_cols(const double* __res
                                                               long long n_grp, const long long* __restrict__ cand_ptr,
                                                               const int32_t* __restrict__ cand_idx,
                                                               const float* __restrict__ lp_ws, float* __restrict__ f2p,
-                                                              int max_m) {
+                                                              int max_m, unsigned long long* __restrict__ ctr) {
     extern __shared__ __align__(16) float smc[];
     float* Lp = smc;                  // [RM][RPM]
     float* rLp = Lp + RM * RPM;       // [RM]
@@ -235,7 +243,17 @@ __global__ void __launch_bounds__(TC_ROWS) k_agg_target_cols(const double* __res
     constexpr int CH = NT >= TC_ROWS ? NT / TC_ROWS : 1;  // row chunks per group
     const int tid = threadIdx.x;
     const long long G0 = grp_ptr[0];
-    for (long long it = blockIdx.x; it < n_grp * CH; it += gridDim.x) {
+    // items (group, row chunk) from a work counter zeroed before the launch: the groups' costs
+    // differ with their sizes (s_next double-buffered, one barrier per fetch)
+    __shared__ long long s_next[2];
+    int nb_ = 0;
+    auto fetch = [&]() -> long long {
+        nb_ ^= 1;
+        if (tid == 0) s_next[nb_] = (long long)atomicAdd(ctr, 1ULL);
+        __syncthreads();
+        return s_next[nb_];
+    };
+    for (long long it = fetch(); it < n_grp * CH; it = fetch()) {
         const long long g = it / CH;
         const int ch = (int)(it % CH);
         const long long g0 = grp_ptr[g];
@@ -315,7 +333,7 @@ __global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
     const long long* __restrict__ grp_ptr, long long n_grp, const long long* __restrict__ cand_ptr,
     const int32_t* __restrict__ cand_idx, int k, int max_m, int32_t* __restrict__ sel_idx,
     int32_t* __restrict__ sel_count, const float* __restrict__ lp_ws, const float* __restrict__ f2p,
-    double* __restrict__ gain, DevStatus* st) {
+    double* __restrict__ gain, unsigned long long* __restrict__ ctr, DevStatus* st) {
     constexpr int LDX = NT + RM;      // staged coordinates: candidates then targets
     constexpr int NW = NT / 32;       // warps
     extern __shared__ __align__(16) float smf[];
@@ -333,7 +351,17 @@ __global__ void __launch_bounds__(NT, RNT / NT) k_select_agg_reg(
     const float NEG = -INFINITY;
     const float diag = kp.s2 + kp.nugget;
 
-    for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
+    // groups from a work counter zeroed before the launch, so that the CTAs finish together
+    // whatever the groups' sizes (s_next double-buffered, one barrier per fetch)
+    __shared__ long long s_next[2];
+    int nb_ = 0;
+    auto fetch = [&]() -> long long {
+        nb_ ^= 1;
+        if (tid == 0) s_next[nb_] = (long long)atomicAdd(ctr, 1ULL);
+        __syncthreads();
+        return s_next[nb_];
+    };
+    for (long long g = fetch(); g < n_grp; g = fetch()) {
         const long long g0 = grp_ptr[g];
         const int m = (int)(grp_ptr[g + 1] - g0);
         const long long b0 = cand_ptr[g];
@@ -525,9 +553,14 @@ bool agg_reg_applies(sic_precision prec, int max_cand, int max_m, int k) {
 
 // the targets' factors (LP_SLOT floats per group), then the targets' columns of every
 // candidate row (at most n_grp * max_m positions of RNT rows)
-size_t agg_reg_workspace(long long n_grp, int max_m) {
+static size_t agg_reg_floats_bytes(long long n_grp, int max_m) {
     const long long g = n_grp > 0 ? n_grp : 1;
-    return sizeof(float) * ((size_t)LP_SLOT * (size_t)g + (size_t)g * (size_t)max_m * RNT);
+    return (sizeof(float) * ((size_t)LP_SLOT * (size_t)g + (size_t)g * (size_t)max_m * RNT) + 15) & ~(size_t)15;
+}
+
+// ... and three work counters (the selection, the targets' columns, the targets' factors)
+size_t agg_reg_workspace(long long n_grp, int max_m) {
+    return agg_reg_floats_bytes(n_grp, max_m) + 3 * sizeof(unsigned long long);
 }
 
 sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const sic_kernel* kp,
@@ -538,8 +571,12 @@ sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const s
     const KP<float> kpf = make_kp<float>(*kp);
     float* lp = (float*)ws;
     float* f2p = lp + (size_t)LP_SLOT * (size_t)(n_grp > 0 ? n_grp : 1);
+    unsigned long long* ctr =
+        reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ws) + agg_reg_floats_bytes(n_grp, max_m));
+    SIC_CUDA_TRY(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), s));
     const int lgrid = persistent_grid(h, k_agg_target_chol, 32 * LP_WARPS, 0, (n_grp + LP_WARPS - 1) / LP_WARPS);
-    k_agg_target_chol<<<lgrid, 32 * LP_WARPS, 0, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp, lp);
+    k_agg_target_chol<<<lgrid, 32 * LP_WARPS, 0, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp, lp,
+                                                      ctr + 2);
     // 128 threads (two groups per SM) when every list has at most 128 candidates, unless the
     // autotuner chose 256 for this bucket (each row's arithmetic is the same either way)
     int nt = max_cand <= 128 ? 128 : RNT;
@@ -551,14 +588,14 @@ sic_status launch_agg_reg(sic_handle* h, const double* pts, long long n, const s
     SIC_CUDA_TRY(cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     const int cgrid = persistent_grid(h, cols, TC_ROWS, TC_SMEM, n_grp * (nt >= TC_ROWS ? nt / TC_ROWS : 1));
     cols<<<cgrid, TC_ROWS, TC_SMEM, s>>>(pts, n, kp->dim, kpf, (const long long*)grp_ptr, n_grp,
-                                          (const long long*)cand_ptr, cand_idx, lp, f2p, max_m);
+                                          (const long long*)cand_ptr, cand_idx, lp, f2p, max_m, ctr + 1);
     auto kern = nt == 128 ? k_select_agg_reg<128> : k_select_agg_reg<RNT>;
     const size_t smem = sizeof(float) * ((size_t)nt * RP * 2 + (size_t)nt * RPM + 3 * (size_t)(nt + RM));
     SIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = persistent_grid(h, kern, nt, smem, n_grp > 0 ? n_grp : 1);
     kern<<<grid, nt, smem, s>>>(pts, n, kp->dim, kpf, (float)sic_floor_of(kp), (const long long*)grp_ptr, n_grp,
                                 (const long long*)cand_ptr, cand_idx, k, max_m, sel_idx, sel_count, lp, f2p, gain,
-                                h->d_status);
+                                ctr, h->d_status);
     SIC_CUDA_TRY(cudaGetLastError());
     return SIC_OK;
 }

@@ -35,7 +35,7 @@ EXPORTS = [
     "sic_build_factor", "sic_prep_partition", "sic_factor_nnz_range", "sic_build_factor_range", "sic_sum_fixed",
     "sic_apply_factor_workspace", "sic_apply_factor",
     "sic_matern_matvec", "sic_pcg_workspace", "sic_pcg_solve", "sic_selftest_wait_timeout",
-    "sic_selftest_fp64_math", "sic_selftest_matern_df",
+    "sic_selftest_fp64_math", "sic_selftest_matern_df", "sic_selftest_fixed_point",
     "sic_mlp_param_count", "sic_proposal_features", "sic_proposal_score",
     "sic_proposal_topk", "sic_proposal_labels", "sic_mlp_train_workspace", "sic_mlp_grads", "sic_adamw_step",
 ]
@@ -126,6 +126,7 @@ def lib():
             "sic_selftest_wait_timeout": (st, [vp, i64, vp, vp]),
             "sic_selftest_fp64_math": (st, [vp, pk, vp, i64, vp, vp, vp, vp, vp]),
             "sic_selftest_matern_df": (st, [vp, pk, vp, vp, i64, vp, vp]),
+            "sic_selftest_fixed_point": (st, [vp, vp, vp, i64, i32, vp, vp, vp, vp, vp]),
             "sic_pcg_workspace": (st, [i64, i32, C.POINTER(sz)]),
             "sic_pcg_solve": (st, [vp, vp, i64, pk, d, st, vp, vp, vp, vp, vp, i32, d, i32, vp, vp, vp, sz, vp]),
             "sic_mlp_param_count": (i32, []),
@@ -700,6 +701,22 @@ def selftest_fp64_math(h: Handle, kp: Kernel, x, stream=None):
                                         *[_dptr(o, torch.float64, "out") for o in outs], _stream(stream)),
            "sic_selftest_fp64_math", h)
     return outs
+
+
+def selftest_fixed_point(h: Handle, pa, pb, ga, gb, stream=None):
+    """The fill's integer routines: squared distances between the rows of pa and pb (CUDA float64,
+    n x dim) and dot products of the rows of ga and gb (n x 4), as the fill forms them."""
+    import torch
+    pa, pb, ga, gb = pa.contiguous(), pb.contiguous(), ga.contiguous(), gb.contiguous()
+    n = pa.shape[0]
+    d2 = torch.empty(n, dtype=torch.float64, device=pa.device)
+    dot = torch.empty(n, dtype=torch.float64, device=pa.device)
+    _check(lib().sic_selftest_fixed_point(h.ptr, _dptr(pa, torch.float64, "pa"), _dptr(pb, torch.float64, "pb"), n,
+                                          pa.shape[1], _dptr(d2, torch.float64, "d2"), _dptr(ga, torch.float64, "ga"),
+                                          _dptr(gb, torch.float64, "gb"), _dptr(dot, torch.float64, "dot"),
+                                          _stream(stream)),
+           "sic_selftest_fixed_point", h)
+    return d2, dot
 
 
 def selftest_matern_df(h: Handle, kp: Kernel, pa, pb, stream=None):

@@ -123,3 +123,47 @@ def test_double_float_matern_against_the_oracle(env, oracle_lib, dim, nu_x2, ell
     print(f"dim {dim} nu {nu_x2}/2 ell {ell}: max abs err {err.max() / variance:.3e} of the variance, "
           f"max rel err where the entry > 1e-3: {np.max(err[ref > 1e-3 * variance] / ref[ref > 1e-3 * variance]):.3e}")
     assert err.max() <= 2e-14 * variance
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fixed_point_routines_against_exact_rationals(env, dim):
+    """The fill's integer arithmetic: squared distances from fixed-point coordinates must be the
+    correctly rounded exact value (0.5 ulp; differences and squares are exact in 128 bits), and
+    the panels' 4-term dot products of fixed-point rows within 12 * 2^-52 max|a| max|b| of the
+    exact sum (each value truncated below 2^-52 of its row's largest, the sum below 2^-51 of
+    the largest product)."""
+    from fractions import Fraction as F
+    torch, sic, h = env
+    n = 20000
+    u = synthetic.uniform(91, dim, n * dim).reshape(n, dim)
+    direc = synthetic.normal(92, n * dim).reshape(n, dim)
+    sep = np.exp(np.log(1e-9) + synthetic.uniform(93, 0, n) * (np.log(1.0) - np.log(1e-9)))
+    pa = u
+    pb = u + direc * sep[:, None]
+    pb[::17] = pa[::17]                     # coincident points
+    pa[::29, 0] = 3e-6 * synthetic.uniform(94, 0, len(pa[::29]))   # coordinates near zero
+    pb[::29, 0] = pa[::29, 0] + 1e-7
+    g = synthetic.normal(95, n * 8).reshape(n, 8)
+    mag = np.exp(np.log(1e-12) + synthetic.uniform(96, 0, n * 8).reshape(n, 8) * (np.log(10.0) - np.log(1e-12)))
+    g = g * mag
+    g[::13, 1] = 0.0
+    ga, gb = g[:, :4].copy(), g[:, 4:].copy()
+    d2, dot = sic.selftest_fixed_point(h, torch.from_numpy(pa).cuda(), torch.from_numpy(pb).cuda(),
+                                       torch.from_numpy(ga).cuda(), torch.from_numpy(gb).cuda())
+    h.sync()
+    d2 = d2.cpu().numpy()
+    dot = dot.cpu().numpy()
+    worst_d2 = worst_dot = 0.0
+    for i in range(n):
+        ex = sum((F(float(a)) - F(float(b))) ** 2 for a, b in zip(pa[i], pb[i]))
+        if ex == 0:
+            assert d2[i] == 0.0
+        else:
+            worst_d2 = max(worst_d2, float(abs(F(float(d2[i])) - ex) / F(math.ulp(float(ex)))))
+        exd = sum(F(float(a)) * F(float(b)) for a, b in zip(ga[i], gb[i]))
+        bound = 12 * 2.0 ** -52 * np.max(np.abs(ga[i])) * np.max(np.abs(gb[i]))
+        err = float(abs(F(float(dot[i])) - exd))
+        worst_dot = max(worst_dot, err / bound if bound > 0 else (0.0 if err == 0 else math.inf))
+    print(f"dim {dim}: d2 worst {worst_d2:.3f} ulp; dot worst {worst_dot:.3f} of the bound")
+    assert worst_d2 <= 0.5
+    assert worst_dot <= 1.0
