@@ -39,6 +39,11 @@ constexpr int LP_PACKED = RM * (RM + 1) / 2;
 constexpr int LP_SLOT = LP_PACKED + RM + 4;
 constexpr int LP_WARPS = 2;  // groups per CTA in the targets' Cholesky kernel (36 KB static smem)
 
+// Two FP32 FMAs in one instruction (sm_100+ packed f32x2): lane-wise exactly the two fmaf with
+// round to nearest, so the dot products below give the same bits as their scalar form with half
+// the FMA instructions.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 __device__ __forceinline__ unsigned score_key(float s) {
     const unsigned b = __float_as_uint(s);
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // monotone in s; 0 is below every key
@@ -48,7 +53,7 @@ __device__ __forceinline__ unsigned score_key(float s) {
 // piv is finite everywhere)
 template <int N>
 __device__ __forceinline__ float reg_dot(float acc, const float (&r)[N], const float* __restrict__ piv, int len) {
-    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float2 a01 = make_float2(acc, 0.f), a23 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int b = 0; b < N / 16; ++b) {
         if (16 * b < len) {
@@ -56,44 +61,38 @@ __device__ __forceinline__ float reg_dot(float acc, const float (&r)[N], const f
             for (int c = 0; c < 4; ++c) {
                 const int e = 16 * b + 4 * c;
                 const float4 p = *reinterpret_cast<const float4*>(piv + e);
-                acc = fmaf(-r[e], p.x, acc);
-                a1 = fmaf(-r[e + 1], p.y, a1);
-                a2 = fmaf(-r[e + 2], p.z, a2);
-                a3 = fmaf(-r[e + 3], p.w, a3);
+                a01 = fma2(make_float2(-r[e], -r[e + 1]), make_float2(p.x, p.y), a01);
+                a23 = fma2(make_float2(-r[e + 2], -r[e + 3]), make_float2(p.z, p.w), a23);
             }
         }
     }
-    return (acc + a1) + (a2 + a3);
+    return (a01.x + a01.y) + (a23.x + a23.y);
 }
 
 // acc - r . piv over the first NB 16-element blocks (static)
 template <int NB, int N>
 __device__ __forceinline__ float dot_blocks(float acc, const float (&r)[N], const float* __restrict__ piv) {
-    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float2 a01 = make_float2(acc, 0.f), a23 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int e = 0; e < 16 * NB; e += 4) {
         const float4 p = *reinterpret_cast<const float4*>(piv + e);
-        acc = fmaf(-r[e], p.x, acc);
-        a1 = fmaf(-r[e + 1], p.y, a1);
-        a2 = fmaf(-r[e + 2], p.z, a2);
-        a3 = fmaf(-r[e + 3], p.w, a3);
+        a01 = fma2(make_float2(-r[e], -r[e + 1]), make_float2(p.x, p.y), a01);
+        a23 = fma2(make_float2(-r[e + 2], -r[e + 3]), make_float2(p.z, p.w), a23);
     }
-    return (acc + a1) + (a2 + a3);
+    return (a01.x + a01.y) + (a23.x + a23.y);
 }
 
 // acc - own . piv over one 16-element block, both read from shared memory
 __device__ __forceinline__ float dot_mirror(float acc, const float* __restrict__ own, const float* __restrict__ piv) {
-    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float2 a01 = make_float2(acc, 0.f), a23 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const float4 r = *reinterpret_cast<const float4*>(own + 4 * c);
         const float4 p = *reinterpret_cast<const float4*>(piv + 4 * c);
-        acc = fmaf(-r.x, p.x, acc);
-        a1 = fmaf(-r.y, p.y, a1);
-        a2 = fmaf(-r.z, p.z, a2);
-        a3 = fmaf(-r.w, p.w, a3);
+        a01 = fma2(make_float2(-r.x, -r.y), make_float2(p.x, p.y), a01);
+        a23 = fma2(make_float2(-r.z, -r.w), make_float2(p.z, p.w), a23);
     }
-    return (acc + a1) + (a2 + a3);
+    return (a01.x + a01.y) + (a23.x + a23.y);
 }
 
 // Sums of a step's products of the own factor rows with the pivot's rows, a[0..3] += four
@@ -103,14 +102,17 @@ __device__ __forceinline__ float dot_mirror(float acc, const float* __restrict__
 // over the 16-element blocks B0 .. NB-1 (static)
 template <int B0, int NB, int N>
 __device__ __forceinline__ void acc_blocks(float (&a)[4], const float (&r)[N], const float* __restrict__ piv) {
+    float2 a01 = make_float2(a[0], a[1]), a23 = make_float2(a[2], a[3]);
 #pragma unroll
     for (int e = 16 * B0; e < 16 * NB; e += 4) {
         const float4 p = *reinterpret_cast<const float4*>(piv + e);
-        a[0] = fmaf(r[e], p.x, a[0]);
-        a[1] = fmaf(r[e + 1], p.y, a[1]);
-        a[2] = fmaf(r[e + 2], p.z, a[2]);
-        a[3] = fmaf(r[e + 3], p.w, a[3]);
+        a01 = fma2(make_float2(r[e], r[e + 1]), make_float2(p.x, p.y), a01);
+        a23 = fma2(make_float2(r[e + 2], r[e + 3]), make_float2(p.z, p.w), a23);
     }
+    a[0] = a01.x;
+    a[1] = a01.y;
+    a[2] = a23.x;
+    a[3] = a23.y;
 }
 
 // the current block: entries below `len` (< 16) of the own row and the pivot's, from shared
@@ -122,10 +124,12 @@ __device__ __forceinline__ void acc_mirror(float (&a)[4], const float* __restric
         if (4 * c < len) {
             const float4 r = *reinterpret_cast<const float4*>(own + 4 * c);
             const float4 p = *reinterpret_cast<const float4*>(piv + 4 * c);
-            a[0] = fmaf(r.x, p.x, a[0]);
-            a[1] = fmaf(r.y, p.y, a[1]);
-            a[2] = fmaf(r.z, p.z, a[2]);
-            a[3] = fmaf(r.w, p.w, a[3]);
+            const float2 a01 = fma2(make_float2(r.x, r.y), make_float2(p.x, p.y), make_float2(a[0], a[1]));
+            const float2 a23 = fma2(make_float2(r.z, r.w), make_float2(p.z, p.w), make_float2(a[2], a[3]));
+            a[0] = a01.x;
+            a[1] = a01.y;
+            a[2] = a23.x;
+            a[3] = a23.y;
         }
     }
 }
