@@ -4,7 +4,7 @@
 //   layer 1  D = X W1 + b1  M = 128 rows, N = 128 hidden, K = 16: 8 features, a constant
 //            1 whose weight row is b1, 7 zeros (the bias comes out of the MMA)
 //   GELU     read D from TMEM (tcgen05.ld, thread = row), 2 gelu(D) (tanh form, see
-//            gelu2_f), round to BF16 and store as the next A operand in shared memory
+//            gelu2_f2), round to BF16 and store as the next A operand in shared memory
 //   layer 2  D = (2 H1) (W2 / 2)   M = 128, N = 128, K = 128 (8 MMAs of K = 16)
 //   head     read D (thread = row: the whole hidden row is in the thread's registers),
 //            s = sum_j 2 gelu(D_j + b2_j) (w3_j / 2) + b3 -- no cross-thread reduction.
@@ -108,10 +108,14 @@ __device__ __forceinline__ float tanh_hw(float x) {
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// twice the GELU: z (1 + tanh(u)), the 1/2 being folded into the consumer's weights
-__device__ __forceinline__ float gelu2_f(float z) {
-    const float u = z * fmaf(0.0356774081f, z * z, 0.7978845608f);
-    return fmaf(z, tanh_hw(u), z);
+// twice the GELU of a pair: z (1 + tanh(u)), u = z (0.7978845608 + 0.0356774081 z^2), the 1/2
+// being folded into the consumer's weights; packed FP32 operations (sm_100+ f32x2: lane-wise
+// the same round-to-nearest operations as the scalar form, half the instructions)
+__device__ __forceinline__ float2 gelu2_f2(float2 z) {
+    const float2 w = __ffma2_rn(make_float2(0.0356774081f, 0.0356774081f), __fmul2_rn(z, z),
+                                make_float2(0.7978845608f, 0.7978845608f));
+    const float2 u = __fmul2_rn(z, w);
+    return __ffma2_rn(z, make_float2(tanh_hw(u.x), tanh_hw(u.y)), z);
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -199,8 +203,10 @@ __global__ void __launch_bounds__(TC_NT) k_mlp_tc(const float* __restrict__ X, l
             tmem_ld32(lane_addr + c * 32, v);
             uint32_t pk[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                pk[j] = pack2(gelu2_f(v[2 * j]), gelu2_f(v[2 * j + 1]));
+            for (int j = 0; j < 16; ++j) {
+                const float2 g = gelu2_f2(make_float2(v[2 * j], v[2 * j + 1]));
+                pk[j] = pack2(g.x, g.y);
+            }
 #pragma unroll
             for (int g = 0; g < 4; ++g)
                 *reinterpret_cast<uint4*>(sm + SA2 + core_off(tid, c * 32 + g * 8, HID)) =
@@ -232,7 +238,12 @@ __global__ void __launch_bounds__(TC_NT) k_mlp_tc(const float* __restrict__ X, l
             float v[32];
             tmem_ld32(lane_addr + c * 32, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) s = fmaf(gelu2_f(v[j] + sb2[c * 32 + j]), sw3[c * 32 + j], s);
+            for (int j = 0; j < 32; j += 2) {
+                const float2 g = gelu2_f2(__fadd2_rn(make_float2(v[j], v[j + 1]),
+                                                     make_float2(sb2[c * 32 + j], sb2[c * 32 + j + 1])));
+                s = fmaf(g.x, sw3[c * 32 + j], s);
+                s = fmaf(g.y, sw3[c * 32 + j + 1], s);
+            }
         }
         if (r < rows) out[r] = s + b3;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
