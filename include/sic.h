@@ -199,7 +199,9 @@ sic_status sic_select_columns(sic_handle* h, const double* pts, int64_t n, const
  * (count <= max_cand <= 4096).  Candidates are scored by var_j / var_j|P, the ratio
  * of their conditional variance given the picks to that given the picks and the
  * targets (eq. greedy_mult).  sel_idx[n_grp * k], sel_count[n_grp] [device] as in
- * sic_select_columns.  1 <= k <= 128.  grp_ptr, cand_ptr [device]. */
+ * sic_select_columns.  1 <= k <= 128.  grp_ptr, cand_ptr [device].  The workspace
+ * (sic_select_aggregated_workspace bytes, [device]) also holds the launches' work counters,
+ * which the call zeroes on the stream itself; one call at a time per workspace. */
 sic_status sic_select_aggregated_workspace(sic_handle* h, int64_t n_grp, int32_t max_cand, int32_t max_m,
                                            int32_t k, sic_precision prec, size_t* bytes);
 sic_status sic_select_aggregated(sic_handle* h, const double* pts, int64_t n, const sic_kernel* kp,
@@ -358,7 +360,8 @@ sic_status sic_factor_nnz_noalloc(sic_handle* h, const int64_t* grp_ptr, int64_t
  * divergence of the factor is (sum_logv - logdet Theta) / 2 (eq. obj_chol).
  * grp_ptr NULL means single columns (n_grp = n).  max_m bounds the group size (1
  * without groups, <= 64).  Needs sic_build_factor_workspace bytes of ws (the fixed-order sum's
- * partials and the launches' work counters, which the call zeroes on the stream itself). */
+ * partials and the launches' work counters, which the call zeroes on the stream itself; one
+ * call at a time per workspace). */
 
 sic_status sic_build_factor_workspace(int64_t n, size_t* bytes);
 /* Autotuned variant (this library's launch tuning; the paper has no counterpart): the same
