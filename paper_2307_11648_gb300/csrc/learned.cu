@@ -33,6 +33,25 @@ __device__ __forceinline__ float dgelu_f(float z) {
 
 // ------------------------------------------------------------------ features --
 
+// The Matern (no nugget) at two distances r in packed FP32 pairs: t = sqrt(2 nu) r / ell,
+// e^-t = 2^(-t log2 e) by the hardware 2^x, s2 e^-t (nu = 1/2), s2 (1 + t) e^-t (3/2),
+// s2 ((1 + t) + t^2 / 3) e^-t (5/2)
+__device__ __forceinline__ float ex2_hw(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 matern_f2(const KP<float>& k, float2 r) {
+    const float2 t = __fmul2_rn(make_float2(k.c_over_ell, k.c_over_ell), r);
+    const float2 l = __fmul2_rn(t, make_float2(-1.4426950408889634f, -1.4426950408889634f));
+    const float2 e = make_float2(ex2_hw(l.x), ex2_hw(l.y));
+    const float2 s2 = make_float2(k.s2, k.s2);
+    if (k.nu_x2 == 1) return __fmul2_rn(s2, e);
+    float2 p = __fadd2_rn(make_float2(1.f, 1.f), t);
+    if (k.nu_x2 != 3) p = __ffma2_rn(__fmul2_rn(t, t), make_float2(1.f / 3.f, 1.f / 3.f), p);
+    return __fmul2_rn(__fmul2_rn(s2, p), e);
+}
+
 __global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts, long long n, int dim, KP<float> kp,
                                                   const long long* __restrict__ grp_ptr, long long n_grp,
                                                   const long long* __restrict__ cand_ptr,
@@ -98,10 +117,30 @@ __global__ void __launch_bounds__(256) k_features(const double* __restrict__ pts
             for (int d = 0; d < 3; ++d) x[d] = (d < dim) ? (float)(pts[p * dim + d] - org[d]) : 0.f;
             float best = INFINITY, ksum = 0.f;
             int ab = 0;
-            for (int a = 0; a < m; ++a) {
-                float dx = x[0] - mx[a * 3], dy = x[1] - mx[a * 3 + 1], dz = x[2] - mx[a * 3 + 2];
-                float d2 = dx * dx + dy * dy + dz * dz;
-                ksum += matern<float>(kp, d2 > 1e-30f ? d2 * rsqrtf(d2) : 0.f);  // hardware rsqrt, ~2 ulp
+            // members two at a time in packed FP32 pairs (sm_100+ f32x2: half the instructions),
+            // the same operations lane-wise as the scalar tail; K summed and the nearest member
+            // taken in member order (lowest index on ties)
+            const float2 nx = make_float2(-x[0], -x[0]), ny = make_float2(-x[1], -x[1]),
+                         nz = make_float2(-x[2], -x[2]);
+            int a = 0;
+            for (; a + 1 < m; a += 2) {
+                const float2 dx = __fadd2_rn(make_float2(mx[a * 3], mx[a * 3 + 3]), nx);
+                const float2 dy = __fadd2_rn(make_float2(mx[a * 3 + 1], mx[a * 3 + 4]), ny);
+                const float2 dz = __fadd2_rn(make_float2(mx[a * 3 + 2], mx[a * 3 + 5]), nz);
+                const float2 d2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                const float2 v = matern_f2(kp, make_float2(d2.x > 1e-30f ? d2.x * rsqrtf(d2.x) : 0.f,
+                                                           d2.y > 1e-30f ? d2.y * rsqrtf(d2.y) : 0.f));
+                ksum += v.x;
+                ksum += v.y;
+                if (d2.x < best) { best = d2.x; ab = a; }
+                if (d2.y < best) { best = d2.y; ab = a + 1; }
+            }
+            if (a < m) {
+                const float dx = __fadd_rn(mx[a * 3], -x[0]), dy = __fadd_rn(mx[a * 3 + 1], -x[1]),
+                            dz = __fadd_rn(mx[a * 3 + 2], -x[2]);
+                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                const float r = d2 > 1e-30f ? d2 * rsqrtf(d2) : 0.f;
+                ksum += matern_f2(kp, make_float2(r, r)).x;
                 if (d2 < best) { best = d2; ab = a; }
             }
             const float dmin = sqrtf(best);
