@@ -203,6 +203,21 @@ __device__ __forceinline__ double i64_scaled(long long s, int e2) {
     return __longlong_as_double((long long)(sg | ((unsigned long long)be << 52) | (((mag << z) >> 11) & 0xfffffffffffffULL)));
 }
 
+// x -= a y in double-float (x = xh + xl, a and y likewise; dfloat.cuh): the exact product of the
+// high parts and its cross terms, TwoSum of the high parts, the low parts added to its error,
+// renormalised (Fast2Sum).  Relative error about 2^-47 of the operands' magnitudes.
+__device__ __forceinline__ void df_sub_mul(float& xh, float& xl, float2 a, float yh, float yl) {
+    const float ph = __fmul_rn(a.x, yh);
+    const float pe = __fmaf_rn(a.x, yl, __fmaf_rn(a.y, yh, __fmaf_rn(a.x, yh, -ph)));
+    const float s = __fsub_rn(xh, ph);
+    const float bb = __fsub_rn(s, xh);
+    const float err = __fadd_rn(__fsub_rn(xh, __fsub_rn(s, bb)), __fsub_rn(-ph, bb));
+    const float lo = __fadd_rn(__fsub_rn(xl, pe), err);
+    const float t = __fadd_rn(s, lo);
+    xl = __fsub_rn(lo, __fsub_rn(t, s));
+    xh = t;
+}
+
 // sum_j g_ij g_lj of rows i and l: 2^52 sum Mh Mh + 2^26 sum (Mh Ml + Ml Mh) exactly in two 64-bit
 // sums of 32 x 32-bit products, scaled down by 2^52 into one 64-bit integer (the dropped fraction
 // and the omitted sum Ml Ml are below 5 units of 2^(Ei + El - 2098)), converted to FP64
@@ -463,12 +478,18 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                 }
                 __syncthreads();
             }
-            // the panel's L entries of row i (read by nobody until the next panel; the trailing
-            // update below touches only columns >= je)
+            // the panel's L entries of row i, as double-float pairs (hi, lo) in their 8-byte slots
+            // (f64_split: 48 significant bits; only the member solves read them, the factorisation
+            // reads the unscaled panel entries and the fixed-point rows; the trailing update below
+            // touches only columns >= je)
             if (worker && i > J && i < nn) {
 #pragma unroll
                 for (int c2 = 0; c2 < FILL_B; ++c2)
-                    if (J + c2 < je && J + c2 < i) G[rowi + J + c2] = lv[c2];
+                    if (J + c2 < je && J + c2 < i) {
+                        float h, l;
+                        f64_split(lv[c2], h, l);
+                        reinterpret_cast<float2*>(G)[rowi + J + c2] = make_float2(h, l);
+                    }
             }
             // the trailing matrix, entries (i, l) with je <= l <= i < nn, takes the panel's update;
             // entry (je, je) and the next pivot are the pivot warp's.  je < nn implies a full panel.
@@ -504,7 +525,11 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
         // (2p, 2p+1), one pair per warp, one member per half-warp; the right-hand side lives in
         // registers (lane h*16 + r of half h owns entries r + 16 q).  The two members' jb
         // differ by one, so each warp instruction serves both, in 16-lane instead of 32-lane
-        // granularity.
+        // granularity.  The substitution runs in double-float on the FP32 pipe (about 15 FP32
+        // instructions per multiply-add against one FP64 instruction that holds this GPU's FP64
+        // pipe for some 64 clocks per warp): its relative error, about 2^-47 per operation,
+        // stays some 1e-13 of the column at the conditioning of these blocks, against the
+        // factorisation's own rounding.
         const int npairs = (m + 1) / 2;
         const int half = lane >> 4, hl = lane & 15;
         for (int p = worker ? warp : npairs; p < npairs; p += FILL_NT / 32) {
@@ -512,20 +537,26 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
             const bool has = a < m;
             const int jb = has ? nn - 1 - a : -1;
             const int jtop = nn - 1 - 2 * p;
-            double bv[FILL_HSLOTS];
+            const float2* Lf = reinterpret_cast<const float2*>(G);  // the L entries (hi, lo)
+            float bh[FILL_HSLOTS], bl[FILL_HSLOTS];
 #pragma unroll
-            for (int q = 0; q < FILL_HSLOTS; ++q) bv[q] = (hl + 16 * q == jb) ? 1.0 : 0.0;
+            for (int q = 0; q < FILL_HSLOTS; ++q) {
+                bh[q] = (hl + 16 * q == jb) ? 1.f : 0.f;
+                bl[q] = 0.f;
+            }
 #pragma unroll
             for (int sb = FILL_HSLOTS - 1; sb >= 0; --sb) {
                 if (16 * sb > jtop) continue;
                 const int top = min(jtop, 16 * sb + 15);
                 for (int l = top; l >= 16 * sb; --l) {
-                    const double y = __shfl_sync(0xffffffffu, bv[sb], (lane & 16) | (l & 15));
+                    const int src = (lane & 16) | (l & 15);
+                    const float yh = __shfl_sync(0xffffffffu, bh[sb], src);
+                    const float yl = __shfl_sync(0xffffffffu, bl[sb], src);
                     const int rl = pk(l, 0);
 #pragma unroll
                     for (int q = 0; q <= sb; ++q) {
                         const int i = hl + 16 * q;
-                        if (i < l) bv[q] = fma(-G[rl + i], y, bv[q]);
+                        if (i < l) df_sub_mul(bh[q], bl[q], Lf[rl + i], yh, yl);
                     }
                 }
             }
@@ -537,7 +568,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                     const int i = hl + 16 * q;
                     if (i <= jb) {
                         row_idx[e0 + jb - i] = pos[i];
-                        val[e0 + jb - i] = bv[q] * sc;
+                        val[e0 + jb - i] = (f32_as_f64(bh[q]) + f32_as_f64(bl[q])) * sc;
                     }
                 }
             }
