@@ -203,18 +203,24 @@ __device__ __forceinline__ double i64_scaled(long long s, int e2) {
     return __longlong_as_double((long long)(sg | ((unsigned long long)be << 52) | (((mag << z) >> 11) & 0xfffffffffffffULL)));
 }
 
-// x -= a y in double-float (x = xh + xl, a and y likewise; dfloat.cuh): the exact product of the
-// high parts and its cross terms, TwoSum of the high parts, the low parts added to its error,
-// renormalised (Fast2Sum).  Relative error about 2^-47 of the operands' magnitudes.
-__device__ __forceinline__ void df_sub_mul(float& xh, float& xl, float2 a, float yh, float yl) {
-    const float ph = __fmul_rn(a.x, yh);
-    const float pe = __fmaf_rn(a.x, yl, __fmaf_rn(a.y, yh, __fmaf_rn(a.x, yh, -ph)));
-    const float s = __fsub_rn(xh, ph);
-    const float bb = __fsub_rn(s, xh);
-    const float err = __fadd_rn(__fsub_rn(xh, __fsub_rn(s, bb)), __fsub_rn(-ph, bb));
-    const float lo = __fadd_rn(__fsub_rn(xl, pe), err);
-    const float t = __fadd_rn(s, lo);
-    xl = __fsub_rn(lo, __fsub_rn(t, s));
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+// Two updates x -= a y in double-float (x = xh + xl, a and y likewise; dfloat.cuh), x0 -= a0 y in
+// the .x halves of xh, xl and x1 -= a1 y in the .y halves, as packed FP32x2 instructions (lane-wise
+// the roundings of the scalar operations): the exact product of the high parts and its cross
+// terms, TwoSum of the high parts, the low parts added to its error, renormalised (Fast2Sum).
+// Relative error about 2^-47 of the operands' magnitudes; a = 0 leaves the value of x unchanged.
+__device__ __forceinline__ void df_sub_mul2(float2& xh, float2& xl, float2 a0, float2 a1, float yh, float yl) {
+    const float2 ah = make_float2(a0.x, a1.x), al = make_float2(a0.y, a1.y);
+    const float2 y2 = make_float2(yh, yh), yl2 = make_float2(yl, yl);
+    const float2 ph = __fmul2_rn(ah, y2);
+    const float2 pe = __ffma2_rn(ah, yl2, __ffma2_rn(al, y2, __ffma2_rn(ah, y2, neg2(ph))));
+    const float2 s = __fadd2_rn(xh, neg2(ph));
+    const float2 bb = __fadd2_rn(s, neg2(xh));
+    const float2 err = __fadd2_rn(__fadd2_rn(xh, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(neg2(ph), neg2(bb)));
+    const float2 lo = __fadd2_rn(__fadd2_rn(xl, neg2(pe)), err);
+    const float2 t = __fadd2_rn(s, lo);
+    xl = __fadd2_rn(lo, neg2(__fadd2_rn(t, neg2(s))));
     xh = t;
 }
 
@@ -537,12 +543,15 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
             const bool has = a < m;
             const int jb = has ? nn - 1 - a : -1;
             const int jtop = nn - 1 - 2 * p;
+            // slots 2j and 2j+1 in the .x and .y halves of bh[j], bl[j] (packed updates); in the
+            // block of rows l of slot sb, the slots below sb take every row, slot sb the rows
+            // above its entry, and a slot above sb none: those get a = 0
             const float2* Lf = reinterpret_cast<const float2*>(G);  // the L entries (hi, lo)
-            float bh[FILL_HSLOTS], bl[FILL_HSLOTS];
+            float2 bh[FILL_HSLOTS / 2], bl[FILL_HSLOTS / 2];
 #pragma unroll
-            for (int q = 0; q < FILL_HSLOTS; ++q) {
-                bh[q] = (hl + 16 * q == jb) ? 1.f : 0.f;
-                bl[q] = 0.f;
+            for (int j = 0; j < FILL_HSLOTS / 2; ++j) {
+                bh[j] = make_float2((hl + 32 * j == jb) ? 1.f : 0.f, (hl + 32 * j + 16 == jb) ? 1.f : 0.f);
+                bl[j] = make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int sb = FILL_HSLOTS - 1; sb >= 0; --sb) {
@@ -550,13 +559,15 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                 const int top = min(jtop, 16 * sb + 15);
                 for (int l = top; l >= 16 * sb; --l) {
                     const int src = (lane & 16) | (l & 15);
-                    const float yh = __shfl_sync(0xffffffffu, bh[sb], src);
-                    const float yl = __shfl_sync(0xffffffffu, bl[sb], src);
+                    const float yh = __shfl_sync(0xffffffffu, (sb & 1) ? bh[sb / 2].y : bh[sb / 2].x, src);
+                    const float yl = __shfl_sync(0xffffffffu, (sb & 1) ? bl[sb / 2].y : bl[sb / 2].x, src);
                     const int rl = pk(l, 0);
 #pragma unroll
-                    for (int q = 0; q <= sb; ++q) {
-                        const int i = hl + 16 * q;
-                        if (i < l) df_sub_mul(bh[q], bl[q], Lf[rl + i], yh, yl);
+                    for (int j = 0; 2 * j <= sb; ++j) {
+                        const int i0 = hl + 32 * j, i1 = i0 + 16;
+                        const float2 a0 = (2 * j < sb || i0 < l) ? Lf[rl + i0] : make_float2(0.f, 0.f);
+                        const float2 a1 = (2 * j + 1 < sb || i1 < l) ? Lf[rl + i1] : make_float2(0.f, 0.f);
+                        df_sub_mul2(bh[j], bl[j], a0, a1, yh, yl);
                     }
                 }
             }
@@ -567,8 +578,10 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                 for (int q = 0; q < FILL_HSLOTS; ++q) {
                     const int i = hl + 16 * q;
                     if (i <= jb) {
+                        const float h = (q & 1) ? bh[q / 2].y : bh[q / 2].x;
+                        const float l = (q & 1) ? bl[q / 2].y : bl[q / 2].x;
                         row_idx[e0 + jb - i] = pos[i];
-                        val[e0 + jb - i] = (f32_as_f64(bh[q]) + f32_as_f64(bl[q])) * sc;
+                        val[e0 + jb - i] = (f32_as_f64(h) + f32_as_f64(l)) * sc;
                     }
                 }
             }
