@@ -139,7 +139,7 @@ __device__ __forceinline__ int pk_row(int e) {
 
 // Pivot of column c of the LDL^T factorisation from its final Schur complement v: D_cc = v
 // (kept on the diagonal) and d^(-1/2) by rsqrt_newton (five FP64 operations with the
-// diagonal's update) into the two-column ring piv (slot c & 1); the column is then scaled as
+// diagonal's update) into piv slot c & 3 (the panel's columns); the column is then scaled as
 // G_ic = U_ic d^(-1/2) and L_ic = G_ic d^(-1/2).  A non-positive pivot raises *bad.  The range
 // test reads the bits (no FP64 compare).
 __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* piv, int* bad) {
@@ -149,7 +149,7 @@ __device__ __forceinline__ void fill_pivot(double v, int c, double* G, double* p
         return;
     }
     G[pk(c, c)] = v;
-    piv[c & 1] = rsqrt_newton(v);
+    piv[c & 3] = rsqrt_newton(v);
 }
 
 // ---- the integer update of a panel ----
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
     double* xyz = tab + EXP_TAB;                            // 3 x nmax, while Theta is formed; then
     int* fx = reinterpret_cast<int*>(xyz);                  // the panel's rows in fixed point (16-byte aligned)
     double* G = xyz + fill_scratch_doubles(nmax);           // packed lower, nmax(nmax+1)/2
-    double* piv = G + (long long)nmax * (nmax + 1) / 2;     // d^(-1/2) of two columns (ring; 4 slots kept)
+    double* piv = G + (long long)nmax * (nmax + 1) / 2;     // d^(-1/2) of the panel's columns (slot c & 3)
     int* pos = reinterpret_cast<int*>(piv + 4);             // nmax
     int* srt = pos + nmax;                                  // k
     __shared__ int s_bad;
@@ -437,73 +437,88 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
         }
         __syncthreads();
         // blocked right-looking LDL^T factorisation Theta_RR = L D L^T in place on the packed
-        // lower triangle, in panels of FILL_B columns.  Within a panel, column by column in FP64:
-        // d_j = A_jj, L_ij = A_ij / d_j, and the panel's later columns are updated
-        // (A_il -= L_ij A_lj, flat over the worker threads).  The rows below the panel keep
-        // G_ij = A_ij d_j^(-1/2) (G = L D^(1/2)) in registers and, once the panel is complete, in
-        // fixed point; the trailing matrix then takes the panel's whole rank-FILL_B update as one
-        // integer dot product of two G rows per entry (exact products), subtracted in FP64
-        // (fx_dot): FILL_B FP64 FMAs become one FP64 addition, the products going to the integer
-        // multiply-add units.  The FP64 units are per SM sub-partition and charge a warp
-        // instruction whatever its active lanes, so the flat loops keep full warps.  The next
-        // pivot (its diagonal update, reciprocal and reciprocal square root, a chain of
-        // dependent FP64 operations) is taken by the pivot warp while the workers update the
-        // rest.
-        // Worker thread i owns row i (nn <= FILL_NT, the launcher's choice).  Within a panel the
-        // triangle keeps the panel's entries unscaled (U_lj = A_lj), so that every row owner can
-        // apply column j to its own row's later panel columns without waiting for the others
-        // (A_il -= L_ij U_lj reads row l's entry (l, j), which nobody writes during the panel);
-        // the owner of row j+1 takes the next pivot from its own updated diagonal, so a column
-        // costs one barrier.  The panel's L entries are written back after its last column.
+        // lower triangle, in panels of FILL_B columns, in FP64: d_j = A_jj, L_ij = A_ij / d_j and
+        // A_il -= L_ij U_lj within the panel (U_lj = A_lj, the panel's entries unscaled).  The
+        // rows below the panel keep G_ij = U_ij d_j^(-1/2) (G = L D^(1/2)) in fixed point; the
+        // trailing matrix then takes the panel's whole rank-FILL_B update as one integer dot
+        // product of two G rows per entry (exact products), subtracted in FP64 (fx_dot): FILL_B
+        // FP64 FMAs become one FP64 addition, the products going to the integer multiply-add
+        // units.  The FP64 units are per SM sub-partition and charge a warp instruction whatever
+        // its active lanes, so the flat loops keep full warps.
+        // The panel's diagonal block (at most FILL_B x FILL_B) is factored by the pivot warp, lane
+        // r owning the block's row r (its pivots and their reciprocal square roots are a chain of
+        // dependent FP64 operations, warp-synchronous): the next panel's block takes the current
+        // panel's update and is factored while the workers update the rest of the trailing matrix.
+        // Every worker row below the block then applies the block's columns to its own panel
+        // entries in registers (A_il -= L_ij U_lj reads the block's unscaled entries, which stay
+        // in place until the block's L entries are written back in the next phase), so that a
+        // panel costs two barriers.  Worker thread i owns row i (nn <= FILL_NT, the launcher's
+        // choice).  Same operations, in the same order, as a column-by-column elimination.
         const int i = tid;
         const int rowi = pk(i, 0);
-        double gv[FILL_B];  // G_ij = U_ij d_j^(-1/2) of the thread's row, when below the panel
-        double lv[FILL_B];  // L_ij = U_ij / d_j of the thread's row
-        if (tid == FILL_NT) fill_pivot(G[0], 0, G, piv, &s_bad);
+        double lb[FILL_B];  // pivot warp: L of the block's row `lane` (columns below it)
+        // the block [J, J + bs) (its entries final): lane r owns row J + r
+        auto factor_block = [&](int J, int bs) {
+            const int r = lane;
+            const int ib = J + r;
+            if (r == 0) fill_pivot(G[pk(J, J)], J, G, piv, &s_bad);
+            __syncwarp();
+#pragma unroll
+            for (int jj = 0; jj < FILL_B - 1; ++jj) {
+                if (jj >= bs - 1) break;
+                const int j = J + jj;
+                if (r > jj && r < bs) {
+                    const double rsd = piv[j & 3];
+                    const double uv = G[pk(ib, j)];
+                    const double g = uv * rsd;
+                    const double l = g * rsd;
+                    lb[jj] = l;
+#pragma unroll
+                    for (int c2 = jj + 1; c2 < FILL_B; ++c2)
+                        if (c2 <= r) G[pk(ib, J + c2)] = fma(-l, G[pk(J + c2, j)], G[pk(ib, J + c2)]);
+                    if (r == jj + 1) fill_pivot(G[pk(ib, ib)], ib, G, piv, &s_bad);
+                }
+                __syncwarp();
+            }
+        };
+        if (!worker) factor_block(0, min(FILL_B, nn));
         __syncthreads();
         for (int J = 0; J < nn && !s_bad; J += FILL_B) {
-            const int je = min(J + FILL_B, nn);
+            const int je = min(J + FILL_B, nn);  // je < nn implies a full panel
+            // the own row's panel entries (rows below the block): L and G by the block's columns
+            if (worker && i >= je && i < nn) {
+                double u[FILL_B], gv[FILL_B], lv[FILL_B];
 #pragma unroll
-            for (int jj = 0; jj < FILL_B; ++jj) {
-                const int j = J + jj;
-                if (j >= je || s_bad) break;  // uniform: s_bad is read after a barrier
-                const double rsd = piv[j & 1];
-                if (worker && i > j && i < nn) {
-                    const double uv = G[rowi + j];  // final
-                    const double g = uv * rsd;
-                    const double l = g * rsd;       // L_ij = U_ij / d_j
-                    lv[jj] = l;
+                for (int c = 0; c < FILL_B; ++c) u[c] = G[rowi + J + c];
+#pragma unroll
+                for (int jj = 0; jj < FILL_B; ++jj) {
+                    const double rsd = piv[jj];  // (J + jj) & 3
+                    const double g = u[jj] * rsd;
+                    const double l = g * rsd;
                     gv[jj] = g;
+                    lv[jj] = l;
 #pragma unroll
-                    for (int c2 = jj + 1; c2 < FILL_B; ++c2) {
-                        const int lc = J + c2;
-                        if (lc < je && lc <= i) G[rowi + lc] = fma(-l, G[pk(lc, j)], G[rowi + lc]);
-                    }
-                    if (i == j + 1 && i < je) fill_pivot(G[rowi + i], i, G, piv, &s_bad);
-                    if (j == je - 1 && i >= je) fx_row_store<FILL_B>(gv, fx, nmax, i);  // rows below: fixed point
+                    for (int c2 = jj + 1; c2 < FILL_B; ++c2) u[c2] = fma(-l, G[pk(J + c2, J + jj)], u[c2]);
                 }
-                __syncthreads();
-            }
-            // the panel's L entries of row i, as double-float pairs (hi, lo) in their 8-byte slots
-            // (f64_split: 48 significant bits; only the member solves read them, the factorisation
-            // reads the unscaled panel entries and the fixed-point rows; the trailing update below
-            // touches only columns >= je)
-            if (worker && i > J && i < nn) {
+                fx_row_store<FILL_B>(gv, fx, nmax, i);
+                // the L entries as double-float pairs (hi, lo) in their 8-byte slots (f64_split: 48
+                // significant bits; only the member solves read them)
 #pragma unroll
-                for (int c2 = 0; c2 < FILL_B; ++c2)
-                    if (J + c2 < je && J + c2 < i) {
-                        float h, l;
-                        f64_split(lv[c2], h, l);
-                        reinterpret_cast<float2*>(G)[rowi + J + c2] = make_float2(h, l);
-                    }
+                for (int c = 0; c < FILL_B; ++c) {
+                    float h, l;
+                    f64_split(lv[c], h, l);
+                    reinterpret_cast<float2*>(G)[rowi + J + c] = make_float2(h, l);
+                }
             }
-            // the trailing matrix, entries (i, l) with je <= l <= i < nn, takes the panel's update;
-            // entry (je, je) and the next pivot are the pivot warp's.  je < nn implies a full panel.
-            if (je < nn && !s_bad) {
-                const int nt = nn - je;
-                if (worker) {
+            __syncthreads();
+            if (worker) {
+                // the trailing matrix, entries (i, l) with je <= l <= i < nn, takes the panel's
+                // update, but for the next panel's block (the first nbt flat entries)
+                if (je < nn) {
+                    const int nt = nn - je;
+                    const int bs2 = min(FILL_B, nt), nbt = bs2 * (bs2 + 1) / 2;
                     // entry e = ii (ii + 1) / 2 + ll of the trailing triangle, stepped by FILL_NT
-                    int ii = pk_row(tid + 1), ll = tid + 1 - ii * (ii + 1) / 2;
+                    int ii = pk_row(tid + nbt), ll = tid + nbt - ii * (ii + 1) / 2;
                     while (ii < nt) {
                         const int i = je + ii, l = je + ll;
                         G[pk(i, l)] -= fx_dot<FILL_B>(fx, nmax, i, l);
@@ -513,12 +528,31 @@ __global__ void __launch_bounds__(FILL_NT + 32, fill_min_ctas(FILL_NT)) k_fill(c
                             ++ii;
                         }
                     }
-                } else if (tid == FILL_NT) {
-                    const int a = pk(je, je);
-                    fill_pivot(G[a] - fx_dot<FILL_B>(fx, nmax, je, je), je, G, piv, &s_bad);
                 }
-                __syncthreads();
+            } else {
+                // the block's L entries, as double-float pairs, now that the workers have read its
+                // unscaled entries; then the next block: its update, and its factorisation
+                const int bs = je - J;
+                if (lane < bs) {
+#pragma unroll
+                    for (int c = 0; c < FILL_B - 1; ++c)
+                        if (c < lane) {
+                            float h, l;
+                            f64_split(lb[c], h, l);
+                            reinterpret_cast<float2*>(G)[pk(J + lane, J + c)] = make_float2(h, l);
+                        }
+                }
+                if (je < nn) {
+                    const int bs2 = min(FILL_B, nn - je);
+                    if (lane < bs2 * (bs2 + 1) / 2) {
+                        const int ii = pk_row(lane), ll = lane - ii * (ii + 1) / 2;
+                        G[pk(je + ii, je + ll)] -= fx_dot<FILL_B>(fx, nmax, je + ii, je + ll);
+                    }
+                    __syncwarp();
+                    factor_block(je, bs2);
+                }
             }
+            __syncthreads();
         }
         __syncthreads();
         if (s_bad) {
