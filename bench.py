@@ -51,10 +51,13 @@ DFMA_PER_SM_CLK = 2     # FP64 FMA per SM per clock on GB300 (1.26 TFLOP/s nomin
 # k_scan_tile + k_scan_partials + k_scan_add, k_fill x 2 (two group-size classes) +
 # k_sum_tiles + k_sum_final (plus one memset node)
 LAUNCHES_PER_STEP = 16
-# DRAM read + write bytes of the two k_fill launches of one learned step at N = 2^19
-# (22,423 supernodes), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
-FILL_DRAM_BYTES_N2E19 = 16787200 + 259102720 + 10191616 + 116883456
-FILL_GROUPS_N2E19 = 22423
+# DRAM read + write bytes of the two k_fill launches, and of the selection's three launches
+# (k_agg_target_chol, k_agg_target_cols, k_select_agg_reg), of one learned step at N = 2^19
+# (22,423 supernodes), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
+# None where the kernel has changed since the capture
+FILL_DRAM_BYTES_N2E19 = 17007616 + 256420096 + 9472512 + 117424384
+SEL_DRAM_BYTES_N2E19 = 10128128 + 2330368 + 70645248 + 471728384 + 572967936 + 5294080
+GROUPS_N2E19 = 22423
 
 
 def measured_peak(key: str, fallback: float) -> float:
@@ -1054,7 +1057,7 @@ def main():
         # DRAM bytes of the two k_fill launches measured at N = 2^19, scaled by the supernode
         # count; the algorithmic bytes are the factor written (row index + value per nonzero),
         # col_ptr and log v, the points and the picks read
-        traffic = FILL_DRAM_BYTES_N2E19 * hp.n_units / FILL_GROUPS_N2E19 if FILL_DRAM_BYTES_N2E19 else None
+        traffic = FILL_DRAM_BYTES_N2E19 * hp.n_units / GROUPS_N2E19 if FILL_DRAM_BYTES_N2E19 else None
         roof = {"bound": "alu", "kernel": "k_fill (FP64 fill, both launches)", "achieved": fill_tf,
                 "peak": f64_peak, "unit": "TFLOP/s", "frac": fill_tf / f64_peak, "traffic": traffic,
                 "traffic_algorithmic": nnz * 12.0 + N * (8.0 + 8.0 + 8.0 * hp.pts.shape[1]) + hp.n_units * hp.k * 4.0,
@@ -1062,10 +1065,13 @@ def main():
                                "throughput kernel saturates at 1.6 FMA/clk/SM = 1.0 TFLOP/s)",
                 "achieved_of": "the LDL^T's and the back substitutions' multiply-adds (2 FLOPs each) per second, "
                                "FP64-equivalent: each panel's trailing update runs as exact integer products "
-                               "with one FP64 addition per entry"}
+                               "with one FP64 addition per entry, the back substitutions in double-float "
+                               "arithmetic on the FP32 pipe"}
     else:
-        roof = {"bound": "alu", "kernel": "k_select_agg<float>", "achieved": sel_tf, "peak": f32_peak,
-                "unit": "TFLOP/s", "frac": sel_tf / f32_peak, "traffic": None,
+        traffic = SEL_DRAM_BYTES_N2E19 * hp.n_units / GROUPS_N2E19 if SEL_DRAM_BYTES_N2E19 else None
+        roof = {"bound": "alu", "kernel": "FP32 supernodal selection (k_agg_target_chol + k_agg_target_cols + "
+                                          "k_select_agg_reg<256>)", "achieved": sel_tf, "peak": f32_peak,
+                "unit": "TFLOP/s", "frac": sel_tf / f32_peak, "traffic": traffic,
                 "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz (derived; measured probe 75 TFLOP/s)"}
 
     pcg = None
