@@ -204,18 +204,25 @@ __device__ __forceinline__ unsigned long long topk_key(float s, int r) {
 // histogram of the keys that match the digits chosen so far and a one-warp scan from the
 // top bin); then the list is compacted in order, keeping keys > T and, among keys == T,
 // the first `need` in list order -- the same set as sorting by (score desc, position asc).
-constexpr int TOPK_NT = 512;
-constexpr int TOPK_KPT = 4096 / TOPK_NT;  // keys per thread
+// A group is a short chain of barrier-separated phases, so the CTAs are small (4 warps) and
+// many per SM: the histograms are double-buffered (the scanning warp clears the buffer of the
+// previous pass), two barriers per pass; the compaction counts every slot's keys == T and
+// kept keys per warp in two barrier phases and writes in a third (eleven barriers a group).
+constexpr int TOPK_NT = 128;
+constexpr int TOPK_NW = TOPK_NT / 32;
+constexpr int TOPK_KPT = 4096 / TOPK_NT;  // key slots per thread (key r = tid + q TOPK_NT in slot q)
+constexpr int TOPK_RK = 8;                // slots held in registers (lists of up to 1024); later ones re-read
 
-__global__ void __launch_bounds__(TOPK_NT) k_topk_compact(const long long* __restrict__ cand_ptr,
+__global__ void __launch_bounds__(TOPK_NT, 12) k_topk_compact(const long long* __restrict__ cand_ptr,
                                                           const int32_t* __restrict__ cand_idx,
                                                           const float* __restrict__ score, long long n_grp, int top,
                                                           const long long* __restrict__ out_ptr,
                                                           int32_t* __restrict__ out_idx, DevStatus* st) {
-    __shared__ unsigned hist[256];
-    __shared__ unsigned s_digit, s_need;
-    __shared__ int warp_a[TOPK_NT / 32], warp_b[TOPK_NT / 32];
+    __shared__ unsigned hist[2][256];
+    __shared__ unsigned s_digit[2], s_need[2];
+    __shared__ int cnt_eq[TOPK_KPT][TOPK_NW], cnt_k[TOPK_KPT][TOPK_NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
         const long long b0 = cand_ptr[g];
         const int C = (int)(cand_ptr[g + 1] - b0);
@@ -228,27 +235,39 @@ __global__ void __launch_bounds__(TOPK_NT) k_topk_compact(const long long* __res
             if (tid == 0) record_error(st, SIC_ERR_UNSUPPORTED, g);
             continue;
         }
-        unsigned key[TOPK_KPT];
+        const int nq = (C + TOPK_NT - 1) / TOPK_NT;  // slots holding keys
+        unsigned key[TOPK_RK];
 #pragma unroll
-        for (int q = 0; q < TOPK_KPT; ++q) {
+        for (int q = 0; q < TOPK_RK; ++q) {
             const int r = tid + q * TOPK_NT;
             key[q] = (r < C) ? (unsigned)(topk_key(score[b0 + r], r) >> 32) : 0u;
         }
+        // slot q's key (q a compile-time index after unrolling)
+        auto kq = [&](int q) -> unsigned {
+            if (q < TOPK_RK) return key[q];
+            const int r = tid + q * TOPK_NT;
+            return (r < C) ? (unsigned)(topk_key(score[b0 + r], r) >> 32) : 0u;
+        };
+        for (int b = tid; b < 512; b += TOPK_NT) (&hist[0][0])[b] = 0u;
+        __syncthreads();
         unsigned prefix = 0, mask = 0, need = (unsigned)top;
-        for (int shift = 24; shift >= 0; shift -= 8) {
-            if (tid < 256) hist[tid] = 0;
-            __syncthreads();
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int shift = 24 - 8 * p;
+            unsigned* h = hist[p & 1];
 #pragma unroll
             for (int q = 0; q < TOPK_KPT; ++q) {
+                if (q >= nq) break;
                 const int r = tid + q * TOPK_NT;
-                if (r < C && (key[q] & mask) == prefix) atomicAdd(&hist[(key[q] >> shift) & 255u], 1u);
+                const unsigned kv = kq(q);
+                if (r < C && (kv & mask) == prefix) atomicAdd(&h[(kv >> shift) & 255u], 1u);
             }
             __syncthreads();
             if (warp == 0) {  // bins from the top: lane l holds bins 255 - 8l - i, i < 8
                 unsigned c[8], sum = 0;
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    c[i] = hist[255 - 8 * lane - i];
+                    c[i] = h[255 - 8 * lane - i];
                     sum += c[i];
                 }
                 unsigned incl = sum;
@@ -263,52 +282,72 @@ __global__ void __launch_bounds__(TOPK_NT) k_topk_compact(const long long* __res
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         if (run + c[i] >= need) {
-                            s_digit = 255u - 8u * lane - i;
-                            s_need = need - run;
+                            s_digit[p & 1] = 255u - 8u * lane - i;
+                            s_need[p & 1] = need - run;
                             break;
                         }
                         run += c[i];
                     }
                 }
+                // the previous pass's buffer (scanned before the barrier above) for the next pass
+#pragma unroll
+                for (int i = 0; i < 8; ++i) hist[(p + 1) & 1][lane + 32 * i] = 0u;
             }
             __syncthreads();
-            prefix |= s_digit << shift;
+            prefix |= s_digit[p & 1] << shift;
             mask |= 255u << shift;
-            need = s_need;
-            __syncthreads();
+            need = s_need[p & 1];
         }
-        // compaction in list order: keys > T, then the first `need` keys == T
+        // compaction in list order (slot-major: r = tid + q TOPK_NT): keys > T, then the first
+        // `need` keys == T
         const unsigned T = prefix;
-        int base = 0, eq_run = 0;
 #pragma unroll
         for (int q = 0; q < TOPK_KPT; ++q) {
-            if (q * TOPK_NT >= C) break;
-            const int r = tid + q * TOPK_NT;
-            const bool in = r < C;
-            const bool eq = in && key[q] == T;
-            const unsigned beq = __ballot_sync(0xffffffffu, eq);
-            if (lane == 0) warp_a[warp] = __popc(beq);
-            __syncthreads();
-            int eq_before = eq_run, eq_total = 0;
-            for (int w = 0; w < TOPK_NT / 32; ++w) {
-                if (w < warp) eq_before += warp_a[w];
-                eq_total += warp_a[w];
-            }
-            eq_before += __popc(beq & ((1u << lane) - 1u));
-            const bool keep = in && (key[q] > T || (eq && eq_before < (int)need));
-            const unsigned bk = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) warp_b[warp] = __popc(bk);
-            __syncthreads();
-            int before = 0, total = 0;
-            for (int w = 0; w < TOPK_NT / 32; ++w) {
-                if (w < warp) before += warp_b[w];
-                total += warp_b[w];
-            }
-            if (keep) out_idx[o0 + base + before + __popc(bk & ((1u << lane) - 1u))] = cand_idx[b0 + r];
-            base += total;
-            eq_run += eq_total;
-            __syncthreads();
+            if (q >= nq) break;
+            const unsigned beq = __ballot_sync(0xffffffffu, tid + q * TOPK_NT < C && kq(q) == T);
+            if (lane == 0) cnt_eq[q][warp] = __popc(beq);
         }
+        __syncthreads();
+        unsigned keepm = 0u;  // bit q: key slot q is kept
+        int eq_run = 0;
+#pragma unroll
+        for (int q = 0; q < TOPK_KPT; ++q) {
+            if (q >= nq) break;
+            int tot = 0, bef = 0;
+#pragma unroll
+            for (int w = 0; w < TOPK_NW; ++w) {
+                const int c = cnt_eq[q][w];
+                tot += c;
+                if (w < warp) bef += c;
+            }
+            const bool in = tid + q * TOPK_NT < C;
+            const unsigned kv = kq(q);
+            const bool eq = in && kv == T;
+            const unsigned beq = __ballot_sync(0xffffffffu, eq);
+            const bool kp = in && (kv > T || (eq && eq_run + bef + __popc(beq & lt) < (int)need));
+            if (kp) keepm |= 1u << q;
+            const unsigned bk = __ballot_sync(0xffffffffu, kp);
+            if (lane == 0) cnt_k[q][warp] = __popc(bk);
+            eq_run += tot;
+        }
+        __syncthreads();
+        int base = 0;
+#pragma unroll
+        for (int q = 0; q < TOPK_KPT; ++q) {
+            if (q >= nq) break;
+            int tot = 0, bef = 0;
+#pragma unroll
+            for (int w = 0; w < TOPK_NW; ++w) {
+                const int c = cnt_k[q][w];
+                tot += c;
+                if (w < warp) bef += c;
+            }
+            const bool kp = (keepm >> q) & 1u;
+            const unsigned bk = __ballot_sync(0xffffffffu, kp);
+            if (kp) out_idx[o0 + base + bef + __popc(bk & lt)] = cand_idx[b0 + tid + q * TOPK_NT];
+            base += tot;
+        }
+        // (the next group rewrites the counts only after its own barriers)
     }
 }
 
