@@ -224,8 +224,10 @@ __global__ void __launch_bounds__(32 * LP_WARPS) k_agg_target_chol(const double*
 // group, FP32, for k_select_agg_reg: one thread per row, one group per CTA and two CTAs per
 // SM, so that the per-row chains (m kernel entries, then a forward substitution of m steps)
 // of several groups are in flight together -- inside the selection kernel, with one group per SM,
-// they left the SM waiting.  Same arithmetic, in the same order, as the selection kernel's own
-// staging would do.  Output: group g's entry (a, r) at f2p[(g0 - G0 + a) * NT + r], g0 =
+// they left the SM waiting.  The kernel entries take the distance as d2 rsqrt(d2), as the
+// selection kernel's own entries do; each substitution step's dot product runs in 4-entry
+// chunks over two packed FP32x2 accumulators.  Output: group g's entry (a, r) at
+// f2p[(g0 - G0 + a) * NT + r], g0 =
 // grp_ptr[g], G0 = grp_ptr[0] (the groups are consecutive positions).  Rows of candidates that
 // are not valid, and groups whose targets' factor failed, are skipped (the selection kernel
 // reports them).
@@ -272,12 +274,19 @@ __global__ void __launch_bounds__(TC_ROWS) k_agg_target_cols(const double* __res
 #pragma unroll
         for (int d = 0; d < 3; ++d)
             if (d < dim) org[d] = pts[g0 * dim + d];
+        // Lp negated below the diagonal and zero from the diagonal to the end of its 4-entry chunk,
+        // so that the substitution's dot products run over whole chunks (fma(x, -l, s) = fma(-x, l, s))
         const int tri = m * (m + 1) / 2;
         for (int e = tid; e < tri; e += TC_ROWS) {
             int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
             while (i * (i + 1) / 2 > e) --i;
             while ((i + 1) * (i + 2) / 2 <= e) ++i;
-            Lp[i * RPM + (e - i * (i + 1) / 2)] = src[e];
+            const int j = e - i * (i + 1) / 2;
+            Lp[i * RPM + j] = j < i ? -src[e] : 0.f;
+        }
+        for (int e = tid; e < 4 * m; e += TC_ROWS) {
+            const int i = e >> 2, j = (i & ~3) + (e & 3);
+            if (j > i) Lp[i * RPM + j] = 0.f;
         }
         if (tid < m) {
             rLp[tid] = src[LP_PACKED + tid];
@@ -297,29 +306,24 @@ __global__ void __launch_bounds__(TC_ROWS) k_agg_target_cols(const double* __res
                     float v[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int a = min(a0 + u, m - 1);
+                        const int a = min(a0 + u, m - 1);  // (past m: a finite value, multiplied by Lp's zeros)
                         const float dx = xr - XP[a], dy = yr - XP[RM + a], dz = zr - XP[2 * RM + a];
-                        v[u] = matern<float>(kp, sqrtf(dx * dx + dy * dy + dz * dz));
+                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        v[u] = matern<float>(kp, d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
                     }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (a0 + u < m) own[a0 + u] = v[u];
+                    *reinterpret_cast<float4*>(own + a0) = make_float4(v[0], v[1], v[2], v[3]);
                 }
                 float* out = f2p + (g0 - G0) * NT + r;
                 for (int a = 0; a < m; ++a) {
                     const float* la = Lp + a * RPM;
-                    float s0 = own[a], s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                    int c = 0;
-                    for (; c + 4 <= a; c += 4) {
+                    float2 s01 = make_float2(own[a], 0.f), s23 = make_float2(0.f, 0.f);
+                    for (int c = 0; c < a; c += 4) {  // whole chunks: Lp is zero from the diagonal on
                         const float4 x4 = *reinterpret_cast<const float4*>(own + c);
                         const float4 l4 = *reinterpret_cast<const float4*>(la + c);
-                        s0 = fmaf(-x4.x, l4.x, s0);
-                        s1 = fmaf(-x4.y, l4.y, s1);
-                        s2 = fmaf(-x4.z, l4.z, s2);
-                        s3 = fmaf(-x4.w, l4.w, s3);
+                        s01 = fma2(make_float2(x4.x, x4.y), make_float2(l4.x, l4.y), s01);
+                        s23 = fma2(make_float2(x4.z, x4.w), make_float2(l4.z, l4.w), s23);
                     }
-                    for (; c < a; ++c) s0 = fmaf(-own[c], la[c], s0);
-                    const float u = ((s0 + s1) + (s2 + s3)) * rLp[a];
+                    const float u = ((s01.x + s01.y) + (s23.x + s23.y)) * rLp[a];
                     own[a] = u;
                     out[(long long)a * NT] = u;
                 }
