@@ -55,8 +55,8 @@ LAUNCHES_PER_STEP = 16
 # (k_agg_target_chol, k_agg_target_cols, k_select_agg_reg), of one learned step at N = 2^19
 # (22,423 supernodes), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
 # None where the kernel has changed since the capture
-FILL_DRAM_BYTES_N2E19 = 17007616 + 256420096 + 9472512 + 117424384
-SEL_DRAM_BYTES_N2E19 = 10128128 + 2330368 + 70645248 + 471728384 + 572967936 + 5294080
+FILL_DRAM_BYTES_N2E19 = 16812544 + 256258560 + 9846272 + 117808640
+SEL_DRAM_BYTES_N2E19 = 10139904 + 2321920 + 70493696 + 471795968 + 572655616 + 5679360
 GROUPS_N2E19 = 22423
 
 
