@@ -7,11 +7,13 @@
 // Theta_{s,s}, U upper triangular.  The CTA forms Theta on the reversed order
 // R = reverse(s) in packed lower storage in shared memory (one entry per thread), factors
 // it Theta_{RR} = L D L^T = G G^T with G = L D^{1/2} (blocked right-looking: panels of
-// FILL_B columns in FP64, each panel's update of the trailing matrix as integer dot products
-// (exact 32 x 32-bit products) of fixed-point G rows, one FP64 subtraction per entry and panel; one thread takes
-// each pivot's reciprocal square root), and since U = J G J (J the reversal), member a's
+// FILL_B columns in FP64, each panel's diagonal block factored by the pivot warp while the
+// workers apply the previous panel, each panel's update of the trailing matrix as integer dot
+// products (exact 32 x 32-bit products) of fixed-point G rows, one FP64 subtraction per entry
+// and panel), and since U = J G J (J the reversal), member a's
 // column is J G^{-T} e_j = d_j^{-1/2} J L^{-T} e_j with j = n-1-a: one back substitution per
-// member, one member per half-warp, the right-hand side in registers.  v_a = G_jj^2 = d_j,
+// member, one member per half-warp, the right-hand side in registers, in double-float
+// arithmetic on the FP32 pipe.  v_a = G_jj^2 = d_j,
 // so logv = log d_j (eq. inverse_cond).  Rows are written diagonal first, then ascending, to
 // the caller's CSC arrays.  Theta entries use the FP64 Matern of matern_d2_fast
 // (table-driven exp and Newton square root, each with its non-critical steps in
